@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the structured-sketch hot path on GB300.
+
+One step = one full pass of the sparse sign embedding over the embedding-throughput workload
+(A 2^22 x 256 BF16 with N(0,1) entries times logspaced column scales, d = 2048, zeta = 8):
+draw S and build its inverted index, gather S*A, reduce -- every step with a fresh seed, so
+nothing is cached between steps.  The metric is GB/s of A read.  A (2.1 GB) is larger than L2, so
+no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (launched by torch.distributed.run): every rank sketches its own A (weak scaling, no
+collective on the data path); rank 0 prints the line with the max step time over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SA GB/s of A read (% HBM peak); LSQ solves/sec at 1e-10 bwd err, mixed vs FP64"
+N_ROWS, K_COLS, D_SKETCH, ZETA = 1 << 22, 256, 2048, 8
+FALLBACK_HBM_GBS = 6800.0
+APPLY_SOURCES = ["paper_2508_21189_gb300/csrc/sparse_sign.cu", "paper_2508_21189_gb300/csrc/common.cuh"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--rows", type=int, default=N_ROWS, help="rows of A (smaller only for profiling captures)")
+    p.add_argument("--dtypes", default="bf16,fp32", help="A storage types to time; the first is the headline")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing
+# ------------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x, device="cpu"):
+    """Max of a float over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# clocks, peaks, traffic
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(key, paths):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != source_hash(paths):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(rows, seed):
+    """Time the FP64 oracle's sparse sign apply on `rows` rows of the workload (S drawn too)."""
+    import torch
+    import synthetic
+    from oracle import sparse_sign as osk
+    A = synthetic.colscaled_gaussian(rows, K_COLS, seed=seed, device="cpu", dtype=torch.float32).double().numpy()
+    t0 = time.perf_counter()
+    osk.apply(A, D_SKETCH, ZETA, seed)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(target_s=12.0, a_bytes=2):
+    rows = 1 << 14
+    t = oracle_sample(rows, 1)
+    while t < target_s / 4 and rows < (1 << 20):
+        rows *= 2
+        t = oracle_sample(rows, 1)
+    gbs = rows * K_COLS * a_bytes / t / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows} of {N_ROWS} rows x {K_COLS} cols (FP64 oracle: Philox+Floyd draw of S, scipy CSR "
+                      f"product), {t:.2f} s; GB/s counted in BF16 bytes of A"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    budget = 150.0
+    rows = 1 << 14
+    t = oracle_sample(rows, 0)
+    per_step = budget / max(1, args.steps + args.warmup)
+    rows = int(max(1 << 12, min(1 << 21, rows * per_step / max(t, 1e-3))))
+    for w in range(args.warmup):
+        oracle_sample(rows, 100 + w)
+    times = [oracle_sample(rows, 1000 + s) for s in range(args.steps)]
+    ms = 1000.0 * sum(times) / len(times)
+    gbs = rows * K_COLS * 2 / (ms / 1e3) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{rows} of {N_ROWS} rows per step, FP64 oracle"},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {"workload": "sparse sign embedding S*A: A 2^22 x 256 BF16 (N(0,1) x logspace(-3,0) column scales), "
+                        "S SparseUniform d=2048, zeta=8, fresh seed per step",
+            "n": N_ROWS, "k": K_COLS, "d": D_SKETCH, "zeta": ZETA, "a_dtype": "bf16", "accumulate": "f32",
+            "l2": "inputs larger than L2 (A is 2.1 GB), no flush"}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def time_steps(rsk, A, out, steps, seed0, torch):
+    """Device time per step (ms) of `steps` sketch applies bracketed by barrier + synchronize."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record()
+    for s in range(steps):
+        rsk.rsk_sparse_sign_apply(A, D_SKETCH, ZETA, seed0 + s, out=out)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def run_ours(args):
+    import torch
+    rank, world = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2508_21189_gb300 as rsk
+    import synthetic
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+
+    result = {}
+    names = [x for x in args.dtypes.split(",") if x]
+    dts = {"bf16": torch.bfloat16, "fp32": torch.float32, "fp64": torch.float64}
+    head = names[0]
+    sampler.start()
+    for name in names:
+        dt = dts[name]
+        A = synthetic.colscaled_gaussian(args.rows, K_COLS, seed=2022 + rank, device=dev, dtype=dt)
+        out = torch.empty(D_SKETCH, K_COLS, device=dev, dtype=torch.float32)
+        a_bytes = A.numel() * A.element_size()
+        for w in range(args.warmup):
+            rsk.rsk_sparse_sign_apply(A, D_SKETCH, ZETA, w, out=out)
+        rsk.rsk_sync_status()
+        rsk.rsk_profile_enable(True)
+        ms_local = time_steps(rsk, A, out, args.steps, 10_000, torch)
+        prof = {k: rsk.rsk_profile_read(k) for k in ("sketch_index", "sketch_apply", "sketch_reduce")}
+        rsk.rsk_profile_enable(False)
+        rsk.rsk_sync_status()
+        ms = max_over_ranks(ms_local, device=dev)
+        apply_ms = prof["sketch_apply"][0] / max(1, prof["sketch_apply"][1])
+        launches = sum(c for _, c in prof.values())
+        r = {"ms_per_step": ms, "value": world * a_bytes / (ms / 1e3) / 1e9, "a_bytes": a_bytes,
+             "apply_ms": apply_ms, "index_ms": prof["sketch_index"][0] / max(1, prof["sketch_index"][1]),
+             "reduce_ms": prof["sketch_reduce"][0] / max(1, prof["sketch_reduce"][1]), "launches": launches}
+        if name == head and not args.no_e2e:
+            # end to end through the public call: pinned host A -> device, sketch, SA -> host
+            A_host = A.cpu().pin_memory()
+            out_host = torch.empty(D_SKETCH, K_COLS, dtype=torch.float32).pin_memory()
+            A_dev = torch.empty_like(A)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            A_dev.copy_(A_host, non_blocking=True)
+            rsk.rsk_sparse_sign_apply(A_dev, D_SKETCH, ZETA, 1, out=out)
+            out_host.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+            barrier()
+            ev0.record()
+            for s in range(args.steps):
+                A_dev.copy_(A_host, non_blocking=True)
+                rsk.rsk_sparse_sign_apply(A_dev, D_SKETCH, ZETA, 20_000 + s, out=out)
+                out_host.copy_(out, non_blocking=True)
+            ev1.record()
+            torch.cuda.synchronize()
+            e2e_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
+            r["e2e"] = {"value": round(world * a_bytes / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+                        "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": out.numel() * 4,
+                        "ms_per_step": round(e2e_ms, 4)}
+            del A_host, A_dev
+        result[name] = r
+        del A
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+
+    if rank != 0:
+        return
+    peak, peak_kind = hbm_peak()
+    main = result[head]
+    alg_bytes = main["a_bytes"] + D_SKETCH * K_COLS * 4
+    achieved = alg_bytes / (main["apply_ms"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(main["value"], 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(main["ms_per_step"], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(),
+        "hbm_frac_of_step": round(main["value"] / world / peak, 4),
+        "roofline": {"kernel": "k_apply (sparse sign gather)", "bound": "hbm", "achieved": round(achieved, 2),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": recorded_traffic("k_apply|bf16|n=4194304,k=256,d=2048,zeta=8", APPLY_SOURCES),
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": round(main["apply_ms"], 4)},
+        "e2e": main.get("e2e"),
+        "gpu_launches": main["launches"],
+        "kernel_ms": {"index": round(main["index_ms"], 4), "apply": round(main["apply_ms"], 4),
+                      "reduce": round(main["reduce_ms"], 4)},
+        "clocks": clocks,
+    }
+    for name in names[1:]:
+        r = result[name]
+        line[name] = {"value": round(r["value"], 3), "unit": "GB/s", "ms_per_step": round(r["ms_per_step"], 4),
+                      "apply_ms": round(r["apply_ms"], 4),
+                      "apply_frac": round((r["a_bytes"] + D_SKETCH * K_COLS * 4) / (r["apply_ms"] / 1e3) / 1e9
+                                          / peak, 4)}
+    if args.rows != N_ROWS:
+        line["config"]["n"] = args.rows
+        line["config"]["workload"] += f" (reduced to {args.rows} rows for profiling)"
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,141 @@
+/*
+ * rsk.h -- C ABI of the GB300 structured-sketch library (librsk.so).
+ *
+ * Method: "Faster Linear Algebra Algorithms with Structured Random Matrices" (arxiv 2508.21189).
+ * Every entry point is extern "C", takes plain pointers and sizes, and returns rsk_status.
+ *
+ * Conventions shared by all calls
+ *   - Matrices are row-major with an explicit leading dimension (elements between rows).
+ *   - Pointers documented as "device" are device memory owned by the caller; the library never
+ *     frees or retains them beyond the call.  "host" pointers are ordinary host memory.
+ *   - Calls are asynchronous on the given stream unless documented as synchronous; results are
+ *     valid once the stream has been synchronised.  Scratch memory comes from the handle, which
+ *     owns a workspace that grows on demand (stream-ordered allocation on the call's stream).
+ *     A handle must not be used from two host threads at once.
+ *   - Invalid arguments are rejected with RSK_ERR_INVALID_ARG before anything is launched.
+ *     CUDA errors map to RSK_ERR_CUDA.  rsk_last_error() returns a message for the last failure.
+ *   - Kernels that detect a problem on the device (a bounded wait that ran out, an index out of
+ *     range) record it in a device status word; rsk_sync_status() synchronises the stream and
+ *     returns it (RSK_ERR_TIMEOUT / RSK_ERR_INTERNAL).
+ *   - Determinism: identical inputs, seed, options and GPU model give bit-identical outputs.
+ *
+ * Randomness.  The paper asks for iid Rademacher signs and positions sampled uniformly without
+ * replacement but fixes no generator.  All random draws come from the counter-based generator
+ * Philox4x32-10 (Salmon et al., SC'11):
+ *     word(seed, stream, entity, t) = Philox4x32-10(key = (seed_lo, seed_hi),
+ *                                                   ctr = (entity_lo, entity_hi, stream, t >> 2))[t & 3]
+ * Streams: 0 = sparse sign left sketch, 1 = SRTT diagonal D, 2 = SRTT subsample P,
+ *          3 = RSVD test matrix Omega.
+ */
+#ifndef RSK_H
+#define RSK_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RSK_OK = 0,
+    RSK_ERR_INVALID_ARG = 1,
+    RSK_ERR_NOMEM = 2,
+    RSK_ERR_CUDA = 3,
+    RSK_ERR_NOT_CONVERGED = 4,
+    RSK_ERR_TIMEOUT = 5,
+    RSK_ERR_UNSUPPORTED = 6,
+    RSK_ERR_INTERNAL = 7
+} rsk_status;
+
+typedef enum { RSK_F64 = 0, RSK_F32 = 1, RSK_BF16 = 2 } rsk_dtype;
+
+typedef struct rsk_handle rsk_handle;
+
+/* Create a handle bound to the CUDA device current on the calling thread.  *out receives the
+ * handle (host pointer owned by the library until rsk_destroy). */
+rsk_status rsk_create(rsk_handle** out);
+/* Release the handle and its workspace.  Synchronises the device first. */
+rsk_status rsk_destroy(rsk_handle* h);
+/* Message describing the last failure on this handle ("" if none).  Owned by the handle. */
+const char* rsk_last_error(const rsk_handle* h);
+/* Synchronise `stream` and return the device status word recorded by kernels of this handle
+ * since the previous call (then clear it). */
+rsk_status rsk_sync_status(rsk_handle* h, cudaStream_t stream);
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t rsk_version(void);
+
+/* Per-kernel timing.  While enabled, the handle records a CUDA event pair on the launch stream
+ * around every kernel launch it makes, tagged with one of these ids. */
+typedef enum {
+    RSK_KERNEL_SKETCH_INDEX = 0,   /* k_index: draw S + chunked inverted index      */
+    RSK_KERNEL_SKETCH_APPLY = 1,   /* k_apply: gather S*A into per-range partials   */
+    RSK_KERNEL_SKETCH_REDUCE = 2,  /* k_reduce: ordered sum of partials, scale      */
+    RSK_KERNEL_SKETCH_GENERATE = 3,/* k_generate: rows/signs of S                   */
+    RSK_KERNEL_SRTT_APPLY = 4,
+    RSK_KERNEL_SRTT_REDUCE = 5,
+    RSK_KERNEL_DENSE = 6,          /* LSQ / RSVD dense helpers (QR, solves, matvecs) */
+    RSK_KERNEL_GEMM = 7,           /* tensor-core GEMMs                             */
+    RSK_KERNEL_COUNT = 16
+} rsk_kernel_id;
+/* Turn recording on (on != 0) or off.  Turning it on clears earlier records. */
+rsk_status rsk_profile_enable(rsk_handle* h, int32_t on);
+/* Synchronise on the recorded events and return, for kernel id `kernel`, the summed device time
+ * in milliseconds and the number of launches recorded (host outputs). */
+rsk_status rsk_profile_read(rsk_handle* h, int32_t kernel, double* total_ms, int64_t* launches);
+
+/* ---------------------------------------------------------------------------------------------
+ * Sparse sign embedding S (d x n), the left form of SparseUniform.
+ * Paper: Def. "SparseUniform" (Sec. 3.2.1): exactly zeta entries zeta^{-1/2}*rho per row of the
+ * right test matrix Omega (= per column of S = Omega^T), positions uniform without replacement,
+ * rho Rademacher.  Sampling rule (both the library and its test oracle): Floyd's algorithm over
+ * column j with draws w_q = word(seed, 0, j, q):  m = d - zeta + q, t = floor(w_q (m+1) / 2^32),
+ * row_q = (t already chosen) ? m : t;  sign of row_q is -1 iff bit q of w_zeta is set.
+ * Limits: 1 <= zeta <= min(d, 32), 1 <= d <= 8192, 1 <= n < 2^31.
+ * ------------------------------------------------------------------------------------------- */
+
+/* a1: draw S.  rows: device int32[n*zeta], rows[j*zeta + q] = q-th row chosen for column j (in
+ * Floyd insertion order).  sign_bits: device uint32[n], bit q set <=> entry (rows[j*zeta+q], j)
+ * is -zeta^{-1/2}.  Either output may be NULL to skip it. */
+rsk_status rsk_sparse_sign_generate(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
+                                    int32_t* rows, uint32_t* sign_bits, cudaStream_t stream);
+
+/* Shape of the inverted index built by rsk_sparse_sign_index for (n, d, zeta): rows of S's
+ * columns are grouped in chunks of *chunk_rows consecutive columns (the last chunk may be
+ * shorter); *n_chunks chunks.  Host outputs. */
+rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows,
+                                      int64_t* n_chunks);
+
+/* a2: the inverted index of S, chunked.  For chunk c (columns j in [c*C, min((c+1)*C, n)),
+ * C = chunk_rows) the entries of sketch row i are
+ *     entries[c*C*zeta + offsets[c*(d+1) + i] ... c*C*zeta + offsets[c*(d+1) + i + 1] - 1],
+ * each a uint16 (j - c*C) | (negative << 15), in ascending j.  Concatenating chunks in order
+ * gives the CSR of S with columns ascending in every row.  offsets: device uint16[n_chunks*(d+1)];
+ * entries: device uint16[n*zeta]. */
+rsk_status rsk_sparse_sign_index(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
+                                 uint16_t* offsets, uint16_t* entries, cudaStream_t stream);
+
+/* a3: SA = S * A.
+ * A: device, n x k row-major, leading dimension lda >= k, element type a_dtype (F64, F32, BF16).
+ * SA: device, d x k row-major, leading dimension ldsa >= k, element type sa_dtype (F64 or F32).
+ * Accumulation is FP64 for F64 input and FP32 otherwise; the +-1 pattern is summed in a fixed
+ * order (ascending j within a chunk, chunks in order, row blocks reduced in index order) and
+ * scaled by zeta^{-1/2} once.  S is drawn from `seed` exactly as rsk_sparse_sign_generate. */
+rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                 int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
+                                 rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
+
+/* Plans keep the inverted index of one S for repeated application (e.g. to A and then to b).
+ * The plan owns device memory allocated on `stream`; destroy it with rsk_sparse_sign_plan_destroy. */
+typedef struct rsk_sketch_plan rsk_sketch_plan;
+rsk_status rsk_sparse_sign_plan_create(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
+                                       rsk_sketch_plan** plan, cudaStream_t stream);
+rsk_status rsk_sparse_sign_plan_apply(rsk_handle* h, const rsk_sketch_plan* plan, const void* A,
+                                      rsk_dtype a_dtype, int64_t k, int64_t lda, void* SA,
+                                      rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
+rsk_status rsk_sparse_sign_plan_destroy(rsk_handle* h, rsk_sketch_plan* plan, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSK_H */

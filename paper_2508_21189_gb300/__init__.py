@@ -1,0 +1,167 @@
+"""GB300-native structured random sketching (arxiv 2508.21189): Python binding of librsk.
+
+Each function has the name of the C entry point it calls and does argument marshalling only
+(torch tensors -> device pointers, dtypes -> rsk_dtype, the current CUDA stream).  Every step
+of the computation runs in librsk's CUDA kernels; there is no CPU path.
+"""
+import ctypes
+
+import torch
+
+from ._lib import RskError, STATUS, load
+
+RSK_F64, RSK_F32, RSK_BF16 = 0, 1, 2
+_DT = {torch.float64: RSK_F64, torch.float32: RSK_F32, torch.bfloat16: RSK_BF16}
+
+_handles = {}
+
+
+def lib():
+    return load()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def handle(device=None):
+    """Per-device rsk_handle (created on first use with that device current)."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+    h = _handles.get(dev.index)
+    if h is None:
+        with torch.cuda.device(dev):
+            out = ctypes.c_void_p()
+            st = load().rsk_create(ctypes.byref(out))
+            if st:
+                raise RskError(st, "rsk_create failed")
+            h = out
+        _handles[dev.index] = h
+    return h
+
+
+def _check(st, h):
+    if st:
+        msg = load().rsk_last_error(h) if h is not None else b""
+        raise RskError(st, (msg or b"").decode())
+
+
+def _dt(t):
+    try:
+        return _DT[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {t.dtype}") from None
+
+
+def _matrix(A, name):
+    if not A.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if A.dim() != 2 or A.stride(1) != 1 or A.stride(0) < A.shape[1]:
+        raise ValueError(f"{name} must be 2-D row-major with unit column stride")
+    return A
+
+
+def rsk_sync_status(stream=None, device=None):
+    h = handle(device)
+    _check(load().rsk_sync_status(h, _stream(stream)), h)
+
+
+def rsk_sparse_sign_generate(n, d, zeta, seed, device=None, stream=None):
+    """Draw S: returns (rows int32 [n, zeta], sign_bits int32 view of uint32 [n]) on the device."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    rows = torch.empty(n, zeta, dtype=torch.int32, device=dev)
+    bits = torch.empty(n, dtype=torch.int32, device=dev)
+    h = handle(dev)
+    _check(load().rsk_sparse_sign_generate(h, n, d, zeta, seed, rows.data_ptr(), bits.data_ptr(), _stream(stream)), h)
+    return rows, bits
+
+
+def rsk_sparse_sign_index_dims(n, d, zeta):
+    c = ctypes.c_int64()
+    m = ctypes.c_int64()
+    _check(load().rsk_sparse_sign_index_dims(n, d, zeta, ctypes.byref(c), ctypes.byref(m)), None)
+    return c.value, m.value
+
+
+def rsk_sparse_sign_index(n, d, zeta, seed, device=None, stream=None):
+    """Chunked inverted index of S: (offsets uint16-as-int16 [n_chunks, d+1], entries [n*zeta])."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    _, nch = rsk_sparse_sign_index_dims(n, d, zeta)
+    offs = torch.empty(nch, d + 1, dtype=torch.int16, device=dev)
+    ents = torch.empty(n * zeta + 8, dtype=torch.int16, device=dev)
+    h = handle(dev)
+    _check(load().rsk_sparse_sign_index(h, n, d, zeta, seed, offs.data_ptr(), ents.data_ptr(), _stream(stream)), h)
+    return offs, ents[: n * zeta]
+
+
+def rsk_sparse_sign_apply(A, d, zeta, seed, out_dtype=torch.float32, out=None, stream=None):
+    """SA = S @ A for a CUDA tensor A (n x k, row-major; F64/F32/BF16)."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=A.device)
+    _matrix(out, "out")
+    h = handle(A.device)
+    st = load().rsk_sparse_sign_apply(h, A.data_ptr(), _dt(A), n, k, A.stride(0), d, zeta, seed,
+                                      out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
+class SparseSignPlan:
+    """rsk_sparse_sign_plan_*: keeps one S's inverted index on the device for reuse."""
+
+    def __init__(self, n, d, zeta, seed, device=None, stream=None):
+        self.n, self.d, self.zeta, self.seed = n, d, zeta, seed
+        self.h = handle(device)
+        p = ctypes.c_void_p()
+        _check(load().rsk_sparse_sign_plan_create(self.h, n, d, zeta, seed, ctypes.byref(p), _stream(stream)), self.h)
+        self.p = p
+
+    def apply(self, A, out_dtype=torch.float32, out=None, stream=None):
+        _matrix(A, "A")
+        if A.shape[0] != self.n:
+            raise ValueError("row count does not match the plan")
+        k = A.shape[1]
+        if out is None:
+            out = torch.empty(self.d, k, dtype=out_dtype, device=A.device)
+        st = load().rsk_sparse_sign_plan_apply(self.h, self.p, A.data_ptr(), _dt(A), k, A.stride(0),
+                                               out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+        _check(st, self.h)
+        return out
+
+    def close(self, stream=None):
+        if self.p:
+            load().rsk_sparse_sign_plan_destroy(self.h, self.p, _stream(stream))
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rsk_sparse_sign_plan_create(n, d, zeta, seed, device=None, stream=None):
+    return SparseSignPlan(n, d, zeta, seed, device, stream)
+
+
+# Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).
+KERNEL_IDS = {"sketch_index": 0, "sketch_apply": 1, "sketch_reduce": 2, "sketch_generate": 3,
+              "srtt_apply": 4, "srtt_reduce": 5, "dense": 6, "gemm": 7}
+
+
+def rsk_profile_enable(on=True, device=None):
+    h = handle(device)
+    _check(load().rsk_profile_enable(h, 1 if on else 0), h)
+
+
+def rsk_profile_read(kernel, device=None):
+    """(total device ms, launches) recorded for one kernel id since profiling was enabled."""
+    h = handle(device)
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    kid = KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(load().rsk_profile_read(h, kid, ctypes.byref(ms), ctypes.byref(cnt)), h)
+    return ms.value, cnt.value

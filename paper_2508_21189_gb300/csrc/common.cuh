@@ -1,0 +1,150 @@
+// Shared host/device plumbing of librsk: the handle, status reporting, the workspace and the
+// bounded waits every kernel uses.  No arithmetic of the method lives here.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "rsk.h"
+
+// Device status word bits (kernels OR them in; rsk_sync_status reads and clears the word).
+#define RSK_DEV_TIMEOUT 1u
+#define RSK_DEV_BOUNDS 2u
+
+struct rsk_handle {
+    int device = 0;
+    int num_sms = 0;
+    unsigned int* dev_status = nullptr;  // device word written by kernels
+    void* ws = nullptr;                  // workspace (stream-ordered allocation)
+    size_t ws_bytes = 0;
+    void* encode_tiled = nullptr;        // cuTensorMapEncodeTiled from the driver
+    char msg[1024] = {0};
+    // optional per-kernel timing (rsk_profile_*)
+    bool prof = false;
+    struct Rec {
+        int kernel;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace rsk {
+
+rsk_status fail(rsk_handle* h, rsk_status st, const char* fmt, ...);
+
+// Grow the handle's workspace to at least `bytes` (stream-ordered on `stream`).
+rsk_status ensure_workspace(rsk_handle* h, size_t bytes, cudaStream_t stream);
+
+// Carve aligned pieces out of the workspace in call order.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+    static size_t round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+};
+
+inline size_t dtype_size(rsk_dtype t) { return t == RSK_F64 ? 8 : (t == RSK_F32 ? 4 : 2); }
+inline bool dtype_ok(int t) { return t == RSK_F64 || t == RSK_F32 || t == RSK_BF16; }
+
+// Profiling brackets around one kernel launch (no-ops unless rsk_profile_enable(h, 1)).
+int prof_begin(rsk_handle* h, cudaStream_t stream, int kernel);
+void prof_end(rsk_handle* h, cudaStream_t stream, int rec);
+
+// Encode a 2-D tiled TMA descriptor (inner dim first).  Returns false if the driver refuses.
+bool encode_2d(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const void* base,
+               uint64_t inner, uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner,
+               uint32_t box_outer);
+
+}  // namespace rsk
+
+#define RSK_CUDA_TRY(h, call)                                                                  \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return rsk::fail((h), RSK_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RSK_LAUNCH_CHECK(h)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                                   \
+        if (e_ != cudaSuccess)                                                                 \
+            return rsk::fail((h), RSK_ERR_CUDA, "kernel launch failed at %s:%d: %s", __FILE__, \
+                             __LINE__, cudaGetErrorString(e_));                                \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// Device-side helpers: mbarrier + TMA in inline PTX, with bounded waits.
+// ------------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace rskd {
+
+// Roughly a few seconds at most before a wait gives up and records RSK_DEV_TIMEOUT.
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  On timeout records RSK_DEV_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned int* status) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 32) __nanosleep(128);
+    }
+    atomicOr(status, RSK_DEV_TIMEOUT);
+    return false;
+}
+
+// 2-D tiled TMA load of box (x = inner coordinate, y = outer) into shared memory; completion is
+// signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace rskd
+#endif

@@ -1,0 +1,706 @@
+// Sparse sign embedding (left form of the paper's SparseUniform, Def. "SparseUniform", Sec. 3.2.1):
+// drawing S, inverting its column->row map into a chunked CSR, and the deterministic gather
+// S*A for tall A (cost O(zeta nnz(A)), Sec. 3.2).
+//
+// Kernels
+//   k_generate  one thread per column j: Philox words -> Floyd sample of zeta distinct rows + signs.
+//   k_index     one CTA per chunk of kChunk columns: redraws the chunk's columns, counts per sketch
+//               row with per-warp counters, scans, and scatters (j_local | neg<<15) stably so every
+//               sketch row lists its columns in ascending j.  Output stays chunk-local.
+//   k_apply     one CTA per (column slice, block of sketch rows, range of chunks).  TMA streams the
+//               chunk's 128-byte row slices of A into shared memory (double buffered); each group of
+//               8 lanes owns some sketch rows and gathers their entries' row slices (16 B per lane,
+//               one 128-B line per group, so no bank conflicts), accumulating in registers.
+//   k_reduce    sums the per-range partials in range order, scales by zeta^{-1/2}, casts, writes SA.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+#include "philox.cuh"
+
+namespace {
+
+constexpr int kChunk = 768;         // columns of S (= rows of A) per chunk
+constexpr int kBoxRows = 256;       // rows per TMA box
+constexpr int kBoxesPerChunk = kChunk / kBoxRows;
+constexpr int kRowBytes = 128;      // staged row slice of A
+constexpr int kStageBytes = kChunk * kRowBytes;
+constexpr int kApplyThreads = 512;
+constexpr int kGroups = kApplyThreads / 8;
+constexpr int kIndexThreads = 256;
+constexpr uint32_t kStreamLeft = 0;
+
+// ------------------------------------------------------------------------------------------
+// Drawing one column of S.
+// ------------------------------------------------------------------------------------------
+template <int ZMAX>
+__device__ __forceinline__ void draw_column(uint64_t seed, uint32_t stream, uint64_t j, int d, int zeta,
+                                            int (&rows)[ZMAX], uint32_t& negbits) {
+    uint32_t w[ZMAX + 4];
+#pragma unroll
+    for (int b = 0; b <= ZMAX / 4; ++b) {
+        if (4 * b <= zeta) {
+            const rskd::Block4 blk = rskd::philox_block(seed, stream, j, uint32_t(b));
+            w[4 * b + 0] = blk.v[0];
+            w[4 * b + 1] = blk.v[1];
+            w[4 * b + 2] = blk.v[2];
+            w[4 * b + 3] = blk.v[3];
+        }
+    }
+    // Floyd: for m = d-zeta .. d-1 draw t uniform in [0, m]; keep t unless already taken, else m.
+#pragma unroll
+    for (int q = 0; q < ZMAX; ++q) {
+        if (q < zeta) {
+            const uint32_t m = uint32_t(d - zeta + q);
+            const int t = int(__umulhi(w[q], m + 1u));
+            bool taken = false;
+#pragma unroll
+            for (int p = 0; p < q; ++p) taken |= (rows[p] == t);
+            rows[q] = taken ? int(m) : t;
+        }
+    }
+    uint32_t sb = 0;
+#pragma unroll
+    for (int t = 0; t <= ZMAX; ++t)
+        if (t == zeta) sb = w[t];
+    negbits = zeta >= 32 ? sb : (sb & ((1u << zeta) - 1u));
+}
+
+template <int ZMAX>
+__global__ void k_generate(int64_t n, int d, int zeta, uint64_t seed, uint32_t stream, int32_t* __restrict__ rows,
+                           uint32_t* __restrict__ signs) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int r[ZMAX];
+    uint32_t nb;
+    draw_column<ZMAX>(seed, stream, uint64_t(j), d, zeta, r, nb);
+    if (rows) {
+#pragma unroll
+        for (int q = 0; q < ZMAX; ++q)
+            if (q < zeta) rows[j * zeta + q] = r[q];
+    }
+    if (signs) signs[j] = nb;
+}
+
+// ------------------------------------------------------------------------------------------
+// Chunked inverted index.
+// ------------------------------------------------------------------------------------------
+struct IndexLayout {
+    int count_warps;
+    size_t tgt_off, neg_off, cnt_off, out_off, scan_off, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline IndexLayout index_layout(int d, int zeta, int count_warps) {
+    IndexLayout L;
+    L.count_warps = count_warps;
+    L.tgt_off = 0;
+    L.neg_off = align16(L.tgt_off + size_t(kChunk) * zeta * 2);
+    L.cnt_off = align16(L.neg_off + size_t(kChunk) * 4);
+    L.out_off = align16(L.cnt_off + size_t(count_warps) * d * 2);
+    L.scan_off = align16(L.out_off + size_t(kChunk) * zeta * 2);
+    L.total = align16(L.scan_off + (kIndexThreads / 32 + 1) * 4 * 2);
+    return L;
+}
+
+template <int ZMAX>
+__global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int zeta, uint64_t seed, uint32_t stream,
+                                                         int count_warps, uint16_t* __restrict__ offsets,
+                                                         uint16_t* __restrict__ entries) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const IndexLayout L = index_layout(d, zeta, count_warps);
+    uint16_t* tgt = reinterpret_cast<uint16_t*>(sm + L.tgt_off);
+    uint32_t* neg = reinterpret_cast<uint32_t*>(sm + L.neg_off);
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(sm + L.cnt_off);
+    uint16_t* out = reinterpret_cast<uint16_t*>(sm + L.out_off);
+    int* wsum = reinterpret_cast<int*>(sm + L.scan_off);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t ch = blockIdx.x;
+    const int64_t j0 = ch * kChunk;
+    const int rows = int((n - j0) < kChunk ? (n - j0) : kChunk);
+    const int nent = rows * zeta;
+
+    // 1. draw the chunk's columns
+    for (int r = tid; r < rows; r += kIndexThreads) {
+        int rr[ZMAX];
+        uint32_t nb;
+        draw_column<ZMAX>(seed, stream, uint64_t(j0 + r), d, zeta, rr, nb);
+#pragma unroll
+        for (int q = 0; q < ZMAX; ++q)
+            if (q < zeta) tgt[r * zeta + q] = uint16_t(rr[q]);
+        neg[r] = nb;
+    }
+    for (int i = tid; i < count_warps * d; i += kIndexThreads) cnt[i] = 0;
+    __syncthreads();
+
+    // 2. per-warp counts over a contiguous range of columns (deterministic: leaders are unique)
+    const int per_w = (rows + count_warps - 1) / count_warps;
+    const int r0 = min(rows, warp * per_w), r1 = min(rows, r0 + per_w);
+    const int f0 = r0 * zeta, f1 = r1 * zeta;
+    if (warp < count_warps) {
+        uint16_t* mine = cnt + size_t(warp) * d;
+        for (int base = f0; base < f1; base += 32) {
+            const int f = base + lane;
+            const bool ok = f < f1;
+            const int t = ok ? int(tgt[f]) : (65536 + lane);
+            const unsigned peers = __match_any_sync(0xffffffffu, t);
+            if (ok && lane == __ffs(peers) - 1) mine[t] = uint16_t(mine[t] + __popc(peers));
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+
+    // 3. exclusive scan over sketch rows; per-warp cursors replace the counts
+    const int per_t = (d + kIndexThreads - 1) / kIndexThreads;
+    const int i0 = min(d, tid * per_t), i1 = min(d, i0 + per_t);
+    int local = 0;
+    for (int i = i0; i < i1; ++i)
+        for (int w = 0; w < count_warps; ++w) local += cnt[size_t(w) * d + i];
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int w = 0; w < kIndexThreads / 32; ++w) {
+            const int v = wsum[w];
+            wsum[w] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
+    int run = wsum[warp] + incl - local;
+    uint16_t* off_out = offsets + ch * (d + 1);
+    for (int i = i0; i < i1; ++i) {
+        off_out[i] = uint16_t(run);
+        for (int w = 0; w < count_warps; ++w) {
+            const int c = cnt[size_t(w) * d + i];
+            cnt[size_t(w) * d + i] = uint16_t(run);
+            run += c;
+        }
+    }
+    if (tid == 0) off_out[d] = uint16_t(nent);
+    __syncthreads();
+
+    // 4. stable scatter: same traversal order as the count
+    if (warp < count_warps) {
+        uint16_t* cur = cnt + size_t(warp) * d;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = f0; base < f1; base += 32) {
+            const int f = base + lane;
+            const bool ok = f < f1;
+            const int t = ok ? int(tgt[f]) : (65536 + lane);
+            const unsigned peers = __match_any_sync(0xffffffffu, t);
+            if (ok) {
+                const int r = f / zeta, q = f - r * zeta;
+                out[cur[t] + __popc(peers & lt)] = uint16_t(r | (((neg[r] >> q) & 1u) << 15));
+            }
+            __syncwarp();
+            if (ok && lane == __ffs(peers) - 1) cur[t] = uint16_t(cur[t] + __popc(peers));
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+
+    // 5. write the chunk's entries (chunk blocks start at multiples of kChunk*zeta*2 bytes)
+    uint16_t* dst = entries + ch * kChunk * zeta;
+    const int n16 = (nent * 2) / 16;
+    for (int v = tid; v < n16; v += kIndexThreads)
+        reinterpret_cast<uint4*>(dst)[v] = reinterpret_cast<const uint4*>(out)[v];
+    for (int e = n16 * 8 + tid; e < nent; e += kIndexThreads) dst[e] = out[e];
+}
+
+// ------------------------------------------------------------------------------------------
+// Gather apply.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct Elem;
+template <>
+struct Elem<double> {
+    using acc = double;
+    static constexpr int kVec = 2;
+    static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+};
+template <>
+struct Elem<float> {
+    using acc = float;
+    static constexpr int kVec = 4;
+    static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+};
+template <>
+struct Elem<__nv_bfloat16> {
+    using acc = float;
+    static constexpr int kVec = 8;
+    static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+};
+
+// acc[v] += (+-1) * x[v] for the 16 bytes x; the sign enters as an XOR of the sign bit.
+__device__ __forceinline__ void accumulate(double (&acc)[2], const uint4 x, uint32_t negative) {
+    const uint32_t sm = negative << 31;
+    acc[0] += __hiloint2double(int(x.y ^ sm), int(x.x));
+    acc[1] += __hiloint2double(int(x.w ^ sm), int(x.z));
+}
+__device__ __forceinline__ void accumulate(float (&acc)[4], const uint4 x, uint32_t negative) {
+    const uint32_t sm = negative << 31;
+    acc[0] += __uint_as_float(x.x ^ sm);
+    acc[1] += __uint_as_float(x.y ^ sm);
+    acc[2] += __uint_as_float(x.z ^ sm);
+    acc[3] += __uint_as_float(x.w ^ sm);
+}
+__device__ __forceinline__ void accumulate(float (&acc)[8], const uint4 x, uint32_t negative) {
+    const uint32_t sm = negative << 31;
+    acc[0] += __uint_as_float((x.x << 16) ^ sm);
+    acc[1] += __uint_as_float((x.x & 0xffff0000u) ^ sm);
+    acc[2] += __uint_as_float((x.y << 16) ^ sm);
+    acc[3] += __uint_as_float((x.y & 0xffff0000u) ^ sm);
+    acc[4] += __uint_as_float((x.z << 16) ^ sm);
+    acc[5] += __uint_as_float((x.z & 0xffff0000u) ^ sm);
+    acc[6] += __uint_as_float((x.w << 16) ^ sm);
+    acc[7] += __uint_as_float((x.w & 0xffff0000u) ^ sm);
+}
+
+struct ApplyArgs {
+    const void* A;
+    int64_t n, k, lda;
+    int d, zeta, dsub, ntsub, nslices, nranges, nchunks;
+    const uint16_t* offs;
+    const uint16_t* ents;
+    void* partials;
+    int64_t pstride, kpad;
+    unsigned int* status;
+};
+
+template <typename T, int SLOTS, bool TMA>
+__global__ void __launch_bounds__(kApplyThreads, 1)
+    k_apply(const __grid_constant__ CUtensorMap tmap, const ApplyArgs a) {
+    using acc_t = typename Elem<T>::acc;
+    constexpr int VEC = Elem<T>::kVec;
+    constexpr int C = 8 * VEC;  // columns of A per slice (128 bytes)
+    extern __shared__ __align__(16) uint8_t sm[];
+    uint8_t* const stage0 = sm;
+    uint8_t* const stage1 = sm + kStageBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (TMA ? 2 : 1) * kStageBytes);
+
+    const int tid = threadIdx.x, g = tid >> 3, l8 = tid & 7;
+    int b = blockIdx.x;
+    const int s = b % a.nslices;
+    b /= a.nslices;
+    const int t = b % a.ntsub;
+    const int r = b / a.ntsub;
+    const int c0 = int(int64_t(r) * a.nchunks / a.nranges);
+    const int c1 = int(int64_t(r + 1) * a.nchunks / a.nranges);
+
+    acc_t acc[SLOTS][VEC];
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[q][v] = acc_t(0);
+
+    auto issue = [&](int ch, uint8_t* dst, uint64_t* bar) {
+        const int64_t row0 = int64_t(ch) * kChunk;
+        int nbox = 0;
+#pragma unroll
+        for (int bx = 0; bx < kBoxesPerChunk; ++bx)
+            if (row0 + bx * kBoxRows < a.n) ++nbox;
+        rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kRowBytes));
+        for (int bx = 0; bx < nbox; ++bx)
+            rskd::tma_load_2d(dst + bx * kBoxRows * kRowBytes, &tmap, s * C, int(row0 + bx * kBoxRows), bar);
+    };
+
+    if constexpr (TMA) {
+        if (tid == 0) {
+            rskd::mbar_init(&bars[0], 1);
+            rskd::mbar_init(&bars[1], 1);
+            rskd::fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (c0 < c1) issue(c0, stage0, &bars[0]);
+            if (c0 + 1 < c1) issue(c0 + 1, stage1, &bars[1]);
+        }
+    }
+
+    for (int ch = c0, it = 0; ch < c1; ++ch, ++it) {
+        const uint8_t* buf;
+        if constexpr (TMA) {
+            const int st = it & 1;
+            const bool ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
+            if (__syncthreads_or(!ok)) break;
+            buf = st ? stage1 : stage0;
+        } else {
+            // Unaligned A: element-wise loads into the single stage.
+            const T* A = static_cast<const T*>(a.A);
+            for (int idx = tid; idx < kChunk * 8; idx += kApplyThreads) {
+                const int row = idx >> 3, piece = idx & 7;
+                const int64_t gr = int64_t(ch) * kChunk + row;
+                __align__(16) T vals[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) {
+                    const int64_t col = int64_t(s) * C + piece * VEC + v;
+                    vals[v] = (gr < a.n && col < a.k) ? A[gr * a.lda + col] : T(0);
+                }
+                *reinterpret_cast<uint4*>(stage0 + row * kRowBytes + piece * 16) = *reinterpret_cast<const uint4*>(vals);
+            }
+            __syncthreads();
+            buf = stage0;
+        }
+        const uint16_t* off = a.offs + int64_t(ch) * (a.d + 1);
+        const uint16_t* ent = a.ents + int64_t(ch) * kChunk * a.zeta;
+        const uint8_t* lane_base = buf + l8 * 16;
+#pragma unroll
+        for (int q = 0; q < SLOTS; ++q) {
+            const int i = t * a.dsub + q * kGroups + g;
+            if (i < a.d) {
+                const int beg = __ldg(off + i), end = __ldg(off + i + 1);
+                for (int e = beg; e < end; ++e) {
+                    const uint32_t v = __ldg(ent + e);
+                    const uint4 x = *reinterpret_cast<const uint4*>(lane_base + (v & 0x7fffu) * kRowBytes);
+                    accumulate(acc[q], x, v >> 15);
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (TMA) {
+            if (tid == 0 && ch + 2 < c1) {
+                rskd::fence_proxy_async();
+                const int st = it & 1;
+                issue(ch + 2, st ? stage1 : stage0, &bars[st]);
+            }
+        }
+    }
+
+    acc_t* part = static_cast<acc_t*>(a.partials) + int64_t(r) * a.pstride;
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) {
+        const int i = t * a.dsub + q * kGroups + g;
+        if (i < a.d) {
+            acc_t* dst = part + int64_t(i) * a.kpad + int64_t(s) * C + l8 * VEC;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) dst[v] = acc[q][v];
+        }
+    }
+}
+
+template <typename Acc, typename Out>
+__global__ void k_reduce(const Acc* __restrict__ partials, int64_t pstride, int64_t kpad, int nranges, int d,
+                         int64_t k, double scale, Out* __restrict__ SA, int64_t ldsa) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= int64_t(d) * k) return;
+    const int64_t i = idx / k, col = idx - i * k;
+    const Acc* p = partials + i * kpad + col;
+    Acc sum = Acc(0);
+    for (int r = 0; r < nranges; ++r) sum += p[int64_t(r) * pstride];
+    SA[i * ldsa + col] = Out(double(sum) * scale);
+}
+
+// ------------------------------------------------------------------------------------------
+// Host side.
+// ------------------------------------------------------------------------------------------
+rsk_status check_dims(rsk_handle* h, int64_t n, int64_t d, int32_t zeta) {
+    if (n < 1 || n >= (int64_t(1) << 31)) return rsk::fail(h, RSK_ERR_INVALID_ARG, "n=%lld out of range", (long long)n);
+    if (d < 1 || d > 8192) return rsk::fail(h, RSK_ERR_INVALID_ARG, "d=%lld out of range [1, 8192]", (long long)d);
+    if (zeta < 1 || zeta > 32 || zeta > d)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "zeta=%d must satisfy 1 <= zeta <= min(d, 32)", zeta);
+    return RSK_OK;
+}
+
+int64_t n_chunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
+
+rsk_status launch_index(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed, uint32_t stream_id,
+                        uint16_t* offs, uint16_t* ents, cudaStream_t stream) {
+    int warps = kIndexThreads / 32;
+    IndexLayout L = index_layout(d, zeta, warps);
+    while (L.total > 200 * 1024 && warps > 1) {
+        warps /= 2;
+        L = index_layout(d, zeta, warps);
+    }
+    if (L.total > 227 * 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "index build needs %zu B of shared memory", L.total);
+    const int64_t nch = n_chunks_of(n);
+    auto go = [&](auto kern) -> rsk_status {
+        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total)));
+        const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_INDEX);
+        kern<<<unsigned(nch), kIndexThreads, L.total, stream>>>(n, d, zeta, seed, stream_id, warps, offs, ents);
+        rsk::prof_end(h, stream, pr);
+        RSK_LAUNCH_CHECK(h);
+        return RSK_OK;
+    };
+    if (zeta <= 8) return go(k_index<8>);
+    if (zeta <= 16) return go(k_index<16>);
+    return go(k_index<32>);
+}
+
+struct ApplyPlan {
+    int slots, dsub, ntsub, nslices, nranges, nchunks;
+    int64_t kpad, pstride;
+    size_t partial_bytes;
+};
+
+ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, rsk_dtype dt) {
+    ApplyPlan p;
+    const int vec = int(16 / rsk::dtype_size(dt));
+    const int C = 8 * vec;
+    const int max_slots = dt == RSK_BF16 ? 8 : 16;
+    p.ntsub = (d + max_slots * kGroups - 1) / (max_slots * kGroups);
+    const int need = (d + p.ntsub * kGroups - 1) / (p.ntsub * kGroups);
+    p.slots = 1;
+    while (p.slots < need) p.slots *= 2;
+    p.dsub = p.slots * kGroups;
+    p.nslices = int((k + C - 1) / C);
+    p.nchunks = int(n_chunks_of(n));
+    const int pairs = p.nslices * p.ntsub;
+    p.nranges = std::max(1, std::min(p.nchunks, h->num_sms / std::max(1, pairs)));
+    p.kpad = int64_t(p.nslices) * C;
+    p.pstride = int64_t(p.ntsub) * p.dsub * p.kpad;
+    const size_t acc = dt == RSK_F64 ? 8 : 4;
+    p.partial_bytes = size_t(p.nranges) * p.pstride * acc;
+    return p;
+}
+
+template <typename T, int SLOTS>
+rsk_status launch_apply_t(rsk_handle* h, const ApplyPlan& p, const ApplyArgs& args, bool use_tma,
+                          const CUtensorMap& map, cudaStream_t stream) {
+    const unsigned grid = unsigned(p.nslices * p.ntsub * p.nranges);
+    if (use_tma) {
+        auto kern = k_apply<T, SLOTS, true>;
+        const int smem = 2 * kStageBytes + 64;
+        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
+        kern<<<grid, kApplyThreads, smem, stream>>>(map, args);
+        rsk::prof_end(h, stream, pr);
+    } else {
+        auto kern = k_apply<T, SLOTS, false>;
+        const int smem = kStageBytes + 64;
+        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
+        kern<<<grid, kApplyThreads, smem, stream>>>(map, args);
+        rsk::prof_end(h, stream, pr);
+    }
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+template <typename T>
+rsk_status launch_apply_slots(rsk_handle* h, const ApplyPlan& p, const ApplyArgs& args, bool use_tma,
+                              const CUtensorMap& map, cudaStream_t stream) {
+    switch (p.slots) {
+        case 1: return launch_apply_t<T, 1>(h, p, args, use_tma, map, stream);
+        case 2: return launch_apply_t<T, 2>(h, p, args, use_tma, map, stream);
+        case 4: return launch_apply_t<T, 4>(h, p, args, use_tma, map, stream);
+        case 8: return launch_apply_t<T, 8>(h, p, args, use_tma, map, stream);
+        default:
+            if constexpr (sizeof(T) >= 4) return launch_apply_t<T, 16>(h, p, args, use_tma, map, stream);
+            return rsk::fail(h, RSK_ERR_INTERNAL, "bad slot count %d", p.slots);
+    }
+}
+
+template <typename Acc>
+rsk_status launch_reduce(rsk_handle* h, const ApplyPlan& p, const void* partials, int d, int64_t k, int zeta,
+                         void* SA, rsk_dtype sa_dt, int64_t ldsa, cudaStream_t stream) {
+    const int64_t total = int64_t(d) * k;
+    const unsigned grid = unsigned((total + 255) / 256);
+    const double scale = 1.0 / sqrt(double(zeta));
+    const Acc* P = static_cast<const Acc*>(partials);
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_REDUCE);
+    if (sa_dt == RSK_F64)
+        k_reduce<Acc, double><<<grid, 256, 0, stream>>>(P, p.pstride, p.kpad, p.nranges, d, k, scale,
+                                                        static_cast<double*>(SA), ldsa);
+    else
+        k_reduce<Acc, float><<<grid, 256, 0, stream>>>(P, p.pstride, p.kpad, p.nranges, d, k, scale,
+                                                       static_cast<float*>(SA), ldsa);
+    rsk::prof_end(h, stream, pr);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status apply_with_index(rsk_handle* h, const uint16_t* offs, const uint16_t* ents, const void* A,
+                            rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda, int d, int zeta, void* SA,
+                            rsk_dtype sa_dt, int64_t ldsa, void* partials, const ApplyPlan& p, cudaStream_t stream) {
+    const size_t es = rsk::dtype_size(a_dt);
+    const int C = int(128 / es);
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    bool use_tma = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * int64_t(es)) % 16 == 0);
+    if (use_tma) {
+        const CUtensorMapDataType tdt = a_dt == RSK_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                        : a_dt == RSK_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        use_tma = rsk::encode_2d(h, &map, tdt, A, uint64_t(k), uint64_t(n), uint64_t(lda) * es, uint32_t(C),
+                                 uint32_t(kBoxRows));
+    }
+    ApplyArgs args;
+    args.A = A;
+    args.n = n;
+    args.k = k;
+    args.lda = lda;
+    args.d = d;
+    args.zeta = zeta;
+    args.dsub = p.dsub;
+    args.ntsub = p.ntsub;
+    args.nslices = p.nslices;
+    args.nranges = p.nranges;
+    args.nchunks = p.nchunks;
+    args.offs = offs;
+    args.ents = ents;
+    args.partials = partials;
+    args.pstride = p.pstride;
+    args.kpad = p.kpad;
+    args.status = h->dev_status;
+    rsk_status st;
+    if (a_dt == RSK_F64) st = launch_apply_slots<double>(h, p, args, use_tma, map, stream);
+    else if (a_dt == RSK_F32) st = launch_apply_slots<float>(h, p, args, use_tma, map, stream);
+    else st = launch_apply_slots<__nv_bfloat16>(h, p, args, use_tma, map, stream);
+    if (st != RSK_OK) return st;
+    if (a_dt == RSK_F64) return launch_reduce<double>(h, p, partials, d, k, zeta, SA, sa_dt, ldsa, stream);
+    return launch_reduce<float>(h, p, partials, d, k, zeta, SA, sa_dt, ldsa, stream);
+}
+
+rsk_status check_apply_args(rsk_handle* h, const void* A, int a_dt, int64_t n, int64_t k, int64_t lda, int64_t d,
+                            const void* SA, int sa_dt, int64_t ldsa) {
+    if (!A || !SA) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null matrix pointer");
+    if (!rsk::dtype_ok(a_dt)) return rsk::fail(h, RSK_ERR_INVALID_ARG, "bad A dtype %d", a_dt);
+    if (sa_dt != RSK_F64 && sa_dt != RSK_F32) return rsk::fail(h, RSK_ERR_INVALID_ARG, "SA dtype must be F64 or F32");
+    if (k < 1 || lda < k || ldsa < k) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need k >= 1, lda >= k, ldsa >= k");
+    (void)n;
+    (void)d;
+    return RSK_OK;
+}
+
+}  // namespace
+
+struct rsk_sketch_plan {
+    int64_t n, d;
+    int zeta;
+    uint64_t seed;
+    int64_t nchunks;
+    uint16_t* offs;
+    uint16_t* ents;
+};
+
+extern "C" {
+
+rsk_status rsk_sparse_sign_generate(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed, int32_t* rows,
+                                    uint32_t* sign_bits, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    if (!rows && !sign_bits) return RSK_OK;
+    const unsigned grid = unsigned((n + 255) / 256);
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_GENERATE);
+    if (zeta <= 8) k_generate<8><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, kStreamLeft, rows, sign_bits);
+    else if (zeta <= 16) k_generate<16><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, kStreamLeft, rows, sign_bits);
+    else k_generate<32><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, kStreamLeft, rows, sign_bits);
+    rsk::prof_end(h, stream, pr);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows, int64_t* n_chunks) {
+    if (check_dims(nullptr, n, d, zeta) != RSK_OK || !chunk_rows || !n_chunks) return RSK_ERR_INVALID_ARG;
+    *chunk_rows = kChunk;
+    *n_chunks = n_chunks_of(n);
+    return RSK_OK;
+}
+
+rsk_status rsk_sparse_sign_index(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed, uint16_t* offsets,
+                                 uint16_t* entries, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    if (!offsets || !entries) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null output pointer");
+    if (reinterpret_cast<uintptr_t>(entries) % 16)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "entries must be 16-byte aligned");
+    return launch_index(h, n, int(d), zeta, seed, kStreamLeft, offsets, entries, stream);
+}
+
+rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                                 int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype, int64_t ldsa,
+                                 cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    st = check_apply_args(h, A, a_dtype, n, k, lda, d, SA, sa_dtype, ldsa);
+    if (st != RSK_OK) return st;
+    const ApplyPlan p = plan_apply(h, n, k, int(d), a_dtype);
+    const size_t off_bytes = size_t(p.nchunks) * (d + 1) * 2;
+    const size_t ent_bytes = size_t(n) * zeta * 2 + 16;
+    const size_t need = rsk::Carver::round(off_bytes) + rsk::Carver::round(ent_bytes) +
+                        rsk::Carver::round(p.partial_bytes) + 256;
+    st = rsk::ensure_workspace(h, need, stream);
+    if (st != RSK_OK) return st;
+    rsk::Carver cv(h->ws);
+    uint16_t* offs = cv.take<uint16_t>(size_t(p.nchunks) * (d + 1));
+    uint16_t* ents = cv.take<uint16_t>(size_t(n) * zeta + 8);
+    void* partials = cv.take<char>(p.partial_bytes);
+    st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
+    if (st != RSK_OK) return st;
+    return apply_with_index(h, offs, ents, A, a_dtype, n, k, lda, int(d), zeta, SA, sa_dtype, ldsa, partials, p,
+                            stream);
+}
+
+rsk_status rsk_sparse_sign_plan_create(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
+                                       rsk_sketch_plan** plan, cudaStream_t stream) {
+    if (!h || !plan) return RSK_ERR_INVALID_ARG;
+    *plan = nullptr;
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    rsk_sketch_plan* p = new (std::nothrow) rsk_sketch_plan();
+    if (!p) return rsk::fail(h, RSK_ERR_NOMEM, "plan allocation failed");
+    p->n = n;
+    p->d = d;
+    p->zeta = zeta;
+    p->seed = seed;
+    p->nchunks = n_chunks_of(n);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p->offs), size_t(p->nchunks) * (d + 1) * 2, stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&p->ents), size_t(n) * zeta * 2 + 16, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->offs) cudaFreeAsync(p->offs, stream);
+        delete p;
+        return rsk::fail(h, RSK_ERR_NOMEM, "plan device allocation failed: %s", cudaGetErrorString(e));
+    }
+    st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, p->offs, p->ents, stream);
+    if (st != RSK_OK) {
+        cudaFreeAsync(p->offs, stream);
+        cudaFreeAsync(p->ents, stream);
+        delete p;
+        return st;
+    }
+    *plan = p;
+    return RSK_OK;
+}
+
+rsk_status rsk_sparse_sign_plan_apply(rsk_handle* h, const rsk_sketch_plan* plan, const void* A, rsk_dtype a_dtype,
+                                      int64_t k, int64_t lda, void* SA, rsk_dtype sa_dtype, int64_t ldsa,
+                                      cudaStream_t stream) {
+    if (!h || !plan) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_apply_args(h, A, a_dtype, plan->n, k, lda, plan->d, SA, sa_dtype, ldsa);
+    if (st != RSK_OK) return st;
+    const ApplyPlan p = plan_apply(h, plan->n, k, int(plan->d), a_dtype);
+    st = rsk::ensure_workspace(h, rsk::Carver::round(p.partial_bytes) + 256, stream);
+    if (st != RSK_OK) return st;
+    rsk::Carver cv(h->ws);
+    void* partials = cv.take<char>(p.partial_bytes);
+    return apply_with_index(h, plan->offs, plan->ents, A, a_dtype, plan->n, k, lda, int(plan->d), plan->zeta, SA,
+                            sa_dtype, ldsa, partials, p, stream);
+}
+
+rsk_status rsk_sparse_sign_plan_destroy(rsk_handle* h, rsk_sketch_plan* plan, cudaStream_t stream) {
+    if (!plan) return RSK_ERR_INVALID_ARG;
+    cudaFreeAsync(plan->offs, stream);
+    cudaFreeAsync(plan->ents, stream);
+    delete plan;
+    (void)h;
+    return RSK_OK;
+}
+
+}  // extern "C"
