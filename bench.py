@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--rows", type=int, default=N_ROWS, help="rows of A (smaller only for profiling captures)")
     p.add_argument("--dtypes", default="bf16,fp32", help="A storage types to time; the first is the headline")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-srtt", action="store_true")
     return p.parse_args()
 
 
@@ -272,6 +273,27 @@ def run_ours(args):
         r = {"ms_per_step": ms, "value": world * a_bytes / (ms / 1e3) / 1e9, "a_bytes": a_bytes,
              "apply_ms": apply_ms, "index_ms": prof["sketch_index"][0] / max(1, prof["sketch_index"][1]),
              "reduce_ms": prof["sketch_reduce"][0] / max(1, prof["sketch_reduce"][1]), "launches": launches}
+        if not args.no_srtt:
+            for w in range(args.warmup):
+                rsk.rsk_srtt_apply(A, D_SKETCH, w, out=out)
+            rsk.rsk_profile_enable(True)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            barrier()
+            ev0.record()
+            for st in range(args.steps):
+                rsk.rsk_srtt_apply(A, D_SKETCH, 30_000 + st, out=out)
+            ev1.record()
+            torch.cuda.synchronize()
+            sp = {k: rsk.rsk_profile_read(k) for k in ("srtt_apply", "srtt_reduce", "dense")}
+            rsk.rsk_profile_enable(False)
+            rsk.rsk_sync_status()
+            sms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
+            r["srtt"] = {"ms_per_step": sms, "value": world * a_bytes / (sms / 1e3) / 1e9,
+                         "apply_ms": sp["srtt_apply"][0] / max(1, sp["srtt_apply"][1]),
+                         "draw_ms": sp["dense"][0] / max(1, sp["dense"][1]),
+                         "launches": sum(c for _, c in sp.values())}
         if name == head and not args.no_e2e:
             # end to end through the public call: pinned host A -> device, sketch, SA -> host
             A_host = A.cpu().pin_memory()
@@ -323,6 +345,15 @@ def run_ours(args):
                       "reduce": round(main["reduce_ms"], 4)},
         "clocks": clocks,
     }
+    for name in names:
+        r = result[name]
+        if "srtt" in r:
+            sr = r["srtt"]
+            key = "srtt" if name == head else f"srtt_{name}"
+            line[key] = {"value": round(sr["value"], 3), "unit": "GB/s", "ms_per_step": round(sr["ms_per_step"], 4),
+                         "apply_ms": round(sr["apply_ms"], 4), "draw_ms": round(sr["draw_ms"], 4),
+                         "apply_hbm_frac": round(r["a_bytes"] / (sr["apply_ms"] / 1e3) / 1e9 / peak, 4),
+                         "workload": f"SRTT d={D_SKETCH} (WHT, n=2^22), A {name}"}
     for name in names[1:]:
         r = result[name]
         line[name] = {"value": round(r["value"], 3), "unit": "GB/s", "ms_per_step": round(r["ms_per_step"], 4),

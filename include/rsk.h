@@ -100,18 +100,20 @@ rsk_status rsk_profile_read(rsk_handle* h, int32_t kernel, double* total_ms, int
 rsk_status rsk_sparse_sign_generate(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
                                     int32_t* rows, uint32_t* sign_bits, cudaStream_t stream);
 
-/* Shape of the inverted index built by rsk_sparse_sign_index for (n, d, zeta): rows of S's
- * columns are grouped in chunks of *chunk_rows consecutive columns (the last chunk may be
- * shorter); *n_chunks chunks.  Host outputs. */
+/* Shape of the inverted index built by rsk_sparse_sign_index for (n, d, zeta): S's columns are
+ * grouped in chunks of *chunk_rows consecutive columns (768 for zeta <= 8; the last chunk may be
+ * shorter), *n_chunks chunks, and each chunk's offsets row has *offsets_pitch >= d + 1 entries.
+ * Host outputs. */
 rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows,
-                                      int64_t* n_chunks);
+                                      int64_t* n_chunks, int64_t* offsets_pitch);
 
 /* a2: the inverted index of S, chunked.  For chunk c (columns j in [c*C, min((c+1)*C, n)),
- * C = chunk_rows) the entries of sketch row i are
- *     entries[c*C*zeta + offsets[c*(d+1) + i] ... c*C*zeta + offsets[c*(d+1) + i + 1] - 1],
- * each a uint16 (j - c*C) | (negative << 15), in ascending j.  Concatenating chunks in order
- * gives the CSR of S with columns ascending in every row.  offsets: device uint16[n_chunks*(d+1)];
- * entries: device uint16[n*zeta]. */
+ * C = chunk_rows, P = offsets_pitch) the entries of sketch row i are
+ *     entries[c*C*zeta + offsets[c*P + i] ... c*C*zeta + offsets[c*P + i + 1] - 1],
+ * each a uint16 (j - c*C) | (negative << 15), in ascending j; offsets[c*P + d .. c*P + P - 1]
+ * hold the chunk's entry count.  Concatenating chunks in order gives the CSR of S with columns
+ * ascending in every row.  offsets: device uint16[n_chunks*P]; entries: device uint16[n*zeta],
+ * 16-byte aligned. */
 rsk_status rsk_sparse_sign_index(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
                                  uint16_t* offsets, uint16_t* entries, cudaStream_t stream);
 
@@ -134,6 +136,29 @@ rsk_status rsk_sparse_sign_plan_apply(rsk_handle* h, const rsk_sketch_plan* plan
                                       rsk_dtype a_dtype, int64_t k, int64_t lda, void* SA,
                                       rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
 rsk_status rsk_sparse_sign_plan_destroy(rsk_handle* h, rsk_sketch_plan* plan, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Subsampled randomized trigonometric transform with the Walsh-Hadamard transform (SRTT).
+ * Paper: Omega = D F S (Sec. 1.6, Eq. "intro-srtt"): D iid Rademacher diagonal, F the unitary
+ * WHT, S a restriction to d coordinates drawn uniformly without replacement, rescaled so Omega is
+ * isotropic; cost steps 1-3 and their subsampled variant (Sec. 4.x "Arithmetic costs").  As a left
+ * sketch of a tall A:  Y = sqrt(n/d) P (H_n / sqrt(n)) D A = d^{-1/2} P H_n D A, with
+ * H_n[i, l] = (-1)^{popcount(i & l)} (Sylvester order).
+ * D_i = -1 iff bit (i & 31) of word(seed, 1, i >> 7, (i >> 5) & 3) is set.  P = Floyd's algorithm
+ * over [0, n) with draws word(seed, 2, 0, q); output row q is the q-th inserted coordinate.
+ * Limits: n = 2^m < 2^31, 1 <= d <= min(n, 2048*4), k >= 1.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Random ingredients of the SRTT.  rows: device int64[d] (P in draw order), dbits: device
+ * uint32[ceil(n/32)] (bit j of word w set <=> D_{32w+j} = -1).  Either may be NULL. */
+rsk_status rsk_srtt_draw(rsk_handle* h, int64_t n, int64_t d, uint64_t seed, int64_t* rows, uint32_t* dbits,
+                         cudaStream_t stream);
+
+/* a4: Y = d^{-1/2} P H_n D A.  A: device n x k row-major (lda >= k), F32 or BF16, base address and
+ * row pitch 16-byte aligned.  Y: device d x k row-major (ldy >= k), F32 or F64.  FP32 arithmetic;
+ * partial sums over 2048-row blocks are reduced in a fixed order (deterministic). */
+rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                          int64_t d, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -78,17 +78,19 @@ def rsk_sparse_sign_generate(n, d, zeta, seed, device=None, stream=None):
 
 
 def rsk_sparse_sign_index_dims(n, d, zeta):
+    """(chunk_rows, n_chunks, offsets_pitch) of the chunked inverted index."""
     c = ctypes.c_int64()
     m = ctypes.c_int64()
-    _check(load().rsk_sparse_sign_index_dims(n, d, zeta, ctypes.byref(c), ctypes.byref(m)), None)
-    return c.value, m.value
+    p = ctypes.c_int64()
+    _check(load().rsk_sparse_sign_index_dims(n, d, zeta, ctypes.byref(c), ctypes.byref(m), ctypes.byref(p)), None)
+    return c.value, m.value, p.value
 
 
 def rsk_sparse_sign_index(n, d, zeta, seed, device=None, stream=None):
-    """Chunked inverted index of S: (offsets uint16-as-int16 [n_chunks, d+1], entries [n*zeta])."""
+    """Chunked inverted index of S: (offsets uint16-as-int16 [n_chunks, pitch], entries [n*zeta])."""
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    _, nch = rsk_sparse_sign_index_dims(n, d, zeta)
-    offs = torch.empty(nch, d + 1, dtype=torch.int16, device=dev)
+    _, nch, pitch = rsk_sparse_sign_index_dims(n, d, zeta)
+    offs = torch.empty(nch, pitch, dtype=torch.int16, device=dev)
     ents = torch.empty(n * zeta + 8, dtype=torch.int16, device=dev)
     h = handle(dev)
     _check(load().rsk_sparse_sign_index(h, n, d, zeta, seed, offs.data_ptr(), ents.data_ptr(), _stream(stream)), h)
@@ -145,6 +147,30 @@ class SparseSignPlan:
 
 def rsk_sparse_sign_plan_create(n, d, zeta, seed, device=None, stream=None):
     return SparseSignPlan(n, d, zeta, seed, device, stream)
+
+
+def rsk_srtt_draw(n, d, seed, device=None, stream=None):
+    """P (int64 [d], draw order) and D bits (int32 view of uint32 [ceil(n/32)]) of the SRTT."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    rows = torch.empty(d, dtype=torch.int64, device=dev)
+    bits = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    h = handle(dev)
+    _check(load().rsk_srtt_draw(h, n, d, seed, rows.data_ptr(), bits.data_ptr(), _stream(stream)), h)
+    return rows, bits
+
+
+def rsk_srtt_apply(A, d, seed, out_dtype=torch.float32, out=None, stream=None):
+    """Y = d^{-1/2} P H_n D A for a CUDA tensor A (n x k, n a power of two; F32/BF16)."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=A.device)
+    _matrix(out, "out")
+    h = handle(A.device)
+    st = load().rsk_srtt_apply(h, A.data_ptr(), _dt(A), n, k, A.stride(0), d, seed, out.data_ptr(), _dt(out),
+                               out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
 
 
 # Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).

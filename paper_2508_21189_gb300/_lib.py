@@ -25,12 +25,14 @@ SIGNATURES = {
     "rsk_profile_enable": [c_p, c_i32],
     "rsk_profile_read": [c_p, c_i32, c_p, c_p],
     "rsk_sparse_sign_generate": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
-    "rsk_sparse_sign_index_dims": [c_i64, c_i64, c_i32, c_p, c_p],
+    "rsk_sparse_sign_index_dims": [c_i64, c_i64, c_i32, c_p, c_p, c_p],
     "rsk_sparse_sign_index": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
     "rsk_sparse_sign_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_create": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p],
     "rsk_sparse_sign_plan_apply": [c_p, c_p, c_p, c_i32, c_i64, c_i64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_destroy": [c_p, c_p, c_p],
+    "rsk_srtt_draw": [c_p, c_i64, c_i64, c_u64, c_p, c_p, c_p],
+    "rsk_srtt_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_u64, c_p, c_i32, c_i64, c_p],
 }
 _RESTYPE = {"rsk_last_error": ctypes.c_char_p}
 

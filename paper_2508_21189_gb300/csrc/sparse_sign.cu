@@ -4,13 +4,14 @@
 //
 // Kernels
 //   k_generate  one thread per column j: Philox words -> Floyd sample of zeta distinct rows + signs.
-//   k_index     one CTA per chunk of kChunk columns: redraws the chunk's columns, counts per sketch
-//               row with per-warp counters, scans, and scatters (j_local | neg<<15) stably so every
-//               sketch row lists its columns in ascending j.  Output stays chunk-local.
-//   k_apply     one CTA per (column slice, block of sketch rows, range of chunks).  TMA streams the
-//               chunk's 128-byte row slices of A into shared memory (double buffered); each group of
-//               8 lanes owns some sketch rows and gathers their entries' row slices (16 B per lane,
-//               one 128-B line per group, so no bank conflicts), accumulating in registers.
+//   k_index     one CTA per chunk of C columns (C = 768 for zeta <= 8): redraws the chunk's columns,
+//               counts per sketch row with per-warp counters, scans, and scatters (j_local | neg<<15)
+//               stably so every sketch row lists its columns in ascending j.  Output is chunk-local.
+//   k_apply     one CTA per (128-byte column slice, block of sketch rows, range of chunks).  Per chunk,
+//               TMA streams the chunk's row slices of A and bulk copies bring the chunk's index into
+//               shared memory (double buffered, one mbarrier per stage).  A group of 8 lanes owns
+//               SLOTS consecutive sketch rows and gathers their entries' row slices (16 B per lane,
+//               one 128-byte line per group: no bank conflicts), accumulating in registers.
 //   k_reduce    sums the per-range partials in range order, scales by zeta^{-1/2}, casts, writes SA.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -24,15 +25,24 @@
 
 namespace {
 
-constexpr int kChunk = 768;         // columns of S (= rows of A) per chunk
-constexpr int kBoxRows = 256;       // rows per TMA box
-constexpr int kBoxesPerChunk = kChunk / kBoxRows;
+constexpr int kBoxRows = 128;       // rows per TMA box
 constexpr int kRowBytes = 128;      // staged row slice of A
-constexpr int kStageBytes = kChunk * kRowBytes;
+constexpr int kMaxChunkEntries = 6144;
 constexpr int kApplyThreads = 512;
 constexpr int kGroups = kApplyThreads / 8;
-constexpr int kIndexThreads = 256;
+constexpr int kIndexThreads = 512;
 constexpr uint32_t kStreamLeft = 0;
+
+// Columns of S (= rows of A) per chunk: 768 for zeta <= 8, fewer for larger zeta so that a chunk
+// holds at most kMaxChunkEntries entries (16-bit offsets, bounded shared memory).
+__host__ __device__ inline int chunk_rows(int zeta) {
+    int c = (kMaxChunkEntries / zeta) / kBoxRows * kBoxRows;
+    return c > 768 ? 768 : (c < kBoxRows ? kBoxRows : c);
+}
+// Offsets of one chunk are stored with a row pitch that keeps every row 16-byte aligned.
+__host__ __device__ inline int offsets_pitch(int d) { return (d + 1 + 7) & ~7; }
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
 // ------------------------------------------------------------------------------------------
 // Drawing one column of S.
@@ -90,21 +100,18 @@ __global__ void k_generate(int64_t n, int d, int zeta, uint64_t seed, uint32_t s
 // Chunked inverted index.
 // ------------------------------------------------------------------------------------------
 struct IndexLayout {
-    int count_warps;
     size_t tgt_off, neg_off, cnt_off, out_off, scan_off, total;
 };
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
 __host__ __device__ inline IndexLayout index_layout(int d, int zeta, int count_warps) {
+    const int C = chunk_rows(zeta);
     IndexLayout L;
-    L.count_warps = count_warps;
     L.tgt_off = 0;
-    L.neg_off = align16(L.tgt_off + size_t(kChunk) * zeta * 2);
-    L.cnt_off = align16(L.neg_off + size_t(kChunk) * 4);
+    L.neg_off = align16(L.tgt_off + size_t(C) * zeta * 2);
+    L.cnt_off = align16(L.neg_off + size_t(C) * 4);
     L.out_off = align16(L.cnt_off + size_t(count_warps) * d * 2);
-    L.scan_off = align16(L.out_off + size_t(kChunk) * zeta * 2);
-    L.total = align16(L.scan_off + (kIndexThreads / 32 + 1) * 4 * 2);
+    L.scan_off = align16(L.out_off + size_t(C) * zeta * 2);
+    L.total = align16(L.scan_off + 2 * 32 * 4);
     return L;
 }
 
@@ -121,9 +128,11 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     int* wsum = reinterpret_cast<int*>(sm + L.scan_off);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int C = chunk_rows(zeta);
+    const int pitch = offsets_pitch(d);
     const int64_t ch = blockIdx.x;
-    const int64_t j0 = ch * kChunk;
-    const int rows = int((n - j0) < kChunk ? (n - j0) : kChunk);
+    const int64_t j0 = ch * C;
+    const int rows = int((n - j0) < C ? (n - j0) : C);
     const int nent = rows * zeta;
 
     // 1. draw the chunk's columns
@@ -131,9 +140,19 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
         int rr[ZMAX];
         uint32_t nb;
         draw_column<ZMAX>(seed, stream, uint64_t(j0 + r), d, zeta, rr, nb);
+        if (ZMAX == 8 && zeta == 8) {
+            // one 16-byte store per column: lanes write consecutive 16-byte pieces (no bank conflicts)
+            uint4 pk;
+            pk.x = uint32_t(rr[0]) | (uint32_t(rr[1 % ZMAX]) << 16);
+            pk.y = uint32_t(rr[2 % ZMAX]) | (uint32_t(rr[3 % ZMAX]) << 16);
+            pk.z = uint32_t(rr[4 % ZMAX]) | (uint32_t(rr[5 % ZMAX]) << 16);
+            pk.w = uint32_t(rr[6 % ZMAX]) | (uint32_t(rr[7 % ZMAX]) << 16);
+            reinterpret_cast<uint4*>(tgt)[r] = pk;
+        } else {
 #pragma unroll
-        for (int q = 0; q < ZMAX; ++q)
-            if (q < zeta) tgt[r * zeta + q] = uint16_t(rr[q]);
+            for (int q = 0; q < ZMAX; ++q)
+                if (q < zeta) tgt[r * zeta + q] = uint16_t(rr[q]);
+        }
         neg[r] = nb;
     }
     for (int i = tid; i < count_warps * d; i += kIndexThreads) cnt[i] = 0;
@@ -156,40 +175,60 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     }
     __syncthreads();
 
-    // 3. exclusive scan over sketch rows; per-warp cursors replace the counts
-    const int per_t = (d + kIndexThreads - 1) / kIndexThreads;
-    const int i0 = min(d, tid * per_t), i1 = min(d, i0 + per_t);
-    int local = 0;
-    for (int i = i0; i < i1; ++i)
-        for (int w = 0; w < count_warps; ++w) local += cnt[size_t(w) * d + i];
-    int incl = local;
+    // 3. exclusive scan over sketch rows.  Warp w scans the contiguous range [w*R, (w+1)*R) with
+    //    lanes on consecutive rows (conflict-free), then the per-warp range totals are combined.
+    constexpr int kWarps = kIndexThreads / 32;
+    const int R = (((d + kWarps - 1) / kWarps) + 31) & ~31;
+    const int t0 = min(d, warp * R), t1 = min(d, t0 + R);
+    int carry = 0;
+    for (int base = t0; base < t1; base += 32) {
+        const int i = base + lane;
+        int tot = 0;
+        if (i < t1)
+            for (int w = 0; w < count_warps; ++w) tot += cnt[size_t(w) * d + i];
+        int incl = tot;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 31) wsum[warp] = incl;
+    if (lane == 0) wsum[warp] = carry;
     __syncthreads();
     if (tid == 0) {
         int acc = 0;
-        for (int w = 0; w < kIndexThreads / 32; ++w) {
-            const int v = wsum[w];
-            wsum[w] = acc;
-            acc += v;
+        for (int w = 0; w < kWarps; ++w) {
+            wsum[32 + w] = acc;
+            acc += wsum[w];
         }
     }
     __syncthreads();
-    int run = wsum[warp] + incl - local;
-    uint16_t* off_out = offsets + ch * (d + 1);
-    for (int i = i0; i < i1; ++i) {
-        off_out[i] = uint16_t(run);
-        for (int w = 0; w < count_warps; ++w) {
-            const int c = cnt[size_t(w) * d + i];
-            cnt[size_t(w) * d + i] = uint16_t(run);
-            run += c;
+    carry = wsum[32 + warp];
+    uint16_t* off_out = offsets + ch * pitch;
+    for (int base = t0; base < t1; base += 32) {
+        const int i = base + lane;
+        int tot = 0;
+        if (i < t1)
+            for (int w = 0; w < count_warps; ++w) tot += cnt[size_t(w) * d + i];
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
+        if (i < t1) {
+            int run = carry + incl - tot;
+            off_out[i] = uint16_t(run);
+            for (int w = 0; w < count_warps; ++w) {
+                const int c = cnt[size_t(w) * d + i];
+                cnt[size_t(w) * d + i] = uint16_t(run);
+                run += c;
+            }
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (tid == 0) off_out[d] = uint16_t(nent);
+    for (int i = d + tid; i < pitch; i += kIndexThreads) off_out[i] = uint16_t(nent);
     __syncthreads();
 
     // 4. stable scatter: same traversal order as the count
@@ -212,8 +251,8 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     }
     __syncthreads();
 
-    // 5. write the chunk's entries (chunk blocks start at multiples of kChunk*zeta*2 bytes)
-    uint16_t* dst = entries + ch * kChunk * zeta;
+    // 5. write the chunk's entries (chunk blocks start at multiples of C*zeta*2 bytes, 16-aligned)
+    uint16_t* dst = entries + ch * C * zeta;
     const int n16 = (nent * 2) / 16;
     for (int v = tid; v < n16; v += kIndexThreads)
         reinterpret_cast<uint4*>(dst)[v] = reinterpret_cast<const uint4*>(out)[v];
@@ -223,56 +262,84 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
 // ------------------------------------------------------------------------------------------
 // Gather apply.
 // ------------------------------------------------------------------------------------------
+// Per-lane accumulator of one sketch row over the lane's 16-byte column segment.  add() takes
+// the 16 staged bytes of one entry and its sign bit.
+struct AccF64 {
+    static constexpr int kVec = 2;
+    using store_t = double;
+    double v[2];
+    __device__ __forceinline__ void zero() { v[0] = v[1] = 0.0; }
+    __device__ __forceinline__ void add(const uint4 x, uint32_t negative) {
+        const uint32_t sm = negative << 31;
+        v[0] += __hiloint2double(int(x.y ^ sm), int(x.x));
+        v[1] += __hiloint2double(int(x.w ^ sm), int(x.z));
+    }
+    __device__ __forceinline__ void store(double* dst) const {
+        dst[0] = v[0];
+        dst[1] = v[1];
+    }
+};
+struct AccF32 {
+    static constexpr int kVec = 4;
+    using store_t = float;
+    float2 v[2];
+    __device__ __forceinline__ void zero() { v[0] = v[1] = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(const uint4 x, uint32_t negative) {
+        const float s = __uint_as_float(0x3f800000u | (negative << 31));
+        const float2 s2 = make_float2(s, s);
+        v[0] = __ffma2_rn(make_float2(__uint_as_float(x.x), __uint_as_float(x.y)), s2, v[0]);
+        v[1] = __ffma2_rn(make_float2(__uint_as_float(x.z), __uint_as_float(x.w)), s2, v[1]);
+    }
+    __device__ __forceinline__ void store(float* dst) const {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+};
+// bf16 words are unpacked with the sign folded in: the low half becomes w*2^16 + s and the high
+// half (w & 0xffff0000) ^ s, where s is 0 or 0x80000000 (adding 2^31 modulo 2^32 flips the top bit),
+// then both halves are accumulated with one packed f32x2 add.
+struct AccBF16 {
+    static constexpr int kVec = 8;
+    using store_t = float;
+    float2 v[4];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ static float2 unpack(uint32_t w, uint32_t sm) {
+        return make_float2(__uint_as_float(w * 65536u + sm), __uint_as_float((w & 0xffff0000u) ^ sm));
+    }
+    __device__ __forceinline__ void add(const uint4 x, uint32_t negative) {
+        const uint32_t sm = negative << 31;
+        v[0] = __fadd2_rn(v[0], unpack(x.x, sm));
+        v[1] = __fadd2_rn(v[1], unpack(x.y, sm));
+        v[2] = __fadd2_rn(v[2], unpack(x.z, sm));
+        v[3] = __fadd2_rn(v[3], unpack(x.w, sm));
+    }
+    __device__ __forceinline__ void store(float* dst) const {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    }
+};
+
 template <typename T>
 struct Elem;
 template <>
 struct Elem<double> {
-    using acc = double;
-    static constexpr int kVec = 2;
-    static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    using acc = AccF64;
 };
 template <>
 struct Elem<float> {
-    using acc = float;
-    static constexpr int kVec = 4;
-    static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    using acc = AccF32;
 };
 template <>
 struct Elem<__nv_bfloat16> {
-    using acc = float;
-    static constexpr int kVec = 8;
-    static constexpr CUtensorMapDataType kTma = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    using acc = AccBF16;
 };
-
-// acc[v] += (+-1) * x[v] for the 16 bytes x; the sign enters as an XOR of the sign bit.
-__device__ __forceinline__ void accumulate(double (&acc)[2], const uint4 x, uint32_t negative) {
-    const uint32_t sm = negative << 31;
-    acc[0] += __hiloint2double(int(x.y ^ sm), int(x.x));
-    acc[1] += __hiloint2double(int(x.w ^ sm), int(x.z));
-}
-__device__ __forceinline__ void accumulate(float (&acc)[4], const uint4 x, uint32_t negative) {
-    const uint32_t sm = negative << 31;
-    acc[0] += __uint_as_float(x.x ^ sm);
-    acc[1] += __uint_as_float(x.y ^ sm);
-    acc[2] += __uint_as_float(x.z ^ sm);
-    acc[3] += __uint_as_float(x.w ^ sm);
-}
-__device__ __forceinline__ void accumulate(float (&acc)[8], const uint4 x, uint32_t negative) {
-    const uint32_t sm = negative << 31;
-    acc[0] += __uint_as_float((x.x << 16) ^ sm);
-    acc[1] += __uint_as_float((x.x & 0xffff0000u) ^ sm);
-    acc[2] += __uint_as_float((x.y << 16) ^ sm);
-    acc[3] += __uint_as_float((x.y & 0xffff0000u) ^ sm);
-    acc[4] += __uint_as_float((x.z << 16) ^ sm);
-    acc[5] += __uint_as_float((x.z & 0xffff0000u) ^ sm);
-    acc[6] += __uint_as_float((x.w << 16) ^ sm);
-    acc[7] += __uint_as_float((x.w & 0xffff0000u) ^ sm);
-}
 
 struct ApplyArgs {
     const void* A;
     int64_t n, k, lda;
-    int d, zeta, dsub, ntsub, nslices, nranges, nchunks;
+    int d, zeta, chunk, pitch, dsub, ntsub, nslices, nranges, nchunks;
     const uint16_t* offs;
     const uint16_t* ents;
     void* partials;
@@ -280,16 +347,50 @@ struct ApplyArgs {
     unsigned int* status;
 };
 
+struct StageLayout {
+    int a_bytes, e_bytes, o_bytes, bytes;
+};
+__host__ __device__ inline StageLayout stage_layout(int chunk, int zeta, int dsub) {
+    StageLayout L;
+    L.a_bytes = chunk * kRowBytes;
+    L.e_bytes = int(align16(size_t(chunk) * zeta * 2));
+    L.o_bytes = (dsub + 8) * 2;
+    L.bytes = int(align128(size_t(L.a_bytes) + L.e_bytes + L.o_bytes));
+    return L;
+}
+
+// Loads the SLOTS+1 offsets of one group from shared memory (SLOTS >= 8: 16-byte aligned).
+template <int SLOTS>
+__device__ __forceinline__ void load_offsets(const uint16_t* o, int (&out)[SLOTS + 1]) {
+    if constexpr (SLOTS >= 8) {
+#pragma unroll
+        for (int b = 0; b < SLOTS / 8; ++b) {
+            const uint4 v = reinterpret_cast<const uint4*>(o)[b];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                out[8 * b + 2 * h] = int(w[h] & 0xffffu);
+                out[8 * b + 2 * h + 1] = int(w[h] >> 16);
+            }
+        }
+        out[SLOTS] = o[SLOTS];
+    } else {
+#pragma unroll
+        for (int q = 0; q <= SLOTS; ++q) out[q] = o[q];
+    }
+}
+
 template <typename T, int SLOTS, bool TMA>
 __global__ void __launch_bounds__(kApplyThreads, 1)
     k_apply(const __grid_constant__ CUtensorMap tmap, const ApplyArgs a) {
-    using acc_t = typename Elem<T>::acc;
-    constexpr int VEC = Elem<T>::kVec;
-    constexpr int C = 8 * VEC;  // columns of A per slice (128 bytes)
-    extern __shared__ __align__(16) uint8_t sm[];
+    using Acc = typename Elem<T>::acc;
+    constexpr int VEC = Acc::kVec;
+    constexpr int C_COLS = 8 * VEC;  // columns of A per slice (128 bytes)
+    extern __shared__ __align__(128) uint8_t sm[];
+    const StageLayout SL = stage_layout(a.chunk, a.zeta, a.dsub);
     uint8_t* const stage0 = sm;
-    uint8_t* const stage1 = sm + kStageBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (TMA ? 2 : 1) * kStageBytes);
+    uint8_t* const stage1 = sm + SL.bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (TMA ? 2 : 1) * SL.bytes);
 
     const int tid = threadIdx.x, g = tid >> 3, l8 = tid & 7;
     int b = blockIdx.x;
@@ -299,22 +400,23 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     const int r = b / a.ntsub;
     const int c0 = int(int64_t(r) * a.nchunks / a.nranges);
     const int c1 = int(int64_t(r + 1) * a.nchunks / a.nranges);
+    const int first = t * a.dsub + g * SLOTS;  // this group's sketch rows: first .. first+SLOTS-1
 
-    acc_t acc[SLOTS][VEC];
+    Acc acc[SLOTS];
 #pragma unroll
-    for (int q = 0; q < SLOTS; ++q)
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) acc[q][v] = acc_t(0);
+    for (int q = 0; q < SLOTS; ++q) acc[q].zero();
 
     auto issue = [&](int ch, uint8_t* dst, uint64_t* bar) {
-        const int64_t row0 = int64_t(ch) * kChunk;
-        int nbox = 0;
-#pragma unroll
-        for (int bx = 0; bx < kBoxesPerChunk; ++bx)
-            if (row0 + bx * kBoxRows < a.n) ++nbox;
-        rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kRowBytes));
+        const int64_t row0 = int64_t(ch) * a.chunk;
+        const int rows = int((a.n - row0) < a.chunk ? (a.n - row0) : a.chunk);
+        const int nbox = (rows + kBoxRows - 1) / kBoxRows;
+        const uint32_t eb = uint32_t(align16(size_t(rows) * a.zeta * 2));
+        rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kRowBytes) + eb + uint32_t(SL.o_bytes));
         for (int bx = 0; bx < nbox; ++bx)
-            rskd::tma_load_2d(dst + bx * kBoxRows * kRowBytes, &tmap, s * C, int(row0 + bx * kBoxRows), bar);
+            rskd::tma_load_2d(dst + bx * kBoxRows * kRowBytes, &tmap, s * C_COLS, int(row0 + bx * kBoxRows), bar);
+        rskd::bulk_load(dst + SL.a_bytes, a.ents + row0 * a.zeta, eb, bar);
+        rskd::bulk_load(dst + SL.a_bytes + SL.e_bytes, a.offs + int64_t(ch) * a.pitch + int64_t(t) * a.dsub,
+                        uint32_t(SL.o_bytes), bar);
     };
 
     if constexpr (TMA) {
@@ -338,34 +440,47 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
             if (__syncthreads_or(!ok)) break;
             buf = st ? stage1 : stage0;
         } else {
-            // Unaligned A: element-wise loads into the single stage.
+            // A not TMA-compatible: plain loads into the single stage.
             const T* A = static_cast<const T*>(a.A);
-            for (int idx = tid; idx < kChunk * 8; idx += kApplyThreads) {
+            const int64_t row0 = int64_t(ch) * a.chunk;
+            for (int idx = tid; idx < a.chunk * 8; idx += kApplyThreads) {
                 const int row = idx >> 3, piece = idx & 7;
-                const int64_t gr = int64_t(ch) * kChunk + row;
+                const int64_t gr = row0 + row;
                 __align__(16) T vals[VEC];
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) {
-                    const int64_t col = int64_t(s) * C + piece * VEC + v;
+                    const int64_t col = int64_t(s) * C_COLS + piece * VEC + v;
                     vals[v] = (gr < a.n && col < a.k) ? A[gr * a.lda + col] : T(0);
                 }
                 *reinterpret_cast<uint4*>(stage0 + row * kRowBytes + piece * 16) = *reinterpret_cast<const uint4*>(vals);
             }
+            const int rows = int((a.n - row0) < a.chunk ? (a.n - row0) : a.chunk);
+            uint16_t* es = reinterpret_cast<uint16_t*>(stage0 + SL.a_bytes);
+            for (int e = tid; e < rows * a.zeta; e += kApplyThreads) es[e] = a.ents[row0 * a.zeta + e];
+            uint16_t* os = reinterpret_cast<uint16_t*>(stage0 + SL.a_bytes + SL.e_bytes);
+            for (int e = tid; e < a.dsub + 8; e += kApplyThreads)
+                os[e] = a.offs[int64_t(ch) * a.pitch + int64_t(t) * a.dsub + e];
             __syncthreads();
             buf = stage0;
         }
-        const uint16_t* off = a.offs + int64_t(ch) * (a.d + 1);
-        const uint16_t* ent = a.ents + int64_t(ch) * kChunk * a.zeta;
+        const uint16_t* es = reinterpret_cast<const uint16_t*>(buf + SL.a_bytes);
+        const uint16_t* os = reinterpret_cast<const uint16_t*>(buf + SL.a_bytes + SL.e_bytes);
         const uint8_t* lane_base = buf + l8 * 16;
+        int o[SLOTS + 1];
+        load_offsets<SLOTS>(os + g * SLOTS, o);
 #pragma unroll
         for (int q = 0; q < SLOTS; ++q) {
-            const int i = t * a.dsub + q * kGroups + g;
-            if (i < a.d) {
-                const int beg = __ldg(off + i), end = __ldg(off + i + 1);
-                for (int e = beg; e < end; ++e) {
-                    const uint32_t v = __ldg(ent + e);
-                    const uint4 x = *reinterpret_cast<const uint4*>(lane_base + (v & 0x7fffu) * kRowBytes);
-                    accumulate(acc[q], x, v >> 15);
+            if (first + q < a.d) {
+                const int end = o[q + 1];
+                for (int e = o[q]; e < end; e += 2) {
+                    const uint32_t v0 = es[e];
+                    const uint32_t v1 = es[e + 1];
+                    const bool two = e + 1 < end;
+                    const uint4 x0 = *reinterpret_cast<const uint4*>(lane_base + (v0 & 0x7fffu) * kRowBytes);
+                    uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
+                    if (two) x1 = *reinterpret_cast<const uint4*>(lane_base + (v1 & 0x7fffu) * kRowBytes);
+                    acc[q].add(x0, v0 >> 15);
+                    if (two) acc[q].add(x1, v1 >> 15);
                 }
             }
         }
@@ -379,15 +494,12 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         }
     }
 
-    acc_t* part = static_cast<acc_t*>(a.partials) + int64_t(r) * a.pstride;
+    using store_t = typename Acc::store_t;
+    store_t* part = static_cast<store_t*>(a.partials) + int64_t(r) * a.pstride;
 #pragma unroll
     for (int q = 0; q < SLOTS; ++q) {
-        const int i = t * a.dsub + q * kGroups + g;
-        if (i < a.d) {
-            acc_t* dst = part + int64_t(i) * a.kpad + int64_t(s) * C + l8 * VEC;
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) dst[v] = acc[q][v];
-        }
+        const int i = first + q;
+        if (i < a.d) acc[q].store(part + int64_t(i) * a.kpad + int64_t(s) * C_COLS + l8 * VEC);
     }
 }
 
@@ -414,18 +526,23 @@ rsk_status check_dims(rsk_handle* h, int64_t n, int64_t d, int32_t zeta) {
     return RSK_OK;
 }
 
-int64_t n_chunks_of(int64_t n) { return (n + kChunk - 1) / kChunk; }
+int64_t n_chunks_of(int64_t n, int zeta) { return (n + chunk_rows(zeta) - 1) / chunk_rows(zeta); }
+
+// Index storage: offsets (n_chunks rows of pitch entries, plus a tail so that any target-block
+// window of the apply kernel stays in bounds) and entries (n*zeta, plus 16 bytes).
+size_t offsets_count(int64_t n, int d, int zeta) { return size_t(n_chunks_of(n, zeta)) * offsets_pitch(d) + 8192 + 16; }
+size_t entries_count(int64_t n, int zeta) { return size_t(n) * zeta + 16; }
 
 rsk_status launch_index(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed, uint32_t stream_id,
                         uint16_t* offs, uint16_t* ents, cudaStream_t stream) {
     int warps = kIndexThreads / 32;
     IndexLayout L = index_layout(d, zeta, warps);
-    while (L.total > 200 * 1024 && warps > 1) {
+    while (L.total > 110 * 1024 && warps > 1) {
         warps /= 2;
         L = index_layout(d, zeta, warps);
     }
     if (L.total > 227 * 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "index build needs %zu B of shared memory", L.total);
-    const int64_t nch = n_chunks_of(n);
+    const int64_t nch = n_chunks_of(n, zeta);
     auto go = [&](auto kern) -> rsk_status {
         RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total)));
         const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_INDEX);
@@ -440,12 +557,12 @@ rsk_status launch_index(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed
 }
 
 struct ApplyPlan {
-    int slots, dsub, ntsub, nslices, nranges, nchunks;
+    int slots, dsub, ntsub, nslices, nranges, nchunks, chunk, pitch;
     int64_t kpad, pstride;
     size_t partial_bytes;
 };
 
-ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, rsk_dtype dt) {
+ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, int zeta, rsk_dtype dt) {
     ApplyPlan p;
     const int vec = int(16 / rsk::dtype_size(dt));
     const int C = 8 * vec;
@@ -456,7 +573,9 @@ ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, rsk_dtype dt) {
     while (p.slots < need) p.slots *= 2;
     p.dsub = p.slots * kGroups;
     p.nslices = int((k + C - 1) / C);
-    p.nchunks = int(n_chunks_of(n));
+    p.chunk = chunk_rows(zeta);
+    p.pitch = offsets_pitch(d);
+    p.nchunks = int(n_chunks_of(n, zeta));
     const int pairs = p.nslices * p.ntsub;
     p.nranges = std::max(1, std::min(p.nchunks, h->num_sms / std::max(1, pairs)));
     p.kpad = int64_t(p.nslices) * C;
@@ -470,21 +589,14 @@ template <typename T, int SLOTS>
 rsk_status launch_apply_t(rsk_handle* h, const ApplyPlan& p, const ApplyArgs& args, bool use_tma,
                           const CUtensorMap& map, cudaStream_t stream) {
     const unsigned grid = unsigned(p.nslices * p.ntsub * p.nranges);
-    if (use_tma) {
-        auto kern = k_apply<T, SLOTS, true>;
-        const int smem = 2 * kStageBytes + 64;
-        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
-        kern<<<grid, kApplyThreads, smem, stream>>>(map, args);
-        rsk::prof_end(h, stream, pr);
-    } else {
-        auto kern = k_apply<T, SLOTS, false>;
-        const int smem = kStageBytes + 64;
-        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
-        kern<<<grid, kApplyThreads, smem, stream>>>(map, args);
-        rsk::prof_end(h, stream, pr);
-    }
+    const StageLayout SL = stage_layout(p.chunk, args.zeta, p.dsub);
+    const int smem = (use_tma ? 2 : 1) * SL.bytes + 64;
+    if (smem > 227 * 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "apply needs %d B of shared memory", smem);
+    auto kern = use_tma ? k_apply<T, SLOTS, true> : k_apply<T, SLOTS, false>;
+    RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
+    kern<<<grid, kApplyThreads, smem, stream>>>(map, args);
+    rsk::prof_end(h, stream, pr);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
@@ -544,6 +656,8 @@ rsk_status apply_with_index(rsk_handle* h, const uint16_t* offs, const uint16_t*
     args.lda = lda;
     args.d = d;
     args.zeta = zeta;
+    args.chunk = p.chunk;
+    args.pitch = p.pitch;
     args.dsub = p.dsub;
     args.ntsub = p.ntsub;
     args.nslices = p.nslices;
@@ -564,14 +678,12 @@ rsk_status apply_with_index(rsk_handle* h, const uint16_t* offs, const uint16_t*
     return launch_reduce<float>(h, p, partials, d, k, zeta, SA, sa_dt, ldsa, stream);
 }
 
-rsk_status check_apply_args(rsk_handle* h, const void* A, int a_dt, int64_t n, int64_t k, int64_t lda, int64_t d,
-                            const void* SA, int sa_dt, int64_t ldsa) {
+rsk_status check_apply_args(rsk_handle* h, const void* A, int a_dt, int64_t k, int64_t lda, const void* SA,
+                            int sa_dt, int64_t ldsa) {
     if (!A || !SA) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null matrix pointer");
     if (!rsk::dtype_ok(a_dt)) return rsk::fail(h, RSK_ERR_INVALID_ARG, "bad A dtype %d", a_dt);
     if (sa_dt != RSK_F64 && sa_dt != RSK_F32) return rsk::fail(h, RSK_ERR_INVALID_ARG, "SA dtype must be F64 or F32");
     if (k < 1 || lda < k || ldsa < k) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need k >= 1, lda >= k, ldsa >= k");
-    (void)n;
-    (void)d;
     return RSK_OK;
 }
 
@@ -604,10 +716,13 @@ rsk_status rsk_sparse_sign_generate(rsk_handle* h, int64_t n, int64_t d, int32_t
     return RSK_OK;
 }
 
-rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows, int64_t* n_chunks) {
-    if (check_dims(nullptr, n, d, zeta) != RSK_OK || !chunk_rows || !n_chunks) return RSK_ERR_INVALID_ARG;
-    *chunk_rows = kChunk;
-    *n_chunks = n_chunks_of(n);
+rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows_out, int64_t* n_chunks,
+                                      int64_t* offsets_pitch_out) {
+    if (check_dims(nullptr, n, d, zeta) != RSK_OK || !chunk_rows_out || !n_chunks || !offsets_pitch_out)
+        return RSK_ERR_INVALID_ARG;
+    *chunk_rows_out = chunk_rows(zeta);
+    *n_chunks = n_chunks_of(n, zeta);
+    *offsets_pitch_out = offsets_pitch(int(d));
     return RSK_OK;
 }
 
@@ -628,18 +743,18 @@ rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype
     if (!h) return RSK_ERR_INVALID_ARG;
     rsk_status st = check_dims(h, n, d, zeta);
     if (st != RSK_OK) return st;
-    st = check_apply_args(h, A, a_dtype, n, k, lda, d, SA, sa_dtype, ldsa);
+    st = check_apply_args(h, A, a_dtype, k, lda, SA, sa_dtype, ldsa);
     if (st != RSK_OK) return st;
-    const ApplyPlan p = plan_apply(h, n, k, int(d), a_dtype);
-    const size_t off_bytes = size_t(p.nchunks) * (d + 1) * 2;
-    const size_t ent_bytes = size_t(n) * zeta * 2 + 16;
+    const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dtype);
+    const size_t off_bytes = offsets_count(n, int(d), zeta) * 2;
+    const size_t ent_bytes = entries_count(n, zeta) * 2;
     const size_t need = rsk::Carver::round(off_bytes) + rsk::Carver::round(ent_bytes) +
                         rsk::Carver::round(p.partial_bytes) + 256;
     st = rsk::ensure_workspace(h, need, stream);
     if (st != RSK_OK) return st;
     rsk::Carver cv(h->ws);
-    uint16_t* offs = cv.take<uint16_t>(size_t(p.nchunks) * (d + 1));
-    uint16_t* ents = cv.take<uint16_t>(size_t(n) * zeta + 8);
+    uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
+    uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
     void* partials = cv.take<char>(p.partial_bytes);
     st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
     if (st != RSK_OK) return st;
@@ -659,9 +774,9 @@ rsk_status rsk_sparse_sign_plan_create(rsk_handle* h, int64_t n, int64_t d, int3
     p->d = d;
     p->zeta = zeta;
     p->seed = seed;
-    p->nchunks = n_chunks_of(n);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p->offs), size_t(p->nchunks) * (d + 1) * 2, stream);
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&p->ents), size_t(n) * zeta * 2 + 16, stream);
+    p->nchunks = n_chunks_of(n, zeta);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p->offs), offsets_count(n, int(d), zeta) * 2, stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&p->ents), entries_count(n, zeta) * 2, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (p->offs) cudaFreeAsync(p->offs, stream);
@@ -683,9 +798,9 @@ rsk_status rsk_sparse_sign_plan_apply(rsk_handle* h, const rsk_sketch_plan* plan
                                       int64_t k, int64_t lda, void* SA, rsk_dtype sa_dtype, int64_t ldsa,
                                       cudaStream_t stream) {
     if (!h || !plan) return RSK_ERR_INVALID_ARG;
-    rsk_status st = check_apply_args(h, A, a_dtype, plan->n, k, lda, plan->d, SA, sa_dtype, ldsa);
+    rsk_status st = check_apply_args(h, A, a_dtype, k, lda, SA, sa_dtype, ldsa);
     if (st != RSK_OK) return st;
-    const ApplyPlan p = plan_apply(h, plan->n, k, int(plan->d), a_dtype);
+    const ApplyPlan p = plan_apply(h, plan->n, k, int(plan->d), plan->zeta, a_dtype);
     st = rsk::ensure_workspace(h, rsk::Carver::round(p.partial_bytes) + 256, stream);
     if (st != RSK_OK) return st;
     rsk::Carver cv(h->ws);

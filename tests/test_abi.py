@@ -50,12 +50,15 @@ def test_argument_counts_match_header(lib):
 
 def test_host_only_calls(lib):
     assert lib.rsk_version() == 100
-    c, m = ctypes.c_int64(), ctypes.c_int64()
-    assert lib.rsk_sparse_sign_index_dims(20000, 400, 8, ctypes.byref(c), ctypes.byref(m)) == 0
-    assert m.value == (20000 + c.value - 1) // c.value
+    c, m, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    args = (ctypes.byref(c), ctypes.byref(m), ctypes.byref(p))
+    assert lib.rsk_sparse_sign_index_dims(20000, 400, 8, *args) == 0
+    assert m.value == (20000 + c.value - 1) // c.value and p.value >= 401
+    assert c.value * 8 <= 6144
+    assert lib.rsk_sparse_sign_index_dims(20000, 400, 32, *args) == 0 and c.value * 32 <= 6144
     # invalid shapes are rejected before any device work
-    assert lib.rsk_sparse_sign_index_dims(100, 4, 8, ctypes.byref(c), ctypes.byref(m)) == 1
-    assert lib.rsk_sparse_sign_index_dims(100, 9000, 8, ctypes.byref(c), ctypes.byref(m)) == 1
-    assert lib.rsk_sparse_sign_index_dims(100, 64, 33, ctypes.byref(c), ctypes.byref(m)) == 1
+    assert lib.rsk_sparse_sign_index_dims(100, 4, 8, *args) == 1
+    assert lib.rsk_sparse_sign_index_dims(100, 9000, 8, *args) == 1
+    assert lib.rsk_sparse_sign_index_dims(100, 64, 33, *args) == 1
     assert lib.rsk_sparse_sign_apply(None, None, 0, 10, 1, 1, 4, 2, 0, None, 0, 1, None) == 1
     assert lib.rsk_destroy(None) == 1

@@ -34,7 +34,8 @@ def global_csr_from_chunks(offs, ents, n, d, zeta, chunk):
     nch = offs.shape[0]
     rows_l, chunk_l, pos_l, j_l, neg_l = [], [], [], [], []
     for c in range(nch):
-        o = offs[c]
+        o = offs[c, : d + 1]
+        assert np.all(offs[c, d:] == o[-1])
         cnt = np.diff(o)
         assert o[0] == 0 and np.all(cnt >= 0)
         m = int(o[-1])
@@ -60,7 +61,8 @@ def test_generate_and_index_bit_exact(rsk, n, d, zeta, seed):
     o_rows, o_signs = osk.columns(n, d, zeta, seed)
     assert np.array_equal(rows.cpu().numpy(), o_rows)
     assert np.array_equal(bits.cpu().numpy().view(np.uint32), osk.sign_bits(o_signs))
-    chunk, nch = rsk.rsk_sparse_sign_index_dims(n, d, zeta)
+    chunk, nch, pitch = rsk.rsk_sparse_sign_index_dims(n, d, zeta)
+    assert pitch >= d + 1 and pitch % 8 == 0
     offs, ents = rsk.rsk_sparse_sign_index(n, d, zeta, seed)
     rowptr, j, neg = global_csr_from_chunks(offs, ents, n, d, zeta, chunk)
     o_rowptr, o_j, o_neg = osk.csr(n, d, zeta, seed)
@@ -162,7 +164,7 @@ def test_full_size_embedding(rsk, dtype):
     check_rows(SA[:, cols], sub32, d, zeta, seed, U[dtype])
     check_rows(SA[:, cols], subr, d, zeta, seed, 2.0 ** -24)
     if dtype == torch.bfloat16:
-        chunk, _ = rsk.rsk_sparse_sign_index_dims(n, d, zeta)
+        chunk, _, _ = rsk.rsk_sparse_sign_index_dims(n, d, zeta)
         offs, ents = rsk.rsk_sparse_sign_index(n, d, zeta, seed)
         rowptr, j, neg = global_csr_from_chunks(offs, ents, n, d, zeta, chunk)
         o_rowptr, o_j, o_neg = osk.csr(n, d, zeta, seed)
