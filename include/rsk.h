@@ -146,7 +146,8 @@ rsk_status rsk_sparse_sign_plan_destroy(rsk_handle* h, rsk_sketch_plan* plan, cu
  * H_n[i, l] = (-1)^{popcount(i & l)} (Sylvester order).
  * D_i = -1 iff bit (i & 31) of word(seed, 1, i >> 7, (i >> 5) & 3) is set.  P = Floyd's algorithm
  * over [0, n) with draws word(seed, 2, 0, q); output row q is the q-th inserted coordinate.
- * Limits: n = 2^m < 2^31, 1 <= d <= min(n, 2048*4), k >= 1.
+ * Limits: n = 2^m < 2^31, k >= 1; 1 <= d <= min(n, 8192) for rsk_srtt_draw and
+ * 1 <= d <= min(n, 2048) for rsk_srtt_apply (RSK_ERR_UNSUPPORTED beyond).
  * ------------------------------------------------------------------------------------------- */
 
 /* Random ingredients of the SRTT.  rows: device int64[d] (P in draw order), dbits: device
@@ -154,11 +155,53 @@ rsk_status rsk_sparse_sign_plan_destroy(rsk_handle* h, rsk_sketch_plan* plan, cu
 rsk_status rsk_srtt_draw(rsk_handle* h, int64_t n, int64_t d, uint64_t seed, int64_t* rows, uint32_t* dbits,
                          cudaStream_t stream);
 
-/* a4: Y = d^{-1/2} P H_n D A.  A: device n x k row-major (lda >= k), F32 or BF16, base address and
- * row pitch 16-byte aligned.  Y: device d x k row-major (ldy >= k), F32 or F64.  FP32 arithmetic;
- * partial sums over 2048-row blocks are reduced in a fixed order (deterministic). */
+/* a4: Y = d^{-1/2} P H_n D A.  A: device n x k row-major (lda >= k), F32 or BF16 (TMA staging when
+ * the base address and row pitch are 16-byte aligned, plain loads otherwise).  Y: device d x k
+ * row-major (ldy >= k), F32 or F64.  FP32 arithmetic; partial sums over 2048-row blocks are
+ * reduced in a fixed order (deterministic). */
 rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
                           int64_t d, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Sketch-and-precondition least squares, min_x ||A x - b||_2 (rows a5-a7).
+ * Paper: sketch-and-solve (Alg. 3, Sec. 2.3) for the warm start; sketch-and-precondition is named
+ * as the standard high-accuracy method (remark closing Sec. 2.3) but not spelled out.  Steps:
+ *   [Ahat | bhat] = S [A | b] (sparse sign, d rows, zeta per column, seed);
+ *   Householder QR of Ahat in FP64 -> R and Q^T bhat;  x0 = R^{-1} Q^T bhat;
+ *   refinement: g = A^T (b - A x) in FP64; eta = ||g|| / (||A||_F ||b - A x||); stop at
+ *   eta <= tol_backward; else CG on (M^T M) z = R^{-T} g with M = A R^{-1} in inner_dtype, then
+ *   x += R^{-1} z.
+ * Precision notes: inner_dtype F32 converges when u_32 * kappa(A) is well below 1 or when A's
+ * ill-conditioning is a column scaling; for kappa(A) ~ 1e8 with mixed columns use F64.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+    int64_t d;               /* sketch rows (k <= d <= 8192) */
+    int32_t zeta;            /* nonzeros per column of S */
+    uint64_t seed;           /* Philox seed of S */
+    rsk_dtype sketch_dtype;  /* precision A is sketched in: F64, F32 or BF16 (FP32 accumulation) */
+    rsk_dtype inner_dtype;   /* precision of the CG operator: F64 or F32 */
+    double tol_backward;     /* target eta (default 1e-10 when <= 0) */
+    int32_t max_refine;      /* refinement steps (default 20 when <= 0) */
+    int32_t max_inner_iters; /* CG iterations per step (default 50 when <= 0) */
+    double inner_tol;        /* relative CG residual reduction per step (default 1e-6 when <= 0) */
+} rsk_lsq_opts;
+
+typedef struct {
+    double backward_err;     /* eta(x) at exit */
+    double residual_norm;    /* ||b - A x||_2 */
+    double frobenius_norm;   /* ||A||_F */
+    int32_t refine_steps;    /* refinement steps taken */
+    int32_t inner_iters;     /* total CG iterations */
+    rsk_status status;       /* RSK_OK or RSK_ERR_NOT_CONVERGED */
+} rsk_lsq_info;
+
+/* A: device n x k row-major (lda >= k), F64 or F32; 1 <= k <= 1024, n >= k.  b: device FP64[n].
+ * x: device FP64[k] (output).  info: host (may be NULL).  Synchronous: returns after the solve
+ * (the refinement loop reads eta on the host).  Returns RSK_ERR_NOT_CONVERGED, with x the last
+ * iterate and info filled, if eta stays above tol_backward after max_refine steps. */
+rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                    int64_t lda, const double* b, double* x, const rsk_lsq_opts* opts,
+                                    rsk_lsq_info* info, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,7 @@ import ctypes
 
 import torch
 
-from ._lib import RskError, STATUS, load
+from ._lib import LsqInfo, LsqOpts, RskError, STATUS, load
 
 RSK_F64, RSK_F32, RSK_BF16 = 0, 1, 2
 _DT = {torch.float64: RSK_F64, torch.float32: RSK_F32, torch.bfloat16: RSK_BF16}
@@ -171,6 +171,32 @@ def rsk_srtt_apply(A, d, seed, out_dtype=torch.float32, out=None, stream=None):
                                out.stride(0), _stream(stream))
     _check(st, h)
     return out
+
+
+def rsk_lstsq_sketch_precond(A, b, d, zeta=8, seed=0, sketch_dtype=torch.bfloat16, inner_dtype=torch.float32,
+                             tol=1e-10, max_refine=20, max_inner=50, inner_tol=1e-6, x=None, stream=None,
+                             raise_on_nonconvergence=True):
+    """x = argmin ||A x - b|| by sketch-and-precondition; returns (x FP64 [k], info dict).
+
+    A: CUDA tensor n x k (F64 or F32, row-major); b: CUDA FP64 [n]."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if b.dtype != torch.float64 or not b.is_cuda or b.numel() != n or not b.is_contiguous():
+        raise ValueError("b must be a contiguous CUDA float64 vector of length n")
+    if x is None:
+        x = torch.empty(k, dtype=torch.float64, device=A.device)
+    opts = LsqOpts(d, zeta, seed, _DT[sketch_dtype], _DT[inner_dtype], tol, max_refine, max_inner, inner_tol)
+    info = LsqInfo()
+    h = handle(A.device)
+    st = load().rsk_lstsq_sketch_precond(h, A.data_ptr(), _dt(A), n, k, A.stride(0), b.data_ptr(), x.data_ptr(),
+                                         ctypes.byref(opts), ctypes.byref(info), _stream(stream))
+    out = {"backward_err": info.backward_err, "residual_norm": info.residual_norm,
+           "frobenius_norm": info.frobenius_norm, "refine_steps": info.refine_steps,
+           "inner_iters": info.inner_iters, "status": STATUS.get(info.status, info.status)}
+    if st == 4 and not raise_on_nonconvergence:
+        return x, out
+    _check(st, h)
+    return x, out
 
 
 # Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).

@@ -33,7 +33,23 @@ SIGNATURES = {
     "rsk_sparse_sign_plan_destroy": [c_p, c_p, c_p],
     "rsk_srtt_draw": [c_p, c_i64, c_i64, c_u64, c_p, c_p, c_p],
     "rsk_srtt_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_lstsq_sketch_precond": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p],
 }
+
+
+class LsqOpts(ctypes.Structure):
+    """rsk_lsq_opts (rsk.h)."""
+    _fields_ = [("d", ctypes.c_int64), ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("sketch_dtype", ctypes.c_int32), ("inner_dtype", ctypes.c_int32),
+                ("tol_backward", ctypes.c_double), ("max_refine", ctypes.c_int32),
+                ("max_inner_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+
+
+class LsqInfo(ctypes.Structure):
+    """rsk_lsq_info (rsk.h)."""
+    _fields_ = [("backward_err", ctypes.c_double), ("residual_norm", ctypes.c_double),
+                ("frobenius_norm", ctypes.c_double), ("refine_steps", ctypes.c_int32),
+                ("inner_iters", ctypes.c_int32), ("status", ctypes.c_int32)]
 _RESTYPE = {"rsk_last_error": ctypes.c_char_p}
 
 _lib = None

@@ -68,6 +68,13 @@ bool encode_2d(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const vo
                uint64_t inner, uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner,
                uint32_t box_outer);
 
+// Sparse sign apply with caller-provided scratch for the per-range partials (used by solvers that
+// carve their own buffers out of the workspace).  sketch_partial_bytes gives the size needed.
+size_t sketch_partial_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int zeta, rsk_dtype a_dt);
+rsk_status sketch_plan_apply_ws(rsk_handle* h, const rsk_sketch_plan* plan, const void* A, rsk_dtype a_dt, int64_t k,
+                                int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa, void* partials,
+                                cudaStream_t stream);
+
 }  // namespace rsk
 
 #define RSK_CUDA_TRY(h, call)                                                                  \

@@ -1,0 +1,628 @@
+// Sketch-and-precondition least squares (rows a5-a7): min_x ||A x - b||_2 for tall A (n x k).
+// Paper: sketch-and-solve, Alg. 3 (Sec. 2.3) gives the warm start from the sketched problem; the
+// paper names sketch-and-precondition as the standard high-accuracy route (remark closing Sec. 2.3)
+// without stating it, so the steps are this library's reading:
+//   L1  [Ahat | bhat] = S [A | b] with one sparse sign S (rsk_sparse_sign_plan_*).
+//   L2  Householder QR of Ahat in FP64 (k_qr: one reflector per column, persistent grid with a
+//       bounded software grid barrier); Q^T bhat comes out of the same sweep as an extra column.
+//   L3  x0 = R^{-1} Q^T bhat; R^{-1} is formed explicitly (k_rinv, FP64) and applied as a matvec.
+//   L4  refinement: g = A^T (b - A x) in FP64 (one fused pass over A), eta(x) = ||g|| / (||A||_F ||r||);
+//       stop at eta <= tol; otherwise solve (M^T M) z = R^{-T} g with CG, M = A R^{-1}, whose
+//       products M^T M p = R^{-T} A^T A R^{-1} p are one fused pass over A in the inner precision,
+//       and set x += R^{-1} z.  Because the right-hand side is the FP64 normal-equation residual,
+//       the fixed point is A^T r = 0 to FP64 accuracy whatever the inner precision; the inner
+//       precision only sets the contraction per step.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int kPassThreads = 256;      // fused normal-equation passes
+constexpr int kMaxK = 1024;
+
+// ------------------------------------------------------------------------------------------
+// Bounded software grid barrier for persistent kernels whose CTAs are all resident.
+// ------------------------------------------------------------------------------------------
+__device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, unsigned int nblocks,
+                             unsigned int* status) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd(const_cast<unsigned int*>(gen), 1u);
+        } else {
+            uint32_t it = 0;
+            while (*gen == g) {
+                if (++it > rskd::kWaitLimit) {
+                    atomicOr(status, RSK_DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (it > 64) __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];  // same order in every thread
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// L2: Householder QR of W = [Ahat | bhat] (d x (k+1), column-major, leading dimension d).
+// Column c is owned by CTA c % gridDim.x.  Step j: the owner of column j has it fully updated
+// and forms reflector j (beta into W[j,j], v below the diagonal with v_j = 1 implicit, tau_j);
+// after one grid barrier every CTA applies reflector j to the columns c > j it owns.
+// ------------------------------------------------------------------------------------------
+__device__ void make_reflector(double* col, int d, int j, double* tau, double* red) {
+    double s = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) {
+        const double v = __ldcg(col + i);
+        s += v * v;
+    }
+    const double sigma = block_sum(s, red);
+    const double alpha = __ldcg(col + j);
+    double t = 0.0, beta = alpha, scale = 0.0;
+    if (sigma > 0.0) {
+        const double nrm = sqrt(alpha * alpha + sigma);
+        beta = alpha > 0.0 ? -nrm : nrm;
+        t = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+    }
+    if (sigma > 0.0)
+        for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) col[i] = __ldcg(col + i) * scale;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        col[j] = beta;
+        tau[j] = t;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_qr(double* W, int d, int k, double* tau, unsigned int* bar,
+                                           unsigned int* status) {
+    __shared__ double red[32];
+    const unsigned int G = gridDim.x;
+    const int cols = k + 1;
+    if (blockIdx.x == 0) make_reflector(W, d, 0, tau, red);
+    for (int j = 0; j < k; ++j) {
+        if (!grid_barrier(bar, bar + 1, G, status)) return;
+        // Reflector j was written by another CTA: read it through L2 (ld.cg), never from a line this
+        // SM's L1 may hold from an earlier step.
+        const double* v = W + size_t(j) * d;
+        const double tj = __ldcg(tau + j);
+        for (int c = j + 1 + ((int(blockIdx.x) - (j + 1)) % int(G) + int(G)) % int(G); c < cols; c += G) {
+            double* col = W + size_t(c) * d;
+            double s = 0.0;
+            for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) s += __ldcg(v + i) * __ldcg(col + i);
+            const double w = tj * (__ldcg(col + j) + block_sum(s, red));
+            if (threadIdx.x == 0) col[j] = __ldcg(col + j) - w;
+            for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) col[i] = __ldcg(col + i) - w * __ldcg(v + i);
+            __syncthreads();
+            if (c == j + 1 && c < k) make_reflector(col, d, c, tau, red);
+        }
+    }
+}
+
+// R^{-1} of the upper triangle of W (column-major, ld d) into X (k x k column-major): one warp
+// per column c solves R x = e_c by column-oriented back substitution.
+__global__ void k_rinv(const double* __restrict__ W, int d, int k, double* __restrict__ X) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= k) return;
+    const int c = warp;
+    double* x = X + size_t(c) * k;
+    for (int i = lane; i < k; i += 32) x[i] = (i == c) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int l = c; l >= 0; --l) {
+        const double* Rl = W + size_t(l) * d;  // column l of R
+        const double xl = x[l] / Rl[l];
+        __syncwarp();
+        if (lane == 0) x[l] = xl;
+        for (int i = lane; i < l; i += 32) x[i] -= Rl[i] * xl;
+        __syncwarp();
+    }
+}
+
+// y = op(X) v for X k x k column-major upper triangular (op = X or X^T); one warp per output.
+__global__ void k_trmv(const double* __restrict__ X, int k, int trans, const double* __restrict__ v,
+                       double* __restrict__ y) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= k) return;
+    double s = 0.0;
+    if (!trans) {
+        for (int l = i + lane; l < k; l += 32) s += X[size_t(l) * k + i] * v[l];   // row i of X
+    } else {
+        for (int l = lane; l <= i; l += 32) s += X[size_t(i) * k + l] * v[l];      // column i of X
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = s;
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused passes over A.  Each warp walks rows; lane l holds columns l, l+32, ... of the row.
+//   CG pass   (Acc = float):  w_i = a_i . y,  q += w_i a_i          (q = A^T A y)
+//   residual  (Acc = double): r_i = b_i - a_i . x, g += r_i a_i, rr += r_i^2, ff += |a_i|^2
+// Per-CTA partials are reduced in CTA order by k_reduce_parts (deterministic).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float to_float(T v) {
+    return float(v);
+}
+template <>
+__device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+template <typename T, typename Acc, int M, bool RESID>
+__global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, int64_t n, int k, int64_t lda,
+                                                        const Acc* __restrict__ y, const double* __restrict__ b,
+                                                        Acc* __restrict__ part, double* __restrict__ part_s,
+                                                        int want_frob) {
+    // dynamic shared memory: gs[warps][k] (per-warp partial sums), ys[k]
+    extern __shared__ __align__(16) uint8_t dsm[];
+    Acc* gs = reinterpret_cast<Acc*>(dsm);
+    Acc* ys = gs + size_t(kPassThreads / 32) * k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ys[j] = y[j];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int64_t r0 = int64_t(blockIdx.x) * n / gridDim.x, r1 = int64_t(blockIdx.x + 1) * n / gridDim.x;
+    Acc g[M], yv[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        g[m] = Acc(0);
+        const int j = lane + 32 * m;
+        yv[m] = j < k ? ys[j] : Acc(0);
+    }
+    double rr = 0.0, ff = 0.0;
+    for (int64_t i = r0 + warp; i < r1; i += nw) {
+        const T* row = A + i * lda;
+        Acc a[M];
+        Acc dot = Acc(0);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int j = lane + 32 * m;
+            if constexpr (sizeof(Acc) == 8) a[m] = j < k ? Acc(row[j]) : Acc(0);
+            else a[m] = j < k ? Acc(to_float<T>(row[j])) : Acc(0);
+            dot += a[m] * yv[m];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        Acc w = dot;
+        if constexpr (RESID) {
+            w = Acc(b[i]) - dot;
+            rr += double(w) * double(w);
+            if (want_frob) {
+#pragma unroll
+                for (int m = 0; m < M; ++m) ff += double(a[m]) * double(a[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) g[m] += w * a[m];
+    }
+    // reduce the warps' partial g in a fixed order through shared memory
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int j = lane + 32 * m;
+        if (j < k) gs[size_t(warp) * k + j] = g[m];
+    }
+    __shared__ double ss[kPassThreads / 32][2];
+    if constexpr (RESID) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+            ff += __shfl_xor_sync(0xffffffffu, ff, o);
+        }
+        if (lane == 0) {
+            ss[warp][0] = rr;
+            ss[warp][1] = ff;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        Acc s = Acc(0);
+        for (int w = 0; w < nw; ++w) s += gs[size_t(w) * k + j];
+        part[size_t(blockIdx.x) * k + j] = s;
+    }
+    if (RESID && threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            a0 += ss[w][0];
+            a1 += ss[w][1];
+        }
+        part_s[2 * blockIdx.x] = a0;
+        part_s[2 * blockIdx.x + 1] = a1;
+    }
+}
+
+template <typename Acc>
+__global__ void k_reduce_parts(const Acc* __restrict__ part, int nparts, int k, double* __restrict__ out,
+                               const double* __restrict__ part_s, double* __restrict__ out_s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; ++p) s += double(part[size_t(p) * k + j]);
+        out[j] = s;
+    }
+    if (part_s && j < 2) {
+        double s = 0.0;
+        for (int p = 0; p < nparts; ++p) s += part_s[2 * p + j];
+        out_s[j] = s;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Small vector kernels (k entries, one CTA).
+// ------------------------------------------------------------------------------------------
+// State of the CG iteration: [0] rho, [1] rho0, [2] done flag, [3] iterations done.
+__global__ void k_cg_init(const double* __restrict__ c, double* __restrict__ z, double* __restrict__ res,
+                          double* __restrict__ p, int k, double* __restrict__ state) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        z[j] = 0.0;
+        res[j] = c[j];
+        p[j] = c[j];
+        s += c[j] * c[j];
+    }
+    const double rho = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        state[0] = rho;
+        state[1] = rho;
+        state[2] = rho > 0.0 ? 0.0 : 1.0;
+        state[3] = 0.0;
+    }
+}
+
+// s = M^T M p (already computed); z += alpha p, res -= alpha s, p = res + beta p.
+__global__ void k_cg_step(const double* __restrict__ s, double* __restrict__ z, double* __restrict__ res,
+                          double* __restrict__ p, int k, double* __restrict__ state, double tol) {
+    __shared__ double red[32];
+    if (state[2] != 0.0) return;
+    double ps = 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) ps += p[j] * s[j];
+    const double pAp = block_sum(ps, red);
+    const double rho = state[0];
+    const double alpha = pAp > 0.0 ? rho / pAp : 0.0;
+    double rn = 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        z[j] += alpha * p[j];
+        res[j] -= alpha * s[j];
+        rn += res[j] * res[j];
+    }
+    const double rho_new = block_sum(rn, red);
+    const double beta = rho > 0.0 ? rho_new / rho : 0.0;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) p[j] = res[j] + beta * p[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        state[0] = rho_new;
+        state[3] += 1.0;
+        if (!(pAp > 0.0) || rho_new <= tol * tol * state[1]) state[2] = 1.0;
+    }
+}
+
+template <typename Acc>
+__global__ void k_cast_vec(const double* __restrict__ src, Acc* __restrict__ dst, int k, const double* state) {
+    if (state && state[2] != 0.0) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) dst[j] = Acc(src[j]);
+}
+
+__global__ void k_axpy(double* __restrict__ x, const double* __restrict__ dx, int k) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) x[j] += dx[j];
+}
+
+// [Ahat | bhat] row-major (d x k, ldsa; d x 1) -> W column-major FP64.
+template <typename S>
+__global__ void k_to_colmajor(const S* __restrict__ SA, int64_t ldsa, const double* __restrict__ Sb, int d, int k,
+                              double* __restrict__ W) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= int64_t(d) * (k + 1)) return;
+    const int c = int(idx / d), i = int(idx - int64_t(c) * d);
+    W[idx] = c < k ? double(SA[int64_t(i) * ldsa + c]) : double(Sb[i]);
+}
+
+template <typename Src, typename Dst>
+__global__ void k_convert(const Src* __restrict__ A, int64_t n, int k, int64_t lda, Dst* __restrict__ B) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k, j = idx - i * k;
+    B[idx] = Dst(float(A[i * lda + j]));
+}
+template <>
+__global__ void k_convert<double, double>(const double* __restrict__ A, int64_t n, int k, int64_t lda,
+                                          double* __restrict__ B) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k, j = idx - i * k;
+    B[idx] = A[i * lda + j];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Host driver.
+// ------------------------------------------------------------------------------------------
+namespace rsk {
+
+struct LsqWork {
+    double *W, *tau, *Rinv, *x, *g, *c, *z, *res, *p, *s, *t, *stats, *parts_s;
+    void* parts;
+    void* yv;
+    unsigned int* bar;
+    float* SA32;
+    double* SA64;
+    void* Sb;
+    void* Alow;  // converted copy of A (sketch / inner precision) when needed
+};
+
+template <typename T, typename Acc>
+static rsk_status launch_pass(rsk_handle* h, const T* A, int64_t n, int k, int64_t lda, const Acc* y, const double* b,
+                              Acc* parts, double* parts_s, int nparts, bool resid, bool frob, cudaStream_t stream) {
+    const int M = (k + 31) / 32;
+    const size_t smem = (size_t(kPassThreads / 32) + 1) * k * sizeof(Acc);
+    rsk_status err = RSK_OK;
+    auto go = [&](auto kern) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+            err = RSK_ERR_CUDA;
+            return;
+        }
+        kern<<<unsigned(nparts), kPassThreads, smem, stream>>>(A, n, k, lda, y, b, parts, parts_s, frob ? 1 : 0);
+    };
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_DENSE);
+#define RSK_PASS_CASE(MM)                                          \
+    case MM:                                                       \
+        if (resid) go(k_pass<T, Acc, MM, true>);                   \
+        else go(k_pass<T, Acc, MM, false>);                        \
+        break;
+    switch (M <= 4 ? 4 : (M <= 8 ? 8 : (M <= 16 ? 16 : 32))) {
+        RSK_PASS_CASE(4)
+        RSK_PASS_CASE(8)
+        RSK_PASS_CASE(16)
+        RSK_PASS_CASE(32)
+        default: return rsk::fail(h, RSK_ERR_INTERNAL, "bad pass width");
+    }
+#undef RSK_PASS_CASE
+    rsk::prof_end(h, stream, pr);
+    if (err != RSK_OK) return rsk::fail(h, err, "cudaFuncSetAttribute failed for the fused pass");
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+}  // namespace rsk
+
+extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                               int64_t lda, const double* b, double* x, const rsk_lsq_opts* opts,
+                                               rsk_lsq_info* info, cudaStream_t stream) {
+    using namespace rsk;
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!A || !b || !x || !opts) return fail(h, RSK_ERR_INVALID_ARG, "null argument");
+    if (a_dtype != RSK_F64 && a_dtype != RSK_F32) return fail(h, RSK_ERR_INVALID_ARG, "A must be F64 or F32");
+    if (k < 1 || k > kMaxK || n < k || lda < k)
+        return fail(h, RSK_ERR_INVALID_ARG, "need 1 <= k <= %d, n >= k, lda >= k", kMaxK);
+    const int64_t d = opts->d;
+    if (d < k || d > 8192) return fail(h, RSK_ERR_INVALID_ARG, "need k <= d <= 8192 (got d=%lld)", (long long)d);
+    if (opts->sketch_dtype != RSK_F64 && opts->sketch_dtype != RSK_F32 && opts->sketch_dtype != RSK_BF16)
+        return fail(h, RSK_ERR_INVALID_ARG, "bad sketch dtype");
+    if (opts->inner_dtype != RSK_F64 && opts->inner_dtype != RSK_F32)
+        return fail(h, RSK_ERR_INVALID_ARG, "inner dtype must be F64 or F32");
+    if (info) memset(info, 0, sizeof(*info));
+    const int K = int(k);
+    const int nparts = std::max(1, std::min<int>(int((n + 255) / 256), 2 * h->num_sms));
+
+    // ---- workspace
+    const bool need_sk_copy = opts->sketch_dtype != a_dtype;
+    const bool need_in_copy = opts->inner_dtype == RSK_F32 && a_dtype == RSK_F64;
+    const size_t es_sk = dtype_size(opts->sketch_dtype);
+    size_t bytes = 0;
+    auto add = [&](size_t b_) { bytes += Carver::round(b_); };
+    add(size_t(d) * (K + 1) * 8);   // W
+    add(size_t(K) * 8 * 12);        // vectors
+    add(size_t(K) * K * 8);         // Rinv
+    add(size_t(nparts) * K * 8);    // parts
+    add(size_t(nparts) * 2 * 8);    // parts_s
+    add(64);                        // barrier
+    add(size_t(d) * K * 8);         // SA (f64 or f32)
+    add(size_t(d) * 8);             // Sb
+    if (need_sk_copy) add(size_t(n) * K * es_sk);
+    if (need_in_copy) add(size_t(n) * K * 4);
+    add(size_t(K) * 8);             // yv
+    add(64);                        // CG state
+    const size_t sk_part = std::max(sketch_partial_bytes(h, n, k, d, opts->zeta, opts->sketch_dtype),
+                                    sketch_partial_bytes(h, n, 1, d, opts->zeta, RSK_F64));
+    add(sk_part);
+    rsk_status st = ensure_workspace(h, bytes + 4096, stream);
+    if (st != RSK_OK) return st;
+    Carver cv(h->ws);
+    LsqWork w;
+    w.W = cv.take<double>(size_t(d) * (K + 1));
+    double* vecs = cv.take<double>(size_t(K) * 12);
+    w.tau = vecs;
+    w.x = vecs + K;
+    w.g = vecs + 2 * K;
+    w.c = vecs + 3 * K;
+    w.z = vecs + 4 * K;
+    w.res = vecs + 5 * K;
+    w.p = vecs + 6 * K;
+    w.s = vecs + 7 * K;
+    w.t = vecs + 8 * K;
+    w.stats = vecs + 9 * K;       // [0] rr, [1] ff (K >= 2 is not required: 12*K >= 12 slots)
+    w.Rinv = cv.take<double>(size_t(K) * K);
+    w.parts = cv.take<double>(size_t(nparts) * K);
+    w.parts_s = cv.take<double>(size_t(nparts) * 2);
+    w.bar = cv.take<unsigned int>(16);
+    w.SA64 = cv.take<double>(size_t(d) * K);
+    w.SA32 = reinterpret_cast<float*>(w.SA64);
+    w.Sb = cv.take<double>(size_t(d));
+    void* Ask = need_sk_copy ? cv.take<char>(size_t(n) * K * es_sk) : nullptr;
+    void* Ain = need_in_copy ? cv.take<char>(size_t(n) * K * 4) : nullptr;
+    w.yv = cv.take<double>(size_t(K));
+    double* cgstate = cv.take<double>(8);
+    void* skpart = cv.take<char>(sk_part);
+    RSK_CUDA_TRY(h, cudaMemsetAsync(w.bar, 0, 64, stream));
+
+    // ---- L1: low-precision copies, sketch of [A | b]
+    const unsigned cg = unsigned((n * k + 255) / 256);
+    if (need_sk_copy) {
+        if (opts->sketch_dtype == RSK_F32) {
+            if (a_dtype == RSK_F64) k_convert<double, float><<<cg, 256, 0, stream>>>((const double*)A, n, K, lda, (float*)Ask);
+        } else if (opts->sketch_dtype == RSK_BF16) {
+            if (a_dtype == RSK_F64) k_convert<double, __nv_bfloat16><<<cg, 256, 0, stream>>>((const double*)A, n, K, lda, (__nv_bfloat16*)Ask);
+            else k_convert<float, __nv_bfloat16><<<cg, 256, 0, stream>>>((const float*)A, n, K, lda, (__nv_bfloat16*)Ask);
+        } else {
+            k_convert<float, double><<<cg, 256, 0, stream>>>((const float*)A, n, K, lda, (double*)Ask);
+        }
+        RSK_LAUNCH_CHECK(h);
+    }
+    if (need_in_copy) {
+        if (opts->sketch_dtype == RSK_F32 && need_sk_copy) Ain = Ask;
+        else {
+            k_convert<double, float><<<cg, 256, 0, stream>>>((const double*)A, n, K, lda, (float*)Ain);
+            RSK_LAUNCH_CHECK(h);
+        }
+    }
+    const void* A_sk = need_sk_copy ? Ask : A;
+    const int64_t lda_sk = need_sk_copy ? k : lda;
+    rsk_sketch_plan* plan = nullptr;
+    st = rsk_sparse_sign_plan_create(h, n, d, opts->zeta, opts->seed, &plan, stream);
+    if (st != RSK_OK) return st;
+    const rsk_dtype sa_dt = opts->sketch_dtype == RSK_F64 ? RSK_F64 : RSK_F32;
+    st = sketch_plan_apply_ws(h, plan, A_sk, opts->sketch_dtype, k, lda_sk, w.SA64, sa_dt, k, skpart, stream);
+    if (st == RSK_OK) st = sketch_plan_apply_ws(h, plan, b, RSK_F64, 1, 1, w.Sb, RSK_F64, 1, skpart, stream);
+    rsk_sparse_sign_plan_destroy(h, plan, stream);
+    if (st != RSK_OK) return st;
+
+    // ---- L2: QR of W = [SA | Sb]
+    const unsigned gw = unsigned((int64_t(d) * (K + 1) + 255) / 256);
+    if (sa_dt == RSK_F64) k_to_colmajor<double><<<gw, 256, 0, stream>>>(w.SA64, k, (const double*)w.Sb, int(d), K, w.W);
+    else k_to_colmajor<float><<<gw, 256, 0, stream>>>(w.SA32, k, (const double*)w.Sb, int(d), K, w.W);
+    RSK_LAUNCH_CHECK(h);
+    {
+        // cooperative launch: all CTAs of the persistent sweep are resident together
+        const int grid = std::min(h->num_sms, K + 1);
+        int dd = int(d);
+        double* Wp = w.W;
+        double* taup = w.tau;
+        unsigned int* barp = w.bar;
+        unsigned int* stp = h->dev_status;
+        void* args[] = {&Wp, &dd, const_cast<int*>(&K), &taup, &barp, &stp};
+        const int pr = prof_begin(h, stream, RSK_KERNEL_DENSE);
+        RSK_CUDA_TRY(h, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_qr), dim3(grid), dim3(256), args, 0, stream));
+        prof_end(h, stream, pr);
+    }
+    k_rinv<<<unsigned((K * 32 + 255) / 256), 256, 0, stream>>>(w.W, int(d), K, w.Rinv);
+    RSK_LAUNCH_CHECK(h);
+    // ---- L3: x0 = R^{-1} (Q^T Sb)[0:k]
+    const unsigned gv = unsigned((K * 32 + 255) / 256);
+    k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 0, w.W + size_t(K) * d, w.x);
+    RSK_LAUNCH_CHECK(h);
+
+    // ---- L4: refinement
+    const double tol = opts->tol_backward > 0 ? opts->tol_backward : 1e-10;
+    const int max_refine = opts->max_refine > 0 ? opts->max_refine : 20;
+    const int max_inner = opts->max_inner_iters > 0 ? opts->max_inner_iters : 50;
+    const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
+    double eta = 1.0, rnorm = 0.0, frob = 0.0;
+    int inner_total = 0, steps = 0;
+    for (steps = 0;; ++steps) {
+        // g = A^T (b - A x) in FP64; rr = ||r||^2; ff = ||A||_F^2 on the first pass
+        if (a_dtype == RSK_F64)
+            st = launch_pass<double, double>(h, (const double*)A, n, K, lda, w.x, b, (double*)w.parts, w.parts_s,
+                                             nparts, true, steps == 0, stream);
+        else
+            st = launch_pass<float, double>(h, (const float*)A, n, K, lda, w.x, b, (double*)w.parts, w.parts_s,
+                                            nparts, true, steps == 0, stream);
+        if (st != RSK_OK) return st;
+        k_reduce_parts<double><<<unsigned((K + 255) / 256), 256, 0, stream>>>((const double*)w.parts, nparts, K, w.g,
+                                                                             w.parts_s, w.stats);
+        RSK_LAUNCH_CHECK(h);
+        double host[2];
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(host, w.stats, 16, cudaMemcpyDeviceToHost, stream));
+        std::vector<double> gh(K);
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(gh.data(), w.g, size_t(K) * 8, cudaMemcpyDeviceToHost, stream));
+        RSK_CUDA_TRY(h, cudaStreamSynchronize(stream));
+        if (steps == 0) frob = sqrt(host[1]);
+        rnorm = sqrt(host[0]);
+        double gn = 0.0;
+        for (double v : gh) gn += v * v;
+        gn = sqrt(gn);
+        eta = (rnorm > 0.0 && frob > 0.0) ? gn / (frob * rnorm) : 0.0;
+        if (eta <= tol || steps >= max_refine) break;
+        // c = R^{-T} g; CG on (M^T M) z = c with M = A R^{-1}
+        k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 1, w.g, w.c);
+        k_cg_init<<<1, 256, 0, stream>>>(w.c, w.z, w.res, w.p, K, cgstate);
+        RSK_LAUNCH_CHECK(h);
+        for (int it = 0; it < max_inner; ++it) {
+            k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 0, w.p, w.t);   // t = R^{-1} p
+            if (opts->inner_dtype == RSK_F32) {
+                k_cast_vec<float><<<unsigned((K + 255) / 256), 256, 0, stream>>>(w.t, (float*)w.yv, K, cgstate);
+                st = launch_pass<float, float>(h, (const float*)(a_dtype == RSK_F32 ? A : Ain), n, K,
+                                               a_dtype == RSK_F32 ? lda : k, (const float*)w.yv, nullptr,
+                                               (float*)w.parts, nullptr, nparts, false, false, stream);
+                if (st != RSK_OK) return st;
+                k_reduce_parts<float><<<unsigned((K + 255) / 256), 256, 0, stream>>>((const float*)w.parts, nparts, K,
+                                                                                    w.g, nullptr, nullptr);
+            } else {
+                if (a_dtype == RSK_F64)
+                    st = launch_pass<double, double>(h, (const double*)A, n, K, lda, w.t, nullptr, (double*)w.parts,
+                                                     nullptr, nparts, false, false, stream);
+                else
+                    st = launch_pass<float, double>(h, (const float*)A, n, K, lda, w.t, nullptr, (double*)w.parts,
+                                                    nullptr, nparts, false, false, stream);
+                if (st != RSK_OK) return st;
+                k_reduce_parts<double><<<unsigned((K + 255) / 256), 256, 0, stream>>>((const double*)w.parts, nparts,
+                                                                                     K, w.g, nullptr, nullptr);
+            }
+            k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 1, w.g, w.s);  // s = R^{-T} A^T A R^{-1} p
+            k_cg_step<<<1, 256, 0, stream>>>(w.s, w.z, w.res, w.p, K, cgstate, inner_tol);
+            RSK_LAUNCH_CHECK(h);
+        }
+        double cgs[4];
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(cgs, cgstate, 32, cudaMemcpyDeviceToHost, stream));
+        // x += R^{-1} z
+        k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 0, w.z, w.t);
+        k_axpy<<<unsigned((K + 255) / 256), 256, 0, stream>>>(w.x, w.t, K);
+        RSK_LAUNCH_CHECK(h);
+        RSK_CUDA_TRY(h, cudaStreamSynchronize(stream));
+        inner_total += int(cgs[3]);
+    }
+    RSK_CUDA_TRY(h, cudaMemcpyAsync(x, w.x, size_t(K) * 8, cudaMemcpyDeviceToDevice, stream));
+    RSK_CUDA_TRY(h, cudaStreamSynchronize(stream));
+    if (info) {
+        info->backward_err = eta;
+        info->residual_norm = rnorm;
+        info->frobenius_norm = frob;
+        info->refine_steps = steps;
+        info->inner_iters = inner_total;
+        info->status = eta <= tol ? RSK_OK : RSK_ERR_NOT_CONVERGED;
+    }
+    rsk_status dev = rsk_sync_status(h, stream);
+    if (dev != RSK_OK) return dev;
+    if (eta > tol) return fail(h, RSK_ERR_NOT_CONVERGED, "backward error %.3e above tolerance %.1e after %d steps", eta,
+                               tol, steps);
+    return RSK_OK;
+}

@@ -109,7 +109,7 @@ __host__ __device__ inline IndexLayout index_layout(int d, int zeta, int count_w
     L.tgt_off = 0;
     L.neg_off = align16(L.tgt_off + size_t(C) * zeta * 2);
     L.cnt_off = align16(L.neg_off + size_t(C) * 4);
-    L.out_off = align16(L.cnt_off + size_t(count_warps) * d * 2);
+    L.out_off = align16(L.cnt_off + size_t(count_warps) * d * 4);
     L.scan_off = align16(L.out_off + size_t(C) * zeta * 2);
     L.total = align16(L.scan_off + 2 * 32 * 4);
     return L;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     const IndexLayout L = index_layout(d, zeta, count_warps);
     uint16_t* tgt = reinterpret_cast<uint16_t*>(sm + L.tgt_off);
     uint32_t* neg = reinterpret_cast<uint32_t*>(sm + L.neg_off);
-    uint16_t* cnt = reinterpret_cast<uint16_t*>(sm + L.cnt_off);
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(sm + L.cnt_off);
     uint16_t* out = reinterpret_cast<uint16_t*>(sm + L.out_off);
     int* wsum = reinterpret_cast<int*>(sm + L.scan_off);
 
@@ -158,20 +158,14 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     for (int i = tid; i < count_warps * d; i += kIndexThreads) cnt[i] = 0;
     __syncthreads();
 
-    // 2. per-warp counts over a contiguous range of columns (deterministic: leaders are unique)
+    // 2. per-warp counts over a contiguous range of columns (shared-memory atomics; the counts do
+    //    not depend on the order of the increments)
     const int per_w = (rows + count_warps - 1) / count_warps;
     const int r0 = min(rows, warp * per_w), r1 = min(rows, r0 + per_w);
     const int f0 = r0 * zeta, f1 = r1 * zeta;
     if (warp < count_warps) {
-        uint16_t* mine = cnt + size_t(warp) * d;
-        for (int base = f0; base < f1; base += 32) {
-            const int f = base + lane;
-            const bool ok = f < f1;
-            const int t = ok ? int(tgt[f]) : (65536 + lane);
-            const unsigned peers = __match_any_sync(0xffffffffu, t);
-            if (ok && lane == __ffs(peers) - 1) mine[t] = uint16_t(mine[t] + __popc(peers));
-            __syncwarp();
-        }
+        unsigned int* mine = cnt + size_t(warp) * d;
+        for (int f = f0 + lane; f < f1; f += 32) atomicAdd(&mine[tgt[f]], 1u);
     }
     __syncthreads();
 
@@ -185,7 +179,7 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
         const int i = base + lane;
         int tot = 0;
         if (i < t1)
-            for (int w = 0; w < count_warps; ++w) tot += cnt[size_t(w) * d + i];
+            for (int w = 0; w < count_warps; ++w) tot += int(cnt[size_t(w) * d + i]);
         int incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -210,7 +204,7 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
         const int i = base + lane;
         int tot = 0;
         if (i < t1)
-            for (int w = 0; w < count_warps; ++w) tot += cnt[size_t(w) * d + i];
+            for (int w = 0; w < count_warps; ++w) tot += int(cnt[size_t(w) * d + i]);
         int incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -221,8 +215,8 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
             int run = carry + incl - tot;
             off_out[i] = uint16_t(run);
             for (int w = 0; w < count_warps; ++w) {
-                const int c = cnt[size_t(w) * d + i];
-                cnt[size_t(w) * d + i] = uint16_t(run);
+                const int c = int(cnt[size_t(w) * d + i]);
+                cnt[size_t(w) * d + i] = unsigned(run);
                 run += c;
             }
         }
@@ -231,9 +225,11 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     for (int i = d + tid; i < pitch; i += kIndexThreads) off_out[i] = uint16_t(nent);
     __syncthreads();
 
-    // 4. stable scatter: same traversal order as the count
+    // 4. stable scatter: each warp walks its columns in order, 32 entries per round.  A round whose
+    //    sketch rows are all distinct (the common case) needs no intra-round rank; otherwise the
+    //    lanes that share a row are ranked with __match_any_sync.
     if (warp < count_warps) {
-        uint16_t* cur = cnt + size_t(warp) * d;
+        unsigned int* cur = cnt + size_t(warp) * d;
         const unsigned lt = (1u << lane) - 1u;
         for (int base = f0; base < f1; base += 32) {
             const int f = base + lane;
@@ -245,7 +241,7 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
                 out[cur[t] + __popc(peers & lt)] = uint16_t(r | (((neg[r] >> q) & 1u) << 15));
             }
             __syncwarp();
-            if (ok && lane == __ffs(peers) - 1) cur[t] = uint16_t(cur[t] + __popc(peers));
+            if (ok && lane == __ffs(peers) - 1) cur[t] += __popc(peers);
             __syncwarp();
         }
     }
@@ -434,10 +430,12 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
 
     for (int ch = c0, it = 0; ch < c1; ++ch, ++it) {
         const uint8_t* buf;
+        bool ok = true;
         if constexpr (TMA) {
             const int st = it & 1;
-            const bool ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
-            if (__syncthreads_or(!ok)) break;
+            // every thread waits on the stage's barrier itself (that is what makes the TMA writes
+            // visible to it); a timeout skips the chunk and ends the loop at the barrier below
+            ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
             buf = st ? stage1 : stage0;
         } else {
             // A not TMA-compatible: plain loads into the single stage.
@@ -463,28 +461,32 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
             __syncthreads();
             buf = stage0;
         }
-        const uint16_t* es = reinterpret_cast<const uint16_t*>(buf + SL.a_bytes);
-        const uint16_t* os = reinterpret_cast<const uint16_t*>(buf + SL.a_bytes + SL.e_bytes);
-        const uint8_t* lane_base = buf + l8 * 16;
-        int o[SLOTS + 1];
-        load_offsets<SLOTS>(os + g * SLOTS, o);
+        if (ok) {
+            const uint16_t* es = reinterpret_cast<const uint16_t*>(buf + SL.a_bytes);
+            const uint16_t* os = reinterpret_cast<const uint16_t*>(buf + SL.a_bytes + SL.e_bytes);
+            const uint8_t* lane_base = buf + l8 * 16;
+            int o[SLOTS + 1];
+            load_offsets<SLOTS>(os + g * SLOTS, o);
 #pragma unroll
-        for (int q = 0; q < SLOTS; ++q) {
-            if (first + q < a.d) {
-                const int end = o[q + 1];
-                for (int e = o[q]; e < end; e += 2) {
-                    const uint32_t v0 = es[e];
-                    const uint32_t v1 = es[e + 1];
-                    const bool two = e + 1 < end;
-                    const uint4 x0 = *reinterpret_cast<const uint4*>(lane_base + (v0 & 0x7fffu) * kRowBytes);
-                    uint4 x1 = make_uint4(0u, 0u, 0u, 0u);
-                    if (two) x1 = *reinterpret_cast<const uint4*>(lane_base + (v1 & 0x7fffu) * kRowBytes);
-                    acc[q].add(x0, v0 >> 15);
-                    if (two) acc[q].add(x1, v1 >> 15);
+            for (int q = 0; q < SLOTS; ++q) {
+                if (first + q < a.d) {
+                    const int end = o[q + 1];
+                    for (int e = o[q]; e < end; e += 4) {
+                        uint32_t v[4];
+                        uint4 x[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[u] = es[e + u];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (e + u < end) x[u] = *reinterpret_cast<const uint4*>(lane_base + (v[u] & 0x7fffu) * kRowBytes);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (e + u < end) acc[q].add(x[u], v[u] >> 15);
+                    }
                 }
             }
         }
-        __syncthreads();
+        if (__syncthreads_or(!ok)) break;
         if constexpr (TMA) {
             if (tid == 0 && ch + 2 < c1) {
                 rskd::fence_proxy_async();
@@ -697,6 +699,21 @@ struct rsk_sketch_plan {
     uint16_t* offs;
     uint16_t* ents;
 };
+
+namespace rsk {
+size_t sketch_partial_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int zeta, rsk_dtype a_dt) {
+    return plan_apply(h, n, k, int(d), zeta, a_dt).partial_bytes;
+}
+rsk_status sketch_plan_apply_ws(rsk_handle* h, const rsk_sketch_plan* plan, const void* A, rsk_dtype a_dt, int64_t k,
+                                int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa, void* partials,
+                                cudaStream_t stream) {
+    rsk_status st = check_apply_args(h, A, a_dt, k, lda, SA, sa_dt, ldsa);
+    if (st != RSK_OK) return st;
+    const ApplyPlan p = plan_apply(h, plan->n, k, int(plan->d), plan->zeta, a_dt);
+    return apply_with_index(h, plan->offs, plan->ents, A, a_dt, plan->n, k, lda, int(plan->d), plan->zeta, SA, sa_dt,
+                            ldsa, partials, p, stream);
+}
+}  // namespace rsk
 
 extern "C" {
 

@@ -103,6 +103,8 @@ __global__ void k_srtt_dbits(int64_t nwords, uint64_t seed, uint32_t* __restrict
 // The transform + gather kernel.
 // ------------------------------------------------------------------------------------------
 struct SrttArgs {
+    const void* A;          // used by the plain-load path
+    int64_t lda;
     int64_t n, k;
     int d, nblocks, nslices, nranges;
     const int32_t* prow;   // d selected rows
@@ -148,10 +150,10 @@ __device__ __forceinline__ void fwht32x2(float (&v)[64]) {
     }
 }
 
-template <typename T, int QPT>
+template <typename T, int QPT, bool TMA>
 __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CUtensorMap tmap, const SrttArgs a) {
     extern __shared__ __align__(128) uint8_t sm[];
-    constexpr int kStageBytes = kBlk * kCols * int(sizeof(T));
+    constexpr int kStageBytes = TMA ? kBlk * kCols * int(sizeof(T)) : 0;
     uint8_t* const stage0 = sm;
     uint8_t* const stage1 = sm + kStageBytes;
     float* Z = reinterpret_cast<float*>(sm + 2 * kStageBytes);
@@ -187,15 +189,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         for (int bx = 0; bx < nbox; ++bx)
             rskd::tma_load_2d(dst + bx * kBoxRows * kCols * sizeof(T), &tmap, s * kCols, int(row0 + bx * kBoxRows), bar);
     };
-    if (tid == 0) {
-        rskd::mbar_init(&bars[0], 1);
-        rskd::mbar_init(&bars[1], 1);
-        rskd::fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (b0 < b1) issue(b0, stage0, &bars[0]);
-        if (b0 + 1 < b1) issue(b0 + 1, stage1, &bars[1]);
+    if constexpr (TMA) {
+        if (tid == 0) {
+            rskd::mbar_init(&bars[0], 1);
+            rskd::mbar_init(&bars[1], 1);
+            rskd::fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (b0 < b1) issue(b0, stage0, &bars[0]);
+            if (b0 + 1 < b1) issue(b0 + 1, stage1, &bars[1]);
+        }
     }
 
     // pass-1 layout: column c1 = tid % 8, rows g1 + 32*x (x < 64), g1 = tid / 8
@@ -213,16 +217,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
             dwords[4 * tid + 2] = w.v[2];
             dwords[4 * tid + 3] = w.v[3];
         }
-        const bool ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
+        bool ok = true;
+        if constexpr (TMA) ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
         if (__syncthreads_or(!ok)) break;
         const T* raw = reinterpret_cast<const T*>(st ? stage1 : stage0);
+        const T* gA = static_cast<const T*>(a.A);
         const int64_t row0 = int64_t(blk) * kBlk;
+        const int64_t col = int64_t(s) * kCols + c1;
         float v[64];
-        // pass 1: load, zero-pad beyond n, sign flip, stages on row bits 5..10
+        // pass 1: load, zero-pad beyond n (and beyond k), sign flip, stages on row bits 5..10
 #pragma unroll
         for (int x = 0; x < 64; ++x) {
             const int row = g1 + 32 * x;
-            float f = (row0 + row < a.n) ? to_f<T>(raw[row * kCols + c1]) : 0.f;
+            float f;
+            if constexpr (TMA)
+                f = (row0 + row < a.n) ? to_f<T>(raw[row * kCols + c1]) : 0.f;
+            else
+                f = (row0 + row < a.n && col < a.k) ? to_f<T>(gA[(row0 + row) * a.lda + col]) : 0.f;
             const uint32_t neg = (dwords[row >> 5] >> (row & 31)) & 1u;
             v[x] = __uint_as_float(__float_as_uint(f) ^ (neg << 31));
         }
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         for (int x = 0; x < 64; ++x) Z[zoff(g1 + 32 * x) + c1] = v[x];
         __syncthreads();
         // stage buffer is free: refill it while the block is finished
-        if (tid == 0 && blk + 2 < b1) {
+        if (TMA && tid == 0 && blk + 2 < b1) {
             rskd::fence_proxy_async();
             issue(blk + 2, st ? stage1 : stage0, &bars[st]);
         }
@@ -315,9 +326,9 @@ rsk_status launch_draw(rsk_handle* h, int64_t n, int d, uint64_t seed, int32_t* 
 }
 
 template <typename T, int QPT>
-rsk_status launch_srtt_t(rsk_handle* h, const CUtensorMap& map, const SrttArgs& args, cudaStream_t stream) {
-    auto kern = k_srtt<T, QPT>;
-    const int smem = 2 * kBlk * kCols * int(sizeof(T)) + kZFloats * 4 + (kBlk / 32) * 4 + 64;
+rsk_status launch_srtt_t(rsk_handle* h, const CUtensorMap& map, const SrttArgs& args, bool tma, cudaStream_t stream) {
+    auto kern = tma ? k_srtt<T, QPT, true> : k_srtt<T, QPT, false>;
+    const int smem = (tma ? 2 * kBlk * kCols * int(sizeof(T)) : 0) + kZFloats * 4 + (kBlk / 32) * 4 + 64;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SRTT_APPLY);
     kern<<<unsigned(args.nslices * args.nranges), kThreads, smem, stream>>>(map, args);
@@ -327,12 +338,12 @@ rsk_status launch_srtt_t(rsk_handle* h, const CUtensorMap& map, const SrttArgs& 
 }
 
 template <typename T>
-rsk_status launch_srtt(rsk_handle* h, const CUtensorMap& map, const SrttArgs& args, cudaStream_t stream) {
+rsk_status launch_srtt(rsk_handle* h, const CUtensorMap& map, const SrttArgs& args, bool tma, cudaStream_t stream) {
     const int qpt = (args.d + kThreads - 1) / kThreads;
-    if (qpt <= 1) return launch_srtt_t<T, 1>(h, map, args, stream);
-    if (qpt <= 2) return launch_srtt_t<T, 2>(h, map, args, stream);
-    if (qpt <= 4) return launch_srtt_t<T, 4>(h, map, args, stream);
-    if (qpt <= 8) return launch_srtt_t<T, 8>(h, map, args, stream);
+    if (qpt <= 1) return launch_srtt_t<T, 1>(h, map, args, tma, stream);
+    if (qpt <= 2) return launch_srtt_t<T, 2>(h, map, args, tma, stream);
+    if (qpt <= 4) return launch_srtt_t<T, 4>(h, map, args, tma, stream);
+    if (qpt <= 8) return launch_srtt_t<T, 8>(h, map, args, tma, stream);
     return rsk::fail(h, RSK_ERR_UNSUPPORTED, "SRTT apply supports d <= %d", 8 * kThreads);
 }
 
@@ -368,10 +379,11 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     if (y_dtype != RSK_F32 && y_dtype != RSK_F64) return rsk::fail(h, RSK_ERR_INVALID_ARG, "Y dtype must be F32 or F64");
     if (k < 1 || lda < k || ldy < k) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need k >= 1, lda >= k, ldy >= k");
     const size_t es = rsk::dtype_size(a_dtype);
-    if (reinterpret_cast<uintptr_t>(A) % 16 || (lda * int64_t(es)) % 16)
-        return rsk::fail(h, RSK_ERR_UNSUPPORTED, "SRTT apply needs a 16-byte aligned A and row pitch");
+    bool tma = reinterpret_cast<uintptr_t>(A) % 16 == 0 && (lda * int64_t(es)) % 16 == 0;
 
     SrttArgs args;
+    args.A = A;
+    args.lda = lda;
     args.n = n;
     args.k = k;
     args.d = int(d);
@@ -395,9 +407,9 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     const CUtensorMapDataType tdt = a_dtype == RSK_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    if (!rsk::encode_2d(h, &map, tdt, A, uint64_t(k), uint64_t(n), uint64_t(lda) * es, kCols, kBoxRows))
-        return rsk::fail(h, RSK_ERR_CUDA, "TMA descriptor encoding failed");
-    st = a_dtype == RSK_F32 ? launch_srtt<float>(h, map, args, stream) : launch_srtt<__nv_bfloat16>(h, map, args, stream);
+    if (tma) tma = rsk::encode_2d(h, &map, tdt, A, uint64_t(k), uint64_t(n), uint64_t(lda) * es, kCols, kBoxRows);
+    st = a_dtype == RSK_F32 ? launch_srtt<float>(h, map, args, tma, stream)
+                            : launch_srtt<__nv_bfloat16>(h, map, args, tma, stream);
     if (st != RSK_OK) return st;
 
     const int64_t total = d * k;

@@ -1,0 +1,95 @@
+"""GPU parity of sketch-and-precondition least squares (rows a5-a7) against the oracle.
+
+The backward error of every returned x is recomputed by the oracle's own FP64 code
+(oracle.lsq.backward_error) and must be <= 1e-10.  The warm start x0 (max_refine = 0) is compared
+with the oracle's sketch-and-solve x0 built from the bit-identical sketch.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lsq as olsq
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsk():
+    import paper_2508_21189_gb300 as m
+    return m
+
+
+def solve(rsk, A, b, d, **kw):
+    return rsk.rsk_lstsq_sketch_precond(A, b, d, **kw)
+
+
+@pytest.mark.parametrize("sketch,inner", [(torch.float64, torch.float64), (torch.float32, torch.float64)])
+def test_ill_conditioned_fp64_truth(rsk, sketch, inner):
+    # A = Q_U diag(logspace(0, -8)) V^T, b = A x* + 1e-6 noise: the least-squares workload shape
+    A, b, _ = synthetic.lsq_problem(40000, 60, seed=3, cond_exp=8.0, device="cpu")
+    Ad, bd = A.cuda(), b.cuda()
+    x, info = solve(rsk, Ad, bd, 240, sketch_dtype=sketch, inner_dtype=inner)
+    eta = olsq.backward_error(A.numpy(), b.numpy(), x.cpu().numpy())
+    assert eta <= 1e-10, (eta, info)
+    assert abs(eta - info["backward_err"]) <= 0.05 * eta + 1e-13
+    xs = olsq.exact(A.numpy(), b.numpy())
+    rn = np.linalg.norm(b.numpy() - A.numpy() @ x.cpu().numpy())
+    rs = np.linalg.norm(b.numpy() - A.numpy() @ xs)
+    assert abs(rn - rs) <= 1e-8 * rs
+
+
+def test_column_scaled_fp32_storage_mixed(rsk):
+    # batched-workload shape: Gaussian A with column scales logspace(-6, 0), FP32 storage, Gaussian b
+    A, b = synthetic.batched_problem(30000, 64, seed=5, device="cpu", dtype=torch.float32)
+    x, info = solve(rsk, A.cuda(), b.cuda(), 256, sketch_dtype=torch.float32, inner_dtype=torch.float32)
+    eta = olsq.backward_error(A.double().numpy(), b.numpy(), x.cpu().numpy())
+    assert eta <= 1e-10, (eta, info)
+
+
+def test_bf16_sketch_fp32_inner_well_conditioned(rsk):
+    A, b = synthetic.batched_problem(20000, 40, seed=6, lo_exp=-2.0, device="cpu", dtype=torch.float32)
+    x, info = solve(rsk, A.cuda(), b.cuda(), 160, sketch_dtype=torch.bfloat16, inner_dtype=torch.float32)
+    eta = olsq.backward_error(A.double().numpy(), b.numpy(), x.cpu().numpy())
+    assert eta <= 1e-10, (eta, info)
+
+
+def test_warm_start_matches_oracle(rsk):
+    A, b, _ = synthetic.lsq_problem(8000, 20, seed=8, cond_exp=3.0, device="cpu")
+    x0, info = solve(rsk, A.cuda(), b.cuda(), 80, zeta=8, seed=11, sketch_dtype=torch.float64,
+                     inner_dtype=torch.float64, max_refine=0, tol=1e-300, raise_on_nonconvergence=False)
+    assert info["status"] == "RSK_ERR_NOT_CONVERGED" and info["refine_steps"] == 0
+    _, oinfo = olsq.sketch_precond(A.numpy(), b.numpy(), 80, 8, 11, max_refine=0)
+    ref = oinfo["x0"]
+    assert np.allclose(x0.cpu().numpy(), ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+def test_k1_and_orthonormal(rsk):
+    g = torch.Generator().manual_seed(0)
+    a = torch.randn(5000, 1, generator=g, dtype=torch.float64)
+    bb = torch.randn(5000, generator=g, dtype=torch.float64)
+    x, _ = solve(rsk, a.cuda(), bb.cuda(), 8, zeta=4, sketch_dtype=torch.float64, inner_dtype=torch.float64)
+    ref = float(a[:, 0] @ bb / (a[:, 0] @ a[:, 0]))
+    assert abs(x.item() - ref) <= 1e-12 * abs(ref)
+    Q, _ = torch.linalg.qr(torch.randn(6000, 30, generator=g, dtype=torch.float64))
+    b2 = torch.randn(6000, generator=g, dtype=torch.float64)
+    x, _ = solve(rsk, Q.cuda(), b2.cuda(), 120, sketch_dtype=torch.float64, inner_dtype=torch.float64)
+    assert torch.allclose(x.cpu(), Q.T @ b2, rtol=0, atol=1e-11)
+
+
+def test_not_converged_reports(rsk):
+    A, b, _ = synthetic.lsq_problem(5000, 10, seed=2, cond_exp=8.0, device="cpu")
+    x, info = solve(rsk, A.cuda(), b.cuda(), 40, max_refine=1, max_inner=1, tol=1e-15,
+                    sketch_dtype=torch.float64, inner_dtype=torch.float64, raise_on_nonconvergence=False)
+    assert info["status"] == "RSK_ERR_NOT_CONVERGED" and info["refine_steps"] == 1
+    with pytest.raises(rsk.RskError) as e:
+        solve(rsk, A.cuda(), b.cuda(), 40, max_refine=1, max_inner=1, tol=1e-15,
+              sketch_dtype=torch.float64, inner_dtype=torch.float64)
+    assert e.value.status == 4
+
+
+def test_invalid(rsk):
+    A = torch.zeros(100, 10, dtype=torch.float64, device="cuda")
+    b = torch.zeros(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(rsk.RskError):
+        solve(rsk, A, b, 5)          # d < k

@@ -57,7 +57,7 @@ def test_apply_parity(rsk, dtype, n, k, d):
 
 
 def test_orthogonal_when_not_subsampled(rsk):
-    n, k = 4096, 16
+    n, k = 2048, 16
     A = synthetic.gaussian(n, k, seed=3, device="cuda", dtype=torch.float32)
     Y = rsk.rsk_srtt_apply(A, n, 11, out_dtype=torch.float64).cpu().numpy()
     A64 = A.double().cpu().numpy()
