@@ -181,7 +181,7 @@ typedef struct {
     rsk_dtype sketch_dtype;  /* precision A is sketched in: F64, F32 or BF16 (FP32 accumulation) */
     rsk_dtype inner_dtype;   /* precision of the CG operator: F64 or F32 */
     double tol_backward;     /* target eta (default 1e-10 when <= 0) */
-    int32_t max_refine;      /* refinement steps (default 20 when <= 0) */
+    int32_t max_refine;      /* refinement steps; 0 returns the warm start x0; < 0 selects 20 */
     int32_t max_inner_iters; /* CG iterations per step (default 50 when <= 0) */
     double inner_tol;        /* relative CG residual reduction per step (default 1e-6 when <= 0) */
 } rsk_lsq_opts;

@@ -543,7 +543,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
 
     // ---- L4: refinement
     const double tol = opts->tol_backward > 0 ? opts->tol_backward : 1e-10;
-    const int max_refine = opts->max_refine > 0 ? opts->max_refine : 20;
+    const int max_refine = opts->max_refine >= 0 ? opts->max_refine : 20;
     const int max_inner = opts->max_inner_iters > 0 ? opts->max_inner_iters : 50;
     const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
     double eta = 1.0, rnorm = 0.0, frob = 0.0;

@@ -32,7 +32,9 @@ def test_ill_conditioned_fp64_truth(rsk, sketch, inner):
     x, info = solve(rsk, Ad, bd, 240, sketch_dtype=sketch, inner_dtype=inner)
     eta = olsq.backward_error(A.numpy(), b.numpy(), x.cpu().numpy())
     assert eta <= 1e-10, (eta, info)
-    assert abs(eta - info["backward_err"]) <= 0.05 * eta + 1e-13
+    # the library's own estimate agrees with the oracle's to rounding noise in A^T r (about
+    # u_64 * sqrt(n) relative), which dominates once eta is near 1e-12
+    assert info["backward_err"] <= 1e-10 and abs(eta - info["backward_err"]) <= 0.05 * eta + 5e-12
     xs = olsq.exact(A.numpy(), b.numpy())
     rn = np.linalg.norm(b.numpy() - A.numpy() @ x.cpu().numpy())
     rs = np.linalg.norm(b.numpy() - A.numpy() @ xs)
@@ -71,7 +73,7 @@ def test_k1_and_orthonormal(rsk):
     x, _ = solve(rsk, a.cuda(), bb.cuda(), 8, zeta=4, sketch_dtype=torch.float64, inner_dtype=torch.float64)
     ref = float(a[:, 0] @ bb / (a[:, 0] @ a[:, 0]))
     assert abs(x.item() - ref) <= 1e-12 * abs(ref)
-    Q, _ = torch.linalg.qr(torch.randn(6000, 30, generator=g, dtype=torch.float64))
+    Q = torch.linalg.qr(torch.randn(6000, 30, generator=g, dtype=torch.float64))[0].contiguous()
     b2 = torch.randn(6000, generator=g, dtype=torch.float64)
     x, _ = solve(rsk, Q.cuda(), b2.cuda(), 120, sketch_dtype=torch.float64, inner_dtype=torch.float64)
     assert torch.allclose(x.cpu(), Q.T @ b2, rtol=0, atol=1e-11)
