@@ -127,6 +127,20 @@ rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype
                                  int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
                                  rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
 
+/* The same SA = S * A for callers that cannot allocate device memory (code where cudaMalloc is
+ * unavailable or forbidden, e.g. inside a host application that owns every device buffer, or a
+ * path that must not allocate after start-up).  The paper has no counterpart: this is a deployment
+ * variant of rsk_sparse_sign_apply with the same arguments minus the handle, and bit-identical
+ * results.  Scratch comes from one fixed 32 MiB array in device memory that every GPU loading the
+ * library holds until exit; no call allocates or frees anything.  Sizes whose scratch (inverted
+ * index plus partial sums) exceeds 32 MiB return RSK_ERR_UNSUPPORTED before any launch.  The first
+ * call on each device looks up the array's device address (make it before any stream capture).
+ * All calls share the array: calls that overlap on the GPU race, and the set-up is not thread safe.
+ * Errors are reported by the status code only (no handle, no message). */
+rsk_status rsk_sparse_sign_apply_noalloc(const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                                         int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype,
+                                         int64_t ldsa, cudaStream_t stream);
+
 /* Plans keep the inverted index of one S for repeated application (e.g. to A and then to b).
  * The plan owns device memory allocated on `stream`; destroy it with rsk_sparse_sign_plan_destroy. */
 typedef struct rsk_sketch_plan rsk_sketch_plan;

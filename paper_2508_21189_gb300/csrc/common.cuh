@@ -75,6 +75,11 @@ rsk_status sketch_plan_apply_ws(rsk_handle* h, const rsk_sketch_plan* plan, cons
                                 int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa, void* partials,
                                 cudaStream_t stream);
 
+size_t sketch_scratch_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int zeta, rsk_dtype a_dt);
+rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda,
+                                int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
+                                void* scratch, cudaStream_t stream);
+
 }  // namespace rsk
 
 #define RSK_CUDA_TRY(h, call)                                                                  \

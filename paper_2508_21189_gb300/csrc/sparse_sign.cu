@@ -713,6 +713,29 @@ rsk_status sketch_plan_apply_ws(rsk_handle* h, const rsk_sketch_plan* plan, cons
     return apply_with_index(h, plan->offs, plan->ents, A, a_dt, plan->n, k, lda, int(plan->d), plan->zeta, SA, sa_dt,
                             ldsa, partials, p, stream);
 }
+// Scratch bytes of one sparse sign apply when the inverted index and the partials are carved from a
+// single caller-provided buffer, and the apply that uses such a buffer.
+size_t sketch_scratch_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int zeta, rsk_dtype a_dt) {
+    const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dt);
+    return Carver::round(offsets_count(n, int(d), zeta) * 2) + Carver::round(entries_count(n, zeta) * 2) +
+           Carver::round(p.partial_bytes) + 256;
+}
+rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda,
+                                int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
+                                void* scratch, cudaStream_t stream) {
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    st = check_apply_args(h, A, a_dt, k, lda, SA, sa_dt, ldsa);
+    if (st != RSK_OK) return st;
+    const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dt);
+    Carver cv(scratch);
+    uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
+    uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
+    void* partials = cv.take<char>(p.partial_bytes);
+    st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
+    if (st != RSK_OK) return st;
+    return apply_with_index(h, offs, ents, A, a_dt, n, k, lda, int(d), zeta, SA, sa_dt, ldsa, partials, p, stream);
+}
 }  // namespace rsk
 
 extern "C" {
