@@ -182,9 +182,10 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
  * as the standard high-accuracy method (remark closing Sec. 2.3) but not spelled out.  Steps:
  *   [Ahat | bhat] = S [A | b] (sparse sign, d rows, zeta per column, seed);
  *   Householder QR of Ahat in FP64 -> R and Q^T bhat;  x0 = R^{-1} Q^T bhat;
- *   refinement: g = A^T (b - A x) in FP64; eta = ||g|| / (||A||_F ||b - A x||); stop at
- *   eta <= tol_backward; else CG on (M^T M) z = R^{-T} g with M = A R^{-1} in inner_dtype, then
- *   x += R^{-1} z.
+ *   refinement: g = A^T (b - A x) in FP64; eta = min(||g|| / (||A||_F ||r||),
+ *   ||r|| / (||A||_F ||x|| + ||b||)) (LSQR's stopping quantities for least-squares and consistent
+ *   problems); stop at eta <= tol_backward; else CG on (M^T M) z = R^{-T} g with M = A R^{-1} in
+ *   inner_dtype, then x += R^{-1} z.
  * Precision notes: inner_dtype F32 converges when u_32 * kappa(A) is well below 1 or when A's
  * ill-conditioning is a column scaling; for kappa(A) ~ 1e8 with mixed columns use F64.
  * ------------------------------------------------------------------------------------------- */
@@ -216,6 +217,28 @@ typedef struct {
 rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
                                     int64_t lda, const double* b, double* x, const rsk_lsq_opts* opts,
                                     rsk_lsq_info* info, cudaStream_t stream);
+
+/* One problem of a batch (row a8): A device n x k row-major (lda >= k), F64 or F32, k <= 256;
+ * b device FP64[n]; x device FP64[k] (output); d sketch rows (0 selects 4k). */
+typedef struct {
+    const void* A;
+    rsk_dtype a_dtype;
+    int64_t n, k, lda, d;
+    const double* b;
+    double* x;
+} rsk_lsq_problem;
+
+/* a8: solve `count` independent problems together.  Problem i is sketched with seed opts->seed + i
+ * (opts->d is ignored; each problem carries its own d) and refined exactly as in
+ * rsk_lstsq_sketch_precond; opts->sketch_dtype must be F64 or F32.  The fused passes of all
+ * problems run in one persistent launch over (problem, 2048-row block) tiles taken from a work
+ * queue; per-problem results are reduced in tile order (deterministic).  One CG iteration is a
+ * captured CUDA graph.  With inner_dtype F32 and FP32 storage, the FP64-accuracy residual passes
+ * use double-float (FP32 pair) arithmetic.  probs and infos are host arrays of `count` entries;
+ * synchronous; RSK_ERR_NOT_CONVERGED if any problem stays above tol_backward (infos[i].status says
+ * which). */
+rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const rsk_lsq_problem* probs,
+                                            const rsk_lsq_opts* opts, rsk_lsq_info* infos, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

@@ -11,7 +11,11 @@ after Cor. 2.x, Sec. 2.3) without spelling it out.  The steps used here:
       full column rank for an embedding).
   L4  refinement: r = b - A x; stop when eta(x) <= tol; otherwise run LSQR (Paige &
       Saunders, ACM TOMS 1982) on min ||A R^{-1} z - r|| from z = 0 and set x += R^{-1} z.
-  L5  eta(x) = ||A^T r||_2 / (||A||_F ||r||_2), r = b - A x, all in FP64.
+  L5  eta(x) = min( ||A^T r||_2 / (||A||_F ||r||_2),  ||r||_2 / (||A||_F ||x||_2 + ||b||_2) ),
+      r = b - A x, all in FP64: the two quantities of Paige & Saunders' LSQR stopping rules (S2 for
+      least-squares problems, S1 for consistent ones).  For an inconsistent problem the first term
+      governs; for a (nearly) consistent one r is rounding noise, the first term is a quotient of
+      rounding errors and the second, the normwise backward error of A x = b, is the meaningful one.
 
 The oracle runs every step in FP64.
 TEST INFRASTRUCTURE: part of the oracle; see oracle/__init__.py.
@@ -23,13 +27,18 @@ from . import sparse_sign
 
 
 def backward_error(A, b, x):
-    """eta(x) = ||A^T (b - A x)|| / (||A||_F ||b - A x||) in FP64 (L5)."""
+    """eta(x) = min(||A^T r|| / (||A||_F ||r||), ||r|| / (||A||_F ||x|| + ||b||)), r = b - A x (L5)."""
     A = np.asarray(A, dtype=np.float64)
-    r = np.asarray(b, dtype=np.float64) - A @ np.asarray(x, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    r = b - A @ x
+    fa = np.linalg.norm(A)
     nr = np.linalg.norm(r)
     if nr == 0.0:
         return 0.0
-    return float(np.linalg.norm(A.T @ r) / (np.linalg.norm(A) * nr))
+    ls = np.linalg.norm(A.T @ r) / (fa * nr)
+    cons = nr / (fa * np.linalg.norm(x) + np.linalg.norm(b))
+    return float(min(ls, cons))
 
 
 def exact(A, b):

@@ -8,7 +8,7 @@ import ctypes
 
 import torch
 
-from ._lib import LsqInfo, LsqOpts, RskError, STATUS, load
+from ._lib import LsqInfo, LsqOpts, LsqProblem, RskError, STATUS, load
 
 RSK_F64, RSK_F32, RSK_BF16 = 0, 1, 2
 _DT = {torch.float64: RSK_F64, torch.float32: RSK_F32, torch.bfloat16: RSK_BF16}
@@ -197,6 +197,34 @@ def rsk_lstsq_sketch_precond(A, b, d, zeta=8, seed=0, sketch_dtype=torch.bfloat1
         return x, out
     _check(st, h)
     return x, out
+
+
+def rsk_lstsq_sketch_precond_batched(As, bs, ds=None, zeta=8, seed=0, sketch_dtype=torch.float32,
+                                     inner_dtype=torch.float32, tol=1e-10, max_refine=20, max_inner=50,
+                                     inner_tol=1e-6, xs=None, stream=None, raise_on_nonconvergence=True):
+    """Batched sketch-and-precondition: lists of CUDA A_i (n_i x k_i) and b_i (FP64); returns
+    (list of x_i, list of info dicts).  Problem i uses seed + i and d_i = ds[i] (default 4 k_i)."""
+    count = len(As)
+    if xs is None:
+        xs = [torch.empty(A.shape[1], dtype=torch.float64, device=A.device) for A in As]
+    arr = (LsqProblem * count)()
+    for i, (A, b, x) in enumerate(zip(As, bs, xs)):
+        _matrix(A, "A")
+        if b.dtype != torch.float64 or not b.is_contiguous() or b.numel() != A.shape[0]:
+            raise ValueError("each b must be a contiguous float64 vector of length n")
+        d = 0 if ds is None else int(ds[i])
+        arr[i] = LsqProblem(A.data_ptr(), _dt(A), A.shape[0], A.shape[1], A.stride(0), d, b.data_ptr(), x.data_ptr())
+    opts = LsqOpts(0, zeta, seed, _DT[sketch_dtype], _DT[inner_dtype], tol, max_refine, max_inner, inner_tol)
+    infos = (LsqInfo * count)()
+    h = handle(As[0].device)
+    st = load().rsk_lstsq_sketch_precond_batched(h, count, arr, ctypes.byref(opts), infos, _stream(stream))
+    out = [{"backward_err": f.backward_err, "residual_norm": f.residual_norm, "frobenius_norm": f.frobenius_norm,
+            "refine_steps": f.refine_steps, "inner_iters": f.inner_iters, "status": STATUS.get(f.status, f.status)}
+           for f in infos]
+    if st == 4 and not raise_on_nonconvergence:
+        return xs, out
+    _check(st, h)
+    return xs, out
 
 
 # Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).

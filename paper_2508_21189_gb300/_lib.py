@@ -35,7 +35,14 @@ SIGNATURES = {
     "rsk_srtt_draw": [c_p, c_i64, c_i64, c_u64, c_p, c_p, c_p],
     "rsk_srtt_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_lstsq_sketch_precond": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p],
+    "rsk_lstsq_sketch_precond_batched": [c_p, c_i32, c_p, c_p, c_p, c_p],
 }
+
+
+class LsqProblem(ctypes.Structure):
+    """rsk_lsq_problem (rsk.h)."""
+    _fields_ = [("A", ctypes.c_void_p), ("a_dtype", ctypes.c_int32), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("d", ctypes.c_int64), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p)]
 
 
 class LsqOpts(ctypes.Structure):

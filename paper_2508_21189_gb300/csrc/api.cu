@@ -42,6 +42,16 @@ rsk_status ensure_workspace(rsk_handle* h, size_t bytes, cudaStream_t stream) {
     return RSK_OK;
 }
 
+rsk_status ensure_streams(rsk_handle* h, int count) {
+    while (int(h->streams.size()) < count) {
+        cudaStream_t s = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail(h, RSK_ERR_CUDA, "cudaStreamCreateWithFlags: %s", cudaGetErrorString(e));
+        h->streams.push_back(s);
+    }
+    return RSK_OK;
+}
+
 bool encode_2d(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
                uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner, uint32_t box_outer) {
     if (!h->encode_tiled) return false;
@@ -155,6 +165,7 @@ rsk_status rsk_destroy(rsk_handle* h) {
     cudaDeviceSynchronize();
     rsk::prof_clear(h);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    for (cudaStream_t s : h->streams) cudaStreamDestroy(s);
     if (h->ws) cudaFree(h->ws);
     if (h->dev_status) cudaFree(h->dev_status);
     delete h;

@@ -32,11 +32,15 @@ struct rsk_handle {
     };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> event_pool;
+    std::vector<cudaStream_t> streams;  // internal non-blocking streams (batched solver)
 };
 
 namespace rsk {
 
 rsk_status fail(rsk_handle* h, rsk_status st, const char* fmt, ...);
+
+// Make sure the handle owns at least `count` internal non-blocking streams.
+rsk_status ensure_streams(rsk_handle* h, int count);
 
 // Grow the handle's workspace to at least `bytes` (stream-ordered on `stream`).
 rsk_status ensure_workspace(rsk_handle* h, size_t bytes, cudaStream_t stream);
@@ -79,6 +83,13 @@ size_t sketch_scratch_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int 
 rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda,
                                 int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
                                 void* scratch, cudaStream_t stream);
+
+size_t sketch_index_bytes(int64_t n, int64_t d, int zeta);
+rsk_status sketch_build_index(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, void* index_mem,
+                              cudaStream_t stream);
+rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta, const void* A,
+                              rsk_dtype a_dt, int64_t k, int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa,
+                              void* partials, cudaStream_t stream);
 
 }  // namespace rsk
 

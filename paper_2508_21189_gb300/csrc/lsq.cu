@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
         const int j = lane + 32 * m;
         yv[m] = j < k ? ys[j] : Acc(0);
     }
-    double rr = 0.0, ff = 0.0;
+    double rr = 0.0, ff = 0.0, bb = 0.0;
     for (int64_t i = r0 + warp; i < r1; i += nw) {
         const T* row = A + i * lda;
         Acc a[M];
@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
             if (want_frob) {
 #pragma unroll
                 for (int m = 0; m < M; ++m) ff += double(a[m]) * double(a[m]);
+                if (lane == 0) bb += b[i] * b[i];
             }
         }
 #pragma unroll
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
         const int j = lane + 32 * m;
         if (j < k) gs[size_t(warp) * k + j] = g[m];
     }
-    __shared__ double ss[kPassThreads / 32][2];
+    __shared__ double ss[kPassThreads / 32][3];
     if constexpr (RESID) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
         if (lane == 0) {
             ss[warp][0] = rr;
             ss[warp][1] = ff;
+            ss[warp][2] = bb;
         }
     }
     __syncthreads();
@@ -248,13 +250,15 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
         part[size_t(blockIdx.x) * k + j] = s;
     }
     if (RESID && threadIdx.x == 0) {
-        double a0 = 0.0, a1 = 0.0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
         for (int w = 0; w < nw; ++w) {
             a0 += ss[w][0];
             a1 += ss[w][1];
+            a2 += ss[w][2];
         }
-        part_s[2 * blockIdx.x] = a0;
-        part_s[2 * blockIdx.x + 1] = a1;
+        part_s[3 * blockIdx.x] = a0;
+        part_s[3 * blockIdx.x + 1] = a1;
+        part_s[3 * blockIdx.x + 2] = a2;
     }
 }
 
@@ -267,9 +271,9 @@ __global__ void k_reduce_parts(const Acc* __restrict__ part, int nparts, int k, 
         for (int p = 0; p < nparts; ++p) s += double(part[size_t(p) * k + j]);
         out[j] = s;
     }
-    if (part_s && j < 2) {
+    if (part_s && j < 3) {
         double s = 0.0;
-        for (int p = 0; p < nparts; ++p) s += part_s[2 * p + j];
+        for (int p = 0; p < nparts; ++p) s += part_s[3 * p + j];
         out_s[j] = s;
     }
 }
@@ -444,7 +448,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     add(size_t(K) * 8 * 12);        // vectors
     add(size_t(K) * K * 8);         // Rinv
     add(size_t(nparts) * K * 8);    // parts
-    add(size_t(nparts) * 2 * 8);    // parts_s
+    add(size_t(nparts) * 3 * 8);    // parts_s
     add(64);                        // barrier
     add(size_t(d) * K * 8);         // SA (f64 or f32)
     add(size_t(d) * 8);             // Sb
@@ -473,7 +477,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     w.stats = vecs + 9 * K;       // [0] rr, [1] ff (K >= 2 is not required: 12*K >= 12 slots)
     w.Rinv = cv.take<double>(size_t(K) * K);
     w.parts = cv.take<double>(size_t(nparts) * K);
-    w.parts_s = cv.take<double>(size_t(nparts) * 2);
+    w.parts_s = cv.take<double>(size_t(nparts) * 3);
     w.bar = cv.take<unsigned int>(16);
     w.SA64 = cv.take<double>(size_t(d) * K);
     w.SA32 = reinterpret_cast<float*>(w.SA64);
@@ -546,7 +550,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     const int max_refine = opts->max_refine >= 0 ? opts->max_refine : 20;
     const int max_inner = opts->max_inner_iters > 0 ? opts->max_inner_iters : 50;
     const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
-    double eta = 1.0, rnorm = 0.0, frob = 0.0;
+    double eta = 1.0, rnorm = 0.0, frob = 0.0, bnorm = 0.0;
     int inner_total = 0, steps = 0;
     for (steps = 0;; ++steps) {
         // g = A^T (b - A x) in FP64; rr = ||r||^2; ff = ||A||_F^2 on the first pass
@@ -560,17 +564,30 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         k_reduce_parts<double><<<unsigned((K + 255) / 256), 256, 0, stream>>>((const double*)w.parts, nparts, K, w.g,
                                                                              w.parts_s, w.stats);
         RSK_LAUNCH_CHECK(h);
-        double host[2];
-        RSK_CUDA_TRY(h, cudaMemcpyAsync(host, w.stats, 16, cudaMemcpyDeviceToHost, stream));
-        std::vector<double> gh(K);
+        double host[3];
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(host, w.stats, 24, cudaMemcpyDeviceToHost, stream));
+        std::vector<double> gh(K), xh(K);
         RSK_CUDA_TRY(h, cudaMemcpyAsync(gh.data(), w.g, size_t(K) * 8, cudaMemcpyDeviceToHost, stream));
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(xh.data(), w.x, size_t(K) * 8, cudaMemcpyDeviceToHost, stream));
         RSK_CUDA_TRY(h, cudaStreamSynchronize(stream));
-        if (steps == 0) frob = sqrt(host[1]);
+        if (steps == 0) {
+            frob = sqrt(host[1]);
+            bnorm = sqrt(host[2]);
+        }
         rnorm = sqrt(host[0]);
-        double gn = 0.0;
+        double gn = 0.0, xn = 0.0;
         for (double v : gh) gn += v * v;
+        for (double v : xh) xn += v * v;
         gn = sqrt(gn);
-        eta = (rnorm > 0.0 && frob > 0.0) ? gn / (frob * rnorm) : 0.0;
+        xn = sqrt(xn);
+        // min of the LSQR stopping quantities: ||A^T r|| / (||A||_F ||r||) and ||r|| / (||A||_F ||x|| + ||b||)
+        eta = 0.0;
+        if (rnorm > 0.0) {
+            const double ls = frob > 0.0 ? gn / (frob * rnorm) : 0.0;
+            const double den = frob * xn + bnorm;
+            const double cons = den > 0.0 ? rnorm / den : ls;
+            eta = std::min(ls, cons);
+        }
         if (eta <= tol || steps >= max_refine) break;
         // c = R^{-T} g; CG on (M^T M) z = c with M = A R^{-1}
         k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 1, w.g, w.c);

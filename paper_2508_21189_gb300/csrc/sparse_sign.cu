@@ -736,6 +736,30 @@ rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, in
     if (st != RSK_OK) return st;
     return apply_with_index(h, offs, ents, A, a_dt, n, k, lda, int(d), zeta, SA, sa_dt, ldsa, partials, p, stream);
 }
+// Index built once into caller memory, then applied to several right-hand sides.
+size_t sketch_index_bytes(int64_t n, int64_t d, int zeta) {
+    return Carver::round(offsets_count(n, int(d), zeta) * 2) + Carver::round(entries_count(n, zeta) * 2) + 256;
+}
+rsk_status sketch_build_index(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, void* index_mem,
+                              cudaStream_t stream) {
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    Carver cv(index_mem);
+    uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
+    uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
+    return launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
+}
+rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta, const void* A,
+                              rsk_dtype a_dt, int64_t k, int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa,
+                              void* partials, cudaStream_t stream) {
+    rsk_status st = check_apply_args(h, A, a_dt, k, lda, SA, sa_dt, ldsa);
+    if (st != RSK_OK) return st;
+    Carver cv(const_cast<void*>(index_mem));
+    const uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
+    const uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
+    const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dt);
+    return apply_with_index(h, offs, ents, A, a_dt, n, k, lda, int(d), zeta, SA, sa_dt, ldsa, partials, p, stream);
+}
 }  // namespace rsk
 
 extern "C" {

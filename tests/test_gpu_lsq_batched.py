@@ -1,0 +1,80 @@
+"""GPU parity of the batched sketch-and-precondition solver (row a8).
+
+Problems of uneven n_i and k_i (the batched workload's shape, scaled down): Gaussian A_i with column
+scales logspaced over [1e-6, 1] in FP32 storage, Gaussian b_i.  Every x_i must have backward error
+<= 1e-10 as recomputed by the oracle's FP64 code, in the mixed form (FP32 sketch, FP32 CG,
+double-float residual passes) and in the all-FP64 form, and the batched solution must agree with
+the single-problem solver run with the same seed.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lsq as olsq
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rsk():
+    import paper_2508_21189_gb300 as m
+    return m
+
+
+def make_batch(count, seed, n_lo=1024, n_hi=20000, k_lo=4, k_hi=64):
+    ns, ks = synthetic.batched_sizes(count, seed, n_lo=n_lo, n_hi=n_hi, k_lo=k_lo, k_hi=k_hi)
+    As, bs = [], []
+    for i, (n, k) in enumerate(zip(ns, ks)):
+        A, b = synthetic.batched_problem(n, k, seed=1000 * seed + i, device="cpu", dtype=torch.float32)
+        As.append(A)
+        bs.append(b)
+    return As, bs
+
+
+@pytest.mark.parametrize("sketch,inner", [(torch.float32, torch.float32), (torch.float64, torch.float64)])
+def test_batched_backward_error(rsk, sketch, inner):
+    As, bs = make_batch(24, 3)
+    xs, infos = rsk.rsk_lstsq_sketch_precond_batched([A.cuda() for A in As], [b.cuda() for b in bs],
+                                                     sketch_dtype=sketch, inner_dtype=inner, seed=7)
+    for A, b, x, info in zip(As, bs, xs, infos):
+        eta = olsq.backward_error(A.double().numpy(), b.numpy(), x.cpu().numpy())
+        assert eta <= 1e-10, (eta, info)
+        assert info["status"] == "RSK_OK"
+
+
+def test_batched_matches_single(rsk):
+    As, bs = make_batch(6, 4)
+    xs, _ = rsk.rsk_lstsq_sketch_precond_batched([A.cuda() for A in As], [b.cuda() for b in bs],
+                                                 sketch_dtype=torch.float32, inner_dtype=torch.float32, seed=21)
+    for i, (A, b, x) in enumerate(zip(As, bs, xs)):
+        xi, _ = rsk.rsk_lstsq_sketch_precond(A.cuda(), b.cuda(), 4 * A.shape[1], seed=21 + i,
+                                             sketch_dtype=torch.float32, inner_dtype=torch.float32)
+        # both satisfy eta <= 1e-10; solutions agree to the conditioning of the problem
+        rel = (x - xi).norm().item() / xi.norm().item()
+        assert rel <= 1e-4, rel
+
+
+@pytest.mark.parametrize("shapes,ds,zeta", [([(1, 1)], [1], 1),
+                                            ([(5, 5), (3000, 1), (2049, 17), (4097, 3)], [16, 8, 68, 12], 4)])
+def test_batched_edge_shapes(rsk, shapes, ds, zeta):
+    # square (consistent) systems, k = 1, row counts one past a tile boundary
+    g = torch.Generator().manual_seed(0)
+    As = [torch.randn(n, k, generator=g, dtype=torch.float32) for n, k in shapes]
+    bs = [torch.randn(A.shape[0], generator=g, dtype=torch.float64) for A in As]
+    xs, infos = rsk.rsk_lstsq_sketch_precond_batched([A.cuda() for A in As], [b.cuda() for b in bs],
+                                                     ds=ds, zeta=zeta, sketch_dtype=torch.float32,
+                                                     inner_dtype=torch.float32, raise_on_nonconvergence=False)
+    for A, b, x, info in zip(As, bs, xs, infos):
+        assert info["status"] == "RSK_OK", info
+        eta = olsq.backward_error(A.double().numpy(), b.numpy(), x.cpu().numpy())
+        assert eta <= 1e-10, (eta, info)
+        ref = np.linalg.lstsq(A.double().numpy(), b.numpy(), rcond=None)[0]
+        assert np.allclose(x.cpu().numpy(), ref, rtol=1e-6, atol=1e-8)
+
+
+def test_batched_invalid(rsk):
+    A = torch.zeros(10, 300, device="cuda")       # k above the batched limit
+    b = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(rsk.RskError):
+        rsk.rsk_lstsq_sketch_precond_batched([A], [b])

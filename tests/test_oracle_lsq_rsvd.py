@@ -58,10 +58,24 @@ def test_backward_error_detects_perturbation():
     xs = lsq.exact(A, b)
     assert lsq.backward_error(A, b, xs) < 1e-14
     assert lsq.backward_error(A, b, xs + 1e-3) > 1e-5
-    # definition: normal-equation residual relative to ||A||_F ||r||
-    r = b - A @ (xs + 1e-3)
-    manual = np.sqrt(((A.T @ r) ** 2).sum()) / (np.sqrt((A ** 2).sum()) * np.sqrt((r ** 2).sum()))
-    assert np.isclose(lsq.backward_error(A, b, xs + 1e-3), manual, rtol=1e-12)
+    # definition (inconsistent problem: the normal-equation term is the smaller one)
+    x1 = xs + 1e-3
+    r = b - A @ x1
+    fa = np.sqrt((A ** 2).sum())
+    ls = np.sqrt(((A.T @ r) ** 2).sum()) / (fa * np.sqrt((r ** 2).sum()))
+    cons = np.sqrt((r ** 2).sum()) / (fa * np.sqrt((x1 ** 2).sum()) + np.sqrt((b ** 2).sum()))
+    assert ls < cons
+    assert np.isclose(lsq.backward_error(A, b, x1), ls, rtol=1e-12)
+
+
+def test_backward_error_consistent_system():
+    # a square nonsingular system solved exactly: r is pure rounding, eta must be tiny
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((6, 6))
+    b = rng.standard_normal(6)
+    x = np.linalg.solve(A, b)
+    assert lsq.backward_error(A, b, x) < 1e-13
+    assert lsq.backward_error(A, b, x + 1e-6) > 1e-9
 
 
 def test_lsqr_unpreconditioned_small():
