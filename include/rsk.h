@@ -240,6 +240,19 @@ typedef struct {
 rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const rsk_lsq_problem* probs,
                                             const rsk_lsq_opts* opts, rsk_lsq_info* infos, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * a9: randomized SVD with a sparse sign test matrix (Alg. 1, Sec. 2.1) and power_iters subspace
+ * iterations (re-orthonormalising after every product; Alg. 1 itself has none).
+ * A: device FP32 m x n row-major (lda >= n).  Omega (n x r) has zeta nonzeros +-zeta^{-1/2} per row,
+ * drawn as the left sparse sign of Philox stream 3 (rsk_sparse_sign_generate's rule with stream 3).
+ * Outputs (device): U FP32 m x r row-major, s FP64[r] descending, Vt FP32 r x n row-major, with
+ * A ~ U diag(s) Vt.  Products run on BF16 copies of A with FP32 accumulation; orthonormalisation is
+ * shifted CholeskyQR3 in FP32; the r x r eigenproblem of B B^T is solved in FP64.
+ * Limits: 1 <= r <= min(m, n, 380), 1 <= zeta <= min(r, 32), m, n < 2^31.  Needs cuBLAS and
+ * cuSOLVER at run time (RSK_ERR_UNSUPPORTED when they cannot be loaded). */
+rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int32_t r, int32_t power_iters,
+                    int32_t zeta, uint64_t seed, float* U, double* s, float* Vt, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

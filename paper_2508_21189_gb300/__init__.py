@@ -227,6 +227,22 @@ def rsk_lstsq_sketch_precond_batched(As, bs, ds=None, zeta=8, seed=0, sketch_dty
     return xs, out
 
 
+def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
+    """Randomized SVD of a CUDA FP32 tensor A (m x n): returns (U [m, r] FP32, s [r] FP64, Vt [r, n] FP32)."""
+    _matrix(A, "A")
+    if A.dtype != torch.float32:
+        raise TypeError("rsk_rsvd takes FP32 A")
+    m, n = A.shape
+    U = torch.empty(m, r, dtype=torch.float32, device=A.device)
+    s = torch.empty(r, dtype=torch.float64, device=A.device)
+    Vt = torch.empty(r, n, dtype=torch.float32, device=A.device)
+    h = handle(A.device)
+    st = load().rsk_rsvd(h, A.data_ptr(), m, n, A.stride(0), r, power_iters, zeta, seed, U.data_ptr(), s.data_ptr(),
+                         Vt.data_ptr(), _stream(stream))
+    _check(st, h)
+    return U, s, Vt
+
+
 # Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).
 KERNEL_IDS = {"sketch_index": 0, "sketch_apply": 1, "sketch_reduce": 2, "sketch_generate": 3,
               "srtt_apply": 4, "srtt_reduce": 5, "dense": 6, "gemm": 7}

@@ -61,7 +61,7 @@ def build(verbose=False, extra=()):
         os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
     if need_link:
         tmp = LIB + ".tmp"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]
         if run(cmd):
             raise RuntimeError("linking librsk failed")
         os.replace(tmp, LIB)

@@ -84,6 +84,8 @@ rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, in
                                 int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
                                 void* scratch, cudaStream_t stream);
 
+rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, uint32_t stream_id,
+                           int32_t* rows, uint32_t* signs, cudaStream_t stream);
 size_t sketch_index_bytes(int64_t n, int64_t d, int zeta);
 rsk_status sketch_build_index(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, void* index_mem,
                               cudaStream_t stream);

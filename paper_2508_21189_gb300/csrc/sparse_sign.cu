@@ -760,6 +760,18 @@ rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, i
     const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dt);
     return apply_with_index(h, offs, ents, A, a_dt, n, k, lda, int(d), zeta, SA, sa_dt, ldsa, partials, p, stream);
 }
+// Draw rows/signs of a sparse sign matrix from any Philox stream (the RSVD test matrix uses stream 3).
+rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, uint32_t stream_id,
+                           int32_t* rows, uint32_t* signs, cudaStream_t stream) {
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    const unsigned grid = unsigned((n + 255) / 256);
+    if (zeta <= 8) k_generate<8><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs);
+    else if (zeta <= 16) k_generate<16><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs);
+    else k_generate<32><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
 }  // namespace rsk
 
 extern "C" {
