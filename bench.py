@@ -29,6 +29,9 @@ if ROOT not in sys.path:
 
 METRIC = "SA GB/s of A read (% HBM peak); LSQ solves/sec at 1e-10 bwd err, mixed vs FP64"
 N_ROWS, K_COLS, D_SKETCH, ZETA = 1 << 22, 256, 2048, 8
+LSQ_N, LSQ_K, LSQ_D = 1 << 20, 500, 2000
+BATCH_COUNT = 512
+RSVD_M, RSVD_N, RSVD_R, RSVD_Q, RSVD_RANK = 262144, 8192, 300, 2, 400
 FALLBACK_HBM_GBS = 6800.0
 APPLY_SOURCES = ["paper_2508_21189_gb300/csrc/sparse_sign.cu", "paper_2508_21189_gb300/csrc/common.cuh"]
 
@@ -44,6 +47,9 @@ def parse():
     p.add_argument("--dtypes", default="bf16,fp32", help="A storage types to time; the first is the headline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-srtt", action="store_true")
+    p.add_argument("--no-lsq", action="store_true", help="skip the least-squares solves/sec measurements")
+    p.add_argument("--no-rsvd", action="store_true")
+    p.add_argument("--solve-reps", type=int, default=3, help="timed calls per least-squares / RSVD form")
     return p.parse_args()
 
 
@@ -236,6 +242,99 @@ def time_steps(rsk, A, out, steps, seed0, torch):
     return ev0.elapsed_time(ev1) / steps
 
 
+def timed_calls(fn, reps, torch, dev, after_warmup=None):
+    """Median device time (ms, max over ranks) of `reps` calls, one warm-up call first."""
+    out = fn()
+    if after_warmup:
+        after_warmup()
+    times = []
+    for _ in range(reps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record()
+        out = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        times.append(max_over_ranks(ev0.elapsed_time(ev1), device=dev))
+    return statistics.median(times), out
+
+
+def bench_lsq(rsk, synthetic, torch, dev, rank, world, reps):
+    """Single least-squares workload (A = Q_U diag(logspace(0,-8)) V^T, 2^20 x 500 FP64, b = A x* +
+    1e-6 noise, d = 2000, zeta = 8): the mixed form (FP32 sketch, double-float inner CG, FP64-accuracy
+    refinement) against the plain FP64 form (FP64 sketch, FP64 inner CG), each to eta <= 1e-10."""
+    A, b, _ = synthetic.lsq_problem(LSQ_N, LSQ_K, seed=31 + rank, cond_exp=8.0, noise=1e-6, device=dev)
+    forms = {"mixed": (torch.float32, "f32x2"), "fp64": (torch.float64, torch.float64)}
+    res = {}
+    for name, (sk, inner) in forms.items():
+        ms, (x, info) = timed_calls(lambda: rsk.rsk_lstsq_sketch_precond(A, b, LSQ_D, zeta=ZETA, seed=7,
+                                                                           sketch_dtype=sk, inner_dtype=inner),
+                                    reps, torch, dev)
+        res[name] = {"solves_per_s": round(world * 1e3 / ms, 3), "ms_per_solve": round(ms, 3),
+                     "backward_err": info["backward_err"], "refine_steps": info["refine_steps"],
+                     "inner_iters": info["inner_iters"],
+                     "sketch": str(sk).replace("torch.", ""), "inner": str(inner).replace("torch.", "")}
+    del A, b
+    torch.cuda.empty_cache()
+    return {"workload": "least squares A = Q_U diag(logspace(0,-8)) V^T 2^20 x 500 FP64, b = A x* + 1e-6 N(0,1), "
+                        "sparse sign d=2000 zeta=8, to eta <= 1e-10",
+            "value": res["mixed"]["solves_per_s"], "unit": "solves/s",
+            "speedup_vs_fp64": round(res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"], 3),
+            "mixed": res["mixed"], "fp64": res["fp64"]}
+
+
+def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps):
+    """512 uneven problems (n_i log-uniform [4096, 262144], k_i uniform [16, 256], Gaussian A_i x
+    logspace(-6, 0) column scales, Gaussian b_i, d_i = 4 k_i, zeta = 8) in one batched call: FP32
+    storage with FP32 sketch and inner CG against FP64 storage with FP64 sketch and inner CG."""
+    ns, ks = synthetic.batched_sizes(BATCH_COUNT, seed=404 + rank)
+    As32, As64, bs = [], [], []
+    for i, (n, k) in enumerate(zip(ns, ks)):
+        A, b = synthetic.batched_problem(n, k, seed=10_000 * (rank + 1) + i, device=dev, dtype=torch.float64)
+        As64.append(A)
+        As32.append(A.float())
+        bs.append(b)
+    res = {}
+    for name, (As, dt) in {"mixed": (As32, torch.float32), "fp64": (As64, torch.float64)}.items():
+        ms, (xs, infos) = timed_calls(lambda: rsk.rsk_lstsq_sketch_precond_batched(As, bs, zeta=ZETA, seed=9,
+                                                                                     sketch_dtype=dt, inner_dtype=dt),
+                                      reps, torch, dev)
+        res[name] = {"solves_per_s": round(world * BATCH_COUNT * 1e3 / ms, 3), "ms_per_batch": round(ms, 3),
+                     "max_backward_err": max(f["backward_err"] for f in infos),
+                     "max_refine_steps": max(f["refine_steps"] for f in infos)}
+    rows = sum(ns)
+    elems = sum(n * k for n, k in zip(ns, ks))
+    del As32, As64, bs
+    torch.cuda.empty_cache()
+    return {"workload": f"{BATCH_COUNT} uneven least-squares problems, n_i log-uniform [4096, 262144], k_i uniform "
+                        "[16, 256], A_i Gaussian x logspace(-6,0) column scales, d_i = 4 k_i, zeta=8, eta <= 1e-10",
+            "total_rows": rows, "total_elements": elems,
+            "value": res["mixed"]["solves_per_s"], "unit": "solves/s",
+            "speedup_vs_fp64": round(res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"], 3),
+            "mixed": res["mixed"], "fp64": res["fp64"]}
+
+
+def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps):
+    """RSVD of A 262144 x 8192 FP32 (rank-400 spectrum j^-2 plus 1e-4 noise), r = 300, q = 2."""
+    A = synthetic.lowrank_plus_noise(RSVD_M, RSVD_N, RSVD_RANK, seed=2025 + rank, noise=1e-4, device=dev)
+    # profiling starts after the warm-up call, which also loads the GEMM library's kernels
+    ms, (U, s, Vt) = timed_calls(lambda: rsk.rsk_rsvd(A, RSVD_R, power_iters=RSVD_Q, zeta=ZETA, seed=0),
+                                 reps, torch, dev, after_warmup=lambda: rsk.rsk_profile_enable(True))
+    gemm = rsk.rsk_profile_read("gemm")
+    rsk.rsk_profile_enable(False)
+    flops = (2 + 2 * RSVD_Q) * 2 * RSVD_M * RSVD_N * RSVD_R
+    gemm_ms = gemm[0] / reps
+    del A, U, s, Vt
+    torch.cuda.empty_cache()
+    return {"workload": "RSVD A 262144 x 8192 FP32 (rank-400 spectrum j^-2 + 1e-4 noise), r=300, q=2, "
+                        "sparse sign Omega zeta=8",
+            "value": round(world * 1e3 / ms, 3), "unit": "calls/s", "ms_per_call": round(ms, 3),
+            "gemm_ms_per_call": round(gemm_ms, 3), "gemm_flops_per_call": flops,
+            "gemm_tflops": round(flops / (gemm_ms / 1e3) / 1e12, 1) if gemm_ms > 0 else None}
+
+
 def run_ours(args):
     import torch
     rank, world = dist_init("nccl")
@@ -322,6 +421,12 @@ def run_ours(args):
         del A
         torch.cuda.empty_cache()
     clocks = sampler.stop()
+    extra = {}
+    if not args.no_lsq:
+        extra["lsq"] = bench_lsq(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
+        extra["lsq_batched"] = bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
+    if not args.no_rsvd:
+        extra["rsvd"] = bench_rsvd(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
 
     if rank != 0:
         return
@@ -360,6 +465,7 @@ def run_ours(args):
                       "apply_ms": round(r["apply_ms"], 4),
                       "apply_frac": round((r["a_bytes"] + D_SKETCH * K_COLS * 4) / (r["apply_ms"] / 1e3) / 1e9
                                           / peak, 4)}
+    line.update(extra)
     if args.rows != N_ROWS:
         line["config"]["n"] = args.rows
         line["config"]["workload"] += f" (reduced to {args.rows} rows for profiling)"

@@ -48,7 +48,9 @@ typedef enum {
     RSK_ERR_INTERNAL = 7
 } rsk_status;
 
-typedef enum { RSK_F64 = 0, RSK_F32 = 1, RSK_BF16 = 2 } rsk_dtype;
+/* RSK_F32X2 is a pair of FP32 arrays (hi, lo) with a = hi + lo (about 48 significant bits); it is
+ * accepted only as the inner precision of the least-squares solvers (double-float arithmetic). */
+typedef enum { RSK_F64 = 0, RSK_F32 = 1, RSK_BF16 = 2, RSK_F32X2 = 3 } rsk_dtype;
 
 typedef struct rsk_handle rsk_handle;
 
@@ -187,14 +189,17 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
  *   problems); stop at eta <= tol_backward; else CG on (M^T M) z = R^{-T} g with M = A R^{-1} in
  *   inner_dtype, then x += R^{-1} z.
  * Precision notes: inner_dtype F32 converges when u_32 * kappa(A) is well below 1 or when A's
- * ill-conditioning is a column scaling; for kappa(A) ~ 1e8 with mixed columns use F64.
+ * ill-conditioning is a column scaling; for kappa(A) ~ 1e8 with mixed columns use F64 or F32X2.
+ * With F32X2 the library splits A into FP32 hi/lo arrays once per solve and runs the CG passes in
+ * double-float arithmetic on FP32 units; the residual passes read an F64 A as stored (48 bits of
+ * hi + lo would move the fixed point) and an F32 A through the same double-float pass.
  * ------------------------------------------------------------------------------------------- */
 typedef struct {
     int64_t d;               /* sketch rows (k <= d <= 8192) */
     int32_t zeta;            /* nonzeros per column of S */
     uint64_t seed;           /* Philox seed of S */
     rsk_dtype sketch_dtype;  /* precision A is sketched in: F64, F32 or BF16 (FP32 accumulation) */
-    rsk_dtype inner_dtype;   /* precision of the CG operator: F64 or F32 */
+    rsk_dtype inner_dtype;   /* precision of the CG operator: F64, F32, or F32X2 (double-float pair) */
     double tol_backward;     /* target eta (default 1e-10 when <= 0) */
     int32_t max_refine;      /* refinement steps; 0 returns the warm start x0; < 0 selects 20 */
     int32_t max_inner_iters; /* CG iterations per step (default 50 when <= 0) */

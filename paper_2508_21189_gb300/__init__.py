@@ -10,8 +10,8 @@ import torch
 
 from ._lib import LsqInfo, LsqOpts, LsqProblem, RskError, STATUS, load
 
-RSK_F64, RSK_F32, RSK_BF16 = 0, 1, 2
-_DT = {torch.float64: RSK_F64, torch.float32: RSK_F32, torch.bfloat16: RSK_BF16}
+RSK_F64, RSK_F32, RSK_BF16, RSK_F32X2 = 0, 1, 2, 3
+_DT = {torch.float64: RSK_F64, torch.float32: RSK_F32, torch.bfloat16: RSK_BF16, "f32x2": RSK_F32X2}
 
 _handles = {}
 

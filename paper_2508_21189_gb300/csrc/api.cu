@@ -143,9 +143,16 @@ rsk_status rsk_create(rsk_handle** out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e == cudaSuccess) e = cudaMalloc(&h->dev_status, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(h->dev_status, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&h->host_flags), kHostFlags * sizeof(double),
+                                            cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->flag_ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->flag_ev[1], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (h->dev_status) cudaFree(h->dev_status);
+        if (h->host_flags) cudaFreeHost(h->host_flags);
+        if (h->flag_ev[0]) cudaEventDestroy(h->flag_ev[0]);
+        if (h->flag_ev[1]) cudaEventDestroy(h->flag_ev[1]);
         delete h;
         return RSK_ERR_CUDA;
     }
@@ -168,6 +175,9 @@ rsk_status rsk_destroy(rsk_handle* h) {
     for (cudaStream_t s : h->streams) cudaStreamDestroy(s);
     if (h->ws) cudaFree(h->ws);
     if (h->dev_status) cudaFree(h->dev_status);
+    if (h->host_flags) cudaFreeHost(h->host_flags);
+    for (cudaEvent_t e : h->flag_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
     return RSK_OK;
 }

@@ -33,7 +33,11 @@ struct rsk_handle {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> event_pool;
     std::vector<cudaStream_t> streams;  // internal non-blocking streams (batched solver)
+    // pinned host words the solvers poll without stalling the stream (early exit of the inner CG)
+    double* host_flags = nullptr;       // kHostFlags doubles
+    cudaEvent_t flag_ev[2] = {nullptr, nullptr};
 };
+constexpr int kHostFlags = 8;
 
 namespace rsk {
 
@@ -89,6 +93,9 @@ rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64
 size_t sketch_index_bytes(int64_t n, int64_t d, int zeta);
 rsk_status sketch_build_index(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, void* index_mem,
                               cudaStream_t stream);
+// S b for one FP64 vector (one warp per sketch row) from an index built by sketch_build_index.
+rsk_status sketch_apply_vec_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta,
+                                  const double* b, double* Sb, cudaStream_t stream);
 rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta, const void* A,
                               rsk_dtype a_dt, int64_t k, int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa,
                               void* partials, cudaStream_t stream);

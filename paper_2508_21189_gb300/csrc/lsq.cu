@@ -262,6 +262,141 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
     }
 }
 
+// ---- double-float pass on A = hi + lo (two FP32 arrays), y = yh + yl (FP32 pair) -------------
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += (ah + al) * (yh + yl), dropping al*yl (below 2^-48 relative)
+__device__ __forceinline__ void df_mac(float& hi, float& lo, float ah, float al, float yh, float yl) {
+    const float p = ah * yh;
+    const float pe = fmaf(ah, yh, -p);
+    const float t = fmaf(ah, yl, fmaf(al, yh, pe));
+    float s, e;
+    two_sum_f(hi, p, s, e);
+    e += lo + t;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float oh, float ol) {
+    float s, e;
+    two_sum_f(hi, oh, s, e);
+    e += lo + ol;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// RESID: r_i = b_i - a_i . x, g += r_i a_i, rr, ff, bb.   CG: w_i = a_i . y, g += w_i a_i.
+template <int M, bool RESID>
+__global__ void __launch_bounds__(kPassThreads) k_pass_df(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                          int64_t n, int k, const double* __restrict__ y,
+                                                          const double* __restrict__ b, double* __restrict__ part,
+                                                          double* __restrict__ part_s, int want_frob) {
+    extern __shared__ __align__(16) uint8_t dsm[];
+    double* gs = reinterpret_cast<double*>(dsm);
+    float* yh = reinterpret_cast<float*>(gs + size_t(kPassThreads / 32) * k);
+    float* yl = yh + k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double v = y[j];
+        const float h = float(v);
+        yh[j] = h;
+        yl[j] = float(v - double(h));
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int64_t r0 = int64_t(blockIdx.x) * n / gridDim.x, r1 = int64_t(blockIdx.x + 1) * n / gridDim.x;
+    float gh[M], gl[M], vh[M], vl[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        gh[m] = gl[m] = 0.f;
+        const int j = lane + 32 * m;
+        vh[m] = j < k ? yh[j] : 0.f;
+        vl[m] = j < k ? yl[j] : 0.f;
+    }
+    double rr = 0.0, ff = 0.0, bb = 0.0;
+    for (int64_t i = r0 + warp; i < r1; i += nw) {
+        const float* rh = Ah + i * k;
+        const float* rl = Al + i * k;
+        float ah[M], al[M], dh = 0.f, dl = 0.f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int j = lane + 32 * m;
+            ah[m] = j < k ? rh[j] : 0.f;
+            al[m] = j < k ? rl[j] : 0.f;
+            df_mac(dh, dl, ah[m], al[m], vh[m], vl[m]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, dh, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, dl, o);
+            df_add(dh, dl, oh, ol);
+        }
+        double w = double(dh) + double(dl);
+        if constexpr (RESID) {
+            w = b[i] - w;
+            rr += w * w;
+            if (want_frob) {
+                float sq = 0.f;
+#pragma unroll
+                for (int m = 0; m < M; ++m) sq = fmaf(ah[m], ah[m], sq);
+                ff += double(sq);
+                if (lane == 0) bb += b[i] * b[i];
+            }
+        }
+        const float wh = float(w), wl = float(w - double(wh));
+#pragma unroll
+        for (int m = 0; m < M; ++m) df_mac(gh[m], gl[m], ah[m], al[m], wh, wl);
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int j = lane + 32 * m;
+        if (j < k) gs[size_t(warp) * k + j] = double(gh[m]) + double(gl[m]);
+    }
+    __shared__ double ss[kPassThreads / 32][3];
+    if constexpr (RESID) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+            ff += __shfl_xor_sync(0xffffffffu, ff, o);
+        }
+        if (lane == 0) {
+            ss[warp][0] = rr;
+            ss[warp][1] = ff;
+            ss[warp][2] = bb;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += gs[size_t(w) * k + j];
+        part[size_t(blockIdx.x) * k + j] = s;
+    }
+    if (RESID && threadIdx.x == 0) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            a0 += ss[w][0];
+            a1 += ss[w][1];
+            a2 += ss[w][2];
+        }
+        part_s[3 * blockIdx.x] = a0;
+        part_s[3 * blockIdx.x + 1] = a1;
+        part_s[3 * blockIdx.x + 2] = a2;
+    }
+}
+
+// A (F64, lda) -> hi, lo FP32 arrays (n x k) with a = hi + lo
+__global__ void k_split_df(const double* __restrict__ A, int64_t n, int k, int64_t lda, float* __restrict__ hi,
+                           float* __restrict__ lo) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k, j = idx - i * k;
+    const double a = A[i * lda + j];
+    const float h = float(a);
+    hi[idx] = h;
+    lo[idx] = float(a - double(h));
+}
+
 template <typename Acc>
 __global__ void k_reduce_parts(const Acc* __restrict__ part, int nparts, int k, double* __restrict__ out,
                                const double* __restrict__ part_s, double* __restrict__ out_s) {
@@ -417,6 +552,30 @@ static rsk_status launch_pass(rsk_handle* h, const T* A, int64_t n, int k, int64
     return RSK_OK;
 }
 
+static rsk_status launch_pass_df(rsk_handle* h, const float* Ah, const float* Al, int64_t n, int k, const double* y,
+                                 const double* b, double* parts, double* parts_s, int nparts, bool resid, bool frob,
+                                 cudaStream_t stream) {
+    const int M = (k + 31) / 32;
+    const size_t smem = size_t(kPassThreads / 32) * k * 8 + size_t(k) * 8;
+    rsk_status err = RSK_OK;
+    auto go = [&](auto kern) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
+            err = RSK_ERR_CUDA;
+            return;
+        }
+        kern<<<unsigned(nparts), kPassThreads, smem, stream>>>(Ah, Al, n, k, y, b, parts, parts_s, frob ? 1 : 0);
+    };
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_DENSE);
+    if (M <= 4) resid ? go(k_pass_df<4, true>) : go(k_pass_df<4, false>);
+    else if (M <= 8) resid ? go(k_pass_df<8, true>) : go(k_pass_df<8, false>);
+    else if (M <= 16) resid ? go(k_pass_df<16, true>) : go(k_pass_df<16, false>);
+    else resid ? go(k_pass_df<32, true>) : go(k_pass_df<32, false>);
+    rsk::prof_end(h, stream, pr);
+    if (err != RSK_OK) return rsk::fail(h, err, "cudaFuncSetAttribute failed for the double-float pass");
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
 }  // namespace rsk
 
 extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
@@ -432,14 +591,16 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     if (d < k || d > 8192) return fail(h, RSK_ERR_INVALID_ARG, "need k <= d <= 8192 (got d=%lld)", (long long)d);
     if (opts->sketch_dtype != RSK_F64 && opts->sketch_dtype != RSK_F32 && opts->sketch_dtype != RSK_BF16)
         return fail(h, RSK_ERR_INVALID_ARG, "bad sketch dtype");
-    if (opts->inner_dtype != RSK_F64 && opts->inner_dtype != RSK_F32)
-        return fail(h, RSK_ERR_INVALID_ARG, "inner dtype must be F64 or F32");
+    if (opts->inner_dtype != RSK_F64 && opts->inner_dtype != RSK_F32 && opts->inner_dtype != RSK_F32X2)
+        return fail(h, RSK_ERR_INVALID_ARG, "inner dtype must be F64, F32 or F32X2");
     if (info) memset(info, 0, sizeof(*info));
+    const bool dfl = opts->inner_dtype == RSK_F32X2;
     const int K = int(k);
     const int nparts = std::max(1, std::min<int>(int((n + 255) / 256), 2 * h->num_sms));
 
     // ---- workspace
-    const bool need_sk_copy = opts->sketch_dtype != a_dtype;
+    // with F32X2 the hi array doubles as the FP32 copy the sketch may need
+    const bool need_sk_copy = opts->sketch_dtype != a_dtype && !(dfl && opts->sketch_dtype == RSK_F32);
     const bool need_in_copy = opts->inner_dtype == RSK_F32 && a_dtype == RSK_F64;
     const size_t es_sk = dtype_size(opts->sketch_dtype);
     size_t bytes = 0;
@@ -456,6 +617,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     if (need_in_copy) add(size_t(n) * K * 4);
     add(size_t(K) * 8);             // yv
     add(64);                        // CG state
+    if (dfl) add(size_t(n) * K * 4 * 2);  // hi, lo
     const size_t sk_part = std::max(sketch_partial_bytes(h, n, k, d, opts->zeta, opts->sketch_dtype),
                                     sketch_partial_bytes(h, n, 1, d, opts->zeta, RSK_F64));
     add(sk_part);
@@ -487,6 +649,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     w.yv = cv.take<double>(size_t(K));
     double* cgstate = cv.take<double>(8);
     void* skpart = cv.take<char>(sk_part);
+    float* Ahi = dfl ? cv.take<float>(size_t(n) * K) : nullptr;
+    float* Alo = dfl ? cv.take<float>(size_t(n) * K) : nullptr;
     RSK_CUDA_TRY(h, cudaMemsetAsync(w.bar, 0, 64, stream));
 
     // ---- L1: low-precision copies, sketch of [A | b]
@@ -509,8 +673,17 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
             RSK_LAUNCH_CHECK(h);
         }
     }
-    const void* A_sk = need_sk_copy ? Ask : A;
-    const int64_t lda_sk = need_sk_copy ? k : lda;
+    if (dfl) {
+        if (a_dtype == RSK_F64) k_split_df<<<cg, 256, 0, stream>>>((const double*)A, n, K, lda, Ahi, Alo);
+        else {
+            k_convert<float, float><<<cg, 256, 0, stream>>>((const float*)A, n, K, lda, Ahi);
+            RSK_CUDA_TRY(h, cudaMemsetAsync(Alo, 0, size_t(n) * K * 4, stream));
+        }
+        RSK_LAUNCH_CHECK(h);
+    }
+    const bool sk_from_hi = dfl && opts->sketch_dtype == RSK_F32 && a_dtype == RSK_F64;
+    const void* A_sk = sk_from_hi ? static_cast<const void*>(Ahi) : (need_sk_copy ? Ask : A);
+    const int64_t lda_sk = (sk_from_hi || need_sk_copy) ? k : lda;
     rsk_sketch_plan* plan = nullptr;
     st = rsk_sparse_sign_plan_create(h, n, d, opts->zeta, opts->seed, &plan, stream);
     if (st != RSK_OK) return st;
@@ -554,7 +727,12 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     int inner_total = 0, steps = 0;
     for (steps = 0;; ++steps) {
         // g = A^T (b - A x) in FP64; rr = ||r||^2; ff = ||A||_F^2 on the first pass
-        if (a_dtype == RSK_F64)
+        // an FP64 A is read as stored: the hi/lo split keeps only 48 bits, and the fixed point of the
+        // refinement must be that of A itself.  An FP32 A is exact in hi (lo = 0): double-float sums.
+        if (dfl && a_dtype == RSK_F32)
+            st = launch_pass_df(h, Ahi, Alo, n, K, w.x, b, (double*)w.parts, w.parts_s, nparts, true, steps == 0,
+                                stream);
+        else if (a_dtype == RSK_F64)
             st = launch_pass<double, double>(h, (const double*)A, n, K, lda, w.x, b, (double*)w.parts, w.parts_s,
                                              nparts, true, steps == 0, stream);
         else
@@ -594,8 +772,20 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         k_cg_init<<<1, 256, 0, stream>>>(w.c, w.z, w.res, w.p, K, cgstate);
         RSK_LAUNCH_CHECK(h);
         for (int it = 0; it < max_inner; ++it) {
+            // early exit: the done flag of iteration it-2 was copied to pinned memory behind an event,
+            // so the host checks it while iterations it-1 (and its pass over A) still run
+            if (it >= 2) {
+                RSK_CUDA_TRY(h, cudaEventSynchronize(h->flag_ev[it & 1]));
+                if (h->host_flags[it & 1] != 0.0) break;
+            }
             k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 0, w.p, w.t);   // t = R^{-1} p
-            if (opts->inner_dtype == RSK_F32) {
+            if (dfl) {
+                st = launch_pass_df(h, Ahi, Alo, n, K, w.t, nullptr, (double*)w.parts, nullptr, nparts, false, false,
+                                    stream);
+                if (st != RSK_OK) return st;
+                k_reduce_parts<double><<<unsigned((K + 255) / 256), 256, 0, stream>>>((const double*)w.parts, nparts,
+                                                                                     K, w.g, nullptr, nullptr);
+            } else if (opts->inner_dtype == RSK_F32) {
                 k_cast_vec<float><<<unsigned((K + 255) / 256), 256, 0, stream>>>(w.t, (float*)w.yv, K, cgstate);
                 st = launch_pass<float, float>(h, (const float*)(a_dtype == RSK_F32 ? A : Ain), n, K,
                                                a_dtype == RSK_F32 ? lda : k, (const float*)w.yv, nullptr,
@@ -617,6 +807,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
             k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 1, w.g, w.s);  // s = R^{-T} A^T A R^{-1} p
             k_cg_step<<<1, 256, 0, stream>>>(w.s, w.z, w.res, w.p, K, cgstate, inner_tol);
             RSK_LAUNCH_CHECK(h);
+            RSK_CUDA_TRY(h, cudaMemcpyAsync(&h->host_flags[it & 1], cgstate + 2, 8, cudaMemcpyDeviceToHost, stream));
+            RSK_CUDA_TRY(h, cudaEventRecord(h->flag_ev[it & 1], stream));
         }
         double cgs[4];
         RSK_CUDA_TRY(h, cudaMemcpyAsync(cgs, cgstate, 32, cudaMemcpyDeviceToHost, stream));

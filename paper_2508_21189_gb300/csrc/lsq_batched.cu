@@ -42,6 +42,7 @@ struct BProb {
     double* cg;         // 8
     void* part;         // ntiles x k (double)
     double* part_s;     // ntiles x 3
+    const float2* bsplit;  // b as FP32 pairs (hi, lo) for the double-float residual pass, else null
     int tile0, ntiles;
 };
 
@@ -62,9 +63,25 @@ __device__ __forceinline__ double block_sum_b(double v, double* red) {
 }
 
 // ---- FP64 Householder QR, one CTA per problem ---------------------------------------------
-__global__ void __launch_bounds__(512) k_qr_b(BProb* P) {
+__device__ void qr_one(const BProb& q, double* red);
+
+// Persistent: one CTA per SM pulls problems from a queue ordered by decreasing work (d k^2), so
+// the largest factorizations start first and the small ones fill in behind them (LPT order).
+__global__ void __launch_bounds__(512) k_qr_b(BProb* P, const int* __restrict__ order, int count,
+                                              unsigned int* queue) {
     __shared__ double red[32];
-    const BProb& q = P[blockIdx.x];
+    __shared__ int next_s;
+    for (;;) {
+        if (threadIdx.x == 0) next_s = int(atomicAdd(queue, 1u));
+        __syncthreads();
+        const int slot = next_s;
+        __syncthreads();
+        if (slot >= count) break;
+        qr_one(P[order[slot]], red);
+    }
+}
+
+__device__ void qr_one(const BProb& q, double* red) {
     const int d = q.d, k = q.k, cols = k + 1;
     double* W = q.W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -174,11 +191,68 @@ __device__ __forceinline__ void df_merge(float& hi, float& lo, float oh, float o
 // MODE 0: CG pass, FP32 storage and arithmetic: q = A^T A y (y = yf).
 // MODE 1: CG pass in FP64 arithmetic (F64 or F32 storage): q = A^T A t (t = slot 7).
 // MODE 2: residual pass in FP64: r = b - A x, g = A^T r, rr, ff.
-// MODE 3: residual pass in double-float FP32 arithmetic (F32 storage only).
+// MODE 3: residual pass in double-float FP32 arithmetic (F32 storage only), b pre-split into
+//         FP32 pairs so that no FP64 instruction runs per row.
+// A warp takes R rows at a time: lanes hold columns lane + 32 m of each row, the R partial dot
+// products are reduce-scattered across the warp (lane L ends with row 2*bit4(L) + bit3(L) for
+// R = 4, bit4(L) for R = 2), and each row's result is read back from its owner lane.
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int R>
+__device__ __forceinline__ int row_owner(int r) {
+    return R == 4 ? (((r >> 1) & 1) << 4) | ((r & 1) << 3) : (r << 4);
+}
+
+template <int R, typename T>
+__device__ __forceinline__ T reduce_scatter(const T (&p)[R], int lane) {
+    T k;
+    if constexpr (R == 4) {
+        const bool b4 = lane & 16;
+        T k0 = b4 ? p[2] : p[0], k1 = b4 ? p[3] : p[1];
+        const T s0 = b4 ? p[0] : p[2], s1 = b4 ? p[1] : p[3];
+        k0 += __shfl_xor_sync(kFull, s0, 16);
+        k1 += __shfl_xor_sync(kFull, s1, 16);
+        const bool b3 = lane & 8;
+        k = b3 ? k1 : k0;
+        k += __shfl_xor_sync(kFull, b3 ? k0 : k1, 8);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(kFull, k, o);
+    } else {
+        const bool b4 = lane & 16;
+        k = b4 ? p[1] : p[0];
+        k += __shfl_xor_sync(kFull, b4 ? p[0] : p[1], 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) k += __shfl_xor_sync(kFull, k, o);
+    }
+    return k;
+}
+
+// the same on double-float pairs
+__device__ __forceinline__ void df_xor_merge(float& h, float& l, float sh, float sl, int o) {
+    const float oh = __shfl_xor_sync(kFull, sh, o), ol = __shfl_xor_sync(kFull, sl, o);
+    df_merge(h, l, oh, ol);
+}
+__device__ __forceinline__ void reduce_scatter_df4(const float (&ph)[4], const float (&pl)[4], int lane, float& h,
+                                                   float& l) {
+    const bool b4 = lane & 16;
+    float k0h = b4 ? ph[2] : ph[0], k0l = b4 ? pl[2] : pl[0];
+    float k1h = b4 ? ph[3] : ph[1], k1l = b4 ? pl[3] : pl[1];
+    df_xor_merge(k0h, k0l, b4 ? ph[0] : ph[2], b4 ? pl[0] : pl[2], 16);
+    df_xor_merge(k1h, k1l, b4 ? ph[1] : ph[3], b4 ? pl[1] : pl[3], 16);
+    const bool b3 = lane & 8;
+    h = b3 ? k1h : k0h;
+    l = b3 ? k1l : k0l;
+    df_xor_merge(h, l, b3 ? k0h : k1h, b3 ? k0l : k1l, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) df_xor_merge(h, l, h, l, o);
+}
+
 template <int MODE, int M>
 __global__ void __launch_bounds__(kBThreads) k_pass_b(BProb* P, const Tile* __restrict__ tiles, int ntiles,
                                                        unsigned int* queue, const int* __restrict__ active,
                                                        int want_frob) {
+    constexpr bool F64 = MODE == 1 || MODE == 2;
+    constexpr int R = F64 ? 2 : 4;
     __shared__ double ys[kBMaxK];
     __shared__ float yh[kBMaxK], yl[kBMaxK];
     __shared__ double gs[kBThreads / 32][kBMaxK];
@@ -198,11 +272,14 @@ __global__ void __launch_bounds__(kBThreads) k_pass_b(BProb* P, const Tile* __re
             continue;
         }
         const int k = q.k;
-        for (int j = threadIdx.x; j < k; j += kBThreads) {
-            double y;
-            if (MODE == 0) y = double(q.yf[j]);
-            else if (MODE == 1) y = q.v[size_t(7) * k + j];
-            else y = q.v[j];  // x
+        const int mk = (k + 31) >> 5;  // column blocks this problem uses (warp-uniform)
+        for (int j = threadIdx.x; j < 32 * M; j += kBThreads) {
+            double y = 0.0;
+            if (j < k) {
+                if (MODE == 0) y = double(q.yf[j]);
+                else if (MODE == 1) y = q.v[size_t(7) * k + j];
+                else y = q.v[j];  // x
+            }
             ys[j] = y;
             const float h = float(y);
             yh[j] = h;
@@ -218,82 +295,143 @@ __global__ void __launch_bounds__(kBThreads) k_pass_b(BProb* P, const Tile* __re
             gl[m] = 0.f;
         }
         double rr = 0.0, ff = 0.0, bb = 0.0;
-        for (int i = T.r0 + warp; i < T.r1; i += nw) {
-            if constexpr (MODE == 0) {
-                const float* row = static_cast<const float*>(q.Ain) + int64_t(i) * q.lda_in;
-                float a[M], dot = 0.f;
+        float rrf = 0.f, fff = 0.f, bbf = 0.f;
+        const float* Af = static_cast<const float*>(MODE == 0 ? q.Ain : q.A);
+        const int64_t ldf = MODE == 0 ? q.lda_in : q.lda;
+        for (int i0 = T.r0 + warp * R; i0 < T.r1; i0 += nw * R) {
+            if constexpr (!F64) {
+                float a[R][M];
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const int j = lane + 32 * m;
-                    a[m] = j < k ? row[j] : 0.f;
-                    dot += a[m] * (j < k ? yh[j] : 0.f);
+                for (int r = 0; r < R; ++r) {
+                    const bool valid = i0 + r < T.r1;
+                    const float* row = Af + int64_t(i0 + r) * ldf;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int j = lane + 32 * m;
+                        a[r][m] = (m < mk && valid && j < k) ? row[j] : 0.f;
+                    }
                 }
+                if constexpr (MODE == 0) {
+                    float p[R];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                    for (int r = 0; r < R; ++r) {
+                        p[r] = 0.f;
 #pragma unroll
-                for (int m = 0; m < M; ++m) gh[m] += dot * a[m];
-            } else if constexpr (MODE == 3) {
-                const float* row = static_cast<const float*>(q.A) + int64_t(i) * q.lda;
-                float a[M], hi = 0.f, lo = 0.f, sq = 0.f;
+                        for (int m = 0; m < M; ++m)
+                            if (m < mk) p[r] = fmaf(a[r][m], yh[lane + 32 * m], p[r]);
+                    }
+                    const float w = reduce_scatter<R, float>(p, lane);
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const int j = lane + 32 * m;
-                    a[m] = j < k ? row[j] : 0.f;
-                    if (j < k) df_acc(hi, lo, a[m], yh[j], yl[j]);
-                    sq += a[m] * a[m];
+                    for (int r = 0; r < R; ++r) {
+                        const float wr = __shfl_sync(kFull, w, row_owner<R>(r));
+#pragma unroll
+                        for (int m = 0; m < M; ++m)
+                            if (m < mk) gh[m] = fmaf(wr, a[r][m], gh[m]);
+                    }
+                } else {  // MODE 3
+                    float ph[R], pl[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        ph[r] = 0.f;
+                        pl[r] = 0.f;
+#pragma unroll
+                        for (int m = 0; m < M; ++m)
+                            if (m < mk) {
+                                const int j = lane + 32 * m;
+                                df_acc(ph[r], pl[r], a[r][m], yh[j], yl[j]);
+                                fff = fmaf(a[r][m], a[r][m], fff);
+                            }
+                    }
+                    float dh, dl;
+                    reduce_scatter_df4(ph, pl, lane, dh, dl);
+                    // this lane's row: r = b - a.x in double-float
+                    const int rho = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                    const int irow = i0 + rho;
+                    float rh = 0.f, rl = 0.f;
+                    if (irow < T.r1) {
+                        const float2 bs = q.bsplit[irow];
+                        float s, e;
+                        two_sum(bs.x, -dh, s, e);
+                        e += bs.y - dl;
+                        rh = s + e;
+                        rl = e - (rh - s);
+                        if ((lane & 7) == 0) {
+                            rrf = fmaf(rh, rh, rrf);
+                            bbf = fmaf(bs.x, bs.x, bbf);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float wh = __shfl_sync(kFull, rh, row_owner<R>(r));
+                        const float wl = __shfl_sync(kFull, rl, row_owner<R>(r));
+#pragma unroll
+                        for (int m = 0; m < M; ++m)
+                            if (m < mk) df_acc(gh[m], gl[m], a[r][m], wh, wl);
+                    }
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
-                    const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
-                    df_merge(hi, lo, oh, ol);
-                }
-                const double r = q.b[i] - (double(hi) + double(lo));
-                rr += r * r;
-                if (want_frob) {
-                    ff += double(sq);
-                    if (lane == 0) bb += q.b[i] * q.b[i];
-                }
-                const float rh = float(r), rl = float(r - double(rh));
-#pragma unroll
-                for (int m = 0; m < M; ++m) df_acc(gh[m], gl[m], a[m], rh, rl);
             } else {
-                double a[M], dot = 0.0;
-                if (q.a_f32) {
-                    const float* row = static_cast<const float*>(q.A) + int64_t(i) * q.lda;
+                double a[R][M];
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const int j = lane + 32 * m;
-                        a[m] = j < k ? double(row[j]) : 0.0;
-                    }
-                } else {
-                    const double* row = static_cast<const double*>(q.A) + int64_t(i) * q.lda;
+                for (int r = 0; r < R; ++r) {
+                    const bool valid = i0 + r < T.r1;
+                    if (q.a_f32) {
+                        const float* row = static_cast<const float*>(q.A) + int64_t(i0 + r) * q.lda;
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const int j = lane + 32 * m;
-                        a[m] = j < k ? row[j] : 0.0;
+                        for (int m = 0; m < M; ++m) {
+                            const int j = lane + 32 * m;
+                            a[r][m] = (m < mk && valid && j < k) ? double(row[j]) : 0.0;
+                        }
+                    } else {
+                        const double* row = static_cast<const double*>(q.A) + int64_t(i0 + r) * q.lda;
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            const int j = lane + 32 * m;
+                            a[r][m] = (m < mk && valid && j < k) ? row[j] : 0.0;
+                        }
                     }
                 }
+                double p[R];
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const int j = lane + 32 * m;
-                    dot += a[m] * (j < k ? ys[j] : 0.0);
+                for (int r = 0; r < R; ++r) {
+                    p[r] = 0.0;
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (m < mk) p[r] = fma(a[r][m], ys[lane + 32 * m], p[r]);
                 }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                double w = dot;
+                double w = reduce_scatter<R, double>(p, lane);
                 if constexpr (MODE == 2) {
-                    w = q.b[i] - dot;
-                    rr += w * w;
+                    const int irow = i0 + ((lane >> 4) & 1);
+                    if (irow < T.r1) {
+                        const double bi = q.b[irow];
+                        w = bi - w;
+                        if ((lane & 15) == 0) {
+                            rr += w * w;
+                            bb += bi * bi;
+                        }
+                    } else {
+                        w = 0.0;
+                    }
                     if (want_frob) {
 #pragma unroll
-                        for (int m = 0; m < M; ++m) ff += a[m] * a[m];
-                        if (lane == 0) bb += q.b[i] * q.b[i];
+                        for (int r = 0; r < R; ++r)
+#pragma unroll
+                            for (int m = 0; m < M; ++m)
+                                if (m < mk) ff = fma(a[r][m], a[r][m], ff);
                     }
                 }
 #pragma unroll
-                for (int m = 0; m < M; ++m) g[m] += w * a[m];
+                for (int r = 0; r < R; ++r) {
+                    const double wr = __shfl_sync(kFull, w, row_owner<R>(r));
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (m < mk) g[m] = fma(wr, a[r][m], g[m]);
+                }
             }
+        }
+        if constexpr (MODE == 3) {
+            rr = double(rrf);
+            ff = double(fff);
+            bb = double(bbf);
         }
 #pragma unroll
         for (int m = 0; m < M; ++m) {
@@ -307,8 +445,9 @@ __global__ void __launch_bounds__(kBThreads) k_pass_b(BProb* P, const Tile* __re
         if (MODE >= 2) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                rr += __shfl_xor_sync(0xffffffffu, rr, o);
-                ff += __shfl_xor_sync(0xffffffffu, ff, o);
+                rr += __shfl_xor_sync(kFull, rr, o);
+                ff += __shfl_xor_sync(kFull, ff, o);
+                bb += __shfl_xor_sync(kFull, bb, o);
             }
             if (lane == 0) {
                 ss[warp][0] = rr;
@@ -412,7 +551,7 @@ __global__ void k_cg_init_b(BProb* P, const int* __restrict__ active) {
     }
 }
 
-__global__ void k_cg_step_b(BProb* P, double tol) {
+__global__ void k_cg_step_b(BProb* P, double tol, unsigned int* running) {
     __shared__ double red[32];
     const BProb& q = P[blockIdx.x];
     if (q.cg[2] != 0.0) return;
@@ -438,6 +577,7 @@ __global__ void k_cg_step_b(BProb* P, double tol) {
         q.cg[0] = rho_new;
         q.cg[3] += 1.0;
         if (!(pAp > 0.0) || rho_new <= tol * tol * q.cg[1]) q.cg[2] = 1.0;
+        else atomicAdd(running, 1u);
     }
 }
 
@@ -461,6 +601,14 @@ __global__ void k_to_colmajor_b(const S* __restrict__ SA, const double* __restri
     if (idx >= int64_t(d) * (k + 1)) return;
     const int c = int(idx / d), i = int(idx - int64_t(c) * d);
     W[idx] = c < k ? double(SA[int64_t(i) * k + c]) : Sb[i];
+}
+
+__global__ void k_split_vec(const double* __restrict__ b, int64_t n, float2* __restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = b[i];
+    const float h = float(v);
+    out[i] = make_float2(h, float(v - double(h)));
 }
 
 __global__ void k_f32_to_f64(const float* __restrict__ A, int64_t n, int k, int64_t lda, double* __restrict__ B) {
@@ -543,6 +691,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         add(size_t(q.ntiles) * 3 * 8);
         const bool sk_copy = (opts->sketch_dtype == RSK_F64) != (pr.a_dtype == RSK_F64);
         const bool in_copy = q.in_f32 && !q.a_f32;
+        add(size_t(pr.n) * 8);  // b split into FP32 pairs (double-float residual pass)
         if (sk_copy) add(size_t(pr.n) * pr.k * (opts->sketch_dtype == RSK_F64 ? 8 : 4));
         if (in_copy && !(sk_copy && opts->sketch_dtype == RSK_F32)) add(size_t(pr.n) * pr.k * 4);
         const size_t sk = sketch_index_bytes(pr.n, d, zeta) +
@@ -557,7 +706,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     add(size_t(count) * 4);          // active flags
     add(size_t(count) * 3 * 8);      // eta, rnorm, fnorm
     add(size_t(count) * 8);          // CG iteration counts
-    add(256);                        // queue counter
+    add(256);                        // queue counters
+    add(size_t(count) * 4);          // QR order (decreasing d k^2)
     add(size_t(kStreams) * max_sketch_scratch);
     rsk_status st = ensure_workspace(h, bytes + 8192, stream);
     if (st != RSK_OK) return st;
@@ -576,6 +726,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         q.cg = cv.take<double>(8);
         q.part = cv.take<double>(size_t(q.ntiles) * q.k);
         q.part_s = cv.take<double>(size_t(q.ntiles) * 3);
+        q.bsplit = cv.take<float2>(size_t(pr.n));
         const bool sk_copy = (opts->sketch_dtype == RSK_F64) != (pr.a_dtype == RSK_F64);
         const bool in_copy = q.in_f32 && !q.a_f32;
         if (sk_copy) sk_copy_ptr[i] = cv.take<char>(size_t(pr.n) * pr.k * (opts->sketch_dtype == RSK_F64 ? 8 : 4));
@@ -591,7 +742,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     int* dactive = cv.take<int>(size_t(count));
     double* deta = cv.take<double>(size_t(count) * 3);
     double* diters = cv.take<double>(size_t(count));
-    unsigned int* dqueue = cv.take<unsigned int>(64);
+    unsigned int* dqueue = cv.take<unsigned int>(64);   // [0] tile queue, [16] QR queue, [32] CG running
+    int* dorder = cv.take<int>(size_t(count));
     char* sk_scratch = cv.take<char>(size_t(kStreams) * max_sketch_scratch);
 
     // all work runs on the handle's internal streams, ordered after the caller's stream
@@ -608,6 +760,12 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     std::vector<int> act(count, 1);
     RSK_CUDA_TRY(h, cudaMemcpyAsync(dactive, act.data(), 4 * size_t(count), cudaMemcpyHostToDevice, main_s));
     RSK_CUDA_TRY(h, cudaMemsetAsync(diters, 0, 8 * size_t(count), main_s));
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b_) {
+        return double(hp[a].d) * hp[a].k * hp[a].k > double(hp[b_].d) * hp[b_].k * hp[b_].k;
+    });
+    RSK_CUDA_TRY(h, cudaMemcpyAsync(dorder, order.data(), 4 * size_t(count), cudaMemcpyHostToDevice, main_s));
     RSK_CUDA_TRY(h, cudaEventRecord(ev_done, main_s));
 
     // ---- sketches, spread over the stream pool
@@ -639,12 +797,13 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
             k_f64_to_f32<<<cgrid, 256, 0, s>>>((const double*)pr.A, pr.n, q.k, pr.lda, (float*)const_cast<void*>(q.Ain));
             RSK_LAUNCH_CHECK(h);
         }
+        k_split_vec<<<unsigned((pr.n + 255) / 256), 256, 0, s>>>(pr.b, pr.n, const_cast<float2*>(q.bsplit));
+        RSK_LAUNCH_CHECK(h);
         st = sketch_build_index(h, pr.n, q.d, zeta, opts->seed + uint64_t(i), index, s);
         if (st == RSK_OK)
             st = sketch_apply_built(h, index, pr.n, q.d, zeta, A_sk, sa_dt, pr.k, lda_sk, SA,
                                     sa_dt == RSK_F64 ? RSK_F64 : RSK_F32, pr.k, parts, s);
-        if (st == RSK_OK)
-            st = sketch_apply_built(h, index, pr.n, q.d, zeta, pr.b, RSK_F64, 1, 1, Sb, RSK_F64, 1, parts, s);
+        if (st == RSK_OK) st = sketch_apply_vec_built(h, index, pr.n, q.d, zeta, pr.b, Sb, s);
         if (st != RSK_OK) return st;
         const unsigned gw = unsigned((int64_t(q.d) * (q.k + 1) + 255) / 256);
         if (sa_dt == RSK_F64) k_to_colmajor_b<double><<<gw, 256, 0, s>>>(SA, Sb, q.d, q.k, q.W);
@@ -658,7 +817,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
 
     // ---- QR, R^{-1}, warm start
     const int pr0 = prof_begin(h, main_s, RSK_KERNEL_DENSE);
-    k_qr_b<<<count, 512, 0, main_s>>>(dP);
+    RSK_CUDA_TRY(h, cudaMemsetAsync(dqueue + 16, 0, 4, main_s));
+    k_qr_b<<<std::min(count, h->num_sms), 512, 0, main_s>>>(dP, dorder, count, dqueue + 16);
     k_rinv_b<<<count, 512, 0, main_s>>>(dP);
     k_trmv_b<<<count, 256, 0, main_s>>>(dP, 0, -1, 0, 0);
     prof_end(h, main_s, pr0);
@@ -674,6 +834,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     std::vector<double> heta(size_t(count) * 3);
     std::vector<int> steps(count, 0);
     cudaGraphExec_t cg_exec = nullptr;
+    volatile unsigned int* running_host = reinterpret_cast<volatile unsigned int*>(h->host_flags + 4);
+    *running_host = 1u;
     int step = 0;
     for (step = 0;; ++step) {
         RSK_CUDA_TRY(h, cudaMemsetAsync(dqueue, 0, 4, main_s));
@@ -713,6 +875,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
             cudaGraph_t graph;
             RSK_CUDA_TRY(h, cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
             cudaMemsetAsync(dqueue, 0, 4, main_s);
+            cudaMemsetAsync(dqueue + 32, 0, 4, main_s);
             k_trmv_b<<<count, 256, 0, main_s>>>(dP, 0, 5, 7, 1);  // t = R^{-1} p
             if (opts->inner_dtype == RSK_F32) {
                 k_cast_b<<<count, 256, 0, main_s>>>(dP, 7);
@@ -722,14 +885,24 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
             }
             k_reduce_b<<<count, 256, 0, main_s>>>(dP, dactive, 1, 0, 1, 0);   // g = A^T A t
             k_trmv_b<<<count, 256, 0, main_s>>>(dP, 1, 1, 6, 1);             // s = R^{-T} g
-            k_cg_step_b<<<count, 256, 0, main_s>>>(dP, inner_tol);
+            k_cg_step_b<<<count, 256, 0, main_s>>>(dP, inner_tol, dqueue + 32);
+            cudaMemcpyAsync(const_cast<unsigned int*>(running_host), dqueue + 32, 4, cudaMemcpyDeviceToHost, main_s);
             const cudaError_t ce = cudaStreamEndCapture(main_s, &graph);
             if (ce != cudaSuccess) return fail(h, RSK_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
             RSK_CUDA_TRY(h, cudaGraphInstantiate(&cg_exec, graph, 0));
             cudaGraphDestroy(graph);
         }
         const int pr2 = prof_begin(h, main_s, RSK_KERNEL_DENSE);
-        for (int it = 0; it < max_inner; ++it) RSK_CUDA_TRY(h, cudaGraphLaunch(cg_exec, main_s));
+        // replay until no problem's CG is running; the count is copied to pinned memory at the end
+        // of each replay, and the host reads it two replays behind so the GPU never waits for it
+        for (int it = 0; it < max_inner; ++it) {
+            if (it >= 2) {
+                RSK_CUDA_TRY(h, cudaEventSynchronize(h->flag_ev[it & 1]));
+                if (*running_host == 0u) break;
+            }
+            RSK_CUDA_TRY(h, cudaGraphLaunch(cg_exec, main_s));
+            RSK_CUDA_TRY(h, cudaEventRecord(h->flag_ev[it & 1], main_s));
+        }
         prof_end(h, main_s, pr2);
         k_trmv_b<<<count, 256, 0, main_s>>>(dP, 0, 3, 7, 0);  // t = R^{-1} z
         k_update_b<<<count, 256, 0, main_s>>>(dP, dactive, diters);

@@ -760,6 +760,42 @@ rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, i
     const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dt);
     return apply_with_index(h, offs, ents, A, a_dt, n, k, lda, int(d), zeta, SA, sa_dt, ldsa, partials, p, stream);
 }
+// S b for one FP64 vector from a built index: one warp per sketch row, lanes stride over the
+// chunks, a fixed-shape warp reduction (the result does not depend on scheduling).
+__global__ void k_apply_vec(const uint16_t* __restrict__ offs, const uint16_t* __restrict__ ents,
+                            const double* __restrict__ b, int64_t n, int d, int zeta, int C, int pitch,
+                            int64_t nch, double* __restrict__ out) {
+    const int r = int(blockIdx.x) * (blockDim.x >> 5) + int(threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= d) return;
+    double acc = 0.0;
+    for (int64_t ch = lane; ch < nch; ch += 32) {
+        const uint16_t* o = offs + ch * pitch;
+        const uint16_t* e = ents + ch * int64_t(C) * zeta;
+        const int64_t base = ch * C;
+        for (int t = o[r]; t < o[r + 1]; ++t) {
+            const uint16_t v = e[t];
+            const double x = b[base + (v & 0x7fff)];
+            acc += (v & 0x8000) ? -x : x;
+        }
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    if (lane == 0) out[r] = acc / sqrt(double(zeta));
+}
+rsk_status sketch_apply_vec_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta,
+                                  const double* b, double* Sb, cudaStream_t stream) {
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    if (!b || !Sb) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null vector");
+    Carver cv(const_cast<void*>(index_mem));
+    const uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
+    const uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
+    k_apply_vec<<<unsigned((d + 7) / 8), 256, 0, stream>>>(offs, ents, b, n, int(d), zeta, chunk_rows(zeta),
+                                                          offsets_pitch(int(d)), n_chunks_of(n, zeta), Sb);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
 // Draw rows/signs of a sparse sign matrix from any Philox stream (the RSVD test matrix uses stream 3).
 rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, uint32_t stream_id,
                            int32_t* rows, uint32_t* signs, cudaStream_t stream) {

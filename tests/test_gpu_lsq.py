@@ -24,7 +24,8 @@ def solve(rsk, A, b, d, **kw):
     return rsk.rsk_lstsq_sketch_precond(A, b, d, **kw)
 
 
-@pytest.mark.parametrize("sketch,inner", [(torch.float64, torch.float64), (torch.float32, torch.float64)])
+@pytest.mark.parametrize("sketch,inner", [(torch.float64, torch.float64), (torch.float32, torch.float64),
+                                          (torch.float32, "f32x2")])
 def test_ill_conditioned_fp64_truth(rsk, sketch, inner):
     # A = Q_U diag(logspace(0, -8)) V^T, b = A x* + 1e-6 noise: the least-squares workload shape
     A, b, _ = synthetic.lsq_problem(40000, 60, seed=3, cond_exp=8.0, device="cpu")
@@ -39,6 +40,14 @@ def test_ill_conditioned_fp64_truth(rsk, sketch, inner):
     rn = np.linalg.norm(b.numpy() - A.numpy() @ x.cpu().numpy())
     rs = np.linalg.norm(b.numpy() - A.numpy() @ xs)
     assert abs(rn - rs) <= 1e-8 * rs
+
+
+def test_double_float_inner_fp32_storage(rsk):
+    # FP32 storage with an all-zero lo array; pins the split path that converts instead of splitting
+    A, b = synthetic.batched_problem(30000, 64, seed=7, device="cpu", dtype=torch.float32)
+    x, info = solve(rsk, A.cuda(), b.cuda(), 256, sketch_dtype=torch.float32, inner_dtype="f32x2")
+    eta = olsq.backward_error(A.double().numpy(), b.numpy(), x.cpu().numpy())
+    assert eta <= 1e-10, (eta, info)
 
 
 def test_column_scaled_fp32_storage_mixed(rsk):

@@ -33,14 +33,22 @@ def make_batch(count, seed, n_lo=1024, n_hi=20000, k_lo=4, k_hi=64):
 
 
 @pytest.mark.parametrize("sketch,inner", [(torch.float32, torch.float32), (torch.float64, torch.float64)])
-def test_batched_backward_error(rsk, sketch, inner):
-    As, bs = make_batch(24, 3)
+@pytest.mark.parametrize("kind", ["narrow", "wide"])
+def test_batched_backward_error(rsk, sketch, inner, kind):
+    # narrow: k_i <= 64 (the four-block column path); wide: k_i in [100, 256] (eight blocks)
+    As, bs = make_batch(24, 3) if kind == "narrow" else make_batch(8, 5, n_lo=2000, n_hi=12000, k_lo=100, k_hi=256)
     xs, infos = rsk.rsk_lstsq_sketch_precond_batched([A.cuda() for A in As], [b.cuda() for b in bs],
                                                      sketch_dtype=sketch, inner_dtype=inner, seed=7)
     for A, b, x, info in zip(As, bs, xs, infos):
-        eta = olsq.backward_error(A.double().numpy(), b.numpy(), x.cpu().numpy())
+        A64, b64, x64 = A.double().numpy(), b.numpy(), x.cpu().numpy()
+        eta = olsq.backward_error(A64, b64, x64)
         assert eta <= 1e-10, (eta, info)
         assert info["status"] == "RSK_OK"
+        # the reported norms are those of the returned x: ||b - A x|| and ||A||_F
+        rn = np.linalg.norm(b64 - A64 @ x64)
+        assert abs(info["residual_norm"] - rn) <= 1e-5 * rn, (info["residual_norm"], rn)
+        fn = np.linalg.norm(A64)
+        assert abs(info["frobenius_norm"] - fn) <= 1e-5 * fn, (info["frobenius_norm"], fn)
 
 
 def test_batched_matches_single(rsk):
