@@ -263,10 +263,11 @@ def timed_calls(fn, reps, torch, dev, after_warmup=None):
 
 def bench_lsq(rsk, synthetic, torch, dev, rank, world, reps):
     """Single least-squares workload (A = Q_U diag(logspace(0,-8)) V^T, 2^20 x 500 FP64, b = A x* +
-    1e-6 noise, d = 2000, zeta = 8): the mixed form (FP32 sketch, double-float inner CG, FP64-accuracy
-    refinement) against the plain FP64 form (FP64 sketch, FP64 inner CG), each to eta <= 1e-10."""
+    1e-6 noise, d = 2000, zeta = 8): the mixed form (A split once into FP32 pairs; double-float sketch
+    and CG operator on FP32 units; FP64 residual refinement) against the plain FP64 form (FP64 sketch,
+    FP64 CG), each to eta <= 1e-10."""
     A, b, _ = synthetic.lsq_problem(LSQ_N, LSQ_K, seed=31 + rank, cond_exp=8.0, noise=1e-6, device=dev)
-    forms = {"mixed": (torch.float32, "f32x2"), "fp64": (torch.float64, torch.float64)}
+    forms = {"mixed": ("f32x2", "f32x2"), "fp64": (torch.float64, torch.float64)}
     res = {}
     for name, (sk, inner) in forms.items():
         ms, (x, info) = timed_calls(lambda: rsk.rsk_lstsq_sketch_precond(A, b, LSQ_D, zeta=ZETA, seed=7,

@@ -48,8 +48,10 @@ typedef enum {
     RSK_ERR_INTERNAL = 7
 } rsk_status;
 
-/* RSK_F32X2 is a pair of FP32 arrays (hi, lo) with a = hi + lo (about 48 significant bits); it is
- * accepted only as the inner precision of the least-squares solvers (double-float arithmetic). */
+/* RSK_F32X2 is the interleaved double-float form: each element is two FP32 values (hi, lo), 8
+ * bytes, value hi + lo (about 48 significant bits).  Accepted as A by rsk_sparse_sign_apply
+ * (double-float accumulation, FP64 or FP32 result) and as sketch or inner precision of the
+ * single-problem least-squares solver; rsk_split_pairs produces it from FP64. */
 typedef enum { RSK_F64 = 0, RSK_F32 = 1, RSK_BF16 = 2, RSK_F32X2 = 3 } rsk_dtype;
 
 typedef struct rsk_handle rsk_handle;
@@ -178,6 +180,14 @@ rsk_status rsk_srtt_draw(rsk_handle* h, int64_t n, int64_t d, uint64_t seed, int
 rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
                           int64_t d, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream);
 
+/* Split an FP64 matrix (n x k, row-major, lda >= k) into the interleaved F32X2 form P (n x k pairs,
+ * packed: 2 k floats per row): hi = FP32 round-to-nearest-even of a, lo = FP32 round-to-nearest-
+ * even of a - hi, computed with integer operations.  Values outside the FP32 normal range are
+ * flushed (|a| < 2^-126 -> (+-0, 0); |a| > FLT_MAX -> +-inf; lo < 2^-126 -> 0).  Not a step of the
+ * paper: the storage form of the double-float solvers.  Device pointers; asynchronous. */
+rsk_status rsk_split_pairs(rsk_handle* h, const double* A, int64_t n, int64_t k, int64_t lda, float* P,
+                           cudaStream_t stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Sketch-and-precondition least squares, min_x ||A x - b||_2 (rows a5-a7).
  * Paper: sketch-and-solve (Alg. 3, Sec. 2.3) for the warm start; sketch-and-precondition is named
@@ -190,15 +200,17 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
  *   inner_dtype, then x += R^{-1} z.
  * Precision notes: inner_dtype F32 converges when u_32 * kappa(A) is well below 1 or when A's
  * ill-conditioning is a column scaling; for kappa(A) ~ 1e8 with mixed columns use F64 or F32X2.
- * With F32X2 the library splits A into FP32 hi/lo arrays once per solve and runs the CG passes in
- * double-float arithmetic on FP32 units; the residual passes read an F64 A as stored (48 bits of
- * hi + lo would move the fixed point) and an F32 A through the same double-float pass.
+ * F32X2 (sketch or inner): A is split once per solve into interleaved (hi, lo) pairs; the sketch
+ * then accumulates in double-float arithmetic and the CG operator runs in double-float arithmetic,
+ * both on FP32 units.  The residual passes read an F64 A as stored (48 bits of hi + lo would move
+ * the fixed point) and an F32 A (exact as (a, 0)) through the double-float pass.
  * ------------------------------------------------------------------------------------------- */
 typedef struct {
     int64_t d;               /* sketch rows (k <= d <= 8192) */
     int32_t zeta;            /* nonzeros per column of S */
     uint64_t seed;           /* Philox seed of S */
-    rsk_dtype sketch_dtype;  /* precision A is sketched in: F64, F32 or BF16 (FP32 accumulation) */
+    rsk_dtype sketch_dtype;  /* precision A is sketched in: F64, F32 or BF16 (FP32 accumulation),
+                                F32X2 (double-float accumulation of the split pairs) */
     rsk_dtype inner_dtype;   /* precision of the CG operator: F64, F32, or F32X2 (double-float pair) */
     double tol_backward;     /* target eta (default 1e-10 when <= 0) */
     int32_t max_refine;      /* refinement steps; 0 returns the warm start x0; < 0 selects 20 */

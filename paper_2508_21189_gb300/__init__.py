@@ -111,6 +111,34 @@ def rsk_sparse_sign_apply(A, d, zeta, seed, out_dtype=torch.float32, out=None, s
     return out
 
 
+def rsk_split_pairs(A, stream=None):
+    """Interleaved double-float form of a CUDA FP64 matrix: float32 tensor (n, k, 2) = (hi, lo)."""
+    _matrix(A, "A")
+    if A.dtype != torch.float64:
+        raise TypeError("rsk_split_pairs takes FP64 A")
+    n, k = A.shape
+    P = torch.empty(n, k, 2, dtype=torch.float32, device=A.device)
+    h = handle(A.device)
+    _check(load().rsk_split_pairs(h, A.data_ptr(), n, k, A.stride(0), P.data_ptr(), _stream(stream)), h)
+    return P
+
+
+def rsk_sparse_sign_apply_pairs(P, d, zeta, seed, out_dtype=torch.float64, out=None, stream=None):
+    """SA = S @ (hi + lo) for interleaved pairs P (float32, n x k x 2), double-float accumulation."""
+    if not P.is_cuda or P.dtype != torch.float32 or P.dim() != 3 or P.shape[2] != 2 or P.stride(2) != 1 \
+            or P.stride(1) != 2:
+        raise ValueError("P must be a CUDA float32 tensor (n, k, 2) with packed pairs")
+    n, k = P.shape[0], P.shape[1]
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=P.device)
+    _matrix(out, "out")
+    h = handle(P.device)
+    st = load().rsk_sparse_sign_apply(h, P.data_ptr(), RSK_F32X2, n, k, P.stride(0) // 2, d, zeta, seed,
+                                      out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
 class SparseSignPlan:
     """rsk_sparse_sign_plan_*: keeps one S's inverted index on the device for reuse."""
 

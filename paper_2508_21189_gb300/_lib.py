@@ -34,6 +34,7 @@ SIGNATURES = {
     "rsk_sparse_sign_plan_destroy": [c_p, c_p, c_p],
     "rsk_srtt_draw": [c_p, c_i64, c_i64, c_u64, c_p, c_p, c_p],
     "rsk_srtt_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_split_pairs": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_p],
     "rsk_lstsq_sketch_precond": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p],
     "rsk_lstsq_sketch_precond_batched": [c_p, c_i32, c_p, c_p, c_p, c_p],
     "rsk_rsvd": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_p, c_p, c_p, c_p],

@@ -64,8 +64,10 @@ struct Carver {
     static size_t round(size_t bytes) { return (bytes + 255) & ~size_t(255); }
 };
 
-inline size_t dtype_size(rsk_dtype t) { return t == RSK_F64 ? 8 : (t == RSK_F32 ? 4 : 2); }
+inline size_t dtype_size(rsk_dtype t) { return (t == RSK_F64 || t == RSK_F32X2) ? 8 : (t == RSK_F32 ? 4 : 2); }
 inline bool dtype_ok(int t) { return t == RSK_F64 || t == RSK_F32 || t == RSK_BF16; }
+// Sketch inputs may also be interleaved (hi, lo) FP32 pairs.
+inline bool sketch_dtype_ok(int t) { return dtype_ok(t) || t == RSK_F32X2; }
 
 // Profiling brackets around one kernel launch (no-ops unless rsk_profile_enable(h, 1)).
 int prof_begin(rsk_handle* h, cudaStream_t stream, int kernel);
@@ -124,7 +126,7 @@ rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, i
 namespace rskd {
 
 // Roughly a few seconds at most before a wait gives up and records RSK_DEV_TIMEOUT.
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -163,7 +165,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned int* status) {
     for (uint32_t it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (it > 32) __nanosleep(128);
+        if (it > 1024) __nanosleep(64);
     }
     atomicOr(status, RSK_DEV_TIMEOUT);
     return false;

@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
         Acc w = dot;
         if constexpr (RESID) {
             w = Acc(b[i]) - dot;
-            rr += double(w) * double(w);
+            if (lane == 0) rr += double(w) * double(w);  // every lane holds the same r_i
             if (want_frob) {
 #pragma unroll
                 for (int m = 0; m < M; ++m) ff += double(a[m]) * double(a[m]);
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, 
     }
 }
 
-// ---- double-float pass on A = hi + lo (two FP32 arrays), y = yh + yl (FP32 pair) -------------
+// ---- double-float operator on interleaved (hi, lo) FP32 pairs ---------------------------------
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
     s = a + b;
     const float bb = s - a;
@@ -286,67 +286,144 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float oh, float ol)
     hi = s + e;
     lo = e - (hi - s);
 }
+__device__ __forceinline__ void df_xor_add(float& h, float& l, float sh, float sl, int o) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+    df_add(h, l, oh, ol);
+}
 
-// RESID: r_i = b_i - a_i . x, g += r_i a_i, rr, ff, bb.   CG: w_i = a_i . y, g += w_i a_i.
+// FP64 -> (hi, lo) with hi = RN32(a) and lo = RN32(a - hi), in integer arithmetic only (FP64
+// conversions run on the FP64 pipe, which is the scarce unit on this part).  Values outside the
+// FP32 normal range are flushed: |a| < 2^-126 gives (+-0, 0), |a| beyond FLT_MAX gives +-inf, a lo
+// below 2^-126 becomes 0 -- a normwise perturbation of at most 2^-126 per entry.
+__device__ __forceinline__ float2 split_pair(double a) {
+    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(a));
+    const uint32_t sign = uint32_t(u >> 63) << 31;
+    const int e = int((u >> 52) & 0x7ffu);
+    const unsigned long long m = u & 0xfffffffffffffull;
+    if (e == 0x7ff) return make_float2(__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f);
+    const int E = e - 1023;
+    if (E < -126) return make_float2(__uint_as_float(sign), 0.f);
+    if (E > 127) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const uint32_t mh = uint32_t(m >> 29);
+    const uint32_t rem = uint32_t(m & 0x1fffffffu);
+    const bool up = rem > 0x10000000u || (rem == 0x10000000u && (mh & 1u));
+    // a carry out of the significand moves into the exponent field (and to inf past FLT_MAX)
+    const uint32_t hb = (uint32_t(E + 127) << 23) + mh + (up ? 1u : 0u);
+    const float hi = __uint_as_float(sign | hb);
+    // a - hi = +rem * 2^(E-52) (rounded down) or -(2^29 - rem) * 2^(E-52) (rounded up), exactly
+    const uint32_t r = up ? (0x20000000u - rem) : rem;
+    if (r == 0u) return make_float2(hi, 0.f);
+    const uint32_t lsign = up ? (sign ^ 0x80000000u) : sign;
+    const int p = 31 - __clz(r);
+    int el = p + E - 52;
+    uint32_t ml;
+    if (p > 23) {
+        const int sh = p - 23;
+        ml = r >> sh;
+        const uint32_t rest = r & ((1u << sh) - 1u), half = 1u << (sh - 1);
+        if (rest > half || (rest == half && (ml & 1u))) ++ml;
+        if (ml == (1u << 24)) {
+            ml >>= 1;
+            ++el;
+        }
+    } else {
+        ml = r << (23 - p);
+    }
+    if (el < -126) return make_float2(hi, 0.f);
+    return make_float2(hi, __uint_as_float(lsign | (uint32_t(el + 127) << 23) | (ml & 0x7fffffu)));
+}
+
+// A (F64 or F32, lda) -> P (n x k interleaved pairs)
+template <typename T>
+__global__ void k_to_pairs(const T* __restrict__ A, int64_t n, int k, int64_t lda, float2* __restrict__ P) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n * k) return;
+    const int64_t i = idx / k, j = idx - i * k;
+    if constexpr (sizeof(T) == 8) P[idx] = split_pair(A[i * lda + j]);
+    else P[idx] = make_float2(float(A[i * lda + j]), 0.f);
+}
+
+// Fused pass over the pairs, two rows per warp at a time (partial dot products reduce-scattered
+// so lane L ends with row bit4(L)).  RESID: r_i = b_i - a_i . x (b as pairs too), g += r_i a_i,
+// ||r||^2, ||A||_F^2, ||b||^2.  CG: w_i = a_i . y, g += w_i a_i.
 template <int M, bool RESID>
-__global__ void __launch_bounds__(kPassThreads) k_pass_df(const float* __restrict__ Ah, const float* __restrict__ Al,
-                                                          int64_t n, int k, const double* __restrict__ y,
-                                                          const double* __restrict__ b, double* __restrict__ part,
-                                                          double* __restrict__ part_s, int want_frob) {
+__global__ void __launch_bounds__(kPassThreads) k_pass_pairs(const float2* __restrict__ P, int64_t n, int k,
+                                                             const double* __restrict__ y,
+                                                             const double* __restrict__ b,
+                                                             double* __restrict__ part,
+                                                             double* __restrict__ part_s, int want_frob) {
     extern __shared__ __align__(16) uint8_t dsm[];
     double* gs = reinterpret_cast<double*>(dsm);
     float* yh = reinterpret_cast<float*>(gs + size_t(kPassThreads / 32) * k);
-    float* yl = yh + k;
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        const double v = y[j];
+    float* yl = yh + 32 * M;
+    for (int j = threadIdx.x; j < 32 * M; j += blockDim.x) {
+        const double v = j < k ? y[j] : 0.0;
         const float h = float(v);
         yh[j] = h;
         yl[j] = float(v - double(h));
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int mk = (k + 31) >> 5;
     const int64_t r0 = int64_t(blockIdx.x) * n / gridDim.x, r1 = int64_t(blockIdx.x + 1) * n / gridDim.x;
-    float gh[M], gl[M], vh[M], vl[M];
+    float gh[M], gl[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-        gh[m] = gl[m] = 0.f;
-        const int j = lane + 32 * m;
-        vh[m] = j < k ? yh[j] : 0.f;
-        vl[m] = j < k ? yl[j] : 0.f;
-    }
-    double rr = 0.0, ff = 0.0, bb = 0.0;
-    for (int64_t i = r0 + warp; i < r1; i += nw) {
-        const float* rh = Ah + i * k;
-        const float* rl = Al + i * k;
-        float ah[M], al[M], dh = 0.f, dl = 0.f;
+    for (int m = 0; m < M; ++m) gh[m] = gl[m] = 0.f;
+    float rrf = 0.f, fff = 0.f, bbf = 0.f;
+    for (int64_t i0 = r0 + 2 * warp; i0 < r1; i0 += 2 * nw) {
+        float2 a[2][M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int j = lane + 32 * m;
-            ah[m] = j < k ? rh[j] : 0.f;
-            al[m] = j < k ? rl[j] : 0.f;
-            df_mac(dh, dl, ah[m], al[m], vh[m], vl[m]);
-        }
+        for (int r = 0; r < 2; ++r) {
+            const bool valid = i0 + r < r1;
+            const float2* row = P + (i0 + r) * int64_t(k);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, dh, o);
-            const float ol = __shfl_xor_sync(0xffffffffu, dl, o);
-            df_add(dh, dl, oh, ol);
-        }
-        double w = double(dh) + double(dl);
-        if constexpr (RESID) {
-            w = b[i] - w;
-            rr += w * w;
-            if (want_frob) {
-                float sq = 0.f;
-#pragma unroll
-                for (int m = 0; m < M; ++m) sq = fmaf(ah[m], ah[m], sq);
-                ff += double(sq);
-                if (lane == 0) bb += b[i] * b[i];
+            for (int m = 0; m < M; ++m) {
+                const int j = lane + 32 * m;
+                a[r][m] = (m < mk && valid && j < k) ? row[j] : make_float2(0.f, 0.f);
             }
         }
-        const float wh = float(w), wl = float(w - double(wh));
+        float ph[2] = {0.f, 0.f}, pl[2] = {0.f, 0.f};
 #pragma unroll
-        for (int m = 0; m < M; ++m) df_mac(gh[m], gl[m], ah[m], al[m], wh, wl);
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (m < mk) {
+                    const int j = lane + 32 * m;
+                    df_mac(ph[r], pl[r], a[r][m].x, a[r][m].y, yh[j], yl[j]);
+                    if (RESID && want_frob) fff = fmaf(a[r][m].x, a[r][m].x, fff);
+                }
+        // reduce-scatter: lanes with bit 4 clear keep row 0, set keep row 1
+        const bool b4 = lane & 16;
+        float dh = b4 ? ph[1] : ph[0], dl = b4 ? pl[1] : pl[0];
+        df_xor_add(dh, dl, b4 ? ph[0] : ph[1], b4 ? pl[0] : pl[1], 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) df_xor_add(dh, dl, dh, dl, o);
+        float wh = dh, wl = dl;
+        if constexpr (RESID) {
+            const int64_t irow = i0 + (b4 ? 1 : 0);
+            wh = wl = 0.f;
+            if (irow < r1) {
+                const double bi = b[irow];
+                const float bh = float(bi), bl = float(bi - double(bh));
+                float s_, e_;
+                two_sum_f(bh, -dh, s_, e_);
+                e_ += bl - dl;
+                wh = s_ + e_;
+                wl = e_ - (wh - s_);
+                if ((lane & 15) == 0) {
+                    rrf = fmaf(wh, wh, rrf);
+                    bbf = fmaf(bh, bh, bbf);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float w_h = __shfl_sync(0xffffffffu, wh, r << 4);
+            const float w_l = __shfl_sync(0xffffffffu, wl, r << 4);
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (m < mk) df_mac(gh[m], gl[m], a[r][m].x, a[r][m].y, w_h, w_l);
+        }
     }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -355,10 +432,12 @@ __global__ void __launch_bounds__(kPassThreads) k_pass_df(const float* __restric
     }
     __shared__ double ss[kPassThreads / 32][3];
     if constexpr (RESID) {
+        double rr = double(rrf), ff = double(fff), bb = double(bbf);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             rr += __shfl_xor_sync(0xffffffffu, rr, o);
             ff += __shfl_xor_sync(0xffffffffu, ff, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
         }
         if (lane == 0) {
             ss[warp][0] = rr;
@@ -368,9 +447,9 @@ __global__ void __launch_bounds__(kPassThreads) k_pass_df(const float* __restric
     }
     __syncthreads();
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += gs[size_t(w) * k + j];
-        part[size_t(blockIdx.x) * k + j] = s;
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += gs[size_t(w) * k + j];
+        part[size_t(blockIdx.x) * k + j] = acc;
     }
     if (RESID && threadIdx.x == 0) {
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -383,18 +462,6 @@ __global__ void __launch_bounds__(kPassThreads) k_pass_df(const float* __restric
         part_s[3 * blockIdx.x + 1] = a1;
         part_s[3 * blockIdx.x + 2] = a2;
     }
-}
-
-// A (F64, lda) -> hi, lo FP32 arrays (n x k) with a = hi + lo
-__global__ void k_split_df(const double* __restrict__ A, int64_t n, int k, int64_t lda, float* __restrict__ hi,
-                           float* __restrict__ lo) {
-    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= n * k) return;
-    const int64_t i = idx / k, j = idx - i * k;
-    const double a = A[i * lda + j];
-    const float h = float(a);
-    hi[idx] = h;
-    lo[idx] = float(a - double(h));
 }
 
 template <typename Acc>
@@ -552,31 +619,46 @@ static rsk_status launch_pass(rsk_handle* h, const T* A, int64_t n, int k, int64
     return RSK_OK;
 }
 
-static rsk_status launch_pass_df(rsk_handle* h, const float* Ah, const float* Al, int64_t n, int k, const double* y,
-                                 const double* b, double* parts, double* parts_s, int nparts, bool resid, bool frob,
-                                 cudaStream_t stream) {
+static rsk_status launch_pass_pairs(rsk_handle* h, const float2* P, int64_t n, int k, const double* y,
+                                    const double* b, double* parts, double* parts_s, int nparts, bool resid, bool frob,
+                                    cudaStream_t stream) {
     const int M = (k + 31) / 32;
-    const size_t smem = size_t(kPassThreads / 32) * k * 8 + size_t(k) * 8;
+    const int Mt = M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : 32;
+    const size_t smem = size_t(kPassThreads / 32) * k * 8 + size_t(32) * Mt * 4 * 2;
     rsk_status err = RSK_OK;
     auto go = [&](auto kern) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
             err = RSK_ERR_CUDA;
             return;
         }
-        kern<<<unsigned(nparts), kPassThreads, smem, stream>>>(Ah, Al, n, k, y, b, parts, parts_s, frob ? 1 : 0);
+        kern<<<unsigned(nparts), kPassThreads, smem, stream>>>(P, n, k, y, b, parts, parts_s, frob ? 1 : 0);
     };
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_DENSE);
-    if (M <= 4) resid ? go(k_pass_df<4, true>) : go(k_pass_df<4, false>);
-    else if (M <= 8) resid ? go(k_pass_df<8, true>) : go(k_pass_df<8, false>);
-    else if (M <= 16) resid ? go(k_pass_df<16, true>) : go(k_pass_df<16, false>);
-    else resid ? go(k_pass_df<32, true>) : go(k_pass_df<32, false>);
+    if (Mt == 4) resid ? go(k_pass_pairs<4, true>) : go(k_pass_pairs<4, false>);
+    else if (Mt == 8) resid ? go(k_pass_pairs<8, true>) : go(k_pass_pairs<8, false>);
+    else if (Mt == 16) resid ? go(k_pass_pairs<16, true>) : go(k_pass_pairs<16, false>);
+    else resid ? go(k_pass_pairs<32, true>) : go(k_pass_pairs<32, false>);
     rsk::prof_end(h, stream, pr);
-    if (err != RSK_OK) return rsk::fail(h, err, "cudaFuncSetAttribute failed for the double-float pass");
+    if (err != RSK_OK) return rsk::fail(h, err, "cudaFuncSetAttribute failed for the pair pass");
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
 
 }  // namespace rsk
+
+extern "C" rsk_status rsk_split_pairs(rsk_handle* h, const double* A, int64_t n, int64_t k, int64_t lda, float* P,
+                                      cudaStream_t stream) {
+    using namespace rsk;
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!A || !P) return fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (n < 0 || k < 0 || (k > 0 && lda < k) || n * k >= (int64_t(1) << 40))
+        return fail(h, RSK_ERR_INVALID_ARG, "need n, k >= 0 and lda >= k");
+    if (n == 0 || k == 0) return RSK_OK;
+    k_to_pairs<double><<<unsigned((n * k + 255) / 256), 256, 0, stream>>>(A, n, int(k), lda,
+                                                                         reinterpret_cast<float2*>(P));
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
 
 extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
                                                int64_t lda, const double* b, double* x, const rsk_lsq_opts* opts,
@@ -589,18 +671,20 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         return fail(h, RSK_ERR_INVALID_ARG, "need 1 <= k <= %d, n >= k, lda >= k", kMaxK);
     const int64_t d = opts->d;
     if (d < k || d > 8192) return fail(h, RSK_ERR_INVALID_ARG, "need k <= d <= 8192 (got d=%lld)", (long long)d);
-    if (opts->sketch_dtype != RSK_F64 && opts->sketch_dtype != RSK_F32 && opts->sketch_dtype != RSK_BF16)
+    if (opts->sketch_dtype != RSK_F64 && opts->sketch_dtype != RSK_F32 && opts->sketch_dtype != RSK_BF16 &&
+        opts->sketch_dtype != RSK_F32X2)
         return fail(h, RSK_ERR_INVALID_ARG, "bad sketch dtype");
     if (opts->inner_dtype != RSK_F64 && opts->inner_dtype != RSK_F32 && opts->inner_dtype != RSK_F32X2)
         return fail(h, RSK_ERR_INVALID_ARG, "inner dtype must be F64, F32 or F32X2");
     if (info) memset(info, 0, sizeof(*info));
-    const bool dfl = opts->inner_dtype == RSK_F32X2;
+    const bool dfl = opts->inner_dtype == RSK_F32X2;                        // CG over the pairs
+    const bool pairs = dfl || opts->sketch_dtype == RSK_F32X2;              // A split once per solve
     const int K = int(k);
     const int nparts = std::max(1, std::min<int>(int((n + 255) / 256), 2 * h->num_sms));
 
     // ---- workspace
     // with F32X2 the hi array doubles as the FP32 copy the sketch may need
-    const bool need_sk_copy = opts->sketch_dtype != a_dtype && !(dfl && opts->sketch_dtype == RSK_F32);
+    const bool need_sk_copy = opts->sketch_dtype != a_dtype && opts->sketch_dtype != RSK_F32X2;
     const bool need_in_copy = opts->inner_dtype == RSK_F32 && a_dtype == RSK_F64;
     const size_t es_sk = dtype_size(opts->sketch_dtype);
     size_t bytes = 0;
@@ -617,7 +701,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     if (need_in_copy) add(size_t(n) * K * 4);
     add(size_t(K) * 8);             // yv
     add(64);                        // CG state
-    if (dfl) add(size_t(n) * K * 4 * 2);  // hi, lo
+    if (pairs) add(size_t(n) * K * 8);     // interleaved (hi, lo) pairs
     const size_t sk_part = std::max(sketch_partial_bytes(h, n, k, d, opts->zeta, opts->sketch_dtype),
                                     sketch_partial_bytes(h, n, 1, d, opts->zeta, RSK_F64));
     add(sk_part);
@@ -649,8 +733,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     w.yv = cv.take<double>(size_t(K));
     double* cgstate = cv.take<double>(8);
     void* skpart = cv.take<char>(sk_part);
-    float* Ahi = dfl ? cv.take<float>(size_t(n) * K) : nullptr;
-    float* Alo = dfl ? cv.take<float>(size_t(n) * K) : nullptr;
+    float2* Ap = pairs ? cv.take<float2>(size_t(n) * K) : nullptr;
     RSK_CUDA_TRY(h, cudaMemsetAsync(w.bar, 0, 64, stream));
 
     // ---- L1: low-precision copies, sketch of [A | b]
@@ -673,21 +756,19 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
             RSK_LAUNCH_CHECK(h);
         }
     }
-    if (dfl) {
-        if (a_dtype == RSK_F64) k_split_df<<<cg, 256, 0, stream>>>((const double*)A, n, K, lda, Ahi, Alo);
-        else {
-            k_convert<float, float><<<cg, 256, 0, stream>>>((const float*)A, n, K, lda, Ahi);
-            RSK_CUDA_TRY(h, cudaMemsetAsync(Alo, 0, size_t(n) * K * 4, stream));
-        }
+    if (pairs) {
+        if (a_dtype == RSK_F64) k_to_pairs<double><<<cg, 256, 0, stream>>>((const double*)A, n, K, lda, Ap);
+        else k_to_pairs<float><<<cg, 256, 0, stream>>>((const float*)A, n, K, lda, Ap);
         RSK_LAUNCH_CHECK(h);
     }
-    const bool sk_from_hi = dfl && opts->sketch_dtype == RSK_F32 && a_dtype == RSK_F64;
-    const void* A_sk = sk_from_hi ? static_cast<const void*>(Ahi) : (need_sk_copy ? Ask : A);
-    const int64_t lda_sk = (sk_from_hi || need_sk_copy) ? k : lda;
+    const bool sk_pairs = opts->sketch_dtype == RSK_F32X2;
+    const void* A_sk = sk_pairs ? static_cast<const void*>(Ap) : (need_sk_copy ? Ask : A);
+    const int64_t lda_sk = (sk_pairs || need_sk_copy) ? k : lda;
     rsk_sketch_plan* plan = nullptr;
     st = rsk_sparse_sign_plan_create(h, n, d, opts->zeta, opts->seed, &plan, stream);
     if (st != RSK_OK) return st;
-    const rsk_dtype sa_dt = opts->sketch_dtype == RSK_F64 ? RSK_F64 : RSK_F32;
+    // double-float sketches keep their ~2^-44 accuracy only in an FP64 result
+    const rsk_dtype sa_dt = (opts->sketch_dtype == RSK_F64 || opts->sketch_dtype == RSK_F32X2) ? RSK_F64 : RSK_F32;
     st = sketch_plan_apply_ws(h, plan, A_sk, opts->sketch_dtype, k, lda_sk, w.SA64, sa_dt, k, skpart, stream);
     if (st == RSK_OK) st = sketch_plan_apply_ws(h, plan, b, RSK_F64, 1, 1, w.Sb, RSK_F64, 1, skpart, stream);
     rsk_sparse_sign_plan_destroy(h, plan, stream);
@@ -730,8 +811,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         // an FP64 A is read as stored: the hi/lo split keeps only 48 bits, and the fixed point of the
         // refinement must be that of A itself.  An FP32 A is exact in hi (lo = 0): double-float sums.
         if (dfl && a_dtype == RSK_F32)
-            st = launch_pass_df(h, Ahi, Alo, n, K, w.x, b, (double*)w.parts, w.parts_s, nparts, true, steps == 0,
-                                stream);
+            st = launch_pass_pairs(h, Ap, n, K, w.x, b, (double*)w.parts, w.parts_s, nparts, true, steps == 0,
+                                   stream);
         else if (a_dtype == RSK_F64)
             st = launch_pass<double, double>(h, (const double*)A, n, K, lda, w.x, b, (double*)w.parts, w.parts_s,
                                              nparts, true, steps == 0, stream);
@@ -780,8 +861,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
             }
             k_trmv<<<gv, 256, 0, stream>>>(w.Rinv, K, 0, w.p, w.t);   // t = R^{-1} p
             if (dfl) {
-                st = launch_pass_df(h, Ahi, Alo, n, K, w.t, nullptr, (double*)w.parts, nullptr, nparts, false, false,
-                                    stream);
+                st = launch_pass_pairs(h, Ap, n, K, w.t, nullptr, (double*)w.parts, nullptr, nparts, false, false,
+                                       stream);
                 if (st != RSK_OK) return st;
                 k_reduce_parts<double><<<unsigned((K + 255) / 256), 256, 0, stream>>>((const double*)w.parts, nparts,
                                                                                      K, w.g, nullptr, nullptr);

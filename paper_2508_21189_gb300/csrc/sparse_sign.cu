@@ -317,8 +317,44 @@ struct AccBF16 {
     }
 };
 
+// Interleaved double-float element: a = hi + lo (both FP32).
+struct __align__(8) DF2 {
+    float hi, lo;
+    __host__ __device__ DF2() {}
+    __host__ __device__ DF2(int) : hi(0.f), lo(0.f) {}
+};
+// Double-float accumulation of (hi, lo) pairs (Knuth's exact sum on the high parts), two pairs per
+// 16 bytes; the partial is stored as the FP64 value hi + lo.
+struct AccDF {
+    static constexpr int kVec = 2;
+    using store_t = double;
+    float h[2], l[2];
+    __device__ __forceinline__ void zero() { h[0] = h[1] = l[0] = l[1] = 0.f; }
+    __device__ __forceinline__ static void acc1(float& hh, float& ll, float ah, float al) {
+        const float s = hh + ah;
+        const float bb = s - hh;
+        float e = (hh - (s - bb)) + (ah - bb);
+        e += ll + al;
+        hh = s + e;
+        ll = e - (hh - s);
+    }
+    __device__ __forceinline__ void add(const uint4 x, uint32_t negative) {
+        const uint32_t sm = negative << 31;
+        acc1(h[0], l[0], __uint_as_float(x.x ^ sm), __uint_as_float(x.y ^ sm));
+        acc1(h[1], l[1], __uint_as_float(x.z ^ sm), __uint_as_float(x.w ^ sm));
+    }
+    __device__ __forceinline__ void store(double* dst) const {
+        dst[0] = double(h[0]) + double(l[0]);
+        dst[1] = double(h[1]) + double(l[1]);
+    }
+};
+
 template <typename T>
 struct Elem;
+template <>
+struct Elem<DF2> {
+    using acc = AccDF;
+};
 template <>
 struct Elem<double> {
     using acc = AccF64;
@@ -582,7 +618,7 @@ ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, int zeta, rsk_d
     p.nranges = std::max(1, std::min(p.nchunks, h->num_sms / std::max(1, pairs)));
     p.kpad = int64_t(p.nslices) * C;
     p.pstride = int64_t(p.ntsub) * p.dsub * p.kpad;
-    const size_t acc = dt == RSK_F64 ? 8 : 4;
+    const size_t acc = (dt == RSK_F64 || dt == RSK_F32X2) ? 8 : 4;
     p.partial_bytes = size_t(p.nranges) * p.pstride * acc;
     return p;
 }
@@ -645,7 +681,7 @@ rsk_status apply_with_index(rsk_handle* h, const uint16_t* offs, const uint16_t*
     memset(&map, 0, sizeof(map));
     bool use_tma = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && ((lda * int64_t(es)) % 16 == 0);
     if (use_tma) {
-        const CUtensorMapDataType tdt = a_dt == RSK_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+        const CUtensorMapDataType tdt = (a_dt == RSK_F64 || a_dt == RSK_F32X2) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
                                         : a_dt == RSK_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
         use_tma = rsk::encode_2d(h, &map, tdt, A, uint64_t(k), uint64_t(n), uint64_t(lda) * es, uint32_t(C),
@@ -673,17 +709,19 @@ rsk_status apply_with_index(rsk_handle* h, const uint16_t* offs, const uint16_t*
     args.status = h->dev_status;
     rsk_status st;
     if (a_dt == RSK_F64) st = launch_apply_slots<double>(h, p, args, use_tma, map, stream);
+    else if (a_dt == RSK_F32X2) st = launch_apply_slots<DF2>(h, p, args, use_tma, map, stream);
     else if (a_dt == RSK_F32) st = launch_apply_slots<float>(h, p, args, use_tma, map, stream);
     else st = launch_apply_slots<__nv_bfloat16>(h, p, args, use_tma, map, stream);
     if (st != RSK_OK) return st;
-    if (a_dt == RSK_F64) return launch_reduce<double>(h, p, partials, d, k, zeta, SA, sa_dt, ldsa, stream);
+    if (a_dt == RSK_F64 || a_dt == RSK_F32X2)
+        return launch_reduce<double>(h, p, partials, d, k, zeta, SA, sa_dt, ldsa, stream);
     return launch_reduce<float>(h, p, partials, d, k, zeta, SA, sa_dt, ldsa, stream);
 }
 
 rsk_status check_apply_args(rsk_handle* h, const void* A, int a_dt, int64_t k, int64_t lda, const void* SA,
                             int sa_dt, int64_t ldsa) {
     if (!A || !SA) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null matrix pointer");
-    if (!rsk::dtype_ok(a_dt)) return rsk::fail(h, RSK_ERR_INVALID_ARG, "bad A dtype %d", a_dt);
+    if (!rsk::sketch_dtype_ok(a_dt)) return rsk::fail(h, RSK_ERR_INVALID_ARG, "bad A dtype %d", a_dt);
     if (sa_dt != RSK_F64 && sa_dt != RSK_F32) return rsk::fail(h, RSK_ERR_INVALID_ARG, "SA dtype must be F64 or F32");
     if (k < 1 || lda < k || ldsa < k) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need k >= 1, lda >= k, ldsa >= k");
     return RSK_OK;

@@ -25,7 +25,7 @@ def solve(rsk, A, b, d, **kw):
 
 
 @pytest.mark.parametrize("sketch,inner", [(torch.float64, torch.float64), (torch.float32, torch.float64),
-                                          (torch.float32, "f32x2")])
+                                          (torch.float32, "f32x2"), ("f32x2", "f32x2")])
 def test_ill_conditioned_fp64_truth(rsk, sketch, inner):
     # A = Q_U diag(logspace(0, -8)) V^T, b = A x* + 1e-6 noise: the least-squares workload shape
     A, b, _ = synthetic.lsq_problem(40000, 60, seed=3, cond_exp=8.0, device="cpu")
@@ -40,6 +40,9 @@ def test_ill_conditioned_fp64_truth(rsk, sketch, inner):
     rn = np.linalg.norm(b.numpy() - A.numpy() @ x.cpu().numpy())
     rs = np.linalg.norm(b.numpy() - A.numpy() @ xs)
     assert abs(rn - rs) <= 1e-8 * rs
+    # the reported norms belong to the returned x
+    assert abs(info["residual_norm"] - rn) <= 1e-6 * rn, (info["residual_norm"], rn)
+    assert abs(info["frobenius_norm"] - np.linalg.norm(A.numpy())) <= 1e-6 * np.linalg.norm(A.numpy())
 
 
 def test_double_float_inner_fp32_storage(rsk):

@@ -170,3 +170,47 @@ def test_full_size_embedding(rsk, dtype):
         o_rowptr, o_j, o_neg = osk.csr(n, d, zeta, seed)
         assert np.array_equal(rowptr, o_rowptr)
         assert np.array_equal(j, o_j) and np.array_equal(neg, o_neg)
+
+
+def _split_reference(a):
+    """hi = RN32(a), lo = RN32(a - hi), with the library's flush rules outside the FP32 normal range."""
+    tiny = np.float64(2.0 ** -126)
+    with np.errstate(over="ignore", invalid="ignore"):
+        hi = a.astype(np.float32)
+        lo = (a - hi.astype(np.float64)).astype(np.float32)
+    small = np.abs(a) < tiny
+    hi = np.where(small, np.copysign(np.float32(0), a).astype(np.float32), hi)
+    lo = np.where(small | (np.abs(lo.astype(np.float64)) < tiny) | ~np.isfinite(hi), np.float32(0), lo)
+    return hi, lo
+
+
+def test_split_pairs_bit_exact(rsk):
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal(200000) * np.exp2(rng.integers(-130, 130, 200000).astype(np.float64))
+    # exact ties: an FP32 value plus half of its ulp (round to even either way), and near-ties
+    base = rng.standard_normal(4000).astype(np.float32).astype(np.float64)
+    ulp = np.spacing(np.abs(base).astype(np.float32)).astype(np.float64)
+    extra = np.concatenate([base + ulp / 2, base - ulp / 2, base + ulp / 2 * (1 + 2.0 ** -25), base + ulp / 2 * (1 - 2.0 ** -25),
+                            [0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.5e38, -1e300, 1e-310, 2.0 ** -126,
+                             2.0 ** -127, 1.0 + 2.0 ** -40, np.finfo(np.float32).max * (1 + 2.0 ** -25)]])
+    a = np.concatenate([a, extra])
+    A = torch.from_numpy(a.reshape(-1, 1)).cuda()
+    P = rsk.rsk_split_pairs(A).cpu().numpy().reshape(-1, 2)
+    hi, lo = _split_reference(a)
+    assert np.array_equal(P[:, 0].view(np.uint32), hi.view(np.uint32))
+    assert np.array_equal(P[:, 1].view(np.uint32), lo.view(np.uint32))
+    # the pair carries a to 2^-48 relative wherever lo cannot be flushed (|a - hi| < 2^-126 only when
+    # that is below 2^-56 |a|)
+    ok = (np.abs(a) > 2.0 ** -70) & (np.abs(a) < 2.0 ** 126)
+    err = np.abs(P[ok, 0].astype(np.float64) + P[ok, 1].astype(np.float64) - a[ok])
+    assert np.all(err <= 2.0 ** -48 * np.abs(a[ok]))
+
+
+def test_pairs_apply_parity(rsk):
+    # double-float accumulation of the split pairs against the FP64 oracle: the pair carries 2^-48
+    # relative per entry and the sum ~2^-44 relative per accumulated row
+    n, k, d, zeta = 30000, 50, 400, 8
+    A = synthetic.gaussian(n, k, seed=12, device="cuda", dtype=torch.float64)
+    P = rsk.rsk_split_pairs(A)
+    SA = rsk.rsk_sparse_sign_apply_pairs(P, d, zeta, 5).cpu().numpy()
+    check_rows(SA, A.cpu().numpy(), d, zeta, 5, 2.0 ** -40)
