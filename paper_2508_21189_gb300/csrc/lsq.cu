@@ -347,7 +347,7 @@ __global__ void k_to_pairs(const T* __restrict__ A, int64_t n, int k, int64_t ld
 // so lane L ends with row bit4(L)).  RESID: r_i = b_i - a_i . x (b as pairs too), g += r_i a_i,
 // ||r||^2, ||A||_F^2, ||b||^2.  CG: w_i = a_i . y, g += w_i a_i.
 template <int M, bool RESID>
-__global__ void __launch_bounds__(kPassThreads) k_pass_pairs(const float2* __restrict__ P, int64_t n, int k,
+__global__ void __launch_bounds__(kPassThreads, 2) k_pass_pairs(const float2* __restrict__ P, int64_t n, int k,
                                                              const double* __restrict__ y,
                                                              const double* __restrict__ b,
                                                              double* __restrict__ part,
