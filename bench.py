@@ -50,6 +50,10 @@ def parse():
     p.add_argument("--no-lsq", action="store_true", help="skip the least-squares solves/sec measurements")
     p.add_argument("--no-rsvd", action="store_true")
     p.add_argument("--solve-reps", type=int, default=3, help="timed calls per least-squares / RSVD form")
+    p.add_argument("--lsq-rows", type=int, default=LSQ_N, help="rows of the single least-squares A (smaller only "
+                   "for profiling captures)")
+    p.add_argument("--batch-count", type=int, default=BATCH_COUNT, help="problems in the batched least-squares "
+                   "workload (smaller only for profiling captures)")
     return p.parse_args()
 
 
@@ -261,12 +265,12 @@ def timed_calls(fn, reps, torch, dev, after_warmup=None):
     return statistics.median(times), out
 
 
-def bench_lsq(rsk, synthetic, torch, dev, rank, world, reps):
+def bench_lsq(rsk, synthetic, torch, dev, rank, world, reps, rows=LSQ_N):
     """Single least-squares workload (A = Q_U diag(logspace(0,-8)) V^T, 2^20 x 500 FP64, b = A x* +
     1e-6 noise, d = 2000, zeta = 8): the mixed form (A split once into FP32 pairs; double-float sketch
     and CG operator on FP32 units; FP64 residual refinement) against the plain FP64 form (FP64 sketch,
     FP64 CG), each to eta <= 1e-10."""
-    A, b, _ = synthetic.lsq_problem(LSQ_N, LSQ_K, seed=31 + rank, cond_exp=8.0, noise=1e-6, device=dev)
+    A, b, _ = synthetic.lsq_problem(rows, LSQ_K, seed=31 + rank, cond_exp=8.0, noise=1e-6, device=dev)
     forms = {"mixed": ("f32x2", "f32x2"), "fp64": (torch.float64, torch.float64)}
     res = {}
     for name, (sk, inner) in forms.items():
@@ -279,18 +283,18 @@ def bench_lsq(rsk, synthetic, torch, dev, rank, world, reps):
                      "sketch": str(sk).replace("torch.", ""), "inner": str(inner).replace("torch.", "")}
     del A, b
     torch.cuda.empty_cache()
-    return {"workload": "least squares A = Q_U diag(logspace(0,-8)) V^T 2^20 x 500 FP64, b = A x* + 1e-6 N(0,1), "
+    return {"workload": f"least squares A = Q_U diag(logspace(0,-8)) V^T {rows} x 500 FP64, b = A x* + 1e-6 N(0,1), "
                         "sparse sign d=2000 zeta=8, to eta <= 1e-10",
             "value": res["mixed"]["solves_per_s"], "unit": "solves/s",
             "speedup_vs_fp64": round(res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"], 3),
             "mixed": res["mixed"], "fp64": res["fp64"]}
 
 
-def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps):
+def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH_COUNT):
     """512 uneven problems (n_i log-uniform [4096, 262144], k_i uniform [16, 256], Gaussian A_i x
     logspace(-6, 0) column scales, Gaussian b_i, d_i = 4 k_i, zeta = 8) in one batched call: FP32
     storage with FP32 sketch and inner CG against FP64 storage with FP64 sketch and inner CG."""
-    ns, ks = synthetic.batched_sizes(BATCH_COUNT, seed=404 + rank)
+    ns, ks = synthetic.batched_sizes(count, seed=404 + rank)
     As32, As64, bs = [], [], []
     for i, (n, k) in enumerate(zip(ns, ks)):
         A, b = synthetic.batched_problem(n, k, seed=10_000 * (rank + 1) + i, device=dev, dtype=torch.float64)
@@ -302,14 +306,14 @@ def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps):
         ms, (xs, infos) = timed_calls(lambda: rsk.rsk_lstsq_sketch_precond_batched(As, bs, zeta=ZETA, seed=9,
                                                                                      sketch_dtype=dt, inner_dtype=dt),
                                       reps, torch, dev)
-        res[name] = {"solves_per_s": round(world * BATCH_COUNT * 1e3 / ms, 3), "ms_per_batch": round(ms, 3),
+        res[name] = {"solves_per_s": round(world * count * 1e3 / ms, 3), "ms_per_batch": round(ms, 3),
                      "max_backward_err": max(f["backward_err"] for f in infos),
                      "max_refine_steps": max(f["refine_steps"] for f in infos)}
     rows = sum(ns)
     elems = sum(n * k for n, k in zip(ns, ks))
     del As32, As64, bs
     torch.cuda.empty_cache()
-    return {"workload": f"{BATCH_COUNT} uneven least-squares problems, n_i log-uniform [4096, 262144], k_i uniform "
+    return {"workload": f"{count} uneven least-squares problems, n_i log-uniform [4096, 262144], k_i uniform "
                         "[16, 256], A_i Gaussian x logspace(-6,0) column scales, d_i = 4 k_i, zeta=8, eta <= 1e-10",
             "total_rows": rows, "total_elements": elems,
             "value": res["mixed"]["solves_per_s"], "unit": "solves/s",
@@ -424,8 +428,9 @@ def run_ours(args):
     clocks = sampler.stop()
     extra = {}
     if not args.no_lsq:
-        extra["lsq"] = bench_lsq(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
-        extra["lsq_batched"] = bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
+        extra["lsq"] = bench_lsq(rsk, synthetic, torch, dev, rank, world, args.solve_reps, args.lsq_rows)
+        extra["lsq_batched"] = bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, args.solve_reps,
+                                                 args.batch_count)
     if not args.no_rsvd:
         extra["rsvd"] = bench_rsvd(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
 

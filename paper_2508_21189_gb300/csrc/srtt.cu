@@ -43,53 +43,103 @@ __device__ __forceinline__ int zoff(int r) { return r * kCols + kCols * (r >> 5)
 // ------------------------------------------------------------------------------------------
 // P and D.
 // ------------------------------------------------------------------------------------------
+// Floyd's sampling of d distinct rows of [0, n): step q (m = n - d + q) draws t = floor(w_q (m+1) / 2^32)
+// and takes t unless an earlier step already holds it, in which case it takes m.  Every t is computed
+// in parallel; a step can only find its t held if t >= n - d (an earlier m) or an earlier step drew
+// the same t, so only those steps ("dirty", about d^2/n of them) are settled one after another in
+// step order, each with one block-wide search of the earlier picks.  The picks equal those of the
+// sequential loop.
 __global__ void __launch_bounds__(1024) k_srtt_draw(int64_t n, int d, uint64_t seed, int32_t* __restrict__ rows,
                                                      int64_t* __restrict__ rows64, int hash_bits,
                                                      unsigned int* status) {
-    extern __shared__ __align__(16) uint8_t sm[];
-    uint32_t* w = reinterpret_cast<uint32_t*>(sm);   // d draws
-    uint32_t* table = w + d;                           // 2^hash_bits slots, 0xffffffff = empty
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint32_t* pick = reinterpret_cast<uint32_t*>(sm);   // d values (t, then settled)
+    uint32_t* keys = pick + d;                          // 2^hash_bits slots: t values
+    int* first = reinterpret_cast<int*>(keys + (1 << hash_bits));  // first step drawing that t
+    __shared__ int ndirty_s;
+    __shared__ int dirty_s[1024];
     const int cap = 1 << hash_bits;
+    const uint32_t mask = uint32_t(cap - 1);
+    const uint32_t nd = uint32_t(n - d);
+    for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+        keys[i] = 0xffffffffu;
+        first[i] = 0x7fffffff;
+    }
+    if (threadIdx.x == 0) ndirty_s = 0;
+    __syncthreads();
     for (int q = threadIdx.x; q < d; q += blockDim.x) {
         const rskd::Block4 b = rskd::philox_block(seed, kStreamP, 0, uint32_t(q >> 2));
-        w[q] = b.v[q & 3];
-    }
-    for (int i = threadIdx.x; i < cap; i += blockDim.x) table[i] = 0xffffffffu;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t mask = uint32_t(cap - 1);
-        for (int q = 0; q < d; ++q) {
-            const uint32_t m = uint32_t(n - d + q);
-            const uint32_t t = uint32_t((uint64_t(w[q]) * (uint64_t(m) + 1)) >> 32);
-            // is t already chosen?
-            uint32_t h = (t * 2654435761u) >> (32 - hash_bits);
-            bool taken = false;
-            int probes = 0;
-            while (table[h] != 0xffffffffu && probes < cap) {
-                if (table[h] == t) {
-                    taken = true;
-                    break;
-                }
-                h = (h + 1) & mask;
-                ++probes;
+        const uint32_t m = nd + uint32_t(q);
+        const uint32_t t = uint32_t((uint64_t(b.v[q & 3]) * (uint64_t(m) + 1)) >> 32);
+        pick[q] = t;
+        // record the earliest step that drew t (t < 2^31, so 0xffffffff marks an empty slot)
+        uint32_t h = (t * 2654435761u) >> (32 - hash_bits);
+        for (int probe = 0; probe < cap; ++probe) {
+            const uint32_t prev = atomicCAS(&keys[h], 0xffffffffu, t);
+            if (prev == 0xffffffffu || prev == t) {
+                atomicMin(&first[h], q);
+                break;
             }
-            const uint32_t v = taken ? m : t;
-            // insert v (m is never present yet: all chosen values so far are < m)
-            h = (v * 2654435761u) >> (32 - hash_bits);
-            probes = 0;
-            while (table[h] != 0xffffffffu && probes < cap) {
-                h = (h + 1) & mask;
-                ++probes;
-            }
-            if (probes >= cap) {
-                atomicOr(status, RSK_DEV_BOUNDS);
-                return;
-            }
-            table[h] = v;
-            if (rows) rows[q] = int32_t(v);
-            if (rows64) rows64[q] = int64_t(v);
+            h = (h + 1) & mask;
         }
     }
+    __syncthreads();
+    // dirty steps, collected in step order (a block-wide ordered compaction per 1024 steps)
+    for (int base = 0; base < d; base += blockDim.x) {
+        const int q = base + int(threadIdx.x);
+        bool dirty = false;
+        if (q < d) {
+            const uint32_t t = pick[q];
+            dirty = t >= nd;
+            uint32_t h = (t * 2654435761u) >> (32 - hash_bits);
+            for (int probe = 0; probe < cap && !dirty; ++probe) {
+                if (keys[h] == t) {
+                    dirty = first[h] < q;
+                    break;
+                }
+                if (keys[h] == 0xffffffffu) break;
+                h = (h + 1) & mask;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, dirty);
+        __shared__ int wcount[32];
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (l == 0) wcount[w] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = ndirty_s;
+            for (int i = 0; i < int(blockDim.x >> 5); ++i) {
+                const int c = wcount[i];
+                wcount[i] = acc;
+                acc += c;
+            }
+            ndirty_s = acc;
+        }
+        __syncthreads();
+        if (dirty) {
+            const int slot = wcount[w] + __popc(bal & ((1u << l) - 1u));
+            if (slot < 1024) dirty_s[slot] = q;
+        }
+        __syncthreads();
+    }
+    // settle the dirty steps in order (all steps when there are more than the list holds, as when
+    // n is close to d); each is one block-wide search of the earlier picks
+    const int ndirty = ndirty_s;
+    const bool all = ndirty > 1024;
+    const int count = all ? d : ndirty;
+    for (int i = 0; i < count; ++i) {
+        const int q = all ? i : dirty_s[i];
+        const uint32_t t = pick[q];
+        int hit = 0;
+        for (int j = threadIdx.x; j < q; j += blockDim.x) hit |= pick[j] == t;
+        if (__syncthreads_or(hit) && threadIdx.x == 0) pick[q] = nd + uint32_t(q);
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < d; q += blockDim.x) {
+        if (rows) rows[q] = int32_t(pick[q]);
+        if (rows64) rows64[q] = int64_t(pick[q]);
+    }
+    (void)status;
 }
 
 __global__ void k_srtt_dbits(int64_t nwords, uint64_t seed, uint32_t* __restrict__ out) {
@@ -102,17 +152,39 @@ __global__ void k_srtt_dbits(int64_t nwords, uint64_t seed, uint32_t* __restrict
 // ------------------------------------------------------------------------------------------
 // The transform + gather kernel.
 // ------------------------------------------------------------------------------------------
+// Work items are (row band, column slice) pairs numbered band-major (item = band * nslices + slice);
+// a band is nblocks / R consecutive 2048-row blocks.  Items are dealt round-robin to the CTAs, so the
+// CTAs running together read the same rows (different 16- or 32-byte column slices of them, which
+// then share DRAM sectors through L2).  Each item writes one partial [d][kCols]; the partials of a
+// slice are summed in band order.
 struct SrttArgs {
     const void* A;          // used by the plain-load path
     int64_t lda;
     int64_t n, k;
-    int d, nblocks, nslices, nranges;
-    const int32_t* prow;   // d selected rows
-    void* partials;        // float or double [nranges][d][kpad]
-    int64_t pstride, kpad;
+    int d, nblocks, nslices, R, nitems;
+    const int32_t* prow;    // d selected rows
+    float* partials;        // [item][d][kCols]
+    int64_t pstride;        // d * kCols
     uint64_t seed;
     unsigned int* status;
 };
+
+// Position in a CTA's sequence of (item, block): items blockIdx.x, + gridDim.x, ...
+struct SrttCursor {
+    int item, s, blk, b1;
+};
+__device__ __forceinline__ void cursor_item(const SrttArgs& a, SrttCursor& c, int item) {
+    // bands are never empty (R <= nblocks), so one step always lands on a block
+    c.item = item;
+    if (item >= a.nitems) return;
+    const int r = item / a.nslices;
+    c.s = item - r * a.nslices;
+    c.blk = int(int64_t(r) * a.nblocks / a.R);
+    c.b1 = int(int64_t(r + 1) * a.nblocks / a.R);
+}
+__device__ __forceinline__ void cursor_next(const SrttArgs& a, SrttCursor& c) {
+    if (++c.blk >= c.b1) cursor_item(a, c, c.item + int(gridDim.x));
+}
 
 template <typename T>
 __device__ __forceinline__ float to_f(T v);
@@ -161,11 +233,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
     uint64_t* bars = reinterpret_cast<uint64_t*>(dwords + kBlk / 32);
 
     const int tid = threadIdx.x;
-    int bidx = blockIdx.x;
-    const int s = bidx % a.nslices;
-    const int r = bidx / a.nslices;
-    const int b0 = int(int64_t(r) * a.nblocks / a.nranges);
-    const int b1 = int(int64_t(r + 1) * a.nblocks / a.nranges);
 
     // outputs of this thread: q = tid + 256*j
     int plo[QPT], phi[QPT];
@@ -180,15 +247,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         for (int c = 0; c < kCols; ++c) acc[j][c] = 0.f;
     }
 
-    auto issue = [&](int blk, uint8_t* dst, uint64_t* bar) {
-        const int64_t row0 = int64_t(blk) * kBlk;
+    auto issue = [&](const SrttCursor& c, uint8_t* dst, uint64_t* bar) {
+        const int64_t row0 = int64_t(c.blk) * kBlk;
         int nbox = 0;
         for (int bx = 0; bx < kBlk / kBoxRows; ++bx)
             if (row0 + bx * kBoxRows < a.n) ++nbox;
         rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kCols * sizeof(T)));
         for (int bx = 0; bx < nbox; ++bx)
-            rskd::tma_load_2d(dst + bx * kBoxRows * kCols * sizeof(T), &tmap, s * kCols, int(row0 + bx * kBoxRows), bar);
+            rskd::tma_load_2d(dst + bx * kBoxRows * kCols * sizeof(T), &tmap, c.s * kCols, int(row0 + bx * kBoxRows), bar);
     };
+    SrttCursor cur, ahead;
+    cursor_item(a, cur, int(blockIdx.x));
+    ahead = cur;
     if constexpr (TMA) {
         if (tid == 0) {
             rskd::mbar_init(&bars[0], 1);
@@ -196,19 +266,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
             rskd::fence_mbar_init();
         }
         __syncthreads();
-        if (tid == 0) {
-            if (b0 < b1) issue(b0, stage0, &bars[0]);
-            if (b0 + 1 < b1) issue(b0 + 1, stage1, &bars[1]);
-        }
+        // two blocks in flight: `ahead` always points two positions past `cur`
+        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage0, &bars[0]);
+        if (ahead.item < a.nitems) cursor_next(a, ahead);
+        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage1, &bars[1]);
+        if (ahead.item < a.nitems) cursor_next(a, ahead);
     }
+    auto flush = [&](int item) {
+        float* part = a.partials + int64_t(item) * a.pstride;
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+            const int q = tid + kThreads * j;
+            if (q < a.d) {
+                float4* dst = reinterpret_cast<float4*>(part + int64_t(q) * kCols);
+                dst[0] = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+                dst[1] = make_float4(acc[j][4], acc[j][5], acc[j][6], acc[j][7]);
+            }
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) acc[j][c] = 0.f;
+        }
+    };
 
     // pass-1 layout: column c1 = tid % 8, rows g1 + 32*x (x < 64), g1 = tid / 8
     const int c1 = tid & 7, g1 = tid >> 3;
     // pass-2 layout: column c2 = tid % 8, rows 32*(g2 + 32*h) + y (y < 32, h < 2), g2 = tid / 8
     const int c2 = tid & 7, g2 = tid >> 3;
 
-    for (int blk = b0, it = 0; blk < b1; ++blk, ++it) {
+    for (int it = 0; cur.item < a.nitems; ++it) {
         const int st = it & 1;
+        const int s = cur.s;
+        const int blk = cur.blk;
         // D words of this block (16 Philox blocks of 4 words)
         if (tid < 16) {
             const rskd::Block4 w = rskd::philox_block(a.seed, kStreamD, uint64_t(blk) * 16 + tid, 0);
@@ -242,9 +329,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         for (int x = 0; x < 64; ++x) Z[zoff(g1 + 32 * x) + c1] = v[x];
         __syncthreads();
         // stage buffer is free: refill it while the block is finished
-        if (TMA && tid == 0 && blk + 2 < b1) {
-            rskd::fence_proxy_async();
-            issue(blk + 2, st ? stage1 : stage0, &bars[st]);
+        if (TMA && ahead.item < a.nitems) {
+            if (tid == 0) {
+                rskd::fence_proxy_async();
+                issue(ahead, st ? stage1 : stage0, &bars[st]);
+            }
+            cursor_next(a, ahead);
         }
         // pass 2: stages on row bits 0..4
 #pragma unroll
@@ -273,29 +363,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
             acc[j][7] += sg * z1.w;
         }
         __syncthreads();
-    }
-
-    float* part = static_cast<float*>(a.partials) + int64_t(r) * a.pstride;
-#pragma unroll
-    for (int j = 0; j < QPT; ++j) {
-        const int q = tid + kThreads * j;
-        if (q < a.d) {
-            float4* dst = reinterpret_cast<float4*>(part + int64_t(q) * a.kpad + int64_t(s) * kCols);
-            dst[0] = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
-            dst[1] = make_float4(acc[j][4], acc[j][5], acc[j][6], acc[j][7]);
-        }
+        const int done_item = cur.item;
+        cursor_next(a, cur);
+        if (cur.item != done_item) flush(done_item);
     }
 }
 
+// Y[i, col] = scale * sum over bands of the partial of item (band, slice of col), in band order.
 template <typename Out>
-__global__ void k_reduce_srtt(const float* __restrict__ partials, int64_t pstride, int64_t kpad, int nranges, int d,
+__global__ void k_reduce_srtt(const float* __restrict__ partials, int64_t pstride, int R, int nslices, int d,
                               int64_t k, double scale, Out* __restrict__ Y, int64_t ldy) {
     const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= int64_t(d) * k) return;
     const int64_t i = idx / k, col = idx - i * k;
-    const float* p = partials + i * kpad + col;
+    const int s = int(col / kCols);
+    const float* p = partials + i * kCols + (col - int64_t(s) * kCols);
     float sum = 0.f;
-    for (int r = 0; r < nranges; ++r) sum += p[int64_t(r) * pstride];
+    for (int r = 0; r < R; ++r) sum += p[(int64_t(r) * nslices + s) * pstride];
     Y[i * ldy + col] = Out(double(sum) * scale);
 }
 
@@ -316,7 +400,7 @@ rsk_status check_srtt(rsk_handle* h, int64_t n, int64_t d) {
 rsk_status launch_draw(rsk_handle* h, int64_t n, int d, uint64_t seed, int32_t* rows, int64_t* rows64,
                        cudaStream_t stream) {
     const int hb = hash_bits_for(d);
-    const size_t smem = (size_t(d) + (size_t(1) << hb)) * 4;
+    const size_t smem = (size_t(d) + 2 * (size_t(1) << hb)) * 4;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_srtt_draw, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_DENSE);
     k_srtt_draw<<<1, 1024, smem, stream>>>(n, d, seed, rows, rows64, hb, h->dev_status);
@@ -331,7 +415,7 @@ rsk_status launch_srtt_t(rsk_handle* h, const CUtensorMap& map, const SrttArgs& 
     const int smem = (tma ? 2 * kBlk * kCols * int(sizeof(T)) : 0) + kZFloats * 4 + (kBlk / 32) * 4 + 64;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SRTT_APPLY);
-    kern<<<unsigned(args.nslices * args.nranges), kThreads, smem, stream>>>(map, args);
+    kern<<<unsigned(std::min(args.nitems, h->num_sms)), kThreads, smem, stream>>>(map, args);
     rsk::prof_end(h, stream, pr);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
@@ -389,17 +473,24 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     args.d = int(d);
     args.nblocks = int((n + kBlk - 1) / kBlk);
     args.nslices = int((k + kCols - 1) / kCols);
-    args.nranges = std::max(1, std::min(args.nblocks, h->num_sms / args.nslices));
-    args.kpad = int64_t(args.nslices) * kCols;
-    args.pstride = int64_t(d) * args.kpad;
+    // bands: R = num_sms / gcd(nslices, num_sms) makes nslices * R a multiple of the SM count
+    int gg = args.nslices, hh = h->num_sms;
+    while (hh) {
+        const int t_ = gg % hh;
+        gg = hh;
+        hh = t_;
+    }
+    args.R = std::max(1, std::min(args.nblocks, h->num_sms / gg));
+    args.nitems = args.nslices * args.R;
+    args.pstride = int64_t(d) * kCols;
     args.seed = seed;
     args.status = h->dev_status;
-    const size_t part_bytes = size_t(args.nranges) * args.pstride * 4;
+    const size_t part_bytes = size_t(args.nitems) * args.pstride * 4;
     st = rsk::ensure_workspace(h, rsk::Carver::round(part_bytes) + rsk::Carver::round(size_t(d) * 4) + 512, stream);
     if (st != RSK_OK) return st;
     rsk::Carver cv(h->ws);
     int32_t* prow = cv.take<int32_t>(size_t(d));
-    args.partials = cv.take<float>(size_t(args.nranges) * args.pstride);
+    args.partials = cv.take<float>(size_t(args.nitems) * args.pstride);
     args.prow = prow;
     st = launch_draw(h, n, int(d), seed, prow, nullptr, stream);
     if (st != RSK_OK) return st;
@@ -417,12 +508,10 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SRTT_REDUCE);
     if (y_dtype == RSK_F64)
         k_reduce_srtt<double><<<unsigned((total + 255) / 256), 256, 0, stream>>>(
-            static_cast<const float*>(args.partials), args.pstride, args.kpad, args.nranges, int(d), k, scale,
-            static_cast<double*>(Y), ldy);
+            args.partials, args.pstride, args.R, args.nslices, int(d), k, scale, static_cast<double*>(Y), ldy);
     else
         k_reduce_srtt<float><<<unsigned((total + 255) / 256), 256, 0, stream>>>(
-            static_cast<const float*>(args.partials), args.pstride, args.kpad, args.nranges, int(d), k, scale,
-            static_cast<float*>(Y), ldy);
+            args.partials, args.pstride, args.R, args.nslices, int(d), k, scale, static_cast<float*>(Y), ldy);
     rsk::prof_end(h, stream, pr);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
