@@ -141,6 +141,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def bf16_peak():
+    """(TFLOP/s, kind): the measured cuBLAS BF16 burst peak, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["bf16_tflops"])
+        return v, "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -329,15 +339,19 @@ def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps):
                                  reps, torch, dev, after_warmup=lambda: rsk.rsk_profile_enable(True))
     gemm = rsk.rsk_profile_read("gemm")
     rsk.rsk_profile_enable(False)
-    flops = (2 + 2 * RSVD_Q) * 2 * RSVD_M * RSVD_N * RSVD_R
+    rp = (RSVD_R + 7) // 8 * 8  # the library pads the GEMM dimension to a multiple of 8
+    flops = (2 + 2 * RSVD_Q) * 2 * RSVD_M * RSVD_N * rp
     gemm_ms = gemm[0] / reps
     del A, U, s, Vt
     torch.cuda.empty_cache()
     return {"workload": "RSVD A 262144 x 8192 FP32 (rank-400 spectrum j^-2 + 1e-4 noise), r=300, q=2, "
                         "sparse sign Omega zeta=8",
             "value": round(world * 1e3 / ms, 3), "unit": "calls/s", "ms_per_call": round(ms, 3),
-            "gemm_ms_per_call": round(gemm_ms, 3), "gemm_flops_per_call": flops,
-            "gemm_tflops": round(flops / (gemm_ms / 1e3) / 1e12, 1) if gemm_ms > 0 else None}
+            "gemm_ms_per_call": round(gemm_ms, 3), "gemm_launches_per_call": gemm[1] // max(1, reps),
+            "gemm_flops_per_call": flops,
+            "gemm_tflops": round(flops / (gemm_ms / 1e3) / 1e12, 1) if gemm_ms > 0 else None,
+            "gemm_frac_of_bf16_peak": (round(flops / (gemm_ms / 1e3) / 1e12 / bf16_peak()[0], 4)
+                                       if gemm_ms > 0 else None)}
 
 
 def run_ours(args):

@@ -79,7 +79,7 @@ typedef enum {
     RSK_KERNEL_SRTT_APPLY = 4,
     RSK_KERNEL_SRTT_REDUCE = 5,
     RSK_KERNEL_DENSE = 6,          /* LSQ / RSVD dense helpers (QR, solves, matvecs) */
-    RSK_KERNEL_GEMM = 7,           /* tensor-core GEMMs                             */
+    RSK_KERNEL_GEMM = 7,           /* BF16 tensor-core GEMMs of the RSVD             */
     RSK_KERNEL_COUNT = 16
 } rsk_kernel_id;
 /* Turn recording on (on != 0) or off.  Turning it on clears earlier records. */
@@ -264,9 +264,10 @@ rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const 
  * drawn as the left sparse sign of Philox stream 3 (rsk_sparse_sign_generate's rule with stream 3).
  * Outputs (device): U FP32 m x r row-major, s FP64[r] descending, Vt FP32 r x n row-major, with
  * A ~ U diag(s) Vt.  Products run on BF16 copies of A with FP32 accumulation; orthonormalisation is
- * shifted CholeskyQR3 in FP32; the r x r eigenproblem of B B^T is solved in FP64.
- * Limits: 1 <= r <= min(m, n, 380), 1 <= zeta <= min(r, 32), m, n < 2^31.  Needs cuBLAS and
- * cuSOLVER at run time (RSK_ERR_UNSUPPORTED when they cannot be loaded). */
+ * shifted CholeskyQR3 in FP32 (the factor's inverse applied as a product); the r x r eigenproblem of
+ * B B^T is solved in FP64.  The first call for a shape times cuBLASLt's candidate algorithms once.
+ * Limits: 1 <= r <= min(m, n, 320), 1 <= zeta <= min(r, 32), m, n < 2^31.  Needs cuBLAS, cuBLASLt
+ * and cuSOLVER at run time (RSK_ERR_UNSUPPORTED when they cannot be loaded). */
 rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int32_t r, int32_t power_iters,
                     int32_t zeta, uint64_t seed, float* U, double* s, float* Vt, cudaStream_t stream);
 

@@ -14,8 +14,12 @@
 // restore orthogonality to O(u_32), below the BF16 error of the products.  The small SVD of
 // B = Z^T comes from the symmetric eigenproblem of Z^T Z (r x r, FP64).
 //
-// The plain products (GEMM, SYRK, TRSM) go through cuBLAS and the r x r eigenproblem through
-// cuSOLVER, both loaded at first use with dlopen; everything else is this file's kernels.
+// The plain products (the BF16 GEMMs, the FP32 Gram matrices and the FP32 products X R^{-1}) go
+// through cuBLASLt matmuls, each shape autotuned once (the heuristic's candidates timed on the
+// operands, the fastest kept); R^{-1} comes from this file's Cholesky kernel, so no triangular solve
+// runs on the tall basis.  The r x r eigenproblem goes through cuSOLVER.  Both libraries are loaded at
+// first use with dlopen; everything else is this file's kernels.
+#include <cublasLt.h>
 #include <cuda_bf16.h>
 #include <dlfcn.h>
 #include <math.h>
@@ -68,6 +72,33 @@ bool sym(void* lib, const char* name, F& fn) {
     return fn != nullptr;
 }
 
+// cuBLASLt: function pointers (types from cublasLt.h), one handle, autotuned plans per shape.
+struct LtLib {
+    void* so = nullptr;
+    decltype(&cublasLtCreate) create = nullptr;
+    decltype(&cublasLtMatmulDescCreate) descCreate = nullptr;
+    decltype(&cublasLtMatmulDescSetAttribute) descSet = nullptr;
+    decltype(&cublasLtMatrixLayoutCreate) layoutCreate = nullptr;
+    decltype(&cublasLtMatmulPreferenceCreate) prefCreate = nullptr;
+    decltype(&cublasLtMatmulPreferenceSetAttribute) prefSet = nullptr;
+    decltype(&cublasLtMatmulPreferenceDestroy) prefDestroy = nullptr;
+    decltype(&cublasLtMatmulAlgoGetHeuristic) heuristic = nullptr;
+    decltype(&cublasLtMatmul) matmul = nullptr;
+    cublasLtHandle_t lh = nullptr;
+};
+LtLib g_lt;
+
+struct LtPlan {
+    int device, ta, tb, atype, ctype, compute;
+    int64_t m, n, k, lda, ldb, ldc;
+    cublasLtMatmulDesc_t desc;
+    cublasLtMatrixLayout_t la, lb, lc;
+    cublasLtMatmulAlgo_t algo;
+    size_t ws;
+};
+std::vector<LtPlan> g_plans;
+constexpr size_t kLtWorkspace = size_t(64) << 20;
+
 rsk_status load_libs(rsk_handle* h) {
     Libs& L = g_libs;
     if (L.tried) return L.ok ? RSK_OK : rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLAS/cuSOLVER could not be loaded");
@@ -86,18 +117,128 @@ rsk_status load_libs(rsk_handle* h) {
     if (!ok) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLAS/cuSOLVER symbols missing");
     if (L.blasCreate(&L.bh) != 0 || L.solverCreate(&L.sh) != 0)
         return rsk::fail(h, RSK_ERR_CUDA, "cuBLAS/cuSOLVER handle creation failed");
+    LtLib& T = g_lt;
+    T.so = dlopen("libcublasLt.so.13", RTLD_NOW | RTLD_LOCAL);
+    if (!T.so) T.so = dlopen("libcublasLt.so", RTLD_NOW | RTLD_LOCAL);
+    if (!T.so) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLASLt not found");
+    ok = sym(T.so, "cublasLtCreate", T.create) && sym(T.so, "cublasLtMatmulDescCreate", T.descCreate) &&
+         sym(T.so, "cublasLtMatmulDescSetAttribute", T.descSet) &&
+         sym(T.so, "cublasLtMatrixLayoutCreate", T.layoutCreate) &&
+         sym(T.so, "cublasLtMatmulPreferenceCreate", T.prefCreate) &&
+         sym(T.so, "cublasLtMatmulPreferenceSetAttribute", T.prefSet) &&
+         sym(T.so, "cublasLtMatmulPreferenceDestroy", T.prefDestroy) &&
+         sym(T.so, "cublasLtMatmulAlgoGetHeuristic", T.heuristic) && sym(T.so, "cublasLtMatmul", T.matmul);
+    if (!ok || T.create(&T.lh) != CUBLAS_STATUS_SUCCESS)
+        return rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLASLt symbols missing or handle creation failed");
     L.ok = true;
+    return RSK_OK;
+}
+
+// D (m x n, column-major, ldc) = alpha op(A) op(B), op given by ta / tb (0 = N, 1 = T), through the
+// fastest of cuBLASLt's heuristic candidates for this shape (timed on first use with these operands).
+rsk_status lt_matmul(rsk_handle* h, int ta, int tb, int64_t m, int64_t n, int64_t k, const void* A, cudaDataType_t at,
+                     int64_t lda, const void* B, int64_t ldb, void* C, cudaDataType_t ct, int64_t ldc, float alpha,
+                     cublasComputeType_t compute, void* ws, cudaStream_t stream) {
+    LtLib& T = g_lt;
+    const float beta = 0.f;
+    LtPlan* plan = nullptr;
+    for (auto& p : g_plans)
+        if (p.device == h->device && p.ta == ta && p.tb == tb && p.atype == int(at) && p.ctype == int(ct) &&
+            p.compute == int(compute) && p.m == m && p.n == n && p.k == k && p.lda == lda && p.ldb == ldb &&
+            p.ldc == ldc)
+            plan = &p;
+    if (!plan) {
+        LtPlan p{};
+        p.device = h->device;
+        p.ta = ta;
+        p.tb = tb;
+        p.atype = int(at);
+        p.ctype = int(ct);
+        p.compute = int(compute);
+        p.m = m;
+        p.n = n;
+        p.k = k;
+        p.lda = lda;
+        p.ldb = ldb;
+        p.ldc = ldc;
+        if (T.descCreate(&p.desc, compute, CUDA_R_32F) != CUBLAS_STATUS_SUCCESS)
+            return rsk::fail(h, RSK_ERR_CUDA, "cublasLtMatmulDescCreate failed");
+        const cublasOperation_t opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N, opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
+        T.descSet(p.desc, CUBLASLT_MATMUL_DESC_TRANSA, &opa, sizeof(opa));
+        T.descSet(p.desc, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb));
+        if (T.layoutCreate(&p.la, at, ta ? k : m, ta ? m : k, lda) != CUBLAS_STATUS_SUCCESS ||
+            T.layoutCreate(&p.lb, at, tb ? n : k, tb ? k : n, ldb) != CUBLAS_STATUS_SUCCESS ||
+            T.layoutCreate(&p.lc, ct, m, n, ldc) != CUBLAS_STATUS_SUCCESS)
+            return rsk::fail(h, RSK_ERR_CUDA, "cublasLtMatrixLayoutCreate failed");
+        cublasLtMatmulPreference_t pref;
+        T.prefCreate(&pref);
+        const uint64_t wsb = kLtWorkspace;
+        T.prefSet(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &wsb, sizeof(wsb));
+        cublasLtMatmulHeuristicResult_t cand[16];
+        int found = 0;
+        const cublasStatus_t hs = T.heuristic(T.lh, p.desc, p.la, p.lb, p.lc, p.lc, pref, 16, cand, &found);
+        T.prefDestroy(pref);
+        if (hs != CUBLAS_STATUS_SUCCESS || found < 1) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "no cuBLASLt algorithm");
+        cudaEvent_t e0, e1;
+        RSK_CUDA_TRY(h, cudaEventCreate(&e0));
+        RSK_CUDA_TRY(h, cudaEventCreate(&e1));
+        float best = 1e30f;
+        int bi = -1;
+        for (int i = 0; i < found; ++i) {
+            if (cand[i].state != CUBLAS_STATUS_SUCCESS || cand[i].workspaceSize > kLtWorkspace) continue;
+            if (T.matmul(T.lh, p.desc, &alpha, A, p.la, B, p.lb, &beta, C, p.lc, C, p.lc, &cand[i].algo, ws,
+                         kLtWorkspace, stream) != CUBLAS_STATUS_SUCCESS)
+                continue;
+            cudaEventRecord(e0, stream);
+            for (int rep = 0; rep < 2; ++rep)
+                T.matmul(T.lh, p.desc, &alpha, A, p.la, B, p.lb, &beta, C, p.lc, C, p.lc, &cand[i].algo, ws,
+                         kLtWorkspace, stream);
+            cudaEventRecord(e1, stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bi = i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaGetLastError();
+        if (bi < 0) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "no cuBLASLt algorithm ran");
+        p.algo = cand[bi].algo;
+        p.ws = cand[bi].workspaceSize;
+        g_plans.push_back(p);
+        plan = &g_plans.back();
+    }
+    if (T.matmul(T.lh, plan->desc, &alpha, A, plan->la, B, plan->lb, &beta, C, plan->lc, C, plan->lc, &plan->algo, ws,
+                 kLtWorkspace, stream) != CUBLAS_STATUS_SUCCESS)
+        return rsk::fail(h, RSK_ERR_CUDA, "cublasLtMatmul failed");
     return RSK_OK;
 }
 
 // ------------------------------------------------------------------------------------------
 // Kernels.
 // ------------------------------------------------------------------------------------------
+// B (m x n, packed) = bf16(A) (lda); grid (ceil(n / 1024), <= 65535) striding over rows, 4
+// consecutive elements per thread.
 __global__ void k_to_bf16(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloat16* __restrict__ B) {
-    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= m * n) return;
-    const int64_t i = idx / n, j = idx - i * n;
-    B[idx] = __float2bfloat16_rn(A[i * lda + j]);
+    const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+    if (j >= n) return;
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
+        const float* a = A + i * lda + j;
+        __nv_bfloat16* b = B + i * n + j;
+        if (j + 4 <= n && (reinterpret_cast<uintptr_t>(a) & 15) == 0 && (reinterpret_cast<uintptr_t>(b) & 7) == 0) {
+            const float4 v = *reinterpret_cast<const float4*>(a);
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+            uint2 o;
+            o.x = *reinterpret_cast<uint32_t*>(&lo);
+            o.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(b) = o;
+        } else {
+            for (int e = 0; e < 4 && j + e < n; ++e) b[e] = __float2bfloat16_rn(a[e]);
+        }
+    }
 }
 
 // B = bf16(A^T): A m x n (lda), B n x m row-major; 32 x 32 tiles through shared memory.
@@ -116,21 +257,22 @@ __global__ void k_transpose_bf16(const float* __restrict__ A, int64_t m, int64_t
     }
 }
 
-// X (rows x r, FP32, row-major) -> bf16(X^T) (r x rows)
-__global__ void k_transpose_f32_bf16(const float* __restrict__ X, int64_t rows, int r, __nv_bfloat16* __restrict__ T) {
+// X (rows x r, FP32, row-major, row stride ldx) -> bf16(X^T) (rp x rows; rows r..rp-1 zero)
+__global__ void k_transpose_f32_bf16(const float* __restrict__ X, int64_t rows, int r, int ldx, int rp,
+                                     __nv_bfloat16* __restrict__ T) {
     __shared__ float tile[32][33];
     const int64_t i0 = int64_t(blockIdx.y) * 32;
     const int j0 = blockIdx.x * 32;
     for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
         const int64_t i = i0 + rr;
         const int j = j0 + threadIdx.x;
-        tile[rr][threadIdx.x] = (i < rows && j < r) ? X[i * r + j] : 0.f;
+        tile[rr][threadIdx.x] = (i < rows && j < r) ? X[i * ldx + j] : 0.f;
     }
     __syncthreads();
     for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
         const int j = j0 + rr;
         const int64_t i = i0 + threadIdx.x;
-        if (j < r && i < rows) T[int64_t(j) * rows + i] = __float2bfloat16_rn(tile[threadIdx.x][rr]);
+        if (j < rp && i < rows) T[int64_t(j) * rows + i] = __float2bfloat16_rn(tile[threadIdx.x][rr]);
     }
 }
 
@@ -151,26 +293,31 @@ __global__ void k_scale(float* __restrict__ X, int64_t count, float s) {
     if (idx < count) X[idx] *= s;
 }
 
-// Cholesky of G (+ shift) in shared memory, packed lower triangle, FP32.  G: r x r symmetric with
-// the lower triangle valid in column-major storage (G[k*r + i], i >= k).  Writes R = L^T into Rout
-// (column-major upper triangle: Rout[i*r + k] = L[i][k] for k <= i, zero elsewhere).  shift_mode 1
-// adds 11 (rows*r + r(r+1)) u_32 trace(G) to the diagonal (the shift of shifted CholeskyQR).
-__global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, int r, float* __restrict__ Rout,
-                                                   int shift_mode, double rows, unsigned int* status) {
-    extern __shared__ float L[];  // r(r+1)/2
+constexpr int kMaxRank = 320;  // the packed factor within 227 KB of shared memory
+
+// Cholesky of G (+ shift) in shared memory, packed lower triangle, FP32.  G: r x r symmetric, read
+// from its lower triangle (column-major, G[k*r + i], i >= k).  Writes L (lower triangular,
+// column-major, zeros above) with G + shift = L L^T, and the identity into Linv for the triangular
+// solve that turns it into L^{-1}; the orthonormalised basis is X R^{-1} with R = L^T, i.e.
+// (X R^{-1})^T = L^{-1} X^T.  shift_mode 1 adds 11 (rows*r + r(r+1)) u_32 trace(G) to the diagonal
+// (the shift of shifted CholeskyQR).
+__global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, int r, int ld,
+                                                   float* __restrict__ Lout, float* __restrict__ Linv, int shift_mode,
+                                                   double rows, unsigned int* status) {
+    extern __shared__ float L[];  // r(r+1)/2 packed
     __shared__ float piv;
     __shared__ double tr;
     auto at = [](int i, int k) { return i * (i + 1) / 2 + k; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int i = 0; i < r; ++i) t += double(G[size_t(i) * r + i]);
+        for (int i = 0; i < r; ++i) t += double(G[size_t(i) * ld + i]);
         tr = t;
     }
     __syncthreads();
     const float shift = shift_mode ? float(11.0 * (rows * r + double(r) * (r + 1)) * 5.960464477539063e-08 * tr) : 0.f;
     for (int i = warp; i < r; i += nw)
-        for (int k = lane; k <= i; k += 32) L[at(i, k)] = G[size_t(k) * r + i] + (i == k ? shift : 0.f);
+        for (int k = lane; k <= i; k += 32) L[at(i, k)] = G[size_t(k) * ld + i] + (i == k ? shift : 0.f);
     __syncthreads();
     for (int j = 0; j < r; ++j) {
         if (threadIdx.x == 0) {
@@ -189,9 +336,13 @@ __global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, 
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
-        const int i = idx / r, k = idx - i * r;
-        Rout[size_t(i) * r + k] = (k <= i) ? L[at(i, k)] : 0.f;
+    // L (lower, column-major, zeros above) and the identity in Linv: L^{-1} then comes from one
+    // r x r triangular solve
+    // ld x ld outputs; rows and columns beyond r are zero (padding of the GEMM dimensions)
+    for (int idx = threadIdx.x; idx < ld * ld; idx += blockDim.x) {
+        const int c = idx / ld, i = idx - c * ld;
+        Lout[idx] = (i >= c && i < r && c < r) ? L[at(i, c)] : 0.f;
+        Linv[idx] = (i == c && i < r) ? 1.f : 0.f;
     }
 }
 
@@ -243,7 +394,8 @@ __global__ void k_scale_cols(float* __restrict__ X, int64_t rows, int r, const f
 
 struct Ws {
     __nv_bfloat16 *Abf, *Atbf, *Ot, *Xt;
-    float *Y, *Z, *G, *R, *Uh, *sinv;
+    float *Y, *Z, *X2, *G, *R, *Lf, *Uh, *sinv;
+    void* ltws;
     double *Gd, *w, *work;
     int* info;
     int32_t* orow;
@@ -255,39 +407,50 @@ struct Ws {
 
 namespace rsk {
 
-// C (M x N, row-major, ldc = N) = A (M x K, K-major bf16) * B (N x K, K-major bf16)^T, FP32 accumulation.
+// C (M x N, row-major, ldc = N) = alpha A (M x K, K-major bf16) * B (N x K, K-major bf16)^T, FP32
+// accumulation on the tensor cores.  In column-major terms C^T (N x M) = B^T A.
 static rsk_status gemm_nt(rsk_handle* h, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int64_t M,
-                          int64_t N, int64_t K, float alpha, cudaStream_t s) {
-    Libs& L = g_libs;
-    L.blasSetStream(L.bh, s);
-    const float beta = 0.f;
+                          int64_t N, int64_t K, float alpha, Ws& w, cudaStream_t s) {
     const int pr = prof_begin(h, s, RSK_KERNEL_GEMM);
-    int st = L.gemmEx(L.bh, kOpT, kOpN, int(N), int(M), int(K), &alpha, B, kR16BF, int(K), A, kR16BF, int(K), &beta, C,
-                      kR32F, int(N), kCompute32F, kGemmDefault);
+    const rsk_status st = lt_matmul(h, 1, 0, N, M, K, B, CUDA_R_16BF, K, A, K, C, CUDA_R_32F, N, alpha,
+                                    CUBLAS_COMPUTE_32F, w.ltws, s);
     prof_end(h, s, pr);
-    if (st != 0) return fail(h, RSK_ERR_CUDA, "cublasGemmEx failed (%d)", st);
-    return RSK_OK;
+    return st;
 }
 
-// X (rows x r, row-major FP32) <- orthonormal basis of range(X): shifted CholeskyQR3.
-static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, Ws& w, cudaStream_t s) {
+// X (rows x r, row-major FP32, row stride rp, columns r..rp-1 zero) <- orthonormal basis of
+// range(X): shifted CholeskyQR3.  Each round: G = X^T X (FP32 matmul, rp x rp), G + shift = L L^T on
+// the leading r x r block and L^{-1} by a triangular solve (both padded with zeros to rp x rp),
+// X <- X L^{-T} computed as (X L^{-T})^T = L^{-1} X^T (FP32 matmul into a second buffer, copied
+// back; the zero padding keeps columns r..rp-1 of X zero).  The dimensions are padded to rp, a
+// multiple of 8, because the GEMM library only takes its fast paths for such shapes.
+static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws& w, cudaStream_t s) {
     Libs& L = g_libs;
-    L.blasSetStream(L.bh, s);
-    const float one = 1.f, zero = 0.f;
     const size_t smem = size_t(r) * (r + 1) / 2 * 4;
     if (smem > 227 * 1024) return fail(h, RSK_ERR_UNSUPPORTED, "r = %d too large for the shared-memory Cholesky", r);
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     for (int round = 0; round < 3; ++round) {
-        // G = X^T X: X row-major = column-major X^T (r x rows)
-        int st = L.ssyrk(L.bh, kFillLower, kOpN, r, int(rows), &one, X, r, &zero, w.G, r);
-        if (st != 0) return fail(h, RSK_ERR_CUDA, "cublasSsyrk failed (%d)", st);
-        const int pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        k_cholesky<<<1, 1024, smem, s>>>(w.G, r, w.R, round == 0 ? 1 : 0, double(rows), h->dev_status);
+        // X row-major is X^T column-major (rp x rows, ld rp):  G = X^T (X^T)^T
+        int pr = prof_begin(h, s, RSK_KERNEL_DENSE);
+        rsk_status st = lt_matmul(h, 0, 1, rp, rp, rows, X, CUDA_R_32F, rp, X, rp, w.G, CUDA_R_32F, rp, 1.f,
+                                  CUBLAS_COMPUTE_32F, w.ltws, s);
+        prof_end(h, s, pr);
+        if (st != RSK_OK) return st;
+        pr = prof_begin(h, s, RSK_KERNEL_DENSE);
+        k_cholesky<<<1, 1024, smem, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows), h->dev_status);
         prof_end(h, s, pr);
         RSK_LAUNCH_CHECK(h);
-        // X <- X R^{-1}:  (X R^{-1})^T = R^{-T} X^T, i.e. solve R^T Y = X^T with R upper (column-major)
-        st = L.strsm(L.bh, kSideLeft, kFillUpper, kOpT, kDiagNonUnit, r, int(rows), &one, w.R, r, X, r);
-        if (st != 0) return fail(h, RSK_ERR_CUDA, "cublasStrsm failed (%d)", st);
+        // w.R <- L^{-1} on the leading r x r block: solve L X = I (lower, column-major, ld rp)
+        const float one = 1.f;
+        L.blasSetStream(L.bh, s);
+        if (L.strsm(L.bh, kSideLeft, kFillLower, kOpN, kDiagNonUnit, r, r, &one, w.Lf, rp, w.R, rp) != 0)
+            return fail(h, RSK_ERR_CUDA, "cublasStrsm failed");
+        pr = prof_begin(h, s, RSK_KERNEL_DENSE);
+        st = lt_matmul(h, 0, 0, rp, rows, rp, w.R, CUDA_R_32F, rp, X, rp, w.X2, CUDA_R_32F, rp, 1.f,
+                       CUBLAS_COMPUTE_32F, w.ltws, s);
+        prof_end(h, s, pr);
+        if (st != RSK_OK) return st;
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(X, w.X2, size_t(rows) * rp * 4, cudaMemcpyDeviceToDevice, s));
     }
     return RSK_OK;
 }
@@ -300,8 +463,8 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     using namespace rsk;
     if (!h) return RSK_ERR_INVALID_ARG;
     if (!A || !U || !s || !Vt) return fail(h, RSK_ERR_INVALID_ARG, "null pointer");
-    if (m < 1 || n < 1 || lda < n || r < 1 || r > 380 || r > std::min(m, n) || power_iters < 0)
-        return fail(h, RSK_ERR_INVALID_ARG, "need 1 <= r <= min(m, n, 380), lda >= n, power_iters >= 0");
+    if (m < 1 || n < 1 || lda < n || r < 1 || r > kMaxRank || r > std::min(m, n) || power_iters < 0)
+        return fail(h, RSK_ERR_INVALID_ARG, "need 1 <= r <= min(m, n, %d), lda >= n, power_iters >= 0", kMaxRank);
     if (zeta < 1 || zeta > r || zeta > 32) return fail(h, RSK_ERR_INVALID_ARG, "need 1 <= zeta <= min(r, 32)");
     if (m >= (int64_t(1) << 31) || n >= (int64_t(1) << 31)) return fail(h, RSK_ERR_INVALID_ARG, "m, n < 2^31");
     rsk_status st = load_libs(h);
@@ -312,15 +475,18 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     if (L.dsyevdBuf(L.sh, kEigModeVector, kFillLower, r, nullptr, r, nullptr, &lwork) != 0)
         return fail(h, RSK_ERR_CUDA, "cusolverDnDsyevd_bufferSize failed");
 
+    const int rp = (r + 7) & ~7;  // GEMM dimension padded to a multiple of 8 (zero columns)
     size_t bytes = 0;
     auto add = [&](size_t b_) { bytes += Carver::round(b_); };
     add(size_t(m) * n * 2);      // A bf16
     add(size_t(m) * n * 2);      // A^T bf16
-    add(size_t(r) * n * 2);      // Omega^T
-    add(size_t(r) * std::max(m, n) * 2);  // X^T bf16
-    add(size_t(std::max(m, n)) * r * 4);      // Y (also the n x r scratch of the final step)
-    add(size_t(n) * r * 4);      // Z
-    add(size_t(r) * r * 4 * 3);  // G, R, Uh
+    add(size_t(rp) * n * 2);     // Omega^T
+    add(size_t(rp) * std::max(m, n) * 2);  // X^T bf16
+    add(size_t(std::max(m, n)) * rp * 4);  // Y (also the n x r scratch of the final step)
+    add(size_t(n) * rp * 4);     // Z
+    add(size_t(std::max(m, n)) * rp * 4);  // X2 (second buffer of orth)
+    add(kLtWorkspace);           // cuBLASLt workspace
+    add(size_t(rp) * rp * 4 * 4);  // G, R (L^{-1}), L, Uh
     add(size_t(r) * 4);          // sinv
     add(size_t(r) * r * 8 + size_t(r) * 8 + size_t(lwork) * 8 + 64);
     add(size_t(n) * zeta * 4 + size_t(n) * 4);
@@ -330,13 +496,16 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     Ws w;
     w.Abf = cv.take<__nv_bfloat16>(size_t(m) * n);
     w.Atbf = cv.take<__nv_bfloat16>(size_t(m) * n);
-    w.Ot = cv.take<__nv_bfloat16>(size_t(r) * n);
-    w.Xt = cv.take<__nv_bfloat16>(size_t(r) * std::max(m, n));
-    w.Y = cv.take<float>(size_t(std::max(m, n)) * r);
-    w.Z = cv.take<float>(size_t(n) * r);
-    w.G = cv.take<float>(size_t(r) * r);
-    w.R = cv.take<float>(size_t(r) * r);
-    w.Uh = cv.take<float>(size_t(r) * r);
+    w.Ot = cv.take<__nv_bfloat16>(size_t(rp) * n);
+    w.Xt = cv.take<__nv_bfloat16>(size_t(rp) * std::max(m, n));
+    w.Y = cv.take<float>(size_t(std::max(m, n)) * rp);
+    w.Z = cv.take<float>(size_t(n) * rp);
+    w.X2 = cv.take<float>(size_t(std::max(m, n)) * rp);
+    w.ltws = cv.take<char>(kLtWorkspace);
+    w.G = cv.take<float>(size_t(rp) * rp);
+    w.R = cv.take<float>(size_t(rp) * rp);
+    w.Lf = cv.take<float>(size_t(rp) * rp);
+    w.Uh = cv.take<float>(size_t(rp) * rp);
     w.sinv = cv.take<float>(size_t(r));
     w.Gd = cv.take<double>(size_t(r) * r);
     w.w = cv.take<double>(size_t(r));
@@ -345,38 +514,39 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     w.orow = cv.take<int32_t>(size_t(n) * zeta);
     w.osgn = cv.take<uint32_t>(size_t(n));
 
-    // ---- A in BF16, both orientations; Omega^T dense +-1
-    const unsigned g1 = unsigned((m * n + 255) / 256);
-    k_to_bf16<<<g1, 256, 0, stream>>>(A, m, n, lda, w.Abf);
+    // ---- A in BF16, both orientations; Omega^T dense +-1 (rows r..rp-1 zero)
+    k_to_bf16<<<dim3(unsigned((n + 1023) / 1024), unsigned(std::min<int64_t>(m, 65535))), 256, 0, stream>>>(
+        A, m, n, lda, w.Abf);
     k_transpose_bf16<<<dim3(unsigned((n + 31) / 32), unsigned((m + 31) / 32)), dim3(32, 8), 0, stream>>>(A, m, n, lda, w.Atbf);
-    RSK_CUDA_TRY(h, cudaMemsetAsync(w.Ot, 0, size_t(r) * n * 2, stream));
+    RSK_CUDA_TRY(h, cudaMemsetAsync(w.Ot, 0, size_t(rp) * n * 2, stream));
     st = sketch_generate(h, n, r, zeta, seed, 3u, w.orow, w.osgn, stream);
     if (st != RSK_OK) return st;
     k_omega_t<<<unsigned((n + 255) / 256), 256, 0, stream>>>(w.orow, w.osgn, n, zeta, w.Ot);
     RSK_LAUNCH_CHECK(h);
 
-    // ---- range finder
+    // ---- range finder (every product has rp columns; columns r..rp-1 stay zero)
     const float zs = float(1.0 / sqrt(double(zeta)));
-    st = gemm_nt(h, w.Abf, w.Ot, w.Y, m, r, n, zs, stream);                 // Y = A Omega
-    if (st == RSK_OK) st = orth(h, w.Y, m, r, w, stream);
+    const unsigned tx = unsigned((rp + 31) / 32);
+    st = gemm_nt(h, w.Abf, w.Ot, w.Y, m, rp, n, zs, w, stream);                // Y = A Omega
+    if (st == RSK_OK) st = orth(h, w.Y, m, r, rp, w, stream);
     for (int it = 0; st == RSK_OK && it < power_iters; ++it) {
-        k_transpose_f32_bf16<<<dim3(unsigned((r + 31) / 32), unsigned((m + 31) / 32)), dim3(32, 8), 0, stream>>>(w.Y, m, r, w.Xt);
-        st = gemm_nt(h, w.Atbf, w.Xt, w.Z, n, r, m, 1.f, stream);          // Z = A^T Q
-        if (st == RSK_OK) st = orth(h, w.Z, n, r, w, stream);
+        k_transpose_f32_bf16<<<dim3(tx, unsigned((m + 31) / 32)), dim3(32, 8), 0, stream>>>(w.Y, m, r, rp, rp, w.Xt);
+        st = gemm_nt(h, w.Atbf, w.Xt, w.Z, n, rp, m, 1.f, w, stream);         // Z = A^T Q
+        if (st == RSK_OK) st = orth(h, w.Z, n, r, rp, w, stream);
         if (st != RSK_OK) break;
-        k_transpose_f32_bf16<<<dim3(unsigned((r + 31) / 32), unsigned((n + 31) / 32)), dim3(32, 8), 0, stream>>>(w.Z, n, r, w.Xt);
-        st = gemm_nt(h, w.Abf, w.Xt, w.Y, m, r, n, 1.f, stream);          // Y = A Z
-        if (st == RSK_OK) st = orth(h, w.Y, m, r, w, stream);
+        k_transpose_f32_bf16<<<dim3(tx, unsigned((n + 31) / 32)), dim3(32, 8), 0, stream>>>(w.Z, n, r, rp, rp, w.Xt);
+        st = gemm_nt(h, w.Abf, w.Xt, w.Y, m, rp, n, 1.f, w, stream);         // Y = A Z
+        if (st == RSK_OK) st = orth(h, w.Y, m, r, rp, w, stream);
     }
     if (st != RSK_OK) return st;
     // ---- B = Q^T A = Z^T with Z = A^T Q
-    k_transpose_f32_bf16<<<dim3(unsigned((r + 31) / 32), unsigned((m + 31) / 32)), dim3(32, 8), 0, stream>>>(w.Y, m, r, w.Xt);
-    st = gemm_nt(h, w.Atbf, w.Xt, w.Z, n, r, m, 1.f, stream);
+    k_transpose_f32_bf16<<<dim3(tx, unsigned((m + 31) / 32)), dim3(32, 8), 0, stream>>>(w.Y, m, r, rp, rp, w.Xt);
+    st = gemm_nt(h, w.Atbf, w.Xt, w.Z, n, rp, m, 1.f, w, stream);
     if (st != RSK_OK) return st;
     // ---- small SVD: Z^T Z = Uhat Sigma^2 Uhat^T
     L.blasSetStream(L.bh, stream);
     const float one = 1.f, zero = 0.f;
-    if (L.ssyrk(L.bh, kFillLower, kOpN, r, int(n), &one, w.Z, r, &zero, w.G, r) != 0)
+    if (L.ssyrk(L.bh, kFillLower, kOpN, r, int(n), &one, w.Z, rp, &zero, w.G, r) != 0)
         return fail(h, RSK_ERR_CUDA, "cublasSsyrk failed");
     k_f32_to_f64<<<unsigned((size_t(r) * r + 255) / 256), 256, 0, stream>>>(w.G, w.Gd, int64_t(r) * r);
     RSK_LAUNCH_CHECK(h);
@@ -385,11 +555,11 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     k_eig_post<<<8, 256, 0, stream>>>(w.w, w.Gd, r, s, w.Uh, w.sinv);
     RSK_LAUNCH_CHECK(h);
     // U = Q Uhat  (row-major m x r = (Uhat^T Q^T)^T): column-major U^T (r x m) = Uhat^T (r x r) * Q^T (r x m)
-    if (L.sgemm(L.bh, kOpT, kOpN, r, int(m), r, &one, w.Uh, r, w.Y, r, &zero, U, r) != 0)
+    if (L.sgemm(L.bh, kOpT, kOpN, r, int(m), r, &one, w.Uh, r, w.Y, rp, &zero, U, r) != 0)
         return fail(h, RSK_ERR_CUDA, "cublasSgemm (U) failed");
     // Vt = Sigma^{-1} Uhat^T Z^T: row-major Vt (r x n) is column-major Vt^T (n x r) = Z Uhat Sigma^{-1};
     // first W = Z Uhat (row-major n x r) = column-major (Uhat^T Z^T) r x n
-    if (L.sgemm(L.bh, kOpT, kOpN, r, int(n), r, &one, w.Uh, r, w.Z, r, &zero, w.Y, r) != 0)
+    if (L.sgemm(L.bh, kOpT, kOpN, r, int(n), r, &one, w.Uh, r, w.Z, rp, &zero, w.Y, r) != 0)
         return fail(h, RSK_ERR_CUDA, "cublasSgemm (V) failed");
     k_scale_cols<<<unsigned((int64_t(n) * r + 255) / 256), 256, 0, stream>>>(w.Y, n, r, w.sinv);
     // Vt (r x n row-major) = W^T

@@ -51,6 +51,8 @@ def test_rsvd_invalid(rsk):
         rsk.rsk_rsvd(A, 60)                                 # r > min(m, n)
     with pytest.raises(rsk.RskError):
         rsk.rsk_rsvd(A, 4, zeta=8)                          # zeta > r
+    with pytest.raises(rsk.RskError):
+        rsk.rsk_rsvd(torch.zeros(1000, 500, device="cuda"), 321)   # r beyond the shared-memory Cholesky
 
 
 def _power_norm(apply, n, iters, gen):
