@@ -175,11 +175,16 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     const int R = (((d + kWarps - 1) / kWarps) + 31) & ~31;
     const int t0 = min(d, warp * R), t1 = min(d, t0 + R);
     int carry = 0;
-    for (int base = t0; base < t1; base += 32) {
+    int tots[16];
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+        const int base = t0 + 32 * it;
+        if (base >= t1) break;
         const int i = base + lane;
         int tot = 0;
         if (i < t1)
             for (int w = 0; w < count_warps; ++w) tot += int(cnt[size_t(w) * d + i]);
+        tots[it] = tot;
         int incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -200,11 +205,12 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     __syncthreads();
     carry = wsum[32 + warp];
     uint16_t* off_out = offsets + ch * pitch;
-    for (int base = t0; base < t1; base += 32) {
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+        const int base = t0 + 32 * it;
+        if (base >= t1) break;
         const int i = base + lane;
-        int tot = 0;
-        if (i < t1)
-            for (int w = 0; w < count_warps; ++w) tot += int(cnt[size_t(w) * d + i]);
+        const int tot = tots[it];
         int incl = tot;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
