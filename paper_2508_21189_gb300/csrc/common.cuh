@@ -95,9 +95,11 @@ rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64
 size_t sketch_index_bytes(int64_t n, int64_t d, int zeta);
 rsk_status sketch_build_index(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, void* index_mem,
                               cudaStream_t stream);
-// S b for one FP64 vector (one warp per sketch row) from an index built by sketch_build_index.
+// S b for one FP64 vector from an index built by sketch_build_index; scratch holds
+// sketch_vec_scratch_bytes(n, d, zeta) bytes (per-chunk partial sums, reduced in chunk order).
+size_t sketch_vec_scratch_bytes(int64_t n, int64_t d, int zeta);
 rsk_status sketch_apply_vec_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta,
-                                  const double* b, double* Sb, cudaStream_t stream);
+                                  const double* b, double* Sb, double* scratch, cudaStream_t stream);
 rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta, const void* A,
                               rsk_dtype a_dt, int64_t k, int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa,
                               void* partials, cudaStream_t stream);

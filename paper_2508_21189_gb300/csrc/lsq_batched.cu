@@ -247,6 +247,147 @@ __device__ __forceinline__ void reduce_scatter_df4(const float (&ph)[4], const f
     for (int o = 4; o > 0; o >>= 1) df_xor_merge(h, l, h, l, o);
 }
 
+// The row loop of one tile, specialised on the number of 32-column blocks the problem uses (MK), so
+// that no predicated-off work is issued for the blocks beyond the problem's k.
+template <int MODE, int M, int MK>
+__device__ __forceinline__ void pass_rows(const BProb& q, const Tile& T, int k, int lane, int warp, int nw,
+                                          const double* ys, const float* yh, const float* yl, const float* Af,
+                                          int64_t ldf, int want_frob, double (&g)[M], float (&gh)[M], float (&gl)[M],
+                                          double& rr, double& ff, double& bb, float& rrf, float& fff, float& bbf) {
+    constexpr bool F64 = MODE == 1 || MODE == 2;
+    constexpr int R = F64 ? 2 : 4;
+        for (int i0 = T.r0 + warp * R; i0 < T.r1; i0 += nw * R) {
+        if constexpr (!F64) {
+            float a[R][M];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bool valid = i0 + r < T.r1;
+                const float* row = Af + int64_t(i0 + r) * ldf;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const int j = lane + 32 * m;
+                    a[r][m] = (m < MK && valid && j < k) ? row[j] : 0.f;
+                }
+            }
+            if constexpr (MODE == 0) {
+                float p[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    p[r] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (m < MK) p[r] = fmaf(a[r][m], yh[lane + 32 * m], p[r]);
+                }
+                const float w = reduce_scatter<R, float>(p, lane);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float wr = __shfl_sync(kFull, w, row_owner<R>(r));
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (m < MK) gh[m] = fmaf(wr, a[r][m], gh[m]);
+                }
+            } else {  // MODE 3
+                float ph[R], pl[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    ph[r] = 0.f;
+                    pl[r] = 0.f;
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (m < MK) {
+                            const int j = lane + 32 * m;
+                            df_acc(ph[r], pl[r], a[r][m], yh[j], yl[j]);
+                            fff = fmaf(a[r][m], a[r][m], fff);
+                        }
+                }
+                float dh, dl;
+                reduce_scatter_df4(ph, pl, lane, dh, dl);
+                // this lane's row: r = b - a.x in double-float
+                const int rho = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+                const int irow = i0 + rho;
+                float rh = 0.f, rl = 0.f;
+                if (irow < T.r1) {
+                    const float2 bs = q.bsplit[irow];
+                    float s, e;
+                    two_sum(bs.x, -dh, s, e);
+                    e += bs.y - dl;
+                    rh = s + e;
+                    rl = e - (rh - s);
+                    if ((lane & 7) == 0) {
+                        rrf = fmaf(rh, rh, rrf);
+                        bbf = fmaf(bs.x, bs.x, bbf);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float wh = __shfl_sync(kFull, rh, row_owner<R>(r));
+                    const float wl = __shfl_sync(kFull, rl, row_owner<R>(r));
+#pragma unroll
+                    for (int m = 0; m < M; ++m)
+                        if (m < MK) df_acc(gh[m], gl[m], a[r][m], wh, wl);
+                }
+            }
+        } else {
+            double a[R][M];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const bool valid = i0 + r < T.r1;
+                if (q.a_f32) {
+                    const float* row = static_cast<const float*>(q.A) + int64_t(i0 + r) * q.lda;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int j = lane + 32 * m;
+                        a[r][m] = (m < MK && valid && j < k) ? double(row[j]) : 0.0;
+                    }
+                } else {
+                    const double* row = static_cast<const double*>(q.A) + int64_t(i0 + r) * q.lda;
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        const int j = lane + 32 * m;
+                        a[r][m] = (m < MK && valid && j < k) ? row[j] : 0.0;
+                    }
+                }
+            }
+            double p[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                p[r] = 0.0;
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    if (m < MK) p[r] = fma(a[r][m], ys[lane + 32 * m], p[r]);
+            }
+            double w = reduce_scatter<R, double>(p, lane);
+            if constexpr (MODE == 2) {
+                const int irow = i0 + ((lane >> 4) & 1);
+                if (irow < T.r1) {
+                    const double bi = q.b[irow];
+                    w = bi - w;
+                    if ((lane & 15) == 0) {
+                        rr += w * w;
+                        bb += bi * bi;
+                    }
+                } else {
+                    w = 0.0;
+                }
+                if (want_frob) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int m = 0; m < M; ++m)
+                            if (m < MK) ff = fma(a[r][m], a[r][m], ff);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const double wr = __shfl_sync(kFull, w, row_owner<R>(r));
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    if (m < MK) g[m] = fma(wr, a[r][m], g[m]);
+            }
+        }
+    }
+}
+
 template <int MODE, int M>
 __global__ void __launch_bounds__(kBThreads) k_pass_b(BProb* P, const Tile* __restrict__ tiles, int ntiles,
                                                        unsigned int* queue, const int* __restrict__ active,
@@ -298,136 +439,21 @@ __global__ void __launch_bounds__(kBThreads) k_pass_b(BProb* P, const Tile* __re
         float rrf = 0.f, fff = 0.f, bbf = 0.f;
         const float* Af = static_cast<const float*>(MODE == 0 ? q.Ain : q.A);
         const int64_t ldf = MODE == 0 ? q.lda_in : q.lda;
-        for (int i0 = T.r0 + warp * R; i0 < T.r1; i0 += nw * R) {
-            if constexpr (!F64) {
-                float a[R][M];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const bool valid = i0 + r < T.r1;
-                    const float* row = Af + int64_t(i0 + r) * ldf;
-#pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const int j = lane + 32 * m;
-                        a[r][m] = (m < mk && valid && j < k) ? row[j] : 0.f;
-                    }
-                }
-                if constexpr (MODE == 0) {
-                    float p[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        p[r] = 0.f;
-#pragma unroll
-                        for (int m = 0; m < M; ++m)
-                            if (m < mk) p[r] = fmaf(a[r][m], yh[lane + 32 * m], p[r]);
-                    }
-                    const float w = reduce_scatter<R, float>(p, lane);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float wr = __shfl_sync(kFull, w, row_owner<R>(r));
-#pragma unroll
-                        for (int m = 0; m < M; ++m)
-                            if (m < mk) gh[m] = fmaf(wr, a[r][m], gh[m]);
-                    }
-                } else {  // MODE 3
-                    float ph[R], pl[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        ph[r] = 0.f;
-                        pl[r] = 0.f;
-#pragma unroll
-                        for (int m = 0; m < M; ++m)
-                            if (m < mk) {
-                                const int j = lane + 32 * m;
-                                df_acc(ph[r], pl[r], a[r][m], yh[j], yl[j]);
-                                fff = fmaf(a[r][m], a[r][m], fff);
-                            }
-                    }
-                    float dh, dl;
-                    reduce_scatter_df4(ph, pl, lane, dh, dl);
-                    // this lane's row: r = b - a.x in double-float
-                    const int rho = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
-                    const int irow = i0 + rho;
-                    float rh = 0.f, rl = 0.f;
-                    if (irow < T.r1) {
-                        const float2 bs = q.bsplit[irow];
-                        float s, e;
-                        two_sum(bs.x, -dh, s, e);
-                        e += bs.y - dl;
-                        rh = s + e;
-                        rl = e - (rh - s);
-                        if ((lane & 7) == 0) {
-                            rrf = fmaf(rh, rh, rrf);
-                            bbf = fmaf(bs.x, bs.x, bbf);
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float wh = __shfl_sync(kFull, rh, row_owner<R>(r));
-                        const float wl = __shfl_sync(kFull, rl, row_owner<R>(r));
-#pragma unroll
-                        for (int m = 0; m < M; ++m)
-                            if (m < mk) df_acc(gh[m], gl[m], a[r][m], wh, wl);
-                    }
-                }
-            } else {
-                double a[R][M];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const bool valid = i0 + r < T.r1;
-                    if (q.a_f32) {
-                        const float* row = static_cast<const float*>(q.A) + int64_t(i0 + r) * q.lda;
-#pragma unroll
-                        for (int m = 0; m < M; ++m) {
-                            const int j = lane + 32 * m;
-                            a[r][m] = (m < mk && valid && j < k) ? double(row[j]) : 0.0;
-                        }
-                    } else {
-                        const double* row = static_cast<const double*>(q.A) + int64_t(i0 + r) * q.lda;
-#pragma unroll
-                        for (int m = 0; m < M; ++m) {
-                            const int j = lane + 32 * m;
-                            a[r][m] = (m < mk && valid && j < k) ? row[j] : 0.0;
-                        }
-                    }
-                }
-                double p[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    p[r] = 0.0;
-#pragma unroll
-                    for (int m = 0; m < M; ++m)
-                        if (m < mk) p[r] = fma(a[r][m], ys[lane + 32 * m], p[r]);
-                }
-                double w = reduce_scatter<R, double>(p, lane);
-                if constexpr (MODE == 2) {
-                    const int irow = i0 + ((lane >> 4) & 1);
-                    if (irow < T.r1) {
-                        const double bi = q.b[irow];
-                        w = bi - w;
-                        if ((lane & 15) == 0) {
-                            rr += w * w;
-                            bb += bi * bi;
-                        }
-                    } else {
-                        w = 0.0;
-                    }
-                    if (want_frob) {
-#pragma unroll
-                        for (int r = 0; r < R; ++r)
-#pragma unroll
-                            for (int m = 0; m < M; ++m)
-                                if (m < mk) ff = fma(a[r][m], a[r][m], ff);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const double wr = __shfl_sync(kFull, w, row_owner<R>(r));
-#pragma unroll
-                    for (int m = 0; m < M; ++m)
-                        if (m < mk) g[m] = fma(wr, a[r][m], g[m]);
-                }
-            }
+        const int mk_ = (k + 31) >> 5;
+#define RSK_PASS_ROWS(MKV)                                                                                   \
+    pass_rows<MODE, M, MKV>(q, T, k, lane, warp, nw, ys, yh, yl, Af, ldf, want_frob, g, gh, gl, rr, ff, bb, rrf, \
+                            fff, bbf)
+        switch (mk_) {
+            case 1: RSK_PASS_ROWS(1); break;
+            case 2: RSK_PASS_ROWS(2); break;
+            case 3: RSK_PASS_ROWS(3); break;
+            case 4: RSK_PASS_ROWS(4); break;
+            case 5: if constexpr (M >= 5) RSK_PASS_ROWS(5); break;
+            case 6: if constexpr (M >= 6) RSK_PASS_ROWS(6); break;
+            case 7: if constexpr (M >= 7) RSK_PASS_ROWS(7); break;
+            default: if constexpr (M >= 8) RSK_PASS_ROWS(8); break;
         }
+#undef RSK_PASS_ROWS
         if constexpr (MODE == 3) {
             rr = double(rrf);
             ff = double(fff);
@@ -696,7 +722,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         if (in_copy && !(sk_copy && opts->sketch_dtype == RSK_F32)) add(size_t(pr.n) * pr.k * 4);
         const size_t sk = sketch_index_bytes(pr.n, d, zeta) +
                           Carver::round(std::max(sketch_partial_bytes(h, pr.n, pr.k, d, zeta, opts->sketch_dtype),
-                                                 sketch_partial_bytes(h, pr.n, 1, d, zeta, RSK_F64))) +
+                                                 sketch_vec_scratch_bytes(pr.n, d, zeta))) +
                           Carver::round(size_t(d) * pr.k * 8) + Carver::round(size_t(d) * 8) + 1024;
         max_sketch_scratch = std::max(max_sketch_scratch, sk);
     }
@@ -782,7 +808,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         double* SA = sc.take<double>(size_t(q.d) * q.k);
         double* Sb = sc.take<double>(size_t(q.d));
         void* parts = sc.take<char>(std::max(sketch_partial_bytes(h, pr.n, pr.k, q.d, zeta, sa_dt),
-                                             sketch_partial_bytes(h, pr.n, 1, q.d, zeta, RSK_F64)));
+                                             sketch_vec_scratch_bytes(pr.n, q.d, zeta)));
         const unsigned cgrid = unsigned((pr.n * pr.k + 255) / 256);
         const void* A_sk = pr.A;
         int64_t lda_sk = pr.lda;
@@ -803,7 +829,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         if (st == RSK_OK)
             st = sketch_apply_built(h, index, pr.n, q.d, zeta, A_sk, sa_dt, pr.k, lda_sk, SA,
                                     sa_dt == RSK_F64 ? RSK_F64 : RSK_F32, pr.k, parts, s);
-        if (st == RSK_OK) st = sketch_apply_vec_built(h, index, pr.n, q.d, zeta, pr.b, Sb, s);
+        // S b after S A (the partials buffer is reused; same stream, so in order)
+        if (st == RSK_OK) st = sketch_apply_vec_built(h, index, pr.n, q.d, zeta, pr.b, Sb, static_cast<double*>(parts), s);
         if (st != RSK_OK) return st;
         const unsigned gw = unsigned((int64_t(q.d) * (q.k + 1) + 255) / 256);
         if (sa_dt == RSK_F64) k_to_colmajor_b<double><<<gw, 256, 0, s>>>(SA, Sb, q.d, q.k, q.W);

@@ -804,39 +804,49 @@ rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, i
     const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dt);
     return apply_with_index(h, offs, ents, A, a_dt, n, k, lda, int(d), zeta, SA, sa_dt, ldsa, partials, p, stream);
 }
-// S b for one FP64 vector from a built index: one warp per sketch row, lanes stride over the
-// chunks, a fixed-shape warp reduction (the result does not depend on scheduling).
-__global__ void k_apply_vec(const uint16_t* __restrict__ offs, const uint16_t* __restrict__ ents,
-                            const double* __restrict__ b, int64_t n, int d, int zeta, int C, int pitch,
-                            int64_t nch, double* __restrict__ out) {
-    const int r = int(blockIdx.x) * (blockDim.x >> 5) + int(threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+// S b for one FP64 vector from a built index, in two launches: one thread per (chunk, sketch row)
+// sums that row's entries of the chunk into partial[chunk][row]; one thread per row then adds the
+// chunk partials in chunk order (so the result does not depend on scheduling) and scales.
+__global__ void k_apply_vec_part(const uint16_t* __restrict__ offs, const uint16_t* __restrict__ ents,
+                                 const double* __restrict__ b, int d, int zeta, int C, int pitch, int64_t nch,
+                                 double* __restrict__ part) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= nch * d) return;
+    const int64_t ch = idx / d;
+    const int r = int(idx - ch * d);
+    const uint16_t* o = offs + ch * pitch;
+    const uint16_t* e = ents + ch * int64_t(C) * zeta;
+    const double* bc = b + ch * C;
+    double acc = 0.0;
+    for (int t = o[r]; t < o[r + 1]; ++t) {
+        const uint16_t v = e[t];
+        const double x = bc[v & 0x7fff];
+        acc += (v & 0x8000) ? -x : x;
+    }
+    part[idx] = acc;
+}
+__global__ void k_apply_vec_sum(const double* __restrict__ part, int d, int64_t nch, double scale,
+                                double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d) return;
     double acc = 0.0;
-    for (int64_t ch = lane; ch < nch; ch += 32) {
-        const uint16_t* o = offs + ch * pitch;
-        const uint16_t* e = ents + ch * int64_t(C) * zeta;
-        const int64_t base = ch * C;
-        for (int t = o[r]; t < o[r + 1]; ++t) {
-            const uint16_t v = e[t];
-            const double x = b[base + (v & 0x7fff)];
-            acc += (v & 0x8000) ? -x : x;
-        }
-    }
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
-    if (lane == 0) out[r] = acc / sqrt(double(zeta));
+    for (int64_t ch = 0; ch < nch; ++ch) acc += part[ch * d + r];
+    out[r] = acc * scale;
 }
+size_t sketch_vec_scratch_bytes(int64_t n, int64_t d, int zeta) { return size_t(n_chunks_of(n, zeta)) * size_t(d) * 8; }
 rsk_status sketch_apply_vec_built(rsk_handle* h, const void* index_mem, int64_t n, int64_t d, int zeta,
-                                  const double* b, double* Sb, cudaStream_t stream) {
+                                  const double* b, double* Sb, double* scratch, cudaStream_t stream) {
     rsk_status st = check_dims(h, n, d, zeta);
     if (st != RSK_OK) return st;
-    if (!b || !Sb) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null vector");
+    if (!b || !Sb || !scratch) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null vector");
     Carver cv(const_cast<void*>(index_mem));
     const uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
     const uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
-    k_apply_vec<<<unsigned((d + 7) / 8), 256, 0, stream>>>(offs, ents, b, n, int(d), zeta, chunk_rows(zeta),
-                                                          offsets_pitch(int(d)), n_chunks_of(n, zeta), Sb);
+    const int64_t nch = n_chunks_of(n, zeta);
+    const int64_t total = nch * d;
+    k_apply_vec_part<<<unsigned((total + 255) / 256), 256, 0, stream>>>(offs, ents, b, int(d), zeta, chunk_rows(zeta),
+                                                                     offsets_pitch(int(d)), nch, scratch);
+    k_apply_vec_sum<<<unsigned((d + 127) / 128), 128, 0, stream>>>(scratch, int(d), nch, 1.0 / sqrt(double(zeta)), Sb);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
