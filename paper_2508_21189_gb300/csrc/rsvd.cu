@@ -16,7 +16,8 @@
 //
 // The plain products (the BF16 GEMMs, the FP32 Gram matrices and the FP32 products X R^{-1}) go
 // through cuBLASLt matmuls, each shape autotuned once (the heuristic's candidates timed on the
-// operands, the fastest kept); R^{-1} comes from this file's Cholesky kernel, so no triangular solve
+// operands, the fastest kept; the FP32 ones use cuBLAS's FP32 emulation on the BF16 tensor cores
+// when it is offered); R^{-1} comes from this file's Cholesky kernel, so no triangular solve
 // runs on the tall basis.  The r x r eigenproblem goes through cuSOLVER.  Both libraries are loaded at
 // first use with dlopen; everything else is this file's kernels.
 #include <cublasLt.h>
@@ -84,6 +85,8 @@ struct LtLib {
     decltype(&cublasLtMatmulPreferenceDestroy) prefDestroy = nullptr;
     decltype(&cublasLtMatmulAlgoGetHeuristic) heuristic = nullptr;
     decltype(&cublasLtMatmul) matmul = nullptr;
+    decltype(&cublasLtMatmulDescDestroy) descDestroy = nullptr;
+    decltype(&cublasLtMatrixLayoutDestroy) layoutDestroy = nullptr;
     cublasLtHandle_t lh = nullptr;
 };
 LtLib g_lt;
@@ -127,7 +130,9 @@ rsk_status load_libs(rsk_handle* h) {
          sym(T.so, "cublasLtMatmulPreferenceCreate", T.prefCreate) &&
          sym(T.so, "cublasLtMatmulPreferenceSetAttribute", T.prefSet) &&
          sym(T.so, "cublasLtMatmulPreferenceDestroy", T.prefDestroy) &&
-         sym(T.so, "cublasLtMatmulAlgoGetHeuristic", T.heuristic) && sym(T.so, "cublasLtMatmul", T.matmul);
+         sym(T.so, "cublasLtMatmulAlgoGetHeuristic", T.heuristic) && sym(T.so, "cublasLtMatmul", T.matmul) &&
+         sym(T.so, "cublasLtMatmulDescDestroy", T.descDestroy) &&
+         sym(T.so, "cublasLtMatrixLayoutDestroy", T.layoutDestroy);
     if (!ok || T.create(&T.lh) != CUBLAS_STATUS_SUCCESS)
         return rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLASLt symbols missing or handle creation failed");
     L.ok = true;
@@ -293,55 +298,120 @@ __global__ void k_scale(float* __restrict__ X, int64_t count, float s) {
     if (idx < count) X[idx] *= s;
 }
 
-constexpr int kMaxRank = 320;  // the packed factor within 227 KB of shared memory
+constexpr int kMaxRank = 320;  // the tiled factor (55 tiles of 4 KB) within 227 KB of shared memory
 
-// Cholesky of G (+ shift) in shared memory, packed lower triangle, FP32.  G: r x r symmetric, read
-// from its lower triangle (column-major, G[k*r + i], i >= k).  Writes L (lower triangular,
-// column-major, zeros above) with G + shift = L L^T, and the identity into Linv for the triangular
-// solve that turns it into L^{-1}; the orthonormalised basis is X R^{-1} with R = L^T, i.e.
-// (X R^{-1})^T = L^{-1} X^T.  shift_mode 1 adds 11 (rows*r + r(r+1)) u_32 trace(G) to the diagonal
-// (the shift of shifted CholeskyQR).
-__global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, int r, int ld,
-                                                   float* __restrict__ Lout, float* __restrict__ Linv, int shift_mode,
-                                                   double rows, unsigned int* status) {
-    extern __shared__ float L[];  // r(r+1)/2 packed
-    __shared__ float piv;
+// Cholesky of G (+ shift) in shared memory, FP32, blocked by 32.  G: r x r symmetric, read from its
+// lower triangle (column-major, G[k*ld + i], i >= k).  The lower triangle is held as nt(nt+1)/2
+// tiles of 32 x 32 (nt = ceil(r/32)), element (i, j) of a tile at i*32 + (j ^ i) so that reading a
+// tile row or a tile column is free of bank conflicts; rows and columns beyond r are padded with the
+// identity.  Per block column kb: one warp factors the diagonal tile, one thread per panel row solves
+// the panel against it, one warp per trailing tile subtracts P_i P_j^T.  Writes L (lower,
+// column-major, ld x ld, zeros above and in the padding) with G + shift = L L^T, and the identity
+// into Linv for the triangular solve that turns it into L^{-1}; the orthonormalised basis is
+// X R^{-1} with R = L^T, i.e. (X R^{-1})^T = L^{-1} X^T.  shift_mode 1 adds
+// 11 (rows*r + r(r+1)) u_32 trace(G) to the diagonal (the shift of shifted CholeskyQR).
+constexpr int kCholThreads = 512;
+__device__ __forceinline__ int chol_tile(int bi, int bj) { return (bi * (bi + 1) / 2 + bj) * 1024; }
+__device__ __forceinline__ int chol_el(int i, int j) { return i * 32 + (j ^ i); }
+
+__global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restrict__ G, int r, int ld,
+                                                           float* __restrict__ Lout, float* __restrict__ Linv,
+                                                           int shift_mode, double rows, unsigned int* status) {
+    extern __shared__ float T[];
     __shared__ double tr;
-    auto at = [](int i, int k) { return i * (i + 1) / 2 + k; };
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) {
+    const int nt = (r + 31) >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = kCholThreads / 32;
+    if (tid == 0) {
         double t = 0.0;
         for (int i = 0; i < r; ++i) t += double(G[size_t(i) * ld + i]);
         tr = t;
     }
     __syncthreads();
     const float shift = shift_mode ? float(11.0 * (rows * r + double(r) * (r + 1)) * 5.960464477539063e-08 * tr) : 0.f;
-    for (int i = warp; i < r; i += nw)
-        for (int k = lane; k <= i; k += 32) L[at(i, k)] = G[size_t(k) * ld + i] + (i == k ? shift : 0.f);
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int e = tid; e < ntiles * 1024; e += kCholThreads) {
+        // tile index -> (bi, bj)
+        const int t = e >> 10, within = e & 1023;
+        int bi = 0;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bj = t - bi * (bi + 1) / 2;
+        const int i = within & 31, j = within >> 5;  // consecutive threads read consecutive rows of G
+        const int R = bi * 32 + i, Cc = bj * 32 + j;
+        float v;
+        if (R >= r || Cc >= r) v = (R == Cc) ? 1.f : 0.f;
+        else if (R >= Cc) v = G[size_t(Cc) * ld + R] + (R == Cc ? shift : 0.f);
+        else v = 0.f;  // above the diagonal inside a diagonal tile: unused
+        T[chol_tile(bi, bj) + chol_el(i, j)] = v;
+    }
     __syncthreads();
-    for (int j = 0; j < r; ++j) {
-        if (threadIdx.x == 0) {
-            const float djj = L[at(j, j)];
-            if (!(djj > 0.f)) atomicOr(status, RSK_DEV_BOUNDS);
-            piv = sqrtf(fmaxf(djj, 1e-30f));
-            L[at(j, j)] = piv;
+    for (int kb = 0; kb < nt; ++kb) {
+        float* D = T + chol_tile(kb, kb);
+        // (a) diagonal tile, one warp (lane = row)
+        if (warp == 0) {
+            for (int j = 0; j < 32; ++j) {
+                if (lane == j) {
+                    const float djj = D[chol_el(j, j)];
+                    if (!(djj > 0.f) && kb * 32 + j < r) atomicOr(status, RSK_DEV_BOUNDS);
+                    D[chol_el(j, j)] = sqrtf(fmaxf(djj, 1e-30f));
+                }
+                __syncwarp();
+                const float piv = D[chol_el(j, j)];
+                if (lane > j) D[chol_el(lane, j)] /= piv;
+                __syncwarp();
+                if (lane > j) {
+                    const float lij = D[chol_el(lane, j)];
+                    for (int k = j + 1; k <= lane; ++k) D[chol_el(lane, k)] -= lij * D[chol_el(k, j)];
+                }
+                __syncwarp();
+            }
         }
         __syncthreads();
-        const float p = piv;
-        for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) L[at(i, j)] /= p;
+        // (b) panel: every row of tiles (bi, kb), bi > kb, solves x D^T = a by forward substitution
+        const int prow = (nt - kb - 1) * 32;
+        for (int pr = tid; pr < prow; pr += kCholThreads) {
+            const int bi = kb + 1 + (pr >> 5), i = pr & 31;
+            float* P = T + chol_tile(bi, kb);
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                float a = P[chol_el(i, j)];
+#pragma unroll
+                for (int t = 0; t < j; ++t) a -= x[t] * D[chol_el(j, t)];
+                x[j] = a / D[chol_el(j, j)];
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) P[chol_el(i, j)] = x[j];
+        }
         __syncthreads();
-        for (int i = j + 1 + warp; i < r; i += nw) {
-            const float lij = L[at(i, j)];
-            for (int k = j + 1 + lane; k <= i; k += 32) L[at(i, k)] -= lij * L[at(k, j)];
+        // (c) trailing tiles (bi, bj), kb < bj <= bi: T -= P_bi P_bj^T, one warp per tile, lane = row
+        const int m = nt - kb - 1;
+        const int ntr = m * (m + 1) / 2;
+        for (int tt = warp; tt < ntr; tt += nw) {
+            int a = 0;
+            while ((a + 1) * (a + 2) / 2 <= tt) ++a;
+            const int bi = kb + 1 + a, bj = kb + 1 + (tt - a * (a + 1) / 2);
+            const float* Pi = T + chol_tile(bi, kb);
+            const float* Pj = T + chol_tile(bj, kb);
+            float acc[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+            for (int t = 0; t < 32; ++t) {
+                const float p = Pi[chol_el(lane, t)];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = fmaf(p, Pj[chol_el(j, t)], acc[j]);
+            }
+            float* Tij = T + chol_tile(bi, bj);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) Tij[chol_el(lane, j)] -= acc[j];
         }
         __syncthreads();
     }
-    // L (lower, column-major, zeros above) and the identity in Linv: L^{-1} then comes from one
-    // r x r triangular solve
     // ld x ld outputs; rows and columns beyond r are zero (padding of the GEMM dimensions)
-    for (int idx = threadIdx.x; idx < ld * ld; idx += blockDim.x) {
+    for (int idx = tid; idx < ld * ld; idx += kCholThreads) {
         const int c = idx / ld, i = idx - c * ld;
-        Lout[idx] = (i >= c && i < r && c < r) ? L[at(i, c)] : 0.f;
+        float v = 0.f;
+        if (i >= c && i < r && c < r) v = T[chol_tile(i >> 5, c >> 5) + chol_el(i & 31, c & 31)];
+        Lout[idx] = v;
         Linv[idx] = (i == c && i < r) ? 1.f : 0.f;
     }
 }
@@ -407,6 +477,35 @@ struct Ws {
 
 namespace rsk {
 
+// FP32 products of the orthonormalisation: cuBLAS's FP32 emulation on the BF16 tensor cores (each
+// FP32 operand split into three BF16 parts, FP32 accumulation) where the library offers it, else
+// plain FP32.  Decided once per process by a probe matmul.
+static cublasComputeType_t fp32_compute(rsk_handle* h) {
+    static int mode = -1;  // 1 emulated, 0 plain
+    if (mode < 0) {
+        LtLib& T = g_lt;
+        cublasLtMatmulDesc_t d;
+        mode = 0;
+        if (T.descCreate(&d, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUDA_R_32F) == CUBLAS_STATUS_SUCCESS) {
+            cublasLtMatrixLayout_t l;
+            if (T.layoutCreate(&l, CUDA_R_32F, 256, 256, 256) == CUBLAS_STATUS_SUCCESS) {
+                cublasLtMatmulPreference_t pref;
+                T.prefCreate(&pref);
+                const uint64_t wsb = kLtWorkspace;
+                T.prefSet(pref, CUBLASLT_MATMUL_PREF_MAX_WORKSPACE_BYTES, &wsb, sizeof(wsb));
+                cublasLtMatmulHeuristicResult_t c[1];
+                int found = 0;
+                if (T.heuristic(T.lh, d, l, l, l, l, pref, 1, c, &found) == CUBLAS_STATUS_SUCCESS && found > 0) mode = 1;
+                T.prefDestroy(pref);
+                T.layoutDestroy(l);
+            }
+            T.descDestroy(d);
+        }
+        (void)h;
+    }
+    return mode == 1 ? CUBLAS_COMPUTE_32F_EMULATED_16BFX9 : CUBLAS_COMPUTE_32F;
+}
+
 // C (M x N, row-major, ldc = N) = alpha A (M x K, K-major bf16) * B (N x K, K-major bf16)^T, FP32
 // accumulation on the tensor cores.  In column-major terms C^T (N x M) = B^T A.
 static rsk_status gemm_nt(rsk_handle* h, const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int64_t M,
@@ -426,18 +525,20 @@ static rsk_status gemm_nt(rsk_handle* h, const __nv_bfloat16* A, const __nv_bflo
 // multiple of 8, because the GEMM library only takes its fast paths for such shapes.
 static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws& w, cudaStream_t s) {
     Libs& L = g_libs;
-    const size_t smem = size_t(r) * (r + 1) / 2 * 4;
+    const int nt = (r + 31) / 32;
+    const size_t smem = size_t(nt) * (nt + 1) / 2 * 1024 * 4;
     if (smem > 227 * 1024) return fail(h, RSK_ERR_UNSUPPORTED, "r = %d too large for the shared-memory Cholesky", r);
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     for (int round = 0; round < 3; ++round) {
         // X row-major is X^T column-major (rp x rows, ld rp):  G = X^T (X^T)^T
         int pr = prof_begin(h, s, RSK_KERNEL_DENSE);
         rsk_status st = lt_matmul(h, 0, 1, rp, rp, rows, X, CUDA_R_32F, rp, X, rp, w.G, CUDA_R_32F, rp, 1.f,
-                                  CUBLAS_COMPUTE_32F, w.ltws, s);
+                                  fp32_compute(h), w.ltws, s);
         prof_end(h, s, pr);
         if (st != RSK_OK) return st;
         pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        k_cholesky<<<1, 1024, smem, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows), h->dev_status);
+        k_cholesky<<<1, kCholThreads, smem, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows),
+                                                  h->dev_status);
         prof_end(h, s, pr);
         RSK_LAUNCH_CHECK(h);
         // w.R <- L^{-1} on the leading r x r block: solve L X = I (lower, column-major, ld rp)
@@ -446,8 +547,8 @@ static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws&
         if (L.strsm(L.bh, kSideLeft, kFillLower, kOpN, kDiagNonUnit, r, r, &one, w.Lf, rp, w.R, rp) != 0)
             return fail(h, RSK_ERR_CUDA, "cublasStrsm failed");
         pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        st = lt_matmul(h, 0, 0, rp, rows, rp, w.R, CUDA_R_32F, rp, X, rp, w.X2, CUDA_R_32F, rp, 1.f,
-                       CUBLAS_COMPUTE_32F, w.ltws, s);
+        st = lt_matmul(h, 0, 0, rp, rows, rp, w.R, CUDA_R_32F, rp, X, rp, w.X2, CUDA_R_32F, rp, 1.f, fp32_compute(h),
+                       w.ltws, s);
         prof_end(h, s, pr);
         if (st != RSK_OK) return st;
         RSK_CUDA_TRY(h, cudaMemcpyAsync(X, w.X2, size_t(rows) * rp * 4, cudaMemcpyDeviceToDevice, s));
