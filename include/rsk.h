@@ -131,6 +131,18 @@ rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype
                                  int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
                                  rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
 
+/* a3 with A in HOST memory (pinned for the copies to overlap; pageable works, serialised): the
+ * same SA = S * A as rsk_sparse_sign_apply, computed while A streams to the device.  A is cut into
+ * row blocks of whole index chunks (about 256 MB each); block b is copied on an internal stream into
+ * one of two device staging buffers while block b-1 is sketched on `stream`; SA is the sum of the
+ * block sketches in block order (deterministic; it can differ from rsk_sparse_sign_apply in the
+ * last bits because the partial sums are grouped by block).  SA is a device array.  Asynchronous
+ * with respect to the host: A_host must stay valid until `stream` has passed this call.  Not a step
+ * of the paper: the end-to-end form of a3 when A lives on the host. */
+rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                      int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
+                                      rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
+
 /* The same SA = S * A for callers that cannot allocate device memory (code where cudaMalloc is
  * unavailable or forbidden, e.g. inside a host application that owns every device buffer, or a
  * path that must not allocate after start-up).  The paper has no counterpart: this is a deployment

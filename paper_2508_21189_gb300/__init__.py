@@ -111,6 +111,22 @@ def rsk_sparse_sign_apply(A, d, zeta, seed, out_dtype=torch.float32, out=None, s
     return out
 
 
+def rsk_sparse_sign_apply_host(A, d, zeta, seed, out_dtype=torch.float32, out=None, device=None, stream=None):
+    """SA = S @ A for a HOST tensor A (n x k row-major, pinned for overlap); SA on the device."""
+    if A.is_cuda or A.dim() != 2 or A.stride(1) != 1 or A.stride(0) < A.shape[1]:
+        raise ValueError("A must be a 2-D row-major host tensor with unit column stride")
+    n, k = A.shape
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=dev)
+    _matrix(out, "out")
+    h = handle(out.device)
+    st = load().rsk_sparse_sign_apply_host(h, A.data_ptr(), _dt(A), n, k, A.stride(0), d, zeta, seed,
+                                           out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
 def rsk_split_pairs(A, stream=None):
     """Interleaved double-float form of a CUDA FP64 matrix: float32 tensor (n, k, 2) = (hi, lo)."""
     _matrix(A, "A")

@@ -29,6 +29,7 @@ SIGNATURES = {
     "rsk_sparse_sign_index": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
     "rsk_sparse_sign_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_apply_noalloc": [c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_sparse_sign_apply_host": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_create": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p],
     "rsk_sparse_sign_plan_apply": [c_p, c_p, c_p, c_i32, c_i64, c_i64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_destroy": [c_p, c_p, c_p],

@@ -559,6 +559,18 @@ __global__ void k_reduce(const Acc* __restrict__ partials, int64_t pstride, int6
     SA[i * ldsa + col] = Out(double(sum) * scale);
 }
 
+// SA = sum over blocks of the per-block sketches (d x k packed, block stride bstride), in order.
+template <typename Out>
+__global__ void k_sum_blocks(const Out* __restrict__ outs, int64_t bstride, int nblk, int d, int64_t k,
+                             Out* __restrict__ SA, int64_t ldsa) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= int64_t(d) * k) return;
+    const int64_t i = idx / k, col = idx - i * k;
+    Out acc = Out(0);
+    for (int b = 0; b < nblk; ++b) acc += outs[int64_t(b) * bstride + idx];
+    SA[i * ldsa + col] = acc;
+}
+
 // ------------------------------------------------------------------------------------------
 // Host side.
 // ------------------------------------------------------------------------------------------
@@ -926,6 +938,90 @@ rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype
     if (st != RSK_OK) return st;
     return apply_with_index(h, offs, ents, A, a_dtype, n, k, lda, int(d), zeta, SA, sa_dtype, ldsa, partials, p,
                             stream);
+}
+
+rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                      int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
+                                      rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    st = check_apply_args(h, A_host, a_dtype, k, lda, SA, sa_dtype, ldsa);
+    if (st != RSK_OK) return st;
+    const size_t es = rsk::dtype_size(a_dtype);
+    const int C = chunk_rows(zeta);
+    // row blocks of whole chunks, about 256 MB of A each; two device staging buffers
+    const int64_t row_bytes = k * int64_t(es);
+    int64_t brows = std::max<int64_t>(C, ((int64_t(256) << 20) / row_bytes) / C * C);
+    brows = std::min<int64_t>(brows, (n + C - 1) / C * C);
+    const int64_t nblk = (n + brows - 1) / brows;
+    const ApplyPlan p = plan_apply(h, std::min<int64_t>(n, brows), k, int(d), zeta, a_dtype);
+    const size_t obytes = size_t(d) * k * (sa_dtype == RSK_F64 ? 8 : 4);
+    const size_t need = rsk::Carver::round(offsets_count(n, int(d), zeta) * 2) +
+                        rsk::Carver::round(entries_count(n, zeta) * 2) + rsk::Carver::round(p.partial_bytes) +
+                        2 * rsk::Carver::round(size_t(brows) * row_bytes) + size_t(nblk) * rsk::Carver::round(obytes) +
+                        1024;
+    st = rsk::ensure_workspace(h, need, stream);
+    if (st != RSK_OK) return st;
+    st = rsk::ensure_streams(h, 2);
+    if (st != RSK_OK) return st;
+    rsk::Carver cv(h->ws);
+    uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
+    uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
+    void* partials = cv.take<char>(p.partial_bytes);
+    char* stage[2] = {cv.take<char>(size_t(brows) * row_bytes), cv.take<char>(size_t(brows) * row_bytes)};
+    char* outs = cv.take<char>(size_t(nblk) * rsk::Carver::round(obytes));
+    const size_t ostride = rsk::Carver::round(obytes);
+    cudaStream_t cs = h->streams[1];  // copy stream
+    cudaEvent_t ev_ready, copied[2], freed[2];
+    RSK_CUDA_TRY(h, cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) {
+        RSK_CUDA_TRY(h, cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming));
+        RSK_CUDA_TRY(h, cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming));
+    }
+    // the copy stream starts after the caller's earlier work on `stream` (the workspace may be reused)
+    RSK_CUDA_TRY(h, cudaEventRecord(ev_ready, stream));
+    RSK_CUDA_TRY(h, cudaStreamWaitEvent(cs, ev_ready, 0));
+    st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
+    for (int64_t b = 0; st == RSK_OK && b < nblk; ++b) {
+        const int64_t r0 = b * brows, rows = std::min<int64_t>(brows, n - r0);
+        char* buf = stage[b & 1];
+        if (b >= 2) RSK_CUDA_TRY(h, cudaStreamWaitEvent(cs, freed[b & 1], 0));
+        const char* src = static_cast<const char*>(A_host) + size_t(r0) * size_t(lda) * es;
+        if (lda == k)
+            RSK_CUDA_TRY(h, cudaMemcpyAsync(buf, src, size_t(rows) * row_bytes, cudaMemcpyHostToDevice, cs));
+        else
+            RSK_CUDA_TRY(h, cudaMemcpy2DAsync(buf, size_t(row_bytes), src, size_t(lda) * es, size_t(row_bytes),
+                                              size_t(rows), cudaMemcpyHostToDevice, cs));
+        RSK_CUDA_TRY(h, cudaEventRecord(copied[b & 1], cs));
+        RSK_CUDA_TRY(h, cudaStreamWaitEvent(stream, copied[b & 1], 0));
+        // the block is whole chunks of the global index: its sub-index starts at chunk r0 / C
+        const int64_t c0 = r0 / C;
+        const ApplyPlan pb = plan_apply(h, rows, k, int(d), zeta, a_dtype);
+        st = apply_with_index(h, offs + c0 * offsets_pitch(int(d)), ents + c0 * C * zeta, buf, a_dtype, rows, k, k,
+                              int(d), zeta, outs + size_t(b) * ostride, sa_dtype, k, partials, pb, stream);
+        RSK_CUDA_TRY(h, cudaEventRecord(freed[b & 1], stream));
+    }
+    if (st == RSK_OK) {
+        // SA = sum of the block sketches, in block order
+        const int64_t total = d * k;
+        if (sa_dtype == RSK_F64)
+            k_sum_blocks<double><<<unsigned((total + 255) / 256), 256, 0, stream>>>(
+                reinterpret_cast<const double*>(outs), int64_t(ostride / 8), int(nblk), int(d), k,
+                static_cast<double*>(SA), ldsa);
+        else
+            k_sum_blocks<float><<<unsigned((total + 255) / 256), 256, 0, stream>>>(
+                reinterpret_cast<const float*>(outs), int64_t(ostride / 4), int(nblk), int(d), k,
+                static_cast<float*>(SA), ldsa);
+        if (cudaGetLastError() != cudaSuccess) st = rsk::fail(h, RSK_ERR_CUDA, "block sum launch failed");
+    }
+    // events may be destroyed while work is pending (the driver releases them on completion)
+    cudaEventDestroy(ev_ready);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventDestroy(copied[i]);
+        cudaEventDestroy(freed[i]);
+    }
+    return st;
 }
 
 rsk_status rsk_sparse_sign_plan_create(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,

@@ -214,3 +214,22 @@ def test_pairs_apply_parity(rsk):
     P = rsk.rsk_split_pairs(A)
     SA = rsk.rsk_sparse_sign_apply_pairs(P, d, zeta, 5).cpu().numpy()
     check_rows(SA, A.cpu().numpy(), d, zeta, 5, 2.0 ** -40)
+
+
+@pytest.mark.parametrize("dtype,n,k,d", [(torch.bfloat16, 1 << 20, 256, 2048), (torch.float32, 300001, 37, 100),
+                                         (torch.float64, 5000, 12, 64)])
+def test_host_input_apply(rsk, dtype, n, k, d):
+    # A streamed from pinned host memory in row blocks (several blocks for the 2^20-row case, a ragged
+    # last block, an odd k that takes the plain-load path): equal to the device-input apply up to the
+    # regrouping of the partial sums, and against the oracle on sampled columns
+    A32 = synthetic.colscaled_gaussian(n, k, seed=n + k, device="cpu", dtype=torch.float32)
+    A = A32.to(dtype).pin_memory()
+    out_dt = torch.float64 if dtype == torch.float64 else torch.float32
+    SA_h = rsk.rsk_sparse_sign_apply_host(A, d, 8, 77, out_dtype=out_dt)
+    SA_d = rsk.rsk_sparse_sign_apply(A.cuda(), d, 8, 77, out_dtype=out_dt)
+    torch.cuda.synchronize()
+    diff = (SA_h.double() - SA_d.double()).abs().max().item()
+    scale = SA_d.double().abs().max().item()
+    assert diff <= (1e-12 if dtype == torch.float64 else 1e-5) * scale, diff
+    cols = list(range(min(k, 3)))
+    check_rows(SA_h.double().cpu().numpy()[:, cols], A.double().numpy()[:, cols], d, 8, 77, 2.0 ** -24)
