@@ -67,7 +67,7 @@ __device__ void qr_one(const BProb& q, double* red);
 
 // Persistent: one CTA per SM pulls problems from a queue ordered by decreasing work (d k^2), so
 // the largest factorizations start first and the small ones fill in behind them (LPT order).
-__global__ void __launch_bounds__(512) k_qr_b(BProb* P, const int* __restrict__ order, int count,
+__global__ void __launch_bounds__(1024) k_qr_b(BProb* P, const int* __restrict__ order, int count,
                                               unsigned int* queue) {
     __shared__ double red[32];
     __shared__ int next_s;
@@ -845,7 +845,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     // ---- QR, R^{-1}, warm start
     const int pr0 = prof_begin(h, main_s, RSK_KERNEL_DENSE);
     RSK_CUDA_TRY(h, cudaMemsetAsync(dqueue + 16, 0, 4, main_s));
-    k_qr_b<<<std::min(count, h->num_sms), 512, 0, main_s>>>(dP, dorder, count, dqueue + 16);
+    k_qr_b<<<std::min(count, h->num_sms), 1024, 0, main_s>>>(dP, dorder, count, dqueue + 16);
     k_rinv_b<<<count, 512, 0, main_s>>>(dP);
     k_trmv_b<<<count, 256, 0, main_s>>>(dP, 0, -1, 0, 0);
     prof_end(h, main_s, pr0);

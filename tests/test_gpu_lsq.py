@@ -107,3 +107,29 @@ def test_invalid(rsk):
     b = torch.zeros(100, dtype=torch.float64, device="cuda")
     with pytest.raises(rsk.RskError):
         solve(rsk, A, b, 5)          # d < k
+
+
+def _eta_torch(A, b, x):
+    """eta of the oracle's definition, recomputed independently in FP64 torch arithmetic on the GPU."""
+    A64, b64, x64 = A.double(), b.double(), x.double()
+    r = b64 - A64 @ x64
+    nr = r.norm().item()
+    if nr == 0.0:
+        return 0.0
+    fa = A64.norm().item()
+    ls = (A64.T @ r).norm().item() / (fa * nr)
+    cons = nr / (fa * x64.norm().item() + b64.norm().item())
+    return min(ls, cons)
+
+
+@pytest.mark.parametrize("sketch,inner", [("f32x2", "f32x2"), (torch.float64, torch.float64)])
+def test_full_size_workload(rsk, sketch, inner):
+    """The benchmark's single least-squares workload: A = Q_U diag(logspace(0,-8)) V^T of 2^20 x 500
+    FP64, b = A x* + 1e-6 noise, d = 2000, zeta = 8; eta <= 1e-10 recomputed independently."""
+    A, b, _ = synthetic.lsq_problem(1 << 20, 500, seed=31, cond_exp=8.0, noise=1e-6, device="cuda")
+    x, info = solve(rsk, A, b, 2000, zeta=8, seed=7, sketch_dtype=sketch, inner_dtype=inner)
+    eta = _eta_torch(A, b, x)
+    assert eta <= 1e-10, (eta, info)
+    assert info["status"] == "RSK_OK"
+    rn = (b - A @ x).norm().item()
+    assert abs(info["residual_norm"] - rn) <= 1e-6 * rn

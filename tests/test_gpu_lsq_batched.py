@@ -86,3 +86,26 @@ def test_batched_invalid(rsk):
     b = torch.zeros(10, dtype=torch.float64, device="cuda")
     with pytest.raises(rsk.RskError):
         rsk.rsk_lstsq_sketch_precond_batched([A], [b])
+
+
+def test_batched_full_size_workload(rsk):
+    """The benchmark's batched workload: 512 problems, n_i log-uniform in [4096, 262144], k_i uniform
+    in [16, 256], Gaussian A_i x logspace(-6, 0) column scales in FP32, Gaussian b_i, d_i = 4 k_i;
+    every eta <= 1e-10 recomputed independently in FP64 torch arithmetic."""
+    ns, ks = synthetic.batched_sizes(512, seed=404)
+    As, bs = [], []
+    for i, (n, k) in enumerate(zip(ns, ks)):
+        A, b = synthetic.batched_problem(n, k, seed=10_000 + i, device="cuda", dtype=torch.float32)
+        As.append(A)
+        bs.append(b)
+    xs, infos = rsk.rsk_lstsq_sketch_precond_batched(As, bs, zeta=8, seed=9, sketch_dtype=torch.float32,
+                                                     inner_dtype=torch.float32)
+    worst = 0.0
+    for A, b, x, info in zip(As, bs, xs, infos):
+        A64, b64 = A.double(), b
+        r = b64 - A64 @ x
+        nr, fa = r.norm().item(), A64.norm().item()
+        eta = min((A64.T @ r).norm().item() / (fa * nr), nr / (fa * x.norm().item() + b64.norm().item()))
+        worst = max(worst, eta)
+        assert info["status"] == "RSK_OK"
+    assert worst <= 1e-10, worst
