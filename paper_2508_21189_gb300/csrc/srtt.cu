@@ -36,9 +36,13 @@ constexpr int kBoxRows = 256;
 constexpr uint32_t kStreamD = 1;
 constexpr uint32_t kStreamP = 2;
 // Z layout: row r of the transformed block starts at float offset r*8 + 8*(r >> 5) (a pad of 8
-// floats after every 32 rows keeps both butterfly layouts free of bank conflicts).
+// floats after every 32 rows keeps both butterfly layouts free of bank conflicts), and its two
+// 16-byte halves are swapped when bit 2 of r is set: a 16-byte load of a random row then falls on
+// any of the 8 bank groups (not 4), while each butterfly access sees one permutation per warp.
 constexpr int kZFloats = kBlk * kCols + (kBlk / 32) * kCols;
 __device__ __forceinline__ int zoff(int r) { return r * kCols + kCols * (r >> 5); }
+__device__ __forceinline__ int zswz(int r) { return ((r >> 2) & 1) << 2; }  // XOR on the column
+__device__ __forceinline__ int zel(int r, int c) { return zoff(r) + (c ^ zswz(r)); }
 
 // ------------------------------------------------------------------------------------------
 // P and D.
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         }
         fwht64(v);
 #pragma unroll
-        for (int x = 0; x < 64; ++x) Z[zoff(g1 + 32 * x) + c1] = v[x];
+        for (int x = 0; x < 64; ++x) Z[zel(g1 + 32 * x, c1)] = v[x];
         __syncthreads();
         // stage buffer is free: refill it while the block is finished
         if (TMA && ahead.item < a.nitems) {
@@ -340,18 +344,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int y = 0; y < 32; ++y) v[32 * h + y] = Z[zoff(32 * (g2 + 32 * h) + y) + c2];
+            for (int y = 0; y < 32; ++y) v[32 * h + y] = Z[zel(32 * (g2 + 32 * h) + y, c2)];
         fwht32x2(v);
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int y = 0; y < 32; ++y) Z[zoff(32 * (g2 + 32 * h) + y) + c2] = v[32 * h + y];
+            for (int y = 0; y < 32; ++y) Z[zel(32 * (g2 + 32 * h) + y, c2)] = v[32 * h + y];
         __syncthreads();
         // gather: Y[q] += (-1)^{popcount(p_hi & blk)} Z[p_lo]
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
             const float4* zr = reinterpret_cast<const float4*>(Z + zoff(plo[j]));
-            const float4 z0 = zr[0], z1 = zr[1];
+            const int sw = (plo[j] >> 2) & 1;  // halves swapped for this row
+            const float4 za = zr[sw], zb = zr[sw ^ 1];
+            const float4 z0 = za, z1 = zb;
             const float sg = (__popc(uint32_t(phi[j]) & uint32_t(blk)) & 1) ? -1.f : 1.f;
             acc[j][0] += sg * z0.x;
             acc[j][1] += sg * z0.y;
