@@ -167,6 +167,7 @@ struct SrttArgs {
     int64_t n, k;
     int d, nblocks, nslices, R, nitems;
     const int32_t* prow;    // d selected rows
+    const uint32_t* dbits;  // nblocks * 64 words of D
     float* partials;        // [item][d][kCols]
     int64_t pstride;        // d * kCols
     uint64_t seed;
@@ -233,8 +234,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
     uint8_t* const stage0 = sm;
     uint8_t* const stage1 = sm + kStageBytes;
     float* Z = reinterpret_cast<float*>(sm + 2 * kStageBytes);
-    uint32_t* dwords = reinterpret_cast<uint32_t*>(Z + kZFloats);  // 64 words of D for the block
-    uint64_t* bars = reinterpret_cast<uint64_t*>(dwords + kBlk / 32);
+    uint32_t* dwords = reinterpret_cast<uint32_t*>(Z + kZFloats);  // 64 words of D (plain-load path)
+    uint32_t* dstage = dwords + kBlk / 32;                          // 2 x 64 words staged with the block (TMA)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(dstage + 2 * (kBlk / 32));
 
     const int tid = threadIdx.x;
 
@@ -256,9 +258,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         int nbox = 0;
         for (int bx = 0; bx < kBlk / kBoxRows; ++bx)
             if (row0 + bx * kBoxRows < a.n) ++nbox;
-        rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kCols * sizeof(T)));
+        rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kCols * sizeof(T)) + uint32_t(kBlk / 32 * 4));
         for (int bx = 0; bx < nbox; ++bx)
             rskd::tma_load_2d(dst + bx * kBoxRows * kCols * sizeof(T), &tmap, c.s * kCols, int(row0 + bx * kBoxRows), bar);
+        // the block's 64 words of D, drawn beforehand by k_srtt_dbits
+        rskd::bulk_load(dstage + (dst == stage0 ? 0 : kBlk / 32), a.dbits + int64_t(c.blk) * (kBlk / 32),
+                        uint32_t(kBlk / 32 * 4), bar);
     };
     SrttCursor cur, ahead;
     cursor_item(a, cur, int(blockIdx.x));
@@ -300,8 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         const int st = it & 1;
         const int s = cur.s;
         const int blk = cur.blk;
-        // D words of this block (16 Philox blocks of 4 words)
-        if (tid < 16) {
+        // D words of this block (16 Philox blocks of 4 words): staged with the block on the TMA path
+        if (!TMA && tid < 16) {
             const rskd::Block4 w = rskd::philox_block(a.seed, kStreamD, uint64_t(blk) * 16 + tid, 0);
             dwords[4 * tid + 0] = w.v[0];
             dwords[4 * tid + 1] = w.v[1];
@@ -311,6 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         bool ok = true;
         if constexpr (TMA) ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
         if (__syncthreads_or(!ok)) break;
+        const uint32_t* dw = TMA ? dstage + st * (kBlk / 32) : dwords;
         const T* raw = reinterpret_cast<const T*>(st ? stage1 : stage0);
         const T* gA = static_cast<const T*>(a.A);
         const int64_t row0 = int64_t(blk) * kBlk;
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
                 f = (row0 + row < a.n) ? to_f<T>(raw[row * kCols + c1]) : 0.f;
             else
                 f = (row0 + row < a.n && col < a.k) ? to_f<T>(gA[(row0 + row) * a.lda + col]) : 0.f;
-            const uint32_t neg = (dwords[row >> 5] >> (row & 31)) & 1u;
+            const uint32_t neg = (dw[row >> 5] >> (row & 31)) & 1u;
             v[x] = __uint_as_float(__float_as_uint(f) ^ (neg << 31));
         }
         fwht64(v);
@@ -418,7 +424,7 @@ rsk_status launch_draw(rsk_handle* h, int64_t n, int d, uint64_t seed, int32_t* 
 template <typename T, int QPT>
 rsk_status launch_srtt_t(rsk_handle* h, const CUtensorMap& map, const SrttArgs& args, bool tma, cudaStream_t stream) {
     auto kern = tma ? k_srtt<T, QPT, true> : k_srtt<T, QPT, false>;
-    const int smem = (tma ? 2 * kBlk * kCols * int(sizeof(T)) : 0) + kZFloats * 4 + (kBlk / 32) * 4 + 64;
+    const int smem = (tma ? 2 * kBlk * kCols * int(sizeof(T)) : 0) + kZFloats * 4 + 3 * (kBlk / 32) * 4 + 64;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SRTT_APPLY);
     kern<<<unsigned(std::min(args.nitems, h->num_sms)), kThreads, smem, stream>>>(map, args);
@@ -492,11 +498,17 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     args.seed = seed;
     args.status = h->dev_status;
     const size_t part_bytes = size_t(args.nitems) * args.pstride * 4;
-    st = rsk::ensure_workspace(h, rsk::Carver::round(part_bytes) + rsk::Carver::round(size_t(d) * 4) + 512, stream);
+    const int64_t ndw = int64_t(args.nblocks) * (kBlk / 32);
+    st = rsk::ensure_workspace(h, rsk::Carver::round(part_bytes) + rsk::Carver::round(size_t(d) * 4) +
+                                      rsk::Carver::round(size_t(ndw) * 4) + 512,
+                               stream);
     if (st != RSK_OK) return st;
     rsk::Carver cv(h->ws);
     int32_t* prow = cv.take<int32_t>(size_t(d));
     args.partials = cv.take<float>(size_t(args.nitems) * args.pstride);
+    uint32_t* dbits = cv.take<uint32_t>(size_t(ndw));
+    k_srtt_dbits<<<unsigned((ndw + 255) / 256), 256, 0, stream>>>(ndw, seed, dbits);
+    args.dbits = dbits;
     args.prow = prow;
     st = launch_draw(h, n, int(d), seed, prow, nullptr, stream);
     if (st != RSK_OK) return st;
