@@ -430,9 +430,18 @@ def run_ours(args):
             ev1.record()
             torch.cuda.synchronize()
             e2e_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
+            # the floor: a plain copy of the same pinned bytes to the device (no sketch)
+            copies = 3
+            ev0.record()
+            for _ in range(copies):
+                A.copy_(A_host, non_blocking=True)
+            ev1.record()
+            torch.cuda.synchronize()
+            copy_ms = ev0.elapsed_time(ev1) / copies
             r["e2e"] = {"value": round(world * a_bytes / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                         "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": out.numel() * 4,
-                        "ms_per_step": round(e2e_ms, 4)}
+                        "ms_per_step": round(e2e_ms, 4),
+                        "h2d_copy_gbs": round(a_bytes / (copy_ms / 1e3) / 1e9, 3)}
             del A_host
         result[name] = r
         del A

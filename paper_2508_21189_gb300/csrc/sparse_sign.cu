@@ -5,8 +5,9 @@
 // Kernels
 //   k_generate  one thread per column j: Philox words -> Floyd sample of zeta distinct rows + signs.
 //   k_index     one CTA per chunk of C columns (C = 768 for zeta <= 8): redraws the chunk's columns,
-//               counts per sketch row with per-warp counters, scans, and scatters (j_local | neg<<15)
-//               stably so every sketch row lists its columns in ascending j.  Output is chunk-local.
+//               counts per sketch row, scans, scatters (j_local | neg<<15) through shared-memory
+//               atomics, then sorts each sketch row's short list by j, so every sketch row lists its
+//               columns in ascending j whatever order the atomics took.  Output is chunk-local.
 //   k_apply     one CTA per (128-byte column slice, block of sketch rows, range of chunks).  Per chunk,
 //               TMA streams the chunk's row slices of A and bulk copies bring the chunk's index into
 //               shared memory (double buffered, one mbarrier per stage).  A group of 8 lanes owns
@@ -30,7 +31,7 @@ constexpr int kRowBytes = 128;      // staged row slice of A
 constexpr int kMaxChunkEntries = 6144;
 constexpr int kApplyThreads = 512;
 constexpr int kGroups = kApplyThreads / 8;
-constexpr int kIndexThreads = 512;
+constexpr int kIndexThreads = 256;
 constexpr uint32_t kStreamLeft = 0;
 
 // Columns of S (= rows of A) per chunk: 768 for zeta <= 8, fewer for larger zeta so that a chunk
@@ -100,16 +101,17 @@ __global__ void k_generate(int64_t n, int d, int zeta, uint64_t seed, uint32_t s
 // Chunked inverted index.
 // ------------------------------------------------------------------------------------------
 struct IndexLayout {
-    size_t tgt_off, neg_off, cnt_off, out_off, scan_off, total;
+    size_t tgt_off, neg_off, cnt_off, beg_off, out_off, scan_off, total;
 };
 
-__host__ __device__ inline IndexLayout index_layout(int d, int zeta, int count_warps) {
+__host__ __device__ inline IndexLayout index_layout(int d, int zeta) {
     const int C = chunk_rows(zeta);
     IndexLayout L;
     L.tgt_off = 0;
     L.neg_off = align16(L.tgt_off + size_t(C) * zeta * 2);
     L.cnt_off = align16(L.neg_off + size_t(C) * 4);
-    L.out_off = align16(L.cnt_off + size_t(count_warps) * d * 4);
+    L.beg_off = align16(L.cnt_off + size_t(d) * 4);
+    L.out_off = align16(L.beg_off + size_t(d + 1) * 4);
     L.scan_off = align16(L.out_off + size_t(C) * zeta * 2);
     L.total = align16(L.scan_off + 2 * 32 * 4);
     return L;
@@ -117,13 +119,13 @@ __host__ __device__ inline IndexLayout index_layout(int d, int zeta, int count_w
 
 template <int ZMAX>
 __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int zeta, uint64_t seed, uint32_t stream,
-                                                         int count_warps, uint16_t* __restrict__ offsets,
-                                                         uint16_t* __restrict__ entries) {
+                                                         uint16_t* __restrict__ offsets, uint16_t* __restrict__ entries) {
     extern __shared__ __align__(16) uint8_t sm[];
-    const IndexLayout L = index_layout(d, zeta, count_warps);
+    const IndexLayout L = index_layout(d, zeta);
     uint16_t* tgt = reinterpret_cast<uint16_t*>(sm + L.tgt_off);
     uint32_t* neg = reinterpret_cast<uint32_t*>(sm + L.neg_off);
     unsigned int* cnt = reinterpret_cast<unsigned int*>(sm + L.cnt_off);
+    int* beg = reinterpret_cast<int*>(sm + L.beg_off);
     uint16_t* out = reinterpret_cast<uint16_t*>(sm + L.out_off);
     int* wsum = reinterpret_cast<int*>(sm + L.scan_off);
 
@@ -141,7 +143,6 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
         uint32_t nb;
         draw_column<ZMAX>(seed, stream, uint64_t(j0 + r), d, zeta, rr, nb);
         if (ZMAX == 8 && zeta == 8) {
-            // one 16-byte store per column: lanes write consecutive 16-byte pieces (no bank conflicts)
             uint4 pk;
             pk.x = uint32_t(rr[0]) | (uint32_t(rr[1 % ZMAX]) << 16);
             pk.y = uint32_t(rr[2 % ZMAX]) | (uint32_t(rr[3 % ZMAX]) << 16);
@@ -155,35 +156,26 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
         }
         neg[r] = nb;
     }
-    for (int i = tid; i < count_warps * d; i += kIndexThreads) cnt[i] = 0;
+    for (int i = tid; i < d; i += kIndexThreads) cnt[i] = 0;
     __syncthreads();
 
-    // 2. per-warp counts over a contiguous range of columns (shared-memory atomics; the counts do
-    //    not depend on the order of the increments)
-    const int per_w = (rows + count_warps - 1) / count_warps;
-    const int r0 = min(rows, warp * per_w), r1 = min(rows, r0 + per_w);
-    const int f0 = r0 * zeta, f1 = r1 * zeta;
-    if (warp < count_warps) {
-        unsigned int* mine = cnt + size_t(warp) * d;
-        for (int f = f0 + lane; f < f1; f += 32) atomicAdd(&mine[tgt[f]], 1u);
-    }
+    // 2. entries per sketch row
+    for (int f = tid; f < nent; f += kIndexThreads) atomicAdd(&cnt[tgt[f]], 1u);
     __syncthreads();
 
-    // 3. exclusive scan over sketch rows.  Warp w scans the contiguous range [w*R, (w+1)*R) with
-    //    lanes on consecutive rows (conflict-free), then the per-warp range totals are combined.
+    // 3. exclusive scan over sketch rows (warp w scans [w*R, (w+1)*R), lanes on consecutive rows)
     constexpr int kWarps = kIndexThreads / 32;
     const int R = (((d + kWarps - 1) / kWarps) + 31) & ~31;
     const int t0 = min(d, warp * R), t1 = min(d, t0 + R);
     int carry = 0;
-    int tots[16];
+    constexpr int kIt = (8192 / kWarps + 31) / 32;  // d <= 8192
+    int tots[kIt];
 #pragma unroll
-    for (int it = 0; it < 16; ++it) {
+    for (int it = 0; it < kIt; ++it) {
         const int base = t0 + 32 * it;
         if (base >= t1) break;
         const int i = base + lane;
-        int tot = 0;
-        if (i < t1)
-            for (int w = 0; w < count_warps; ++w) tot += int(cnt[size_t(w) * d + i]);
+        const int tot = i < t1 ? int(cnt[i]) : 0;
         tots[it] = tot;
         int incl = tot;
 #pragma unroll
@@ -195,18 +187,21 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     }
     if (lane == 0) wsum[warp] = carry;
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            wsum[32 + w] = acc;
-            acc += wsum[w];
+    if (warp == 0) {
+        const int v = lane < kWarps ? wsum[lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
+        if (lane < kWarps) wsum[32 + lane] = incl - v;
     }
     __syncthreads();
     carry = wsum[32 + warp];
     uint16_t* off_out = offsets + ch * pitch;
 #pragma unroll
-    for (int it = 0; it < 16; ++it) {
+    for (int it = 0; it < kIt; ++it) {
         const int base = t0 + 32 * it;
         if (base >= t1) break;
         const int i = base + lane;
@@ -218,42 +213,43 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
             if (lane >= o) incl += v;
         }
         if (i < t1) {
-            int run = carry + incl - tot;
+            const int run = carry + incl - tot;
             off_out[i] = uint16_t(run);
-            for (int w = 0; w < count_warps; ++w) {
-                const int c = int(cnt[size_t(w) * d + i]);
-                cnt[size_t(w) * d + i] = unsigned(run);
-                run += c;
-            }
+            beg[i] = run;
+            cnt[i] = unsigned(run);
         }
         carry += __shfl_sync(0xffffffffu, incl, 31);
     }
+    if (tid == 0) beg[d] = nent;
     for (int i = d + tid; i < pitch; i += kIndexThreads) off_out[i] = uint16_t(nent);
     __syncthreads();
 
-    // 4. stable scatter: each warp walks its columns in order, 32 entries per round.  A round whose
-    //    sketch rows are all distinct (the common case) needs no intra-round rank; otherwise the
-    //    lanes that share a row are ranked with __match_any_sync.
-    if (warp < count_warps) {
-        unsigned int* cur = cnt + size_t(warp) * d;
-        const unsigned lt = (1u << lane) - 1u;
-        for (int base = f0; base < f1; base += 32) {
-            const int f = base + lane;
-            const bool ok = f < f1;
-            const int t = ok ? int(tgt[f]) : (65536 + lane);
-            const unsigned peers = __match_any_sync(0xffffffffu, t);
-            if (ok) {
-                const int r = f / zeta, q = f - r * zeta;
-                out[cur[t] + __popc(peers & lt)] = uint16_t(r | (((neg[r] >> q) & 1u) << 15));
+    // 4. scatter in any order (the slot a shared-memory atomic hands out)
+    for (int f = tid; f < nent; f += kIndexThreads) {
+        const int r = f / zeta, q = f - r * zeta;
+        const unsigned pos = atomicAdd(&cnt[tgt[f]], 1u);
+        out[pos] = uint16_t(r | (((neg[r] >> q) & 1u) << 15));
+    }
+    __syncthreads();
+
+    // 5. order each sketch row's entries by column (columns within a row are distinct, so the
+    //    order is unique): insertion sort of the short per-row lists
+    for (int i = tid; i < d; i += kIndexThreads) {
+        const int b = beg[i], e = beg[i + 1];
+        for (int a = b + 1; a < e; ++a) {
+            const uint16_t v = out[a];
+            const int key = v & 0x7fff;
+            int k = a;
+            while (k > b && int(out[k - 1] & 0x7fff) > key) {
+                out[k] = out[k - 1];
+                --k;
             }
-            __syncwarp();
-            if (ok && lane == __ffs(peers) - 1) cur[t] += __popc(peers);
-            __syncwarp();
+            out[k] = v;
         }
     }
     __syncthreads();
 
-    // 5. write the chunk's entries (chunk blocks start at multiples of C*zeta*2 bytes, 16-aligned)
+    // 6. write the chunk's entries (chunk blocks start at multiples of C*zeta*2 bytes, 16-aligned)
     uint16_t* dst = entries + ch * C * zeta;
     const int n16 = (nent * 2) / 16;
     for (int v = tid; v < n16; v += kIndexThreads)
@@ -591,18 +587,13 @@ size_t entries_count(int64_t n, int zeta) { return size_t(n) * zeta + 16; }
 
 rsk_status launch_index(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed, uint32_t stream_id,
                         uint16_t* offs, uint16_t* ents, cudaStream_t stream) {
-    int warps = kIndexThreads / 32;
-    IndexLayout L = index_layout(d, zeta, warps);
-    while (L.total > 110 * 1024 && warps > 1) {
-        warps /= 2;
-        L = index_layout(d, zeta, warps);
-    }
+    const IndexLayout L = index_layout(d, zeta);
     if (L.total > 227 * 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "index build needs %zu B of shared memory", L.total);
     const int64_t nch = n_chunks_of(n, zeta);
     auto go = [&](auto kern) -> rsk_status {
         RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total)));
         const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_INDEX);
-        kern<<<unsigned(nch), kIndexThreads, L.total, stream>>>(n, d, zeta, seed, stream_id, warps, offs, ents);
+        kern<<<unsigned(nch), kIndexThreads, L.total, stream>>>(n, d, zeta, seed, stream_id, offs, ents);
         rsk::prof_end(h, stream, pr);
         RSK_LAUNCH_CHECK(h);
         return RSK_OK;
