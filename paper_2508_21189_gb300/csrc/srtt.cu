@@ -15,6 +15,9 @@
 //   k_srtt_draw   one CTA: P by Floyd's algorithm over [0, n) with d Philox draws (stream 2), the
 //                 q-th inserted coordinate being output row q; membership in a shared hash set.
 //   k_srtt_dbits  D as bits: word w of D is word(seed, 1, w >> 2, w & 3) (bit j set => D_{32w+j} = -1).
+//   k_srtt_dbits_t the same bits transposed per 2048-row block, as the transform kernel reads them.
+//   k_srtt_deal   one CTA: assigns the d output rows to the gather's slots so that the 8 lanes of each
+//                 quarter-warp read 8 different shared-memory bank groups (no gather conflicts).
 //   k_srtt        one CTA (256 threads) per (8-column slice, range of blocks): TMA double-buffered
 //                 block staging, sign flip + convert + FWHT, gather-accumulate into per-range partials.
 //   k_reduce_srtt sums the partials in range order and scales by d^{-1/2}.
@@ -153,6 +156,93 @@ __global__ void k_srtt_dbits(int64_t nwords, uint64_t seed, uint32_t* __restrict
     out[wd] = b.v[wd & 3];
 }
 
+// D as the transform kernel reads it: per 2048-row block, word 2g + h holds the signs of rows
+// g + 32 (32h + x), x = 0..31, in bit x (a 32 x 32 bit transpose of the block's natural words
+// 32h .. 32h + 31, done with one ballot per bit).  One warp per (block, h).
+__global__ void k_srtt_dbits_t(int64_t nblocks, uint64_t seed, uint32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
+    const int64_t b = blockIdx.x;
+    if (b >= nblocks) return;
+    const int64_t wd = b * (kBlk / 32) + 32 * h + lane;  // natural word index: rows 32 wd .. 32 wd + 31
+    const rskd::Block4 blk = rskd::philox_block(seed, kStreamD, uint64_t(wd >> 2), 0);
+    const uint32_t word = blk.v[wd & 3];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int g = 0; g < 32; ++g) {
+        const uint32_t t = __ballot_sync(0xffffffffu, (word >> g) & 1u);
+        if (lane == g) mine = t;
+    }
+    out[b * (kBlk / 32) + 2 * lane + h] = mine;
+}
+
+// Bank group (16-byte unit modulo 8) of the first 16-byte load the gather makes for transformed
+// row r; its second load falls on the group with the low bit flipped.
+__host__ __device__ inline int gather_group(int r) { return 2 * ((r + (r >> 5)) & 3) + ((r >> 2) & 1); }
+
+// Deal the d output rows to the gather's slots (slot tid + 256*j of k_srtt) so that the 8 lanes of
+// every quarter-warp read 8 different bank groups: the i-th output row (in row order) whose sampled
+// row falls in group g takes quarter i, lane g; rows beyond a group's share of quarters fill the
+// quarters other groups left empty, in order.  Deterministic; every output row gets one slot.
+__global__ void __launch_bounds__(1024) k_srtt_deal(const int32_t* __restrict__ prow, int d, int nslots,
+                                                    int32_t* __restrict__ slot_q) {
+    __shared__ int wc[32][8];
+    __shared__ int base[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nq = nslots / 8;
+    for (int s = tid; s < nslots; s += blockDim.x) slot_q[s] = -1;
+    if (tid < 8) base[tid] = 0;
+    __syncthreads();
+    constexpr int kPer = 2;  // d <= 2048 = 2 * 1024
+    int myg[kPer], myr[kPer];
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+        const int q = c * 1024 + tid;
+        const int g = q < d ? gather_group(prow[q] & (kBlk - 1)) : -1;
+        int lrank = 0;
+#pragma unroll
+        for (int gg = 0; gg < 8; ++gg) {
+            const unsigned bal = __ballot_sync(0xffffffffu, g == gg);
+            if (lane == 0) wc[warp][gg] = __popc(bal);
+            if (g == gg) lrank = __popc(bal & ((1u << lane) - 1u));
+        }
+        __syncthreads();
+        if (tid < 8) {
+            int acc = base[tid];
+            for (int w = 0; w < 32; ++w) {
+                const int t = wc[w][tid];
+                wc[w][tid] = acc;
+                acc += t;
+            }
+            base[tid] = acc;
+        }
+        __syncthreads();
+        myg[c] = g;
+        myr[c] = g >= 0 ? wc[warp][g] + lrank : 0;
+        __syncthreads();
+    }
+    int hole_pre[9], ovf_pre[9];
+    hole_pre[0] = ovf_pre[0] = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        hole_pre[g + 1] = hole_pre[g] + max(0, nq - base[g]);
+        ovf_pre[g + 1] = ovf_pre[g] + max(0, base[g] - nq);
+    }
+#pragma unroll
+    for (int c = 0; c < kPer; ++c) {
+        const int g = myg[c];
+        if (g < 0) continue;
+        int i = myr[c], l = g;
+        if (i >= nq) {
+            const int kk = ovf_pre[g] + (i - nq);
+            int h = 0;
+            while (h < 7 && hole_pre[h + 1] <= kk) ++h;
+            i = base[h] + (kk - hole_pre[h]);
+            l = h;
+        }
+        slot_q[8 * (i & 31) + l + 256 * (i >> 5)] = c * 1024 + tid;
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // The transform + gather kernel.
 // ------------------------------------------------------------------------------------------
@@ -167,7 +257,8 @@ struct SrttArgs {
     int64_t n, k;
     int d, nblocks, nslices, R, nitems;
     const int32_t* prow;    // d selected rows
-    const uint32_t* dbits;  // nblocks * 64 words of D
+    const int32_t* slot_q;  // output row handled by slot tid + 256*j, or -1
+    const uint32_t* dbits;  // nblocks * 64 words of D, transposed per block (k_srtt_dbits_t)
     float* partials;        // [item][d][kCols]
     int64_t pstride;        // d * kCols
     uint64_t seed;
@@ -198,30 +289,44 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// 64 values held as v[x] for rows base + stride*x; butterflies over the 6 bits of x.
-__device__ __forceinline__ void fwht64(float (&v)[64]) {
+// 64 values held as v[x] for rows base + stride*x; butterflies over the 6 bits of x.  The values
+// sit in register pairs (v[2i], v[2i+1]): the stage on bit 0 pairs the two halves of one register
+// pair, every later stage pairs two whole register pairs, which one packed FP32x2 add and one packed
+// subtract (fma by -1, exact) cover.
+__device__ __forceinline__ float2 bf_sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void fwht64(float2 (&w)[32]) {
 #pragma unroll
-    for (int h = 1; h < 64; h <<= 1) {
+    for (int i = 0; i < 32; ++i) {
+        const float a = w[i].x, b = w[i].y;
+        w[i] = make_float2(a + b, a - b);
+    }
 #pragma unroll
-        for (int x = 0; x < 64; ++x) {
-            if ((x & h) == 0) {
-                const float a = v[x], b = v[x + h];
-                v[x] = a + b;
-                v[x + h] = a - b;
+    for (int hh = 1; hh < 32; hh <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if ((i & hh) == 0) {
+                const float2 a = w[i], b = w[i + hh];
+                w[i] = __fadd2_rn(a, b);
+                w[i + hh] = bf_sub2(a, b);
             }
         }
     }
 }
 // 32 values per half: butterflies over the 5 bits of y inside each half of v.
-__device__ __forceinline__ void fwht32x2(float (&v)[64]) {
+__device__ __forceinline__ void fwht32x2(float2 (&w)[32]) {
 #pragma unroll
-    for (int h = 1; h < 32; h <<= 1) {
+    for (int i = 0; i < 32; ++i) {
+        const float a = w[i].x, b = w[i].y;
+        w[i] = make_float2(a + b, a - b);
+    }
 #pragma unroll
-        for (int x = 0; x < 64; ++x) {
-            if ((x & h) == 0 && ((x & 31) + h) < 32) {
-                const float a = v[x], b = v[x + h];
-                v[x] = a + b;
-                v[x + h] = a - b;
+    for (int hh = 1; hh < 16; hh <<= 1) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if ((i & hh) == 0 && ((i & 15) + hh) < 16) {
+                const float2 a = w[i], b = w[i + hh];
+                w[i] = __fadd2_rn(a, b);
+                w[i + hh] = bf_sub2(a, b);
             }
         }
     }
@@ -245,8 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
     float acc[QPT][kCols];
 #pragma unroll
     for (int j = 0; j < QPT; ++j) {
-        const int q = tid + kThreads * j;
-        const int p = q < a.d ? a.prow[q] : 0;
+        const int q = a.slot_q[tid + kThreads * j];
+        const int p = q >= 0 ? a.prow[q] : 0;
         plo[j] = p & (kBlk - 1);
         phi[j] = p >> 11;
 #pragma unroll
@@ -285,8 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         float* part = a.partials + int64_t(item) * a.pstride;
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
-            const int q = tid + kThreads * j;
-            if (q < a.d) {
+            const int q = a.slot_q[tid + kThreads * j];
+            if (q >= 0) {
                 float4* dst = reinterpret_cast<float4*>(part + int64_t(q) * kCols);
                 dst[0] = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
                 dst[1] = make_float4(acc[j][4], acc[j][5], acc[j][6], acc[j][7]);
@@ -305,23 +410,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         const int st = it & 1;
         const int s = cur.s;
         const int blk = cur.blk;
-        // D words of this block (16 Philox blocks of 4 words): staged with the block on the TMA path
-        if (!TMA && tid < 16) {
-            const rskd::Block4 w = rskd::philox_block(a.seed, kStreamD, uint64_t(blk) * 16 + tid, 0);
-            dwords[4 * tid + 0] = w.v[0];
-            dwords[4 * tid + 1] = w.v[1];
-            dwords[4 * tid + 2] = w.v[2];
-            dwords[4 * tid + 3] = w.v[3];
-        }
+        // D words of this block (transposed layout): staged with the block on the TMA path
+        if (!TMA && tid < kBlk / 32) dwords[tid] = a.dbits[int64_t(blk) * (kBlk / 32) + tid];
         bool ok = true;
         if constexpr (TMA) ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
         if (__syncthreads_or(!ok)) break;
         const uint32_t* dw = TMA ? dstage + st * (kBlk / 32) : dwords;
+        const uint2 tw = *reinterpret_cast<const uint2*>(dw + 2 * g1);  // signs of rows g1 + 32x
         const T* raw = reinterpret_cast<const T*>(st ? stage1 : stage0);
         const T* gA = static_cast<const T*>(a.A);
         const int64_t row0 = int64_t(blk) * kBlk;
         const int64_t col = int64_t(s) * kCols + c1;
-        float v[64];
+        float2 w[32];
         // pass 1: load, zero-pad beyond n (and beyond k), sign flip, stages on row bits 5..10
 #pragma unroll
         for (int x = 0; x < 64; ++x) {
@@ -331,12 +431,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
                 f = (row0 + row < a.n) ? to_f<T>(raw[row * kCols + c1]) : 0.f;
             else
                 f = (row0 + row < a.n && col < a.k) ? to_f<T>(gA[(row0 + row) * a.lda + col]) : 0.f;
-            const uint32_t neg = (dw[row >> 5] >> (row & 31)) & 1u;
-            v[x] = __uint_as_float(__float_as_uint(f) ^ (neg << 31));
+            const uint32_t sbit = ((x < 32 ? tw.x : tw.y) << (31 - (x & 31))) & 0x80000000u;
+            const float fv = __uint_as_float(__float_as_uint(f) ^ sbit);
+            if (x & 1) w[x >> 1].y = fv; else w[x >> 1].x = fv;
         }
-        fwht64(v);
+        fwht64(w);
 #pragma unroll
-        for (int x = 0; x < 64; ++x) Z[zel(g1 + 32 * x, c1)] = v[x];
+        for (int x = 0; x < 64; ++x) Z[zel(g1 + 32 * x, c1)] = (x & 1) ? w[x >> 1].y : w[x >> 1].x;
         __syncthreads();
         // stage buffer is free: refill it while the block is finished
         if (TMA && ahead.item < a.nitems) {
@@ -350,12 +451,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int y = 0; y < 32; ++y) v[32 * h + y] = Z[zel(32 * (g2 + 32 * h) + y, c2)];
-        fwht32x2(v);
+            for (int y = 0; y < 32; y += 2)
+                w[16 * h + (y >> 1)] = make_float2(Z[zel(32 * (g2 + 32 * h) + y, c2)], Z[zel(32 * (g2 + 32 * h) + y + 1, c2)]);
+        fwht32x2(w);
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int y = 0; y < 32; ++y) Z[zel(32 * (g2 + 32 * h) + y, c2)] = v[32 * h + y];
+            for (int y = 0; y < 32; y += 2) {
+                Z[zel(32 * (g2 + 32 * h) + y, c2)] = w[16 * h + (y >> 1)].x;
+                Z[zel(32 * (g2 + 32 * h) + y + 1, c2)] = w[16 * h + (y >> 1)].y;
+            }
         __syncthreads();
         // gather: Y[q] += (-1)^{popcount(p_hi & blk)} Z[p_lo]
 #pragma unroll
@@ -365,14 +470,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
             const float4 za = zr[sw], zb = zr[sw ^ 1];
             const float4 z0 = za, z1 = zb;
             const float sg = (__popc(uint32_t(phi[j]) & uint32_t(blk)) & 1) ? -1.f : 1.f;
-            acc[j][0] += sg * z0.x;
-            acc[j][1] += sg * z0.y;
-            acc[j][2] += sg * z0.z;
-            acc[j][3] += sg * z0.w;
-            acc[j][4] += sg * z1.x;
-            acc[j][5] += sg * z1.y;
-            acc[j][6] += sg * z1.z;
-            acc[j][7] += sg * z1.w;
+            const float2 sg2 = make_float2(sg, sg);
+            float2 t0 = __ffma2_rn(make_float2(z0.x, z0.y), sg2, make_float2(acc[j][0], acc[j][1]));
+            float2 t1 = __ffma2_rn(make_float2(z0.z, z0.w), sg2, make_float2(acc[j][2], acc[j][3]));
+            float2 t2 = __ffma2_rn(make_float2(z1.x, z1.y), sg2, make_float2(acc[j][4], acc[j][5]));
+            float2 t3 = __ffma2_rn(make_float2(z1.z, z1.w), sg2, make_float2(acc[j][6], acc[j][7]));
+            acc[j][0] = t0.x; acc[j][1] = t0.y; acc[j][2] = t1.x; acc[j][3] = t1.y;
+            acc[j][4] = t2.x; acc[j][5] = t2.y; acc[j][6] = t3.x; acc[j][7] = t3.y;
         }
         __syncthreads();
         const int done_item = cur.item;
@@ -499,19 +603,28 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     args.status = h->dev_status;
     const size_t part_bytes = size_t(args.nitems) * args.pstride * 4;
     const int64_t ndw = int64_t(args.nblocks) * (kBlk / 32);
+    // gather slots: kThreads x QPT, QPT the power of two launch_srtt picks for d
+    const int qpt_need = (int(d) + kThreads - 1) / kThreads;
+    const int nslots = kThreads * (qpt_need <= 1 ? 1 : qpt_need <= 2 ? 2 : qpt_need <= 4 ? 4 : 8);
     st = rsk::ensure_workspace(h, rsk::Carver::round(part_bytes) + rsk::Carver::round(size_t(d) * 4) +
-                                      rsk::Carver::round(size_t(ndw) * 4) + 512,
+                                      rsk::Carver::round(size_t(ndw) * 4) + rsk::Carver::round(size_t(nslots) * 4) + 512,
                                stream);
     if (st != RSK_OK) return st;
     rsk::Carver cv(h->ws);
     int32_t* prow = cv.take<int32_t>(size_t(d));
     args.partials = cv.take<float>(size_t(args.nitems) * args.pstride);
     uint32_t* dbits = cv.take<uint32_t>(size_t(ndw));
-    k_srtt_dbits<<<unsigned((ndw + 255) / 256), 256, 0, stream>>>(ndw, seed, dbits);
+    int32_t* slot_q = cv.take<int32_t>(size_t(nslots));
+    k_srtt_dbits_t<<<unsigned(args.nblocks), 64, 0, stream>>>(args.nblocks, seed, dbits);
     args.dbits = dbits;
     args.prow = prow;
     st = launch_draw(h, n, int(d), seed, prow, nullptr, stream);
     if (st != RSK_OK) return st;
+    if (d <= 8 * kThreads) {
+        k_srtt_deal<<<1, 1024, 0, stream>>>(prow, int(d), nslots, slot_q);
+        RSK_LAUNCH_CHECK(h);
+    }
+    args.slot_q = slot_q;
 
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
