@@ -277,7 +277,8 @@ rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const 
  * Outputs (device): U FP32 m x r row-major, s FP64[r] descending, Vt FP32 r x n row-major, with
  * A ~ U diag(s) Vt.  Products run on BF16 copies of A with FP32 accumulation; orthonormalisation is
  * shifted CholeskyQR3 in FP32 (the factor's inverse applied as a product); the r x r eigenproblem of
- * B B^T is solved in FP64.  The first call for a shape times cuBLASLt's candidate algorithms once.
+ * B B^T is solved in FP32 (B B^T is formed in FP32).  The first call for a shape times cuBLASLt's
+ * candidate algorithms once.
  * Limits: 1 <= r <= min(m, n, 320), 1 <= zeta <= min(r, 32), m, n < 2^31.  Needs cuBLAS, cuBLASLt
  * and cuSOLVER at run time (RSK_ERR_UNSUPPORTED when they cannot be loaded). */
 rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t n, int64_t lda, int32_t r, int32_t power_iters,

@@ -5,21 +5,22 @@
 // power iterations; q subspace iterations Q = orth(A^T Q), Q = orth(A Q) are applied after the
 // sketch (re-orthonormalising after every product).
 //
-// Precision plan.  A (FP32) is converted once to BF16 in both orientations (A and A^T) so that
-// every product is a GEMM with both operands K-major:
+// Precision plan.  A (FP32) is converted once to BF16 in both orientations (A and A^T, one pass
+// over A) so that every product is a GEMM with both operands K-major:
 //     Y = A Omega      : [m x n] * [r x n]^T      Z = A^T Q : [n x m] * [r x m]^T
 // with FP32 accumulation on the tensor cores.  orth() is shifted CholeskyQR3 in FP32 (one shifted
-// round, two plain ones): the Gram G = X^T X, a Cholesky of G (+ shift) in shared memory, and
+// round, two plain ones): the Gram G = X^T X, a Cholesky of G (+ shift) by cuSOLVER, and
 // X <- X R^{-1}; the shift keeps the first Cholesky defined up to kappa(X) ~ u^{-1}, the plain rounds
 // restore orthogonality to O(u_32), below the BF16 error of the products.  The small SVD of
-// B = Z^T comes from the symmetric eigenproblem of Z^T Z (r x r, FP64).
+// B = Z^T comes from the symmetric eigenproblem of Z^T Z (r x r, FP32: Z^T Z is formed in FP32, so
+// an FP64 eigensolver would add no accuracy).
 //
 // The plain products (the BF16 GEMMs, the FP32 Gram matrices and the FP32 products X R^{-1}) go
 // through cuBLASLt matmuls, each shape autotuned once (the heuristic's candidates timed on the
 // operands, the fastest kept; the FP32 ones use cuBLAS's FP32 emulation on the BF16 tensor cores
-// when it is offered); R^{-1} comes from this file's Cholesky kernel, so no triangular solve
-// runs on the tall basis.  The r x r eigenproblem goes through cuSOLVER.  Both libraries are loaded at
-// first use with dlopen; everything else is this file's kernels.
+// when it is offered); R^{-1} comes from a triangular solve on the r x r factor, so no triangular
+// solve runs on the tall basis.  The r x r Cholesky and eigenproblem go through cuSOLVER.  Both
+// libraries are loaded at first use with dlopen; everything else is this file's kernels.
 #include <cublasLt.h>
 #include <cuda_bf16.h>
 #include <dlfcn.h>
@@ -60,8 +61,10 @@ struct Libs {
                  float*, int);
     int (*solverCreate)(cusolverH*);
     int (*solverSetStream)(cusolverH, cudaStream_t);
-    int (*dsyevdBuf)(cusolverH, int, int, int, const double*, int, const double*, int*);
-    int (*dsyevd)(cusolverH, int, int, int, double*, int, double*, double*, int, int*);
+    int (*ssyevdBuf)(cusolverH, int, int, int, const float*, int, const float*, int*);
+    int (*ssyevd)(cusolverH, int, int, int, float*, int, float*, float*, int, int*);
+    int (*spotrfBuf)(cusolverH, int, int, float*, int, int*);
+    int (*spotrf)(cusolverH, int, int, float*, int, float*, int, int*);
     cublasH bh = nullptr;
     cusolverH sh = nullptr;
 };
@@ -87,6 +90,9 @@ struct LtLib {
     decltype(&cublasLtMatmul) matmul = nullptr;
     decltype(&cublasLtMatmulDescDestroy) descDestroy = nullptr;
     decltype(&cublasLtMatrixLayoutDestroy) layoutDestroy = nullptr;
+    decltype(&cublasLtEmulationDescCreate) emuCreate = nullptr;       // optional
+    decltype(&cublasLtEmulationDescSetAttribute) emuSet = nullptr;    // optional
+    cublasLtEmulationDesc_t emu = nullptr;  // emulation without special-value handling
     cublasLtHandle_t lh = nullptr;
 };
 LtLib g_lt;
@@ -116,7 +122,8 @@ rsk_status load_libs(rsk_handle* h) {
               sym(L.blas, "cublasStrsm_v2", L.strsm) && sym(L.blas, "cublasSgemm_v2", L.sgemm) &&
               sym(L.solver, "cusolverDnCreate", L.solverCreate) &&
               sym(L.solver, "cusolverDnSetStream", L.solverSetStream) &&
-              sym(L.solver, "cusolverDnDsyevd_bufferSize", L.dsyevdBuf) && sym(L.solver, "cusolverDnDsyevd", L.dsyevd);
+              sym(L.solver, "cusolverDnSsyevd_bufferSize", L.ssyevdBuf) && sym(L.solver, "cusolverDnSsyevd", L.ssyevd) &&
+              sym(L.solver, "cusolverDnSpotrf_bufferSize", L.spotrfBuf) && sym(L.solver, "cusolverDnSpotrf", L.spotrf);
     if (!ok) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLAS/cuSOLVER symbols missing");
     if (L.blasCreate(&L.bh) != 0 || L.solverCreate(&L.sh) != 0)
         return rsk::fail(h, RSK_ERR_CUDA, "cuBLAS/cuSOLVER handle creation failed");
@@ -133,6 +140,15 @@ rsk_status load_libs(rsk_handle* h) {
          sym(T.so, "cublasLtMatmulAlgoGetHeuristic", T.heuristic) && sym(T.so, "cublasLtMatmul", T.matmul) &&
          sym(T.so, "cublasLtMatmulDescDestroy", T.descDestroy) &&
          sym(T.so, "cublasLtMatrixLayoutDestroy", T.layoutDestroy);
+    // The FP32 products only ever see finite operands (orthonormalisation intermediates; a failed
+    // factorization is reported through the status word), so the emulated matmuls are told not to
+    // scan for and patch infinities and NaNs.
+    if (ok && sym(T.so, "cublasLtEmulationDescCreate", T.emuCreate) && sym(T.so, "cublasLtEmulationDescSetAttribute", T.emuSet) &&
+        T.emuCreate(&T.emu) == CUBLAS_STATUS_SUCCESS) {
+        const int32_t none = int32_t(CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
+        if (T.emuSet(T.emu, CUBLASLT_EMULATION_DESC_SPECIAL_VALUES_SUPPORT, &none, sizeof(none)) != CUBLAS_STATUS_SUCCESS)
+            T.emu = nullptr;
+    }
     if (!ok || T.create(&T.lh) != CUBLAS_STATUS_SUCCESS)
         return rsk::fail(h, RSK_ERR_UNSUPPORTED, "cuBLASLt symbols missing or handle creation failed");
     L.ok = true;
@@ -171,6 +187,8 @@ rsk_status lt_matmul(rsk_handle* h, int ta, int tb, int64_t m, int64_t n, int64_
         const cublasOperation_t opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N, opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
         T.descSet(p.desc, CUBLASLT_MATMUL_DESC_TRANSA, &opa, sizeof(opa));
         T.descSet(p.desc, CUBLASLT_MATMUL_DESC_TRANSB, &opb, sizeof(opb));
+        if (compute == CUBLAS_COMPUTE_32F_EMULATED_16BFX9 && T.emu)
+            T.descSet(p.desc, CUBLASLT_MATMUL_DESC_EMULATION_DESCRIPTOR, &T.emu, sizeof(T.emu));
         if (T.layoutCreate(&p.la, at, ta ? k : m, ta ? m : k, lda) != CUBLAS_STATUS_SUCCESS ||
             T.layoutCreate(&p.lb, at, tb ? n : k, tb ? k : n, ldb) != CUBLAS_STATUS_SUCCESS ||
             T.layoutCreate(&p.lc, ct, m, n, ldc) != CUBLAS_STATUS_SUCCESS)
@@ -225,40 +243,56 @@ rsk_status lt_matmul(rsk_handle* h, int ta, int tb, int64_t m, int64_t n, int64_
 // ------------------------------------------------------------------------------------------
 // Kernels.
 // ------------------------------------------------------------------------------------------
-// B (m x n, packed) = bf16(A) (lda); grid (ceil(n / 1024), <= 65535) striding over rows, 4
-// consecutive elements per thread.
-__global__ void k_to_bf16(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda, __nv_bfloat16* __restrict__ B) {
-    const int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
-    if (j >= n) return;
-    for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
-        const float* a = A + i * lda + j;
-        __nv_bfloat16* b = B + i * n + j;
-        if (j + 4 <= n && (reinterpret_cast<uintptr_t>(a) & 15) == 0 && (reinterpret_cast<uintptr_t>(b) & 7) == 0) {
-            const float4 v = *reinterpret_cast<const float4*>(a);
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
-            uint2 o;
-            o.x = *reinterpret_cast<uint32_t*>(&lo);
-            o.y = *reinterpret_cast<uint32_t*>(&hi);
-            *reinterpret_cast<uint2*>(b) = o;
-        } else {
-            for (int e = 0; e < 4 && j + e < n; ++e) b[e] = __float2bfloat16_rn(a[e]);
+// B = bf16(A) (m x n, packed) and Bt = bf16(A^T) (n x m, packed) in one pass over A: one CTA per
+// 64 x 64 tile; the tile is written row-major straight from the loads and column-major through a
+// padded shared-memory transpose.  vec: A rows 16-byte aligned (float4 loads) and n % 4 == 0;
+// m % 2 == 0 for the paired transposed stores.
+constexpr int kCvt = 64;
+__global__ void __launch_bounds__(256) k_to_bf16_both(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                                      int vec, __nv_bfloat16* __restrict__ B,
+                                                      __nv_bfloat16* __restrict__ Bt) {
+    __shared__ float tT[kCvt][kCvt + 1];  // tT[j][i]
+    const int64_t ntj = (n + kCvt - 1) / kCvt;
+    const int64_t ti = int64_t(blockIdx.x) / ntj, tj = int64_t(blockIdx.x) - ti * ntj;
+    const int64_t i0 = ti * kCvt, j0 = tj * kCvt;
+    for (int e = threadIdx.x; e < kCvt * kCvt / 4; e += blockDim.x) {
+        const int il = e >> 4, jl = (e & 15) * 4;
+        const int64_t i = i0 + il, j = j0 + jl;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (i < m) {
+            const float* a = A + i * lda + j;
+            if (vec && j + 4 <= n) {
+                const float4 f = *reinterpret_cast<const float4*>(a);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(f.x, f.y), hi = __floats2bfloat162_rn(f.z, f.w);
+                uint2 o;
+                o.x = *reinterpret_cast<const uint32_t*>(&lo);
+                o.y = *reinterpret_cast<const uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(B + i * n + j) = o;
+            } else {
+                for (int c = 0; c < 4; ++c)
+                    if (j + c < n) {
+                        v[c] = a[c];
+                        B[i * n + j + c] = __float2bfloat16_rn(v[c]);
+                    }
+            }
         }
-    }
-}
-
-// B = bf16(A^T): A m x n (lda), B n x m row-major; 32 x 32 tiles through shared memory.
-__global__ void k_transpose_bf16(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
-                                 __nv_bfloat16* __restrict__ B) {
-    __shared__ float tile[32][33];
-    const int64_t i0 = int64_t(blockIdx.y) * 32, j0 = int64_t(blockIdx.x) * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t i = i0 + r, j = j0 + threadIdx.x;
-        tile[r][threadIdx.x] = (i < m && j < n) ? A[i * lda + j] : 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tT[jl + c][il] = v[c];
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int64_t j = j0 + r, i = i0 + threadIdx.x;
-        if (j < n && i < m) B[j * m + i] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+    for (int e = threadIdx.x; e < kCvt * kCvt / 2; e += blockDim.x) {
+        const int jl = e >> 5, il = (e & 31) * 2;
+        const int64_t j = j0 + jl, i = i0 + il;
+        if (j >= n || i >= m) continue;
+        __nv_bfloat16* d = Bt + j * m + i;
+        if (vec && i + 2 <= m) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(tT[jl][il], tT[jl][il + 1]);
+            *reinterpret_cast<__nv_bfloat162*>(d) = p;
+        } else {
+            d[0] = __float2bfloat16_rn(tT[jl][il]);
+            if (i + 1 < m) d[1] = __float2bfloat16_rn(tT[jl][il + 1]);
+        }
     }
 }
 
@@ -293,128 +327,7 @@ __global__ void k_omega_t(const int32_t* __restrict__ rows, const uint32_t* __re
     }
 }
 
-__global__ void k_scale(float* __restrict__ X, int64_t count, float s) {
-    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx < count) X[idx] *= s;
-}
-
-constexpr int kMaxRank = 320;  // the tiled factor (55 tiles of 4 KB) within 227 KB of shared memory
-
-// Cholesky of G (+ shift) in shared memory, FP32, blocked by 32.  G: r x r symmetric, read from its
-// lower triangle (column-major, G[k*ld + i], i >= k).  The lower triangle is held as nt(nt+1)/2
-// tiles of 32 x 32 (nt = ceil(r/32)), element (i, j) of a tile at i*32 + (j ^ i) so that reading a
-// tile row or a tile column is free of bank conflicts; rows and columns beyond r are padded with the
-// identity.  Per block column kb: one warp factors the diagonal tile, one thread per panel row solves
-// the panel against it, one warp per trailing tile subtracts P_i P_j^T.  Writes L (lower,
-// column-major, ld x ld, zeros above and in the padding) with G + shift = L L^T, and the identity
-// into Linv for the triangular solve that turns it into L^{-1}; the orthonormalised basis is
-// X R^{-1} with R = L^T, i.e. (X R^{-1})^T = L^{-1} X^T.  shift_mode 1 adds
-// 11 (rows*r + r(r+1)) u_32 trace(G) to the diagonal (the shift of shifted CholeskyQR).
-constexpr int kCholThreads = 512;
-__device__ __forceinline__ int chol_tile(int bi, int bj) { return (bi * (bi + 1) / 2 + bj) * 1024; }
-__device__ __forceinline__ int chol_el(int i, int j) { return i * 32 + (j ^ i); }
-
-__global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restrict__ G, int r, int ld,
-                                                           float* __restrict__ Lout, float* __restrict__ Linv,
-                                                           int shift_mode, double rows, unsigned int* status) {
-    extern __shared__ float T[];
-    __shared__ double tr;
-    const int nt = (r + 31) >> 5;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = kCholThreads / 32;
-    if (tid == 0) {
-        double t = 0.0;
-        for (int i = 0; i < r; ++i) t += double(G[size_t(i) * ld + i]);
-        tr = t;
-    }
-    __syncthreads();
-    const float shift = shift_mode ? float(11.0 * (rows * r + double(r) * (r + 1)) * 5.960464477539063e-08 * tr) : 0.f;
-    const int ntiles = nt * (nt + 1) / 2;
-    for (int e = tid; e < ntiles * 1024; e += kCholThreads) {
-        // tile index -> (bi, bj)
-        const int t = e >> 10, within = e & 1023;
-        int bi = 0;
-        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-        const int bj = t - bi * (bi + 1) / 2;
-        const int i = within & 31, j = within >> 5;  // consecutive threads read consecutive rows of G
-        const int R = bi * 32 + i, Cc = bj * 32 + j;
-        float v;
-        if (R >= r || Cc >= r) v = (R == Cc) ? 1.f : 0.f;
-        else if (R >= Cc) v = G[size_t(Cc) * ld + R] + (R == Cc ? shift : 0.f);
-        else v = 0.f;  // above the diagonal inside a diagonal tile: unused
-        T[chol_tile(bi, bj) + chol_el(i, j)] = v;
-    }
-    __syncthreads();
-    for (int kb = 0; kb < nt; ++kb) {
-        float* D = T + chol_tile(kb, kb);
-        // (a) diagonal tile, one warp (lane = row)
-        if (warp == 0) {
-            for (int j = 0; j < 32; ++j) {
-                if (lane == j) {
-                    const float djj = D[chol_el(j, j)];
-                    if (!(djj > 0.f) && kb * 32 + j < r) atomicOr(status, RSK_DEV_BOUNDS);
-                    D[chol_el(j, j)] = sqrtf(fmaxf(djj, 1e-30f));
-                }
-                __syncwarp();
-                const float piv = D[chol_el(j, j)];
-                if (lane > j) D[chol_el(lane, j)] /= piv;
-                __syncwarp();
-                if (lane > j) {
-                    const float lij = D[chol_el(lane, j)];
-                    for (int k = j + 1; k <= lane; ++k) D[chol_el(lane, k)] -= lij * D[chol_el(k, j)];
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        // (b) panel: every row of tiles (bi, kb), bi > kb, solves x D^T = a by forward substitution
-        const int prow = (nt - kb - 1) * 32;
-        for (int pr = tid; pr < prow; pr += kCholThreads) {
-            const int bi = kb + 1 + (pr >> 5), i = pr & 31;
-            float* P = T + chol_tile(bi, kb);
-            float x[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                float a = P[chol_el(i, j)];
-#pragma unroll
-                for (int t = 0; t < j; ++t) a -= x[t] * D[chol_el(j, t)];
-                x[j] = a / D[chol_el(j, j)];
-            }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) P[chol_el(i, j)] = x[j];
-        }
-        __syncthreads();
-        // (c) trailing tiles (bi, bj), kb < bj <= bi: T -= P_bi P_bj^T, one warp per tile, lane = row
-        const int m = nt - kb - 1;
-        const int ntr = m * (m + 1) / 2;
-        for (int tt = warp; tt < ntr; tt += nw) {
-            int a = 0;
-            while ((a + 1) * (a + 2) / 2 <= tt) ++a;
-            const int bi = kb + 1 + a, bj = kb + 1 + (tt - a * (a + 1) / 2);
-            const float* Pi = T + chol_tile(bi, kb);
-            const float* Pj = T + chol_tile(bj, kb);
-            float acc[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-            for (int t = 0; t < 32; ++t) {
-                const float p = Pi[chol_el(lane, t)];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[j] = fmaf(p, Pj[chol_el(j, t)], acc[j]);
-            }
-            float* Tij = T + chol_tile(bi, bj);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) Tij[chol_el(lane, j)] -= acc[j];
-        }
-        __syncthreads();
-    }
-    // ld x ld outputs; rows and columns beyond r are zero (padding of the GEMM dimensions)
-    for (int idx = tid; idx < ld * ld; idx += kCholThreads) {
-        const int c = idx / ld, i = idx - c * ld;
-        float v = 0.f;
-        if (i >= c && i < r && c < r) v = T[chol_tile(i >> 5, c >> 5) + chol_el(i & 31, c & 31)];
-        Lout[idx] = v;
-        Linv[idx] = (i == c && i < r) ? 1.f : 0.f;
-    }
-}
+constexpr int kMaxRank = 320;  // largest rank the workspace plan and the tests cover
 
 // T (cols x rows, row-major) = X^T for X (rows x cols, row-major), FP32.
 __global__ void k_transpose_f32(const float* __restrict__ X, int64_t rows, int cols, float* __restrict__ T) {
@@ -434,21 +347,16 @@ __global__ void k_transpose_f32(const float* __restrict__ X, int64_t rows, int c
     }
 }
 
-__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, int64_t count) {
-    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx < count) b[idx] = double(a[idx]);
-}
-
 // eigenvalues ascending (w) and vectors (columns of V, column-major) -> descending s = sqrt(max(w,0)),
 // Uhat (r x r, FP32 column-major of reversed columns), sinv
-__global__ void k_eig_post(const double* __restrict__ w, const double* __restrict__ V, int r, double* __restrict__ s,
-                           float* __restrict__ Uh, float* __restrict__ sinv) {
+__global__ void k_eig_post(const float* __restrict__ w, const float* __restrict__ V, int r, double* __restrict__ s,
+                             float* __restrict__ Uh, float* __restrict__ sinv) {
     for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < r * r; idx += blockDim.x * gridDim.x) {
         const int c = idx / r, i = idx - c * r;       // column c of Uhat = column r-1-c of V
-        Uh[size_t(c) * r + i] = float(V[size_t(r - 1 - c) * r + i]);
+        Uh[size_t(c) * r + i] = V[size_t(r - 1 - c) * r + i];
     }
     for (int c = threadIdx.x + blockIdx.x * blockDim.x; c < r; c += blockDim.x * gridDim.x) {
-        const double lam = w[r - 1 - c];
+        const double lam = double(w[r - 1 - c]);
         const double sv = lam > 0.0 ? sqrt(lam) : 0.0;
         s[c] = sv;
         sinv[c] = sv > 0.0 ? float(1.0 / sv) : 0.f;
@@ -466,8 +374,11 @@ struct Ws {
     __nv_bfloat16 *Abf, *Atbf, *Ot, *Xt;
     float *Y, *Z, *X2, *G, *R, *Lf, *Uh, *sinv;
     void* ltws;
-    double *Gd, *w, *work;
+    float *w, *work;
     int* info;
+    float* cwork;
+    int clwork;
+    int* cinfo;
     int32_t* orow;
     uint32_t* osgn;
     int lwork;
@@ -517,6 +428,35 @@ static rsk_status gemm_nt(rsk_handle* h, const __nv_bfloat16* A, const __nv_bflo
     return st;
 }
 
+// Lout (ld x ld, column-major) = lower triangle of G + shift I on the leading r x r block, zero
+// elsewhere; Linv = I on the leading r x r block, zero elsewhere.  With shift_mode the shift is
+// 11 (rows r + r (r + 1)) u trace(G), u = 2^-24 (the shifted CholeskyQR rule).
+__global__ void __launch_bounds__(512) k_chol_prep(const float* __restrict__ G, int r, int ld, float* __restrict__ Lout,
+                                                   float* __restrict__ Linv, int shift_mode, double rows) {
+    __shared__ double part[16];
+    const int tid = threadIdx.x;
+    double t = 0.0;
+    for (int i = tid; i < r; i += blockDim.x) t += double(G[size_t(i) * ld + i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((tid & 31) == 0) part[tid >> 5] = t;
+    __syncthreads();
+    double tr = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) tr += part[w];
+    const float shift = shift_mode ? float(11.0 * (rows * r + double(r) * (r + 1)) * 5.960464477539063e-08 * tr) : 0.f;
+    for (int idx = tid; idx < ld * ld; idx += blockDim.x) {
+        const int c = idx / ld, i = idx - c * ld;
+        const bool in = i < r && c < r;
+        Lout[idx] = (in && i >= c) ? G[idx] + (i == c ? shift : 0.f) : 0.f;
+        Linv[idx] = (in && i == c) ? 1.f : 0.f;
+    }
+}
+
+// A failed factorization (a non-positive pivot) is recorded in the handle's status word.
+__global__ void k_chol_check(const int* __restrict__ info, unsigned int* status) {
+    if (threadIdx.x == 0 && *info != 0) atomicOr(status, RSK_DEV_BOUNDS);
+}
+
 // X (rows x r, row-major FP32, row stride rp, columns r..rp-1 zero) <- orthonormal basis of
 // range(X): shifted CholeskyQR3.  Each round: G = X^T X (FP32 matmul, rp x rp), G + shift = L L^T on
 // the leading r x r block and L^{-1} by a triangular solve (both padded with zeros to rp x rp),
@@ -525,10 +465,6 @@ static rsk_status gemm_nt(rsk_handle* h, const __nv_bfloat16* A, const __nv_bflo
 // multiple of 8, because the GEMM library only takes its fast paths for such shapes.
 static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws& w, cudaStream_t s) {
     Libs& L = g_libs;
-    const int nt = (r + 31) / 32;
-    const size_t smem = size_t(nt) * (nt + 1) / 2 * 1024 * 4;
-    if (smem > 227 * 1024) return fail(h, RSK_ERR_UNSUPPORTED, "r = %d too large for the shared-memory Cholesky", r);
-    RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     for (int round = 0; round < 3; ++round) {
         // X row-major is X^T column-major (rp x rows, ld rp):  G = X^T (X^T)^T
         int pr = prof_begin(h, s, RSK_KERNEL_DENSE);
@@ -537,8 +473,11 @@ static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws&
         prof_end(h, s, pr);
         if (st != RSK_OK) return st;
         pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        k_cholesky<<<1, kCholThreads, smem, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows),
-                                                  h->dev_status);
+        k_chol_prep<<<1, 512, 0, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows));
+        RSK_LAUNCH_CHECK(h);
+        if (L.spotrf(L.sh, kFillLower, r, w.Lf, rp, w.cwork, w.clwork, w.cinfo) != 0)
+            return fail(h, RSK_ERR_CUDA, "cusolverDnSpotrf failed");
+        k_chol_check<<<1, 32, 0, s>>>(w.cinfo, h->dev_status);
         prof_end(h, s, pr);
         RSK_LAUNCH_CHECK(h);
         // w.R <- L^{-1} on the leading r x r block: solve L X = I (lower, column-major, ld rp)
@@ -573,10 +512,13 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     Libs& L = g_libs;
     L.solverSetStream(L.sh, stream);
     int lwork = 0;
-    if (L.dsyevdBuf(L.sh, kEigModeVector, kFillLower, r, nullptr, r, nullptr, &lwork) != 0)
-        return fail(h, RSK_ERR_CUDA, "cusolverDnDsyevd_bufferSize failed");
+    if (L.ssyevdBuf(L.sh, kEigModeVector, kFillLower, r, nullptr, r, nullptr, &lwork) != 0)
+        return fail(h, RSK_ERR_CUDA, "cusolverDnSsyevd_bufferSize failed");
 
     const int rp = (r + 7) & ~7;  // GEMM dimension padded to a multiple of 8 (zero columns)
+    int clwork = 0;
+    if (L.spotrfBuf(L.sh, kFillLower, r, nullptr, rp, &clwork) != 0)
+        return fail(h, RSK_ERR_CUDA, "cusolverDnSpotrf_bufferSize failed");
     size_t bytes = 0;
     auto add = [&](size_t b_) { bytes += Carver::round(b_); };
     add(size_t(m) * n * 2);      // A bf16
@@ -589,8 +531,9 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     add(kLtWorkspace);           // cuBLASLt workspace
     add(size_t(rp) * rp * 4 * 4);  // G, R (L^{-1}), L, Uh
     add(size_t(r) * 4);          // sinv
-    add(size_t(r) * r * 8 + size_t(r) * 8 + size_t(lwork) * 8 + 64);
+    add(size_t(r) * 4 + size_t(lwork) * 4 + 64);   // eigenvalues, eigensolver work, info
     add(size_t(n) * zeta * 4 + size_t(n) * 4);
+    add(size_t(clwork) * 4 + 64);
     st = ensure_workspace(h, bytes + 4096, stream);
     if (st != RSK_OK) return st;
     Carver cv(h->ws);
@@ -608,17 +551,22 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     w.Lf = cv.take<float>(size_t(rp) * rp);
     w.Uh = cv.take<float>(size_t(rp) * rp);
     w.sinv = cv.take<float>(size_t(r));
-    w.Gd = cv.take<double>(size_t(r) * r);
-    w.w = cv.take<double>(size_t(r));
-    w.work = cv.take<double>(size_t(lwork));
+    w.w = cv.take<float>(size_t(r));
+    w.work = cv.take<float>(size_t(lwork));
     w.info = cv.take<int>(16);
     w.orow = cv.take<int32_t>(size_t(n) * zeta);
     w.osgn = cv.take<uint32_t>(size_t(n));
+    w.cwork = cv.take<float>(size_t(clwork) + 1);
+    w.clwork = clwork;
+    w.cinfo = cv.take<int>(16);
 
     // ---- A in BF16, both orientations; Omega^T dense +-1 (rows r..rp-1 zero)
-    k_to_bf16<<<dim3(unsigned((n + 1023) / 1024), unsigned(std::min<int64_t>(m, 65535))), 256, 0, stream>>>(
-        A, m, n, lda, w.Abf);
-    k_transpose_bf16<<<dim3(unsigned((n + 31) / 32), unsigned((m + 31) / 32)), dim3(32, 8), 0, stream>>>(A, m, n, lda, w.Atbf);
+    {
+        const int vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0 && n % 4 == 0 && m % 2 == 0) ? 1 : 0;
+        const int64_t tiles = ((m + kCvt - 1) / kCvt) * ((n + kCvt - 1) / kCvt);
+        k_to_bf16_both<<<unsigned(tiles), 256, 0, stream>>>(A, m, n, lda, vec, w.Abf, w.Atbf);
+        RSK_LAUNCH_CHECK(h);
+    }
     RSK_CUDA_TRY(h, cudaMemsetAsync(w.Ot, 0, size_t(rp) * n * 2, stream));
     st = sketch_generate(h, n, r, zeta, seed, 3u, w.orow, w.osgn, stream);
     if (st != RSK_OK) return st;
@@ -649,11 +597,9 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     const float one = 1.f, zero = 0.f;
     if (L.ssyrk(L.bh, kFillLower, kOpN, r, int(n), &one, w.Z, rp, &zero, w.G, r) != 0)
         return fail(h, RSK_ERR_CUDA, "cublasSsyrk failed");
-    k_f32_to_f64<<<unsigned((size_t(r) * r + 255) / 256), 256, 0, stream>>>(w.G, w.Gd, int64_t(r) * r);
-    RSK_LAUNCH_CHECK(h);
-    if (L.dsyevd(L.sh, kEigModeVector, kFillLower, r, w.Gd, r, w.w, w.work, lwork, w.info) != 0)
-        return fail(h, RSK_ERR_CUDA, "cusolverDnDsyevd failed");
-    k_eig_post<<<8, 256, 0, stream>>>(w.w, w.Gd, r, s, w.Uh, w.sinv);
+    if (L.ssyevd(L.sh, kEigModeVector, kFillLower, r, w.G, r, w.w, w.work, lwork, w.info) != 0)
+        return fail(h, RSK_ERR_CUDA, "cusolverDnSsyevd failed");
+    k_eig_post<<<8, 256, 0, stream>>>(w.w, w.G, r, s, w.Uh, w.sinv);
     RSK_LAUNCH_CHECK(h);
     // U = Q Uhat  (row-major m x r = (Uhat^T Q^T)^T): column-major U^T (r x m) = Uhat^T (r x r) * Q^T (r x m)
     if (L.sgemm(L.bh, kOpT, kOpN, r, int(m), r, &one, w.Uh, r, w.Y, rp, &zero, U, r) != 0)

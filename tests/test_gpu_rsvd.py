@@ -52,7 +52,7 @@ def test_rsvd_invalid(rsk):
     with pytest.raises(rsk.RskError):
         rsk.rsk_rsvd(A, 4, zeta=8)                          # zeta > r
     with pytest.raises(rsk.RskError):
-        rsk.rsk_rsvd(torch.zeros(1000, 500, device="cuda"), 321)   # r beyond the shared-memory Cholesky
+        rsk.rsk_rsvd(torch.zeros(1000, 500, device="cuda"), 321)   # r beyond the supported rank (320)
 
 
 def _power_norm(apply, n, iters, gen):
