@@ -3,8 +3,10 @@
 // paper names sketch-and-precondition as the standard high-accuracy route (remark closing Sec. 2.3)
 // without stating it, so the steps are this library's reading:
 //   L1  [Ahat | bhat] = S [A | b] with one sparse sign S (rsk_sparse_sign_plan_*).
-//   L2  Householder QR of Ahat in FP64 (k_qr: one reflector per column, persistent grid with a
-//       bounded software grid barrier); Q^T bhat comes out of the same sweep as an extra column.
+//   L2  Householder QR of Ahat in FP64, one reflector per column: k_qr_col (one CTA per column,
+//       column in registers, reflectors handed on through release/acquire flags) when k + 1 CTAs
+//       fit on the GPU at once, else k_qr (persistent grid, bounded software grid barrier); Q^T bhat
+//       comes out of the same sweep as an extra column.
 //   L3  x0 = R^{-1} Q^T bhat; R^{-1} is formed explicitly (k_rinv, FP64) and applied as a matvec.
 //   L4  refinement: g = A^T (b - A x) in FP64 (one fused pass over A), eta(x) = ||g|| / (||A||_F ||r||);
 //       stop at eta <= tol; otherwise solve (M^T M) z = R^{-T} g with CG, M = A R^{-1}, whose
@@ -122,6 +124,109 @@ __global__ void __launch_bounds__(256) k_qr(double* W, int d, int k, double* tau
             for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) col[i] = __ldcg(col + i) - w * __ldcg(v + i);
             __syncthreads();
             if (c == j + 1 && c < k) make_reflector(col, d, c, tau, red);
+        }
+    }
+}
+
+// The same QR with one CTA per column (grid = k + 1, all resident: cooperative launch) and no grid
+// barrier.  CTA c keeps column c in registers (row i = threadIdx.x + 256 t, t < T).  For
+// j = 0 .. min(c, k) - 1 it waits until reflector j is published (ready[j]), reads v_j and tau_j
+// through L2 and applies H_j; CTA c < k then forms reflector c from rows c.., writes its column
+// (R entries in rows < c, beta in row c, v_c below) and tau_c, and publishes ready[c].  Reflector
+// j + 1 therefore follows reflector j after one flag hand-off, one L2 read of v_j and two block
+// reductions, instead of a grid barrier and several L2 round trips of the column.
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) k_qr_col(double* W, int d, int k, double* tau, unsigned int* ready,
+                                               unsigned int* status) {
+    __shared__ double red[32];
+    __shared__ double xj_s;
+    __shared__ int ok_s;
+    const int c = blockIdx.x, tid = threadIdx.x;
+    double* col = W + size_t(c) * d;
+    double x[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int i = tid + 256 * t;
+        x[t] = i < d ? col[i] : 0.0;
+    }
+    const int nref = c < k ? c : k;
+    for (int j = 0; j < nref; ++j) {
+        if (tid == 0) {
+            uint32_t it = 0;
+            int ok = 1;
+            while (ld_acquire_u32(ready + j) == 0u) {
+                if (++it > rskd::kWaitLimit) {
+                    atomicOr(status, RSK_DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (it > 32) __nanosleep(32);
+            }
+            ok_s = ok;
+        }
+        __syncthreads();
+        if (!ok_s) return;
+        const double* v = W + size_t(j) * d;
+        const double tj = __ldcg(tau + j);
+        double vv[T];
+        double s = 0.0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            vv[t] = (i > j && i < d) ? __ldcg(v + i) : 0.0;
+            s += vv[t] * x[t];
+            if (i == j) xj_s = x[t];
+        }
+        s = block_sum(s, red);  // its barriers also publish xj_s
+        const double w = tj * (xj_s + s);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            x[t] -= (i == j) ? w : w * vv[t];
+        }
+    }
+    if (c < k) {
+        double sg = 0.0, ap = 0.0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            if (i > c && i < d) sg += x[t] * x[t];
+            if (i == c) ap = x[t];
+        }
+        const double sigma = block_sum(sg, red);
+        const double alpha = block_sum(ap, red);  // one nonzero term: exact
+        double tc = 0.0, beta = alpha, scale = 0.0;
+        if (sigma > 0.0) {
+            const double nrm = sqrt(alpha * alpha + sigma);
+            beta = alpha > 0.0 ? -nrm : nrm;
+            tc = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            if (i > c && sigma > 0.0) x[t] *= scale;
+            if (i == c) x[t] = beta;
+            if (i < d) col[i] = x[t];
+        }
+        if (tid == 0) tau[c] = tc;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_release_u32(ready + c, 1u);
+    } else {
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int i = tid + 256 * t;
+            if (i < d) col[i] = x[t];
         }
     }
 }
@@ -695,6 +800,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     add(size_t(nparts) * K * 8);    // parts
     add(size_t(nparts) * 3 * 8);    // parts_s
     add(64);                        // barrier
+    add(size_t(K + 1) * 4 + 64);    // reflector-ready flags
     add(size_t(d) * K * 8);         // SA (f64 or f32)
     add(size_t(d) * 8);             // Sb
     if (need_sk_copy) add(size_t(n) * K * es_sk);
@@ -725,6 +831,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     w.parts = cv.take<double>(size_t(nparts) * K);
     w.parts_s = cv.take<double>(size_t(nparts) * 3);
     w.bar = cv.take<unsigned int>(16);
+    unsigned int* qr_ready = cv.take<unsigned int>(size_t(K + 1) + 16);
     w.SA64 = cv.take<double>(size_t(d) * K);
     w.SA32 = reinterpret_cast<float*>(w.SA64);
     w.Sb = cv.take<double>(size_t(d));
@@ -779,9 +886,34 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
     if (sa_dt == RSK_F64) k_to_colmajor<double><<<gw, 256, 0, stream>>>(w.SA64, k, (const double*)w.Sb, int(d), K, w.W);
     else k_to_colmajor<float><<<gw, 256, 0, stream>>>(w.SA32, k, (const double*)w.Sb, int(d), K, w.W);
     RSK_LAUNCH_CHECK(h);
-    {
+    // one CTA per column when k + 1 CTAs fit on the GPU at once, else the barrier sweep
+    auto qr_col = [&](auto kern) -> int {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess) return -1;
+        if (int64_t(per_sm) * h->num_sms < K + 1) return 0;
+        RSK_CUDA_TRY(h, cudaMemsetAsync(qr_ready, 0, size_t(K + 1) * 4, stream));
+        int dd = int(d);
+        double* Wp = w.W;
+        double* taup = w.tau;
+        unsigned int* rp_ = qr_ready;
+        unsigned int* stp = h->dev_status;
+        void* args[] = {&Wp, &dd, const_cast<int*>(&K), &taup, &rp_, &stp};
+        const int pr = prof_begin(h, stream, RSK_KERNEL_DENSE);
+        const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), dim3(K + 1), dim3(256), args, 0, stream);
+        prof_end(h, stream, pr);
+        return e == cudaSuccess ? 1 : -1;
+    };
+    int qr_done = 0;
+    if (d <= 2048) qr_done = qr_col(k_qr_col<8>);
+    else if (d <= 4096) qr_done = qr_col(k_qr_col<16>);
+    if (qr_done < 0) return fail(h, RSK_ERR_CUDA, "QR launch failed");
+    if (!qr_done) {
         // cooperative launch: all CTAs of the persistent sweep are resident together
-        const int grid = std::min(h->num_sms, K + 1);
+        // as many co-resident CTAs as the columns need: each step then waits on at most one column
+        // update per CTA instead of ceil((k + 1) / num_sms)
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+        const int grid = std::min(h->num_sms * per_sm, K + 1);
         int dd = int(d);
         double* Wp = w.W;
         double* taup = w.tau;
