@@ -102,6 +102,18 @@ def test_not_converged_reports(rsk):
     assert e.value.status == 4
 
 
+@pytest.mark.parametrize("n,k,d", [(12000, 700, 1400), (9000, 200, 2500)])
+def test_sketch_qr_paths(rsk, n, k, d):
+    # k + 1 = 701 columns exceed the CTAs that can be resident at once for the one-CTA-per-column QR
+    # (the barrier sweep runs instead); d = 2500 > 2048 takes its 16-rows-per-thread instance
+    A, b, _ = synthetic.lsq_problem(n, k, seed=k, cond_exp=4.0, device="cpu")
+    x, info = solve(rsk, A.cuda(), b.cuda(), d, sketch_dtype=torch.float64, inner_dtype=torch.float64)
+    eta = olsq.backward_error(A.numpy(), b.numpy(), x.cpu().numpy())
+    assert eta <= 1e-10, (eta, info)
+    xs = olsq.exact(A.numpy(), b.numpy())
+    assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
 def test_invalid(rsk):
     A = torch.zeros(100, 10, dtype=torch.float64, device="cuda")
     b = torch.zeros(100, dtype=torch.float64, device="cuda")
