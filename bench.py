@@ -54,6 +54,10 @@ def parse():
                    "for profiling captures)")
     p.add_argument("--batch-count", type=int, default=BATCH_COUNT, help="problems in the batched least-squares "
                    "workload (smaller only for profiling captures)")
+    p.add_argument("--rsvd-rows", type=int, default=RSVD_M, help="rows of the RSVD A (smaller only for profiling "
+                   "captures)")
+    p.add_argument("--profile-rsvd", action="store_true", help="open the CUDA profiler range around the timed RSVD "
+                   "calls only (for ncu --profile-from-start off)")
     return p.parse_args()
 
 
@@ -331,20 +335,31 @@ def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH
             "mixed": res["mixed"], "fp64": res["fp64"]}
 
 
-def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps):
-    """RSVD of A 262144 x 8192 FP32 (rank-400 spectrum j^-2 plus 1e-4 noise), r = 300, q = 2."""
-    A = synthetic.lowrank_plus_noise(RSVD_M, RSVD_N, RSVD_RANK, seed=2025 + rank, noise=1e-4, device=dev)
-    # profiling starts after the warm-up call, which also loads the GEMM library's kernels
+def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps, rows=RSVD_M, profiler_range=False):
+    """RSVD of A 262144 x 8192 FP32 (rank-400 spectrum j^-2 plus 1e-4 noise), r = 300, q = 2.
+    profiler_range: open the CUDA profiler range (cudaProfilerStart/Stop) around the timed calls only,
+    so that a capture with --profile-from-start off skips the warm-up call's GEMM autotuning."""
+    A = synthetic.lowrank_plus_noise(rows, RSVD_N, RSVD_RANK, seed=2025 + rank, noise=1e-4, device=dev)
+
+    def after_warmup():
+        # profiling starts after the warm-up call, which also loads the GEMM library's kernels
+        rsk.rsk_profile_enable(True)
+        if profiler_range:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+
     ms, (U, s, Vt) = timed_calls(lambda: rsk.rsk_rsvd(A, RSVD_R, power_iters=RSVD_Q, zeta=ZETA, seed=0),
-                                 reps, torch, dev, after_warmup=lambda: rsk.rsk_profile_enable(True))
+                                 reps, torch, dev, after_warmup=after_warmup)
+    if profiler_range:
+        torch.cuda.profiler.stop()
     gemm = rsk.rsk_profile_read("gemm")
     rsk.rsk_profile_enable(False)
     rp = (RSVD_R + 7) // 8 * 8  # the library pads the GEMM dimension to a multiple of 8
-    flops = (2 + 2 * RSVD_Q) * 2 * RSVD_M * RSVD_N * rp
+    flops = (2 + 2 * RSVD_Q) * 2 * rows * RSVD_N * rp
     gemm_ms = gemm[0] / reps
     del A, U, s, Vt
     torch.cuda.empty_cache()
-    return {"workload": "RSVD A 262144 x 8192 FP32 (rank-400 spectrum j^-2 + 1e-4 noise), r=300, q=2, "
+    return {"workload": f"RSVD A {rows} x {RSVD_N} FP32 (rank-400 spectrum j^-2 + 1e-4 noise), r=300, q=2, "
                         "sparse sign Omega zeta=8",
             "value": round(world * 1e3 / ms, 3), "unit": "calls/s", "ms_per_call": round(ms, 3),
             "gemm_ms_per_call": round(gemm_ms, 3), "gemm_launches_per_call": gemm[1] // max(1, reps),
@@ -453,7 +468,8 @@ def run_ours(args):
         extra["lsq_batched"] = bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, args.solve_reps,
                                                  args.batch_count)
     if not args.no_rsvd:
-        extra["rsvd"] = bench_rsvd(rsk, synthetic, torch, dev, rank, world, args.solve_reps)
+        extra["rsvd"] = bench_rsvd(rsk, synthetic, torch, dev, rank, world, args.solve_reps, rows=args.rsvd_rows,
+                                   profiler_range=args.profile_rsvd)
 
     if rank != 0:
         return
