@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -431,12 +432,14 @@ static rsk_status gemm_nt(rsk_handle* h, const __nv_bfloat16* A, const __nv_bflo
 // Lout (ld x ld, column-major) = lower triangle of G + shift I on the leading r x r block, zero
 // elsewhere; Linv = I on the leading r x r block, zero elsewhere.  With shift_mode the shift is
 // 11 (rows r + r (r + 1)) u trace(G), u = 2^-24 (the shifted CholeskyQR rule).
-__global__ void __launch_bounds__(512) k_chol_prep(const float* __restrict__ G, int r, int ld, float* __restrict__ Lout,
+__global__ void __launch_bounds__(256) k_chol_prep(const float* __restrict__ G, int r, int ld, float* __restrict__ Lout,
                                                    float* __restrict__ Linv, int shift_mode, double rows) {
-    __shared__ double part[16];
-    const int tid = threadIdx.x;
+    // one CTA per column c of the ld x ld outputs; every CTA forms the (same) trace
+    __shared__ double part[8];
+    const int tid = threadIdx.x, c = blockIdx.x;
     double t = 0.0;
-    for (int i = tid; i < r; i += blockDim.x) t += double(G[size_t(i) * ld + i]);
+    if (shift_mode)
+        for (int i = tid; i < r; i += blockDim.x) t += double(G[size_t(i) * ld + i]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if ((tid & 31) == 0) part[tid >> 5] = t;
@@ -444,8 +447,8 @@ __global__ void __launch_bounds__(512) k_chol_prep(const float* __restrict__ G, 
     double tr = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) tr += part[w];
     const float shift = shift_mode ? float(11.0 * (rows * r + double(r) * (r + 1)) * 5.960464477539063e-08 * tr) : 0.f;
-    for (int idx = tid; idx < ld * ld; idx += blockDim.x) {
-        const int c = idx / ld, i = idx - c * ld;
+    for (int i = tid; i < ld; i += blockDim.x) {
+        const size_t idx = size_t(c) * ld + i;
         const bool in = i < r && c < r;
         Lout[idx] = (in && i >= c) ? G[idx] + (i == c ? shift : 0.f) : 0.f;
         Linv[idx] = (in && i == c) ? 1.f : 0.f;
@@ -465,15 +468,17 @@ __global__ void k_chol_check(const int* __restrict__ info, unsigned int* status)
 // multiple of 8, because the GEMM library only takes its fast paths for such shapes.
 static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws& w, cudaStream_t s) {
     Libs& L = g_libs;
+    float* src = X;
+    float* dst = w.X2;
     for (int round = 0; round < 3; ++round) {
         // X row-major is X^T column-major (rp x rows, ld rp):  G = X^T (X^T)^T
         int pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        rsk_status st = lt_matmul(h, 0, 1, rp, rp, rows, X, CUDA_R_32F, rp, X, rp, w.G, CUDA_R_32F, rp, 1.f,
+        rsk_status st = lt_matmul(h, 0, 1, rp, rp, rows, src, CUDA_R_32F, rp, src, rp, w.G, CUDA_R_32F, rp, 1.f,
                                   fp32_compute(h), w.ltws, s);
         prof_end(h, s, pr);
         if (st != RSK_OK) return st;
         pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        k_chol_prep<<<1, 512, 0, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows));
+        k_chol_prep<<<unsigned(rp), 256, 0, s>>>(w.G, r, rp, w.Lf, w.R, round == 0 ? 1 : 0, double(rows));
         RSK_LAUNCH_CHECK(h);
         if (L.spotrf(L.sh, kFillLower, r, w.Lf, rp, w.cwork, w.clwork, w.cinfo) != 0)
             return fail(h, RSK_ERR_CUDA, "cusolverDnSpotrf failed");
@@ -486,12 +491,13 @@ static rsk_status orth(rsk_handle* h, float* X, int64_t rows, int r, int rp, Ws&
         if (L.strsm(L.bh, kSideLeft, kFillLower, kOpN, kDiagNonUnit, r, r, &one, w.Lf, rp, w.R, rp) != 0)
             return fail(h, RSK_ERR_CUDA, "cublasStrsm failed");
         pr = prof_begin(h, s, RSK_KERNEL_DENSE);
-        st = lt_matmul(h, 0, 0, rp, rows, rp, w.R, CUDA_R_32F, rp, X, rp, w.X2, CUDA_R_32F, rp, 1.f, fp32_compute(h),
+        st = lt_matmul(h, 0, 0, rp, rows, rp, w.R, CUDA_R_32F, rp, src, rp, dst, CUDA_R_32F, rp, 1.f, fp32_compute(h),
                        w.ltws, s);
         prof_end(h, s, pr);
         if (st != RSK_OK) return st;
-        RSK_CUDA_TRY(h, cudaMemcpyAsync(X, w.X2, size_t(rows) * rp * 4, cudaMemcpyDeviceToDevice, s));
+        std::swap(src, dst);
     }
+    if (src != X) RSK_CUDA_TRY(h, cudaMemcpyAsync(X, src, size_t(rows) * rp * 4, cudaMemcpyDeviceToDevice, s));
     return RSK_OK;
 }
 
@@ -602,8 +608,9 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     k_eig_post<<<8, 256, 0, stream>>>(w.w, w.G, r, s, w.Uh, w.sinv);
     RSK_LAUNCH_CHECK(h);
     // U = Q Uhat  (row-major m x r = (Uhat^T Q^T)^T): column-major U^T (r x m) = Uhat^T (r x r) * Q^T (r x m)
-    if (L.sgemm(L.bh, kOpT, kOpN, r, int(m), r, &one, w.Uh, r, w.Y, rp, &zero, U, r) != 0)
-        return fail(h, RSK_ERR_CUDA, "cublasSgemm (U) failed");
+    st = lt_matmul(h, 1, 0, r, m, r, w.Uh, CUDA_R_32F, r, w.Y, rp, U, CUDA_R_32F, r, 1.f, fp32_compute(h), w.ltws,
+                   stream);
+    if (st != RSK_OK) return st;
     // Vt = Sigma^{-1} Uhat^T Z^T: row-major Vt (r x n) is column-major Vt^T (n x r) = Z Uhat Sigma^{-1};
     // first W = Z Uhat (row-major n x r) = column-major (Uhat^T Z^T) r x n
     if (L.sgemm(L.bh, kOpT, kOpN, r, int(n), r, &one, w.Uh, r, w.Z, rp, &zero, w.Y, r) != 0)
