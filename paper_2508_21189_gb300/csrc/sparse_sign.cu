@@ -8,7 +8,8 @@
 //               counts per sketch row, scans, scatters (j_local | neg<<15) through shared-memory
 //               atomics, then sorts each sketch row's short list by j, so every sketch row lists its
 //               columns in ascending j whatever order the atomics took.  Output is chunk-local.
-//   k_apply     one CTA per (128-byte column slice, block of sketch rows, range of chunks).  Per chunk,
+//   k_apply     persistent CTAs (at most one per SM) over (range of chunks, 128-byte column slice, block
+//               of sketch rows) items, numbered range-major and dealt round-robin.  Per chunk,
 //               TMA streams the chunk's row slices of A and bulk copies bring the chunk's index into
 //               shared memory (double buffered, one mbarrier per stage).  A group of 8 lanes owns
 //               SLOTS consecutive sketch rows and gathers their entries' row slices (16 B per lane,
@@ -373,7 +374,7 @@ struct Elem<__nv_bfloat16> {
 struct ApplyArgs {
     const void* A;
     int64_t n, k, lda;
-    int d, zeta, chunk, pitch, dsub, ntsub, nslices, nranges, nchunks;
+    int d, zeta, chunk, pitch, dsub, ntsub, nslices, nranges, nchunks, nitems;
     const uint16_t* offs;
     const uint16_t* ents;
     void* partials;
@@ -427,32 +428,46 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (TMA ? 2 : 1) * SL.bytes);
 
     const int tid = threadIdx.x, g = tid >> 3, l8 = tid & 7;
-    int b = blockIdx.x;
-    const int s = b % a.nslices;
-    b /= a.nslices;
-    const int t = b % a.ntsub;
-    const int r = b / a.ntsub;
-    const int c0 = int(int64_t(r) * a.nchunks / a.nranges);
-    const int c1 = int(int64_t(r + 1) * a.nchunks / a.nranges);
-    const int first = t * a.dsub + g * SLOTS;  // this group's sketch rows: first .. first+SLOTS-1
+    // Work items are (row range, column slice, block of sketch rows), numbered range-major; CTA b
+    // takes items b, b + gridDim.x, ...  The CTAs running together therefore work on the same rows.
+    const int pairs = a.nslices * a.ntsub;
+    struct Cursor {
+        int item, r, s, t, ch, c1;
+    };
+    auto set_item = [&](Cursor& c, int item) {
+        c.item = item;
+        if (item >= a.nitems) return;
+        c.r = item / pairs;
+        const int pr = item - c.r * pairs;
+        c.t = pr / a.nslices;
+        c.s = pr - c.t * a.nslices;
+        c.ch = int(int64_t(c.r) * a.nchunks / a.nranges);  // ranges are never empty (nranges <= nchunks)
+        c.c1 = int(int64_t(c.r + 1) * a.nchunks / a.nranges);
+    };
+    auto advance = [&](Cursor& c) {
+        if (++c.ch >= c.c1) set_item(c, c.item + int(gridDim.x));
+    };
 
     Acc acc[SLOTS];
 #pragma unroll
     for (int q = 0; q < SLOTS; ++q) acc[q].zero();
 
-    auto issue = [&](int ch, uint8_t* dst, uint64_t* bar) {
-        const int64_t row0 = int64_t(ch) * a.chunk;
+    auto issue = [&](const Cursor& c, uint8_t* dst, uint64_t* bar) {
+        const int64_t row0 = int64_t(c.ch) * a.chunk;
         const int rows = int((a.n - row0) < a.chunk ? (a.n - row0) : a.chunk);
         const int nbox = (rows + kBoxRows - 1) / kBoxRows;
         const uint32_t eb = uint32_t(align16(size_t(rows) * a.zeta * 2));
         rskd::mbar_expect_tx(bar, uint32_t(nbox * kBoxRows * kRowBytes) + eb + uint32_t(SL.o_bytes));
         for (int bx = 0; bx < nbox; ++bx)
-            rskd::tma_load_2d(dst + bx * kBoxRows * kRowBytes, &tmap, s * C_COLS, int(row0 + bx * kBoxRows), bar);
+            rskd::tma_load_2d(dst + bx * kBoxRows * kRowBytes, &tmap, c.s * C_COLS, int(row0 + bx * kBoxRows), bar);
         rskd::bulk_load(dst + SL.a_bytes, a.ents + row0 * a.zeta, eb, bar);
-        rskd::bulk_load(dst + SL.a_bytes + SL.e_bytes, a.offs + int64_t(ch) * a.pitch + int64_t(t) * a.dsub,
+        rskd::bulk_load(dst + SL.a_bytes + SL.e_bytes, a.offs + int64_t(c.ch) * a.pitch + int64_t(c.t) * a.dsub,
                         uint32_t(SL.o_bytes), bar);
     };
 
+    Cursor cur, ahead;
+    set_item(cur, int(blockIdx.x));
+    ahead = cur;
     if constexpr (TMA) {
         if (tid == 0) {
             rskd::mbar_init(&bars[0], 1);
@@ -460,13 +475,16 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
             rskd::fence_mbar_init();
         }
         __syncthreads();
-        if (tid == 0) {
-            if (c0 < c1) issue(c0, stage0, &bars[0]);
-            if (c0 + 1 < c1) issue(c0 + 1, stage1, &bars[1]);
-        }
+        // two chunks in flight: `ahead` always points two positions past `cur`
+        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage0, &bars[0]);
+        if (ahead.item < a.nitems) advance(ahead);
+        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage1, &bars[1]);
+        if (ahead.item < a.nitems) advance(ahead);
     }
 
-    for (int ch = c0, it = 0; ch < c1; ++ch, ++it) {
+    for (int it = 0; cur.item < a.nitems; ++it) {
+        const int ch = cur.ch, s = cur.s, t = cur.t;
+        const int first = t * a.dsub + g * SLOTS;  // this group's sketch rows: first .. first+SLOTS-1
         const uint8_t* buf;
         bool ok = true;
         if constexpr (TMA) {
@@ -526,20 +544,28 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         }
         if (__syncthreads_or(!ok)) break;
         if constexpr (TMA) {
-            if (tid == 0 && ch + 2 < c1) {
-                rskd::fence_proxy_async();
-                const int st = it & 1;
-                issue(ch + 2, st ? stage1 : stage0, &bars[st]);
+            if (ahead.item < a.nitems) {
+                if (tid == 0) {
+                    rskd::fence_proxy_async();
+                    const int st = it & 1;
+                    issue(ahead, st ? stage1 : stage0, &bars[st]);
+                }
+                advance(ahead);
             }
         }
-    }
-
-    using store_t = typename Acc::store_t;
-    store_t* part = static_cast<store_t*>(a.partials) + int64_t(r) * a.pstride;
+        const int done_item = cur.item, done_r = cur.r;
+        advance(cur);
+        if (cur.item != done_item) {
+            // item finished: its partial sums go to the row range's slot, then start afresh
+            using store_t = typename Acc::store_t;
+            store_t* part = static_cast<store_t*>(a.partials) + int64_t(done_r) * a.pstride;
 #pragma unroll
-    for (int q = 0; q < SLOTS; ++q) {
-        const int i = first + q;
-        if (i < a.d) acc[q].store(part + int64_t(i) * a.kpad + int64_t(s) * C_COLS + l8 * VEC);
+            for (int q = 0; q < SLOTS; ++q) {
+                const int i = first + q;
+                if (i < a.d) acc[q].store(part + int64_t(i) * a.kpad + int64_t(s) * C_COLS + l8 * VEC);
+                acc[q].zero();
+            }
+        }
     }
 }
 
@@ -604,7 +630,7 @@ rsk_status launch_index(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed
 }
 
 struct ApplyPlan {
-    int slots, dsub, ntsub, nslices, nranges, nchunks, chunk, pitch;
+    int slots, dsub, ntsub, nslices, nranges, nchunks, chunk, pitch, nitems;
     int64_t kpad, pstride;
     size_t partial_bytes;
 };
@@ -624,10 +650,23 @@ ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, int zeta, rsk_d
     p.pitch = offsets_pitch(d);
     p.nchunks = int(n_chunks_of(n, zeta));
     const int pairs = p.nslices * p.ntsub;
-    p.nranges = std::max(1, std::min(p.nchunks, h->num_sms / std::max(1, pairs)));
     p.kpad = int64_t(p.nslices) * C;
     p.pstride = int64_t(p.ntsub) * p.dsub * p.kpad;
     const size_t acc = (dt == RSK_F64 || dt == RSK_F32X2) ? 8 : 4;
+    // row ranges R with R * pairs a multiple of the SM count (R = num_sms / gcd(pairs, num_sms)), so
+    // that the persistent CTAs get equal shares of (range, slice, sketch-row block) items; at most one
+    // range per chunk and at most 512 MB of partial sums
+    int gg = pairs, hh = h->num_sms;
+    while (hh) {
+        const int t_ = gg % hh;
+        gg = hh;
+        hh = t_;
+    }
+    int R = pairs >= h->num_sms ? 1 : h->num_sms / std::max(1, gg);
+    const int64_t cap = std::max<int64_t>(1, int64_t(512) * (1 << 20) / int64_t(p.pstride * acc));
+    R = int(std::min<int64_t>(std::min<int64_t>(R, cap), p.nchunks));
+    p.nranges = std::max(1, R);
+    p.nitems = p.nranges * pairs;
     p.partial_bytes = size_t(p.nranges) * p.pstride * acc;
     return p;
 }
@@ -635,7 +674,7 @@ ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, int zeta, rsk_d
 template <typename T, int SLOTS>
 rsk_status launch_apply_t(rsk_handle* h, const ApplyPlan& p, const ApplyArgs& args, bool use_tma,
                           const CUtensorMap& map, cudaStream_t stream) {
-    const unsigned grid = unsigned(p.nslices * p.ntsub * p.nranges);
+    const unsigned grid = unsigned(std::min(p.nitems, h->num_sms));
     const StageLayout SL = stage_layout(p.chunk, args.zeta, p.dsub);
     const int smem = (use_tma ? 2 : 1) * SL.bytes + 64;
     if (smem > 227 * 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "apply needs %d B of shared memory", smem);
@@ -710,6 +749,7 @@ rsk_status apply_with_index(rsk_handle* h, const uint16_t* offs, const uint16_t*
     args.nslices = p.nslices;
     args.nranges = p.nranges;
     args.nchunks = p.nchunks;
+    args.nitems = p.nitems;
     args.offs = offs;
     args.ents = ents;
     args.partials = partials;
