@@ -147,9 +147,9 @@ rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dty
  * unavailable or forbidden, e.g. inside a host application that owns every device buffer, or a
  * path that must not allocate after start-up).  The paper has no counterpart: this is a deployment
  * variant of rsk_sparse_sign_apply with the same arguments minus the handle, and bit-identical
- * results.  Scratch comes from one fixed 32 MiB array in device memory that every GPU loading the
+ * results.  Scratch comes from one fixed 64 MiB array in device memory that every GPU loading the
  * library holds until exit; no call allocates or frees anything.  Sizes whose scratch (inverted
- * index plus partial sums) exceeds 32 MiB return RSK_ERR_UNSUPPORTED before any launch.  The first
+ * index plus partial sums) exceeds 64 MiB return RSK_ERR_UNSUPPORTED before any launch.  The first
  * call on each device looks up the array's device address (make it before any stream capture).
  * All calls share the array: calls that overlap on the GPU race, and the set-up is not thread safe.
  * Errors are reported by the status code only (no handle, no message). */
