@@ -117,3 +117,23 @@ def test_omega_rows_sparse():
     # same pattern as the left sparse sign drawn from stream 3
     S = sparse_sign.dense(500, 30, 8, seed=2, stream=sparse_sign.STREAM_RSVD)
     assert np.array_equal(Om, S.T)
+
+
+def test_sketch_and_solve_residual_bound():
+    # Sketch-and-solve with an OSI (Sec. 2.3, theorem on sketch-and-solve): with probability >= 9/10
+    # the warm start's squared residual is within C / alpha of the optimum.  With d = 4k the
+    # injectivity is about (1 - sqrt(k/d))^2 = 1/4; the check takes C = 1 (a bound of 4) on 10 seeds
+    # and requires 9 to pass, and every ratio to be >= 1 (the exact solution is optimal).
+    g = np.random.default_rng(1)
+    ratios = []
+    for seed in range(10):
+        n, k = 4000, 20
+        A = g.standard_normal((n, k))
+        b = g.standard_normal(n)
+        _, info = lsq.sketch_precond(A, b, 4 * k, 8, seed, max_refine=0)
+        xs = lsq.exact(A, b)
+        r0 = np.linalg.norm(A @ info["x0"] - b) ** 2
+        rs = np.linalg.norm(A @ xs - b) ** 2
+        ratios.append(r0 / rs)
+    assert min(ratios) >= 1 - 1e-12, ratios
+    assert sum(r <= 4.0 for r in ratios) >= 9, ratios

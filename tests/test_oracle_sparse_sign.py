@@ -148,3 +148,21 @@ def test_csr_inverts_columns():
         for q in range(zeta):
             assert rebuilt[(int(rows[j, q]), j)] == signs[j, q]
     assert len(rebuilt) == n * zeta
+
+
+def test_injectivity_dilation_coordinate_subspace():
+    # The injectivity / dilation estimator of the paper's OSI experiment (Fig. 2, Sec. 1.5): the
+    # adversarial orthonormal Q = [e_1 ... e_r] and embedding dimension 2r.  With zeta = 8 the sparse
+    # embedding should behave like a 2r x r Gaussian, whose squared extreme singular values tend to
+    # (1 -+ 1/sqrt 2)^2 (Marchenko-Pastur).  A missing zeta^{-1/2}, a repeated row within a column or
+    # a wrong zeta moves them far outside 25 %.
+    r = 200
+    lo, hi = [], []
+    for seed in range(5):
+        SQ = sparse_sign.dense(r, 2 * r, 8, seed)   # S restricted to its first r columns
+        sv = np.linalg.svd(SQ, compute_uv=False)
+        lo.append(sv[-1] ** 2)
+        hi.append(sv[0] ** 2)
+    alpha, beta = (1 - 2 ** -0.5) ** 2, (1 + 2 ** -0.5) ** 2
+    assert abs(np.median(lo) / alpha - 1) < 0.25, lo
+    assert abs(np.median(hi) / beta - 1) < 0.25, hi
