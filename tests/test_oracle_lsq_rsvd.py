@@ -137,3 +137,26 @@ def test_sketch_and_solve_residual_bound():
         ratios.append(r0 / rs)
     assert min(ratios) >= 1 - 1e-12, ratios
     assert sum(r <= 4.0 for r in ratios) >= 9, ratios
+
+
+@pytest.mark.parametrize("q", [0, 1])
+def test_rsvd_error_close_to_gaussian_test_matrix(q):
+    # The paper's RSVD comparison (Sec. 1.4, Fig. 1): a sparse test matrix gives about the error of
+    # a Gaussian one.  Baseline written here with numpy (Gaussian Omega, QR after every product);
+    # the medians over 5 seeds must agree to 25 % and both must respect Eckart-Young.
+    import synthetic
+    A = synthetic.lowrank_plus_noise(3000, 600, 60, seed=7, noise=1e-3, device="cpu").double().numpy()
+    r = 40
+    sv = np.linalg.svd(A, compute_uv=False)
+    es, eg = [], []
+    for seed in range(5):
+        Q = rsvd.range_finder(A, r, q, zeta=8, seed=seed)
+        es.append(rsvd.spectral_error(A, Q, iters=60, seed=1))
+        g = np.random.default_rng(100 + seed)
+        Qg, _ = np.linalg.qr(A @ g.standard_normal((A.shape[1], r)))
+        for _ in range(q):
+            Qg, _ = np.linalg.qr(A.T @ Qg)
+            Qg, _ = np.linalg.qr(A @ Qg)
+        eg.append(np.linalg.norm(A - Qg @ (Qg.T @ A), 2))
+    assert min(es) >= sv[r] * (1 - 1e-6) and min(eg) >= sv[r] * (1 - 1e-6)
+    assert abs(np.median(es) / np.median(eg) - 1) < 0.25, (es, eg)
