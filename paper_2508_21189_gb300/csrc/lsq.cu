@@ -276,10 +276,6 @@ template <typename T>
 __device__ __forceinline__ float to_float(T v) {
     return float(v);
 }
-template <>
-__device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 v) {
-    return __bfloat162float(v);
-}
 
 template <typename T, typename Acc, int M, bool RESID>
 __global__ void __launch_bounds__(kPassThreads) k_pass(const T* __restrict__ A, int64_t n, int k, int64_t lda,
@@ -664,15 +660,6 @@ __global__ void k_convert(const Src* __restrict__ A, int64_t n, int k, int64_t l
     const int64_t i = idx / k, j = idx - i * k;
     B[idx] = Dst(float(A[i * lda + j]));
 }
-template <>
-__global__ void k_convert<double, double>(const double* __restrict__ A, int64_t n, int k, int64_t lda,
-                                          double* __restrict__ B) {
-    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= n * k) return;
-    const int64_t i = idx / k, j = idx - i * k;
-    B[idx] = A[i * lda + j];
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
