@@ -12,14 +12,17 @@ Modules, each citing the passage it follows:
                vectors.
   sparse_sign  SparseUniform (Def. "SparseUniform", Sec. 3.2.1) as the left sketch S = Psi^T,
                Floyd sampling without replacement; pinned by uniformity of subsets, the
-               zeta/d marginals, isotropy E[S^T S] = I, dense brute force.
+               zeta/d marginals, isotropy E[S^T S] = I, dense brute force, and the injectivity /
+               dilation of the adversarial coordinate subspace against the Gaussian asymptotes.
   srtt         Omega = D F S with the WHT (Eq. "intro-srtt", Sec. 1.6; cost steps 1-3 of
                Sec. 4.x); pinned by scipy's Sylvester Hadamard matrix, H^T H = n I,
                the unsubsampled case being orthogonal, isotropy by Monte Carlo.
   lsq          sketch-and-solve (Alg. 3) warm start + preconditioned LSQR refinement; pinned
-               by k = 1 closed form, orthonormal columns (x* = A^T b), consistent systems, and
-               agreement with LAPACK least squares.
+               by k = 1 closed form, orthonormal columns (x* = A^T b), consistent systems,
+               agreement with LAPACK least squares, and the warm start's residual within the
+               sketch-and-solve bound (Sec. 2.3).
   rsvd         Alg. 1 with power iterations; pinned by exact recovery of low-rank matrices,
-               the Eckart-Young lower bound and the HMT-style upper bound.
+               the Eckart-Young lower bound, the HMT-style upper bound, and agreement with a
+               Gaussian test matrix's error (Fig. 1's comparison).
 Every function above is pinned; none is "parity unpinned".
 """
