@@ -9,8 +9,10 @@ no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (launched by torch.distributed.run): every rank sketches its own A (weak scaling, no
-collective on the data path); rank 0 prints the line with the max step time over ranks.
+N > 1 (launched by torch.distributed.run): the headline A is split into N row blocks, one per rank
+(strong scaling); each rank sketches its block (rsk_sparse_sign_apply_rows, its columns of the one
+S), the N partial d x k sketches are gathered over NCCL and summed in rank order on every rank
+(rsk_sketch_sum_partials); rank 0 prints the line with the max step time over ranks.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 """
 import argparse
@@ -234,18 +236,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config():
-    return {"workload": "sparse sign embedding S*A: A 2^22 x 256 BF16 (N(0,1) x logspace(-3,0) column scales), "
-                        "S SparseUniform d=2048, zeta=8, fresh seed per step",
-            "n": N_ROWS, "k": K_COLS, "d": D_SKETCH, "zeta": ZETA, "a_dtype": "bf16", "accumulate": "f32",
-            "l2": "inputs larger than L2 (A is 2.1 GB), no flush"}
+def workload_config(world=1):
+    cfg = {"workload": "sparse sign embedding S*A: A 2^22 x 256 BF16 (N(0,1) x logspace(-3,0) column scales), "
+                       "S SparseUniform d=2048, zeta=8, fresh seed per step",
+           "n": N_ROWS, "k": K_COLS, "d": D_SKETCH, "zeta": ZETA, "a_dtype": "bf16", "accumulate": "f32",
+           "l2": "inputs larger than L2 (A is 2.1 GB), no flush"}
+    if world > 1:
+        cfg["parallelism"] = (f"A split into {world} row blocks (one per GPU); partial sketches gathered over "
+                              "NCCL and summed in rank order")
+    return cfg
 
 
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
-def time_steps(rsk, A, out, steps, seed0, torch):
-    """Device time per step (ms) of `steps` sketch applies bracketed by barrier + synchronize."""
+def sketch_step(rsk, A, out, seed, row0, world):
+    """One headline step: S*A on one GPU, or this rank's row block plus the rank-ordered sum."""
+    if world == 1:
+        return rsk.rsk_sparse_sign_apply(A, D_SKETCH, ZETA, seed, out=out)
+    from paper_2508_21189_gb300 import sharded
+    return sharded.sparse_sign_apply(A, row0, D_SKETCH, ZETA, seed)
+
+
+def srtt_step(rsk, A, out, seed, row0, n_total, world):
+    if world == 1:
+        return rsk.rsk_srtt_apply(A, D_SKETCH, seed, out=out)
+    from paper_2508_21189_gb300 import sharded
+    return sharded.srtt_apply(A, row0, n_total, D_SKETCH, seed)
+
+
+def time_steps(rsk, A, out, steps, seed0, torch, row0=0, world=1):
+    """Device time per step (ms) of `steps` sketch steps bracketed by barrier + synchronize."""
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -253,7 +274,7 @@ def time_steps(rsk, A, out, steps, seed0, torch):
     torch.cuda.synchronize()
     ev0.record()
     for s in range(steps):
-        rsk.rsk_sparse_sign_apply(A, D_SKETCH, ZETA, seed0 + s, out=out)
+        sketch_step(rsk, A, out, seed0 + s, row0, world)
     ev1.record()
     torch.cuda.synchronize()
     barrier()
@@ -387,28 +408,33 @@ def run_ours(args):
     dts = {"bf16": torch.bfloat16, "fp32": torch.float32, "fp64": torch.float64}
     head = names[0]
     sampler.start()
+    from paper_2508_21189_gb300.sharded import row_partition
+    # rows of this rank: the whole A on one GPU; a row block of it (2048-row aligned, so the SRTT
+    # can use the same blocks) on several
+    row0, n_local = row_partition(args.rows, world, 2048)[rank]
     for name in names:
         dt = dts[name]
-        A = synthetic.colscaled_gaussian(args.rows, K_COLS, seed=2022 + rank, device=dev, dtype=dt)
+        A = synthetic.colscaled_gaussian(n_local, K_COLS, seed=2022 + rank, device=dev, dtype=dt)
         out = torch.empty(D_SKETCH, K_COLS, device=dev, dtype=torch.float32)
-        a_bytes = A.numel() * A.element_size()
+        a_bytes = args.rows * K_COLS * A.element_size()  # the whole A, over all ranks
         for w in range(args.warmup):
-            rsk.rsk_sparse_sign_apply(A, D_SKETCH, ZETA, w, out=out)
+            sketch_step(rsk, A, out, w, row0, world)
         rsk.rsk_sync_status()
         rsk.rsk_profile_enable(True)
-        ms_local = time_steps(rsk, A, out, args.steps, 10_000, torch)
+        ms_local = time_steps(rsk, A, out, args.steps, 10_000, torch, row0, world)
         prof = {k: rsk.rsk_profile_read(k) for k in ("sketch_index", "sketch_apply", "sketch_reduce")}
         rsk.rsk_profile_enable(False)
         rsk.rsk_sync_status()
         ms = max_over_ranks(ms_local, device=dev)
         apply_ms = prof["sketch_apply"][0] / max(1, prof["sketch_apply"][1])
         launches = sum(c for _, c in prof.values())
-        r = {"ms_per_step": ms, "value": world * a_bytes / (ms / 1e3) / 1e9, "a_bytes": a_bytes,
+        r = {"ms_per_step": ms, "value": a_bytes / (ms / 1e3) / 1e9, "a_bytes": a_bytes,
+             "local_bytes": A.numel() * A.element_size(),
              "apply_ms": apply_ms, "index_ms": prof["sketch_index"][0] / max(1, prof["sketch_index"][1]),
              "reduce_ms": prof["sketch_reduce"][0] / max(1, prof["sketch_reduce"][1]), "launches": launches}
         if not args.no_srtt:
             for w in range(args.warmup):
-                rsk.rsk_srtt_apply(A, D_SKETCH, w, out=out)
+                srtt_step(rsk, A, out, w, row0, args.rows, world)
             rsk.rsk_profile_enable(True)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
@@ -416,18 +442,38 @@ def run_ours(args):
             barrier()
             ev0.record()
             for st in range(args.steps):
-                rsk.rsk_srtt_apply(A, D_SKETCH, 30_000 + st, out=out)
+                srtt_step(rsk, A, out, 30_000 + st, row0, args.rows, world)
             ev1.record()
             torch.cuda.synchronize()
             sp = {k: rsk.rsk_profile_read(k) for k in ("srtt_apply", "srtt_reduce", "dense")}
             rsk.rsk_profile_enable(False)
             rsk.rsk_sync_status()
             sms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
-            r["srtt"] = {"ms_per_step": sms, "value": world * a_bytes / (sms / 1e3) / 1e9,
+            r["srtt"] = {"ms_per_step": sms, "value": a_bytes / (sms / 1e3) / 1e9,
                          "apply_ms": sp["srtt_apply"][0] / max(1, sp["srtt_apply"][1]),
                          "draw_ms": sp["dense"][0] / max(1, sp["dense"][1]),
                          "launches": sum(c for _, c in sp.values())}
-        if name == head and not args.no_e2e:
+        if name == head and not args.no_e2e and world > 1:
+            # end to end at N GPUs: every rank copies its row block from pinned host memory, the
+            # sharded sketch runs, and the result is read back to the host
+            A_host = A.cpu().pin_memory()
+            out_host = torch.empty(D_SKETCH, K_COLS, dtype=torch.float32).pin_memory()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            barrier()
+            ev0.record()
+            for s in range(args.steps):
+                A.copy_(A_host, non_blocking=True)
+                out_host.copy_(sketch_step(rsk, A, out, 20_000 + s, row0, world), non_blocking=True)
+            ev1.record()
+            torch.cuda.synchronize()
+            e2e_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, device=dev)
+            r["e2e"] = {"value": round(a_bytes / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+                        "h2d_bytes_per_step": r["local_bytes"], "d2h_bytes_per_step": out.numel() * 4,
+                        "ms_per_step": round(e2e_ms, 4)}
+            del A_host
+        elif name == head and not args.no_e2e:
             # end to end through the public host-input call: A in pinned host memory streams to the
             # device in row blocks while earlier blocks are sketched; SA is read back to the host
             A_host = A.cpu().pin_memory()
@@ -453,7 +499,7 @@ def run_ours(args):
             ev1.record()
             torch.cuda.synchronize()
             copy_ms = ev0.elapsed_time(ev1) / copies
-            r["e2e"] = {"value": round(world * a_bytes / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
+            r["e2e"] = {"value": round(a_bytes / (e2e_ms / 1e3) / 1e9, 3), "unit": "GB/s",
                         "h2d_bytes_per_step": a_bytes, "d2h_bytes_per_step": out.numel() * 4,
                         "ms_per_step": round(e2e_ms, 4),
                         "h2d_copy_gbs": round(a_bytes / (copy_ms / 1e3) / 1e9, 3)}
@@ -475,13 +521,13 @@ def run_ours(args):
         return
     peak, peak_kind = hbm_peak()
     main = result[head]
-    alg_bytes = main["a_bytes"] + D_SKETCH * K_COLS * 4
+    alg_bytes = main["local_bytes"] + D_SKETCH * K_COLS * 4  # one launch reads this rank's rows
     achieved = alg_bytes / (main["apply_ms"] / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": round(main["value"], 3), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(main["ms_per_step"], 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config(),
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(world),
         "hbm_frac_of_step": round(main["value"] / world / peak, 4),
         "roofline": {"kernel": "k_apply (sparse sign gather)", "bound": "hbm", "achieved": round(achieved, 2),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -500,13 +546,13 @@ def run_ours(args):
             key = "srtt" if name == head else f"srtt_{name}"
             line[key] = {"value": round(sr["value"], 3), "unit": "GB/s", "ms_per_step": round(sr["ms_per_step"], 4),
                          "apply_ms": round(sr["apply_ms"], 4), "draw_ms": round(sr["draw_ms"], 4),
-                         "apply_hbm_frac": round(r["a_bytes"] / (sr["apply_ms"] / 1e3) / 1e9 / peak, 4),
+                         "apply_hbm_frac": round(r["local_bytes"] / (sr["apply_ms"] / 1e3) / 1e9 / peak, 4),
                          "workload": f"SRTT d={D_SKETCH} (WHT, n=2^22), A {name}"}
     for name in names[1:]:
         r = result[name]
         line[name] = {"value": round(r["value"], 3), "unit": "GB/s", "ms_per_step": round(r["ms_per_step"], 4),
                       "apply_ms": round(r["apply_ms"], 4),
-                      "apply_frac": round((r["a_bytes"] + D_SKETCH * K_COLS * 4) / (r["apply_ms"] / 1e3) / 1e9
+                      "apply_frac": round((r["local_bytes"] + D_SKETCH * K_COLS * 4) / (r["apply_ms"] / 1e3) / 1e9
                                           / peak, 4)}
     line.update(extra)
     if args.rows != N_ROWS:

@@ -25,7 +25,7 @@
  *     word(seed, stream, entity, t) = Philox4x32-10(key = (seed_lo, seed_hi),
  *                                                   ctr = (entity_lo, entity_hi, stream, t >> 2))[t & 3]
  * Streams: 0 = sparse sign left sketch, 1 = SRTT diagonal D, 2 = SRTT subsample P,
- *          3 = RSVD test matrix Omega.
+ *          3 = RSVD test matrix Omega, 4 = SparseStack, 5 = SparseRTT's SparseCol positions.
  */
 #ifndef RSK_H
 #define RSK_H
@@ -66,6 +66,13 @@ const char* rsk_last_error(const rsk_handle* h);
 /* Synchronise `stream` and return the device status word recorded by kernels of this handle
  * since the previous call (then clear it). */
 rsk_status rsk_sync_status(rsk_handle* h, cudaStream_t stream);
+/* Iteration limit of the bounded polls on global-memory flags that this handle's kernels make
+ * (the persistent QR's grid barrier and reflector-ready flags): a poll that reaches it gives up,
+ * records RSK_ERR_TIMEOUT in the device status word and the kernel returns, so a wait that can
+ * never end (a CTA that is not resident, a flag nothing sets) cannot hang the GPU.  spins = 0
+ * restores the default (about 4 million polls, seconds).  The mbarrier waits on TMA and bulk
+ * copies keep the default.  Not a step of the paper: failure detection of the library. */
+rsk_status rsk_set_wait_limit(rsk_handle* h, uint32_t spins);
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t rsk_version(void);
 
@@ -131,6 +138,27 @@ rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype
                                  int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
                                  rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
 
+/* a3 on a block of rows of A, for a row-sharded A (one process per GPU): with S the d x N sparse
+ * sign of `seed` (N the rows of the whole A), SA = S[:, row0 : row0 + n] * A_block, where A is the
+ * n x k block holding rows row0 .. row0 + n - 1 of the whole A (device, row-major, lda >= k).  The
+ * columns of S depend only on their global index, so the blocks of any row partition give partial
+ * sketches whose sum is S * A_whole; SA is such a partial (scaled by zeta^{-1/2}).  Paper: the sketch
+ * application cost O(zeta nnz(A)) (Sec. 3.2) is additive over row blocks.  rsk_sparse_sign_apply is
+ * this call with row0 = 0.  Requires 0 <= row0 and row0 + n < 2^31; otherwise as rsk_sparse_sign_apply. */
+rsk_status rsk_sparse_sign_apply_rows(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                      int64_t lda, int64_t row0, int64_t d, int32_t zeta, uint64_t seed, void* SA,
+                                      rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
+
+/* out = parts[0] + parts[1] + ... + parts[count-1], summed in that order for every element (so the
+ * result does not depend on how the partials were produced or gathered).  parts: device, count
+ * packed d x k blocks (row-major, leading dimension k) of dtype F32 or F64, block g starting at
+ * element g * part_stride (part_stride >= d*k).  out: device d x k, leading dimension ldo >= k, same
+ * dtype.  The reduction step of a row-sharded sketch: each rank's partial from
+ * rsk_sparse_sign_apply_rows or rsk_srtt_apply_rows, gathered in rank order, summed in rank order. */
+rsk_status rsk_sketch_sum_partials(rsk_handle* h, const void* parts, rsk_dtype dtype, int32_t count,
+                                   int64_t part_stride, int64_t d, int64_t k, void* out, int64_t ldo,
+                                   cudaStream_t stream);
+
 /* a3 with A in HOST memory (pinned for the copies to overlap; pageable works, serialised): the
  * same SA = S * A as rsk_sparse_sign_apply, computed while A streams to the device.  A is cut into
  * row blocks of whole index chunks (about 256 MB each); block b is copied on an internal stream into
@@ -148,14 +176,33 @@ rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dty
  * path that must not allocate after start-up).  The paper has no counterpart: this is a deployment
  * variant of rsk_sparse_sign_apply with the same arguments minus the handle, and bit-identical
  * results.  Scratch comes from one fixed 64 MiB array in device memory that every GPU loading the
- * library holds until exit; no call allocates or frees anything.  Sizes whose scratch (inverted
- * index plus partial sums) exceeds 64 MiB return RSK_ERR_UNSUPPORTED before any launch.  The first
- * call on each device looks up the array's device address (make it before any stream capture).
- * All calls share the array: calls that overlap on the GPU race, and the set-up is not thread safe.
- * Errors are reported by the status code only (no handle, no message). */
+ * library holds until exit; no call allocates or frees anything.  Invalid arguments return
+ * RSK_ERR_INVALID_ARG before anything else; valid sizes whose scratch (inverted index plus partial
+ * sums) exceeds 64 MiB return RSK_ERR_UNSUPPORTED before any launch.  The first call on each device
+ * looks up the array's device address (make it before any stream capture).  All calls share the
+ * array: calls that overlap on the GPU race, and the set-up is not thread safe.  The return code
+ * carries the errors found on the host (no handle, no message); a failure found on the device
+ * while the call runs (a bounded wait that ran out, a failed bounds check) cannot be returned by
+ * an asynchronous call, so the call's last kernel then fills SA with NaN. */
 rsk_status rsk_sparse_sign_apply_noalloc(const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
                                          int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype,
                                          int64_t ldsa, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * SparseStack (Def. SparseStack, Sec. 1.5): zeta stacked CountSketches.  With b = d / zeta, every
+ * column j of S (d x n) has exactly one entry +-zeta^{-1/2} in each block of b consecutive rows:
+ * row q*b + floor(w_q * b / 2^32) of block q, w_q = word(seed, 4, j, q) (Philox stream 4); its sign
+ * is -1 iff bit q of w_zeta is set.  Limits as SparseUniform plus d % zeta == 0
+ * (RSK_ERR_INVALID_ARG otherwise).  The inverted index and gather are those of
+ * rsk_sparse_sign_apply: only the column draw differs.
+ * ------------------------------------------------------------------------------------------- */
+/* Draw S: rows device int32[n*zeta] (entry q of column j in block q), sign_bits device uint32[n]. */
+rsk_status rsk_sparse_stack_generate(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed,
+                                     int32_t* rows, uint32_t* sign_bits, cudaStream_t stream);
+/* SA = S * A with the conventions, accumulation and summation order of rsk_sparse_sign_apply. */
+rsk_status rsk_sparse_stack_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                  int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
+                                  rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
 
 /* Plans keep the inverted index of one S for repeated application (e.g. to A and then to b).
  * The plan owns device memory allocated on `stream`; destroy it with rsk_sparse_sign_plan_destroy. */
@@ -191,6 +238,41 @@ rsk_status rsk_srtt_draw(rsk_handle* h, int64_t n, int64_t d, uint64_t seed, int
  * reduced in a fixed order (deterministic). */
 rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
                           int64_t d, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream);
+
+/* a4 on a block of rows of A (row-sharded A): Y = d^{-1/2} P H_N[:, row0 : row0 + n_rows] D_block A_block
+ * for the SRTT of an N-row A (N = 2^m; P and D drawn for N exactly as rsk_srtt_apply), with A_block
+ * the n_rows x k block holding rows row0 .. row0 + n_rows - 1.  Because H_N = H_{N/2048} (x) H_2048,
+ * a block that starts on a 2048-row boundary contributes sum_b (-1)^{popcount(p_hi & b)} (H_2048 x_b)
+ * over its own 2048-row blocks b only, so the partials of any such partition sum to the whole Y.
+ * Requires row0 % 2048 == 0 and row0 + n_rows <= N; otherwise as rsk_srtt_apply, which is this call
+ * with row0 = 0 and n_rows = N. */
+rsk_status rsk_srtt_apply_rows(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n_rows, int64_t k,
+                               int64_t lda, int64_t row0, int64_t n, int64_t d, uint64_t seed, void* Y,
+                               rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * SparseRTT (Def. SparseRTT with Def. SparseCol, Sec. 4): Omega = D F S with D the Rademacher
+ * diagonal of the SRTT, F the unitary WHT (Sylvester order), S a SparseCol matrix whose columns
+ * are iid copies of sqrt(n/xi) sum_{t<xi} rho_t e_{s_t} scaled by d^{-1/2}, the xi positions s_t of
+ * a column distinct and uniform on [0, n).  As a left sketch of a tall A:
+ *     Y[q, :] = (d xi)^{-1/2} sum_{t < xi} rho_{qt} (H_n D A)[s_{qt}, :].
+ * Draw rule: column q's positions are Floyd's algorithm over [0, n) with draws
+ * w_t = word(seed, 5, q, t), t < xi (Philox stream 5); rho_{qt} = -1 iff bit t of w_xi is set.
+ * D_i is the SRTT's (stream 1).  xi = 0 selects the recommended ceil(1.5 ln d) (Sec. 4,
+ * "Implementation guidance").  Limits: n = 2^m < 2^31, 1 <= d <= 2048, 1 <= xi <= min(n, 32).
+ * ------------------------------------------------------------------------------------------- */
+/* The recommended column sparsity ceil(1.5 ln d), clamped to [1, 32]. */
+int32_t rsk_sparse_rtt_default_xi(int64_t d);
+/* The SparseCol positions: positions device int32[d*xi] (positions[q*xi + t] = s_qt, Floyd
+ * insertion order), sign_bits device uint32[d] (bit t set <=> rho_qt = -1).  Either may be NULL. */
+rsk_status rsk_sparse_rtt_draw(rsk_handle* h, int64_t n, int64_t d, int32_t xi, uint64_t seed, int32_t* positions,
+                               uint32_t* sign_bits, cudaStream_t stream);
+/* Y = Omega^T A for A device n x k (F32 or BF16, lda >= k); Y device d x k (F32 or F64, ldy >= k).
+ * One pass over A: each 2048-row block is transformed on chip as in rsk_srtt_apply and every output
+ * row adds its xi signed transformed rows; FP32 arithmetic, partials summed in a fixed order. */
+rsk_status rsk_sparse_rtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                                int64_t d, int32_t xi, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy,
+                                cudaStream_t stream);
 
 /* Split an FP64 matrix (n x k, row-major, lda >= k) into the interleaved F32X2 form P (n x k pairs,
  * packed: 2 k floats per row): hi = FP32 round-to-nearest-even of a, lo = FP32 round-to-nearest-

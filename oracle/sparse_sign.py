@@ -26,14 +26,15 @@ STREAM_LEFT = 0
 STREAM_RSVD = 3
 
 
-def columns(n, d, zeta, seed, stream=STREAM_LEFT):
-    """Rows (n x zeta, int64, insertion order) and signs (n x zeta, int8 in {+1,-1}).
+def columns(n, d, zeta, seed, stream=STREAM_LEFT, col0=0):
+    """Rows (n x zeta, int64, insertion order) and signs (n x zeta, int8 in {+1,-1}) of the
+    columns col0 .. col0 + n - 1 of S.
 
     Row q of column j is the q-th index Floyd's algorithm inserts.
     """
     if not (1 <= zeta <= 32 and zeta <= d):
         raise ValueError("need 1 <= zeta <= min(d, 32)")
-    j = np.arange(n, dtype=np.uint64)
+    j = np.arange(col0, col0 + n, dtype=np.uint64)
     rows = np.empty((n, zeta), dtype=np.int64)
     for q in range(zeta):
         w = words(seed, stream, j, q).astype(np.uint64)
@@ -105,3 +106,24 @@ def abs_apply(A, d, zeta, seed, stream=STREAM_LEFT):
     n = A.shape[0]
     St = abs(matrix(n, d, zeta, seed, stream))
     return np.asarray(St @ A)
+
+
+def apply_block(A_block, col0, d, zeta, seed, stream=STREAM_LEFT):
+    """zeta^{-1/2} * S~[:, col0:col0+nb] @ A_block: the part of S A that rows col0 .. col0+nb-1 of
+    a row-partitioned A contribute (S A is the sum of these over the blocks of any partition)."""
+    A_block = np.asarray(A_block, dtype=np.float64)
+    nb = A_block.shape[0]
+    rows, signs = columns(nb, d, zeta, seed, stream, col0=col0)
+    jj = np.repeat(np.arange(nb), zeta)
+    St = sp.csr_matrix((signs.reshape(-1).astype(np.float64), (rows.reshape(-1), jj)), shape=(d, nb))
+    return np.asarray(St @ A_block) / np.sqrt(zeta)
+
+
+def abs_apply_block(A_block, col0, d, zeta, seed, stream=STREAM_LEFT):
+    """(|S~[:, col0:col0+nb]| @ |A_block|) in float64: abs_apply for a row block."""
+    A_block = np.abs(np.asarray(A_block, dtype=np.float64))
+    nb = A_block.shape[0]
+    rows, _ = columns(nb, d, zeta, seed, stream, col0=col0)
+    jj = np.repeat(np.arange(nb), zeta)
+    St = sp.csr_matrix((np.ones(nb * zeta), (rows.reshape(-1), jj)), shape=(d, nb))
+    return np.asarray(St @ A_block)

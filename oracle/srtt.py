@@ -19,9 +19,11 @@ TEST INFRASTRUCTURE: part of the oracle; see oracle/__init__.py.
 import numpy as np
 
 from .philox import words
+from . import sparse_sign as _ss
 
 STREAM_D = 1
 STREAM_P = 2
+STREAM_SPARSECOL = 5
 
 
 def diag_signs(n, seed):
@@ -97,3 +99,44 @@ def apply_rows(A, rows_q, d, seed):
         h = 1.0 - 2.0 * par
         out.append((h * D) @ A / np.sqrt(d))
     return np.stack(out)
+
+
+def apply_block(A_block, row0, n, d, seed):
+    """The part of the n-row SRTT that rows row0 .. row0 + nb - 1 contribute, from the definition:
+    Y_block[q, :] = d^{-1/2} * sum_{i in block} (-1)^{popcount(P_q & i)} D_i A[i, :].  The SRTT of A
+    is the sum of these over the blocks of any row partition."""
+    A_block = np.asarray(A_block, dtype=np.float64)
+    nb = A_block.shape[0]
+    if row0 < 0 or row0 + nb > n:
+        raise ValueError("block outside [0, n)")
+    D = diag_signs(n, seed)[row0:row0 + nb].astype(np.float64)
+    P = subsample(n, d, seed)
+    x = P[:, None] & np.arange(row0, row0 + nb, dtype=np.int64)[None, :]
+    par = np.zeros_like(x)
+    while np.any(x):
+        par ^= x & 1
+        x >>= 1
+    H = 1.0 - 2.0 * par
+    return H @ (D[:, None] * A_block.reshape(nb, -1)) / np.sqrt(d)
+
+
+def sparse_rtt_positions(n, d, xi, seed):
+    """SparseCol positions of the SparseRTT (Def. SparseCol): output row q < d takes xi distinct
+    coordinates of [0, n), uniform without replacement (Floyd's algorithm on Philox stream 5, entity
+    q), with Rademacher signs (bit t of the draw after the xi picks).  Returns (positions d x xi,
+    signs d x xi in {+1, -1}), positions in insertion order."""
+    return _ss.columns(d, n, xi, seed, stream=STREAM_SPARSECOL)
+
+
+def sparse_rtt_apply(A, d, xi, seed):
+    """Y = Omega^T A for the SparseRTT Omega = D F S (Def. SparseRTT) with F = H_n / sqrt(n):
+    Y[q, :] = (d xi)^{-1/2} sum_t rho_qt (H_n D A)[s_qt, :] in float64."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    D = diag_signs(n, seed).astype(np.float64)
+    HDA = fwht(D[:, None] * A.reshape(n, -1))
+    pos, sg = sparse_rtt_positions(n, d, xi, seed)
+    Y = np.zeros((d, HDA.shape[1]))
+    for t in range(xi):
+        Y += sg[:, t, None] * HDA[pos[:, t]]
+    return Y / np.sqrt(d * xi)

@@ -67,6 +67,12 @@ def rsk_sync_status(stream=None, device=None):
     _check(load().rsk_sync_status(h, _stream(stream)), h)
 
 
+def rsk_set_wait_limit(spins, device=None):
+    """Iteration limit of the handle's bounded polls on global-memory flags (0 = default)."""
+    h = handle(device)
+    _check(load().rsk_set_wait_limit(h, spins), h)
+
+
 def rsk_sparse_sign_generate(n, d, zeta, seed, device=None, stream=None):
     """Draw S: returns (rows int32 [n, zeta], sign_bits int32 view of uint32 [n]) on the device."""
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -213,6 +219,102 @@ def rsk_srtt_apply(A, d, seed, out_dtype=torch.float32, out=None, stream=None):
     h = handle(A.device)
     st = load().rsk_srtt_apply(h, A.data_ptr(), _dt(A), n, k, A.stride(0), d, seed, out.data_ptr(), _dt(out),
                                out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
+def rsk_sparse_stack_generate(n, d, zeta, seed, device=None, stream=None):
+    """Draw a SparseStack S: (rows int32 [n, zeta], sign_bits int32 view of uint32 [n]) on the device."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    rows = torch.empty(n, zeta, dtype=torch.int32, device=dev)
+    bits = torch.empty(n, dtype=torch.int32, device=dev)
+    h = handle(dev)
+    _check(load().rsk_sparse_stack_generate(h, n, d, zeta, seed, rows.data_ptr(), bits.data_ptr(), _stream(stream)), h)
+    return rows, bits
+
+
+def rsk_sparse_stack_apply(A, d, zeta, seed, out_dtype=torch.float32, out=None, stream=None):
+    """SA = S @ A with S a SparseStack (d = b * zeta)."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=A.device)
+    _matrix(out, "out")
+    h = handle(A.device)
+    st = load().rsk_sparse_stack_apply(h, A.data_ptr(), _dt(A), n, k, A.stride(0), d, zeta, seed,
+                                       out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
+def rsk_sparse_sign_apply_rows(A, row0, d, zeta, seed, out_dtype=torch.float32, out=None, stream=None):
+    """Partial sketch S[:, row0:row0+n] @ A of a row block A (n x k) of a row-sharded matrix."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=A.device)
+    _matrix(out, "out")
+    h = handle(A.device)
+    st = load().rsk_sparse_sign_apply_rows(h, A.data_ptr(), _dt(A), n, k, A.stride(0), row0, d, zeta, seed,
+                                           out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
+def rsk_srtt_apply_rows(A, row0, n_total, d, seed, out_dtype=torch.float32, out=None, stream=None):
+    """Partial SRTT d^{-1/2} P H[:, row0:row0+n] D A of a row block A (n x k, row0 % 2048 == 0)."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=A.device)
+    _matrix(out, "out")
+    h = handle(A.device)
+    st = load().rsk_srtt_apply_rows(h, A.data_ptr(), _dt(A), n, k, A.stride(0), row0, n_total, d, seed,
+                                    out.data_ptr(), _dt(out), out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
+def rsk_sketch_sum_partials(parts, out=None, stream=None):
+    """out = parts[0] + parts[1] + ... in that order; parts is a CUDA tensor [count, d, k] (F32/F64)."""
+    if not parts.is_cuda or parts.dim() != 3 or not parts.is_contiguous():
+        raise ValueError("parts must be a contiguous CUDA tensor [count, d, k]")
+    count, d, k = parts.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=parts.dtype, device=parts.device)
+    _matrix(out, "out")
+    h = handle(parts.device)
+    st = load().rsk_sketch_sum_partials(h, parts.data_ptr(), _dt(parts), count, d * k, d, k, out.data_ptr(),
+                                        out.stride(0), _stream(stream))
+    _check(st, h)
+    return out
+
+
+def rsk_sparse_rtt_default_xi(d):
+    return int(load().rsk_sparse_rtt_default_xi(d))
+
+
+def rsk_sparse_rtt_draw(n, d, seed, xi=0, device=None, stream=None):
+    """SparseCol positions of a SparseRTT: (positions int32 [d, xi], sign_bits int32 view of uint32 [d])."""
+    xi = xi or rsk_sparse_rtt_default_xi(d)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    pos = torch.empty(d, xi, dtype=torch.int32, device=dev)
+    bits = torch.empty(d, dtype=torch.int32, device=dev)
+    h = handle(dev)
+    _check(load().rsk_sparse_rtt_draw(h, n, d, xi, seed, pos.data_ptr(), bits.data_ptr(), _stream(stream)), h)
+    return pos, bits
+
+
+def rsk_sparse_rtt_apply(A, d, seed, xi=0, out_dtype=torch.float32, out=None, stream=None):
+    """Y = Omega^T A with Omega = D F S a SparseRTT (WHT, xi positions per output row; 0 = default)."""
+    _matrix(A, "A")
+    n, k = A.shape
+    if out is None:
+        out = torch.empty(d, k, dtype=out_dtype, device=A.device)
+    _matrix(out, "out")
+    h = handle(A.device)
+    st = load().rsk_sparse_rtt_apply(h, A.data_ptr(), _dt(A), n, k, A.stride(0), d, xi, seed, out.data_ptr(),
+                                     _dt(out), out.stride(0), _stream(stream))
     _check(st, h)
     return out
 

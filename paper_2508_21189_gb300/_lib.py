@@ -22,19 +22,29 @@ SIGNATURES = {
     "rsk_last_error": [c_p],
     "rsk_sync_status": [c_p, c_p],
     "rsk_version": [],
+    "rsk_set_wait_limit": [c_p, ctypes.c_uint32],
     "rsk_profile_enable": [c_p, c_i32],
     "rsk_profile_read": [c_p, c_i32, c_p, c_p],
     "rsk_sparse_sign_generate": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
     "rsk_sparse_sign_index_dims": [c_i64, c_i64, c_i32, c_p, c_p, c_p],
     "rsk_sparse_sign_index": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
     "rsk_sparse_sign_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_sparse_sign_apply_rows": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64,
+                                   c_p],
+    "rsk_sketch_sum_partials": [c_p, c_p, c_i32, c_i32, c_i64, c_i64, c_i64, c_p, c_i64, c_p],
+    "rsk_srtt_apply_rows": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i64, c_i64, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_apply_noalloc": [c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_apply_host": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_sparse_stack_generate": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
+    "rsk_sparse_stack_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_create": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p],
     "rsk_sparse_sign_plan_apply": [c_p, c_p, c_p, c_i32, c_i64, c_i64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_destroy": [c_p, c_p, c_p],
     "rsk_srtt_draw": [c_p, c_i64, c_i64, c_u64, c_p, c_p, c_p],
     "rsk_srtt_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_sparse_rtt_default_xi": [c_i64],
+    "rsk_sparse_rtt_draw": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
+    "rsk_sparse_rtt_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_split_pairs": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_p],
     "rsk_lstsq_sketch_precond": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p],
     "rsk_lstsq_sketch_precond_batched": [c_p, c_i32, c_p, c_p, c_p, c_p],

@@ -195,6 +195,12 @@ rsk_status rsk_sync_status(rsk_handle* h, cudaStream_t stream) {
     return RSK_OK;
 }
 
-int32_t rsk_version(void) { return 100; }
+rsk_status rsk_set_wait_limit(rsk_handle* h, uint32_t spins) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    h->wait_limit = spins ? spins : rskd::kWaitLimit;
+    return RSK_OK;
+}
+
+int32_t rsk_version(void) { return 200; }
 
 }  // extern "C"

@@ -36,6 +36,9 @@ struct rsk_handle {
     // pinned host words the solvers poll without stalling the stream (early exit of the inner CG)
     double* host_flags = nullptr;       // kHostFlags doubles
     cudaEvent_t flag_ev[2] = {nullptr, nullptr};
+    // iteration limit of the bounded polls on global-memory flags (grid barrier, reflector-ready
+    // flags); rsk_set_wait_limit changes it, 0 restores the default
+    uint32_t wait_limit = 1u << 22;
 };
 constexpr int kHostFlags = 8;
 
@@ -85,6 +88,8 @@ rsk_status sketch_plan_apply_ws(rsk_handle* h, const rsk_sketch_plan* plan, cons
                                 int64_t lda, void* SA, rsk_dtype sa_dt, int64_t ldsa, void* partials,
                                 cudaStream_t stream);
 
+rsk_status sketch_check_args(rsk_handle* h, const void* A, rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda,
+                             int64_t d, int zeta, const void* SA, rsk_dtype sa_dt, int64_t ldsa);
 size_t sketch_scratch_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int zeta, rsk_dtype a_dt);
 rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda,
                                 int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
@@ -127,7 +132,9 @@ rsk_status sketch_apply_built(rsk_handle* h, const void* index_mem, int64_t n, i
 #ifdef __CUDACC__
 namespace rskd {
 
-// Roughly a few seconds at most before a wait gives up and records RSK_DEV_TIMEOUT.
+// Roughly a few seconds at most before a wait gives up and records RSK_DEV_TIMEOUT.  The mbarrier
+// waits on TMA/bulk copies always use it; the polls on global-memory flags take the handle's
+// wait_limit (this value unless rsk_set_wait_limit changed it).
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

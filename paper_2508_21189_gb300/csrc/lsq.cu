@@ -33,7 +33,7 @@ constexpr int kMaxK = 1024;
 // Bounded software grid barrier for persistent kernels whose CTAs are all resident.
 // ------------------------------------------------------------------------------------------
 __device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, unsigned int nblocks,
-                             unsigned int* status) {
+                             unsigned int* status, uint32_t limit) {
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
@@ -46,7 +46,7 @@ __device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, un
         } else {
             uint32_t it = 0;
             while (*gen == g) {
-                if (++it > rskd::kWaitLimit) {
+                if (++it > limit) {
                     atomicOr(status, RSK_DEV_TIMEOUT);
                     ok = 0;
                     break;
@@ -104,13 +104,13 @@ __device__ void make_reflector(double* col, int d, int j, double* tau, double* r
 }
 
 __global__ void __launch_bounds__(256) k_qr(double* W, int d, int k, double* tau, unsigned int* bar,
-                                           unsigned int* status) {
+                                           unsigned int* status, uint32_t limit) {
     __shared__ double red[32];
     const unsigned int G = gridDim.x;
     const int cols = k + 1;
     if (blockIdx.x == 0) make_reflector(W, d, 0, tau, red);
     for (int j = 0; j < k; ++j) {
-        if (!grid_barrier(bar, bar + 1, G, status)) return;
+        if (!grid_barrier(bar, bar + 1, G, status, limit)) return;
         // Reflector j was written by another CTA: read it through L2 (ld.cg), never from a line this
         // SM's L1 may hold from an earlier step.
         const double* v = W + size_t(j) * d;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) 
 
 template <int T>
 __global__ void __launch_bounds__(256) k_qr_col(double* W, int d, int k, double* tau, unsigned int* ready,
-                                               unsigned int* status) {
+                                               unsigned int* status, uint32_t limit) {
     __shared__ double red[32];
     __shared__ double xj_s;
     __shared__ int ok_s;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_qr_col(double* W, int d, int k, double*
             uint32_t it = 0;
             int ok = 1;
             while (ld_acquire_u32(ready + j) == 0u) {
-                if (++it > rskd::kWaitLimit) {
+                if (++it > limit) {
                     atomicOr(status, RSK_DEV_TIMEOUT);
                     ok = 0;
                     break;
@@ -884,7 +884,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         double* taup = w.tau;
         unsigned int* rp_ = qr_ready;
         unsigned int* stp = h->dev_status;
-        void* args[] = {&Wp, &dd, const_cast<int*>(&K), &taup, &rp_, &stp};
+        uint32_t lim = h->wait_limit;
+        void* args[] = {&Wp, &dd, const_cast<int*>(&K), &taup, &rp_, &stp, &lim};
         const int pr = prof_begin(h, stream, RSK_KERNEL_DENSE);
         const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), dim3(K + 1), dim3(256), args, 0, stream);
         prof_end(h, stream, pr);
@@ -906,7 +907,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         double* taup = w.tau;
         unsigned int* barp = w.bar;
         unsigned int* stp = h->dev_status;
-        void* args[] = {&Wp, &dd, const_cast<int*>(&K), &taup, &barp, &stp};
+        uint32_t lim = h->wait_limit;
+        void* args[] = {&Wp, &dd, const_cast<int*>(&K), &taup, &barp, &stp, &lim};
         const int pr = prof_begin(h, stream, RSK_KERNEL_DENSE);
         RSK_CUDA_TRY(h, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_qr), dim3(grid), dim3(256), args, 0, stream));
         prof_end(h, stream, pr);
@@ -949,6 +951,9 @@ extern "C" rsk_status rsk_lstsq_sketch_precond(rsk_handle* h, const void* A, rsk
         RSK_CUDA_TRY(h, cudaMemcpyAsync(xh.data(), w.x, size_t(K) * 8, cudaMemcpyDeviceToHost, stream));
         RSK_CUDA_TRY(h, cudaStreamSynchronize(stream));
         if (steps == 0) {
+            // a bounded wait of the QR that ran out leaves R undefined: stop before refining with it
+            const rsk_status dev = rsk_sync_status(h, stream);
+            if (dev != RSK_OK) return dev;
             frob = sqrt(host[1]);
             bnorm = sqrt(host[2]);
         }

@@ -15,7 +15,15 @@
 // zero: the index kernel writes every offset and entry the apply reads, and the apply writes every
 // partial the reduction reads.  Calls whose work overlaps on the GPU (other streams, or without
 // synchronisation in between) race on the array; the host-side set-up is not thread safe either.
+//
+// Device-side failures.  The kernels record a bounded wait that ran out, or a failed bounds check,
+// in the device word g_status.  A call cannot return that status (it does not synchronise), so
+// each call clears g_status in its first launch and, in its last, overwrites SA with NaN when the
+// word is set: a result that may hold stale or missing partial sums is never returned as valid.
+#include <math.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -26,6 +34,19 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocScratchBytes];
 static __device__ unsigned int g_status;
+
+__global__ void k_noalloc_clear_status() { g_status = 0u; }
+
+// SA (d x k, leading dimension ldsa) := NaN if any kernel of this call recorded a failure.
+template <typename T>
+__global__ void k_noalloc_check_status(T* SA, int64_t d, int64_t k, int64_t ldsa) {
+    if (*static_cast<volatile unsigned int*>(&g_status) == 0u) return;
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < d * k;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = idx / k, c = idx - i * k;
+        SA[i * ldsa + c] = T(NAN);
+    }
+}
 
 struct DeviceContext {
     bool ready = false;
@@ -70,6 +91,9 @@ rsk_status setup(DeviceContext& c, int dev) {
 extern "C" rsk_status rsk_sparse_sign_apply_noalloc(const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
                                                     int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
                                                     rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream) {
+    // every argument is checked before anything else (the scratch sizing below assumes valid sizes)
+    rsk_status st = rsk::sketch_check_args(nullptr, A, a_dtype, n, k, lda, d, zeta, SA, sa_dtype, ldsa);
+    if (st != RSK_OK) return st;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -78,12 +102,20 @@ extern "C" rsk_status rsk_sparse_sign_apply_noalloc(const void* A, rsk_dtype a_d
     if (dev < 0 || dev >= kMaxDevices) return RSK_ERR_UNSUPPORTED;
     DeviceContext& c = g_ctx[dev];
     if (!c.ready) {
-        const rsk_status st = setup(c, dev);
+        st = setup(c, dev);
         if (st != RSK_OK) return st;
     }
-    if (n < 1 || k < 1 || d < 1 || zeta < 1) return RSK_ERR_INVALID_ARG;
     // sizes whose index and partials do not fit the fixed array are refused before any launch
     if (rsk::sketch_scratch_bytes(&c.h, n, k, d, zeta, a_dtype) > kNoAllocScratchBytes) return RSK_ERR_UNSUPPORTED;
-    return rsk::sketch_apply_scratch(&c.h, A, a_dtype, n, k, lda, d, zeta, seed, SA, sa_dtype, ldsa, c.scratch,
-                                     stream);
+    k_noalloc_clear_status<<<1, 1, 0, stream>>>();
+    if (cudaGetLastError() != cudaSuccess) return RSK_ERR_CUDA;
+    st = rsk::sketch_apply_scratch(&c.h, A, a_dtype, n, k, lda, d, zeta, seed, SA, sa_dtype, ldsa, c.scratch, stream);
+    if (st != RSK_OK) return st;
+    const unsigned grid = unsigned(std::min<int64_t>((d * k + 255) / 256, int64_t(c.h.num_sms) * 8));
+    if (sa_dtype == RSK_F64)
+        k_noalloc_check_status<double><<<grid, 256, 0, stream>>>(static_cast<double*>(SA), d, k, ldsa);
+    else
+        k_noalloc_check_status<float><<<grid, 256, 0, stream>>>(static_cast<float*>(SA), d, k, ldsa);
+    if (cudaGetLastError() != cudaSuccess) return RSK_ERR_CUDA;
+    return RSK_OK;
 }

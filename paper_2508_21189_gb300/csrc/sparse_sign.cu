@@ -49,9 +49,15 @@ __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~size_
 // ------------------------------------------------------------------------------------------
 // Drawing one column of S.
 // ------------------------------------------------------------------------------------------
+// Column distributions: SparseUniform (Def. SparseUniform: zeta rows uniform without replacement,
+// Floyd's algorithm) and SparseStack (Def. SparseStack: zeta stacked CountSketches, one row drawn
+// uniformly in each block of b = d / zeta consecutive rows: row q*b + floor(w_q * b / 2^32)).
+enum ColumnKind : int { kUniform = 0, kStack = 1 };
+constexpr uint32_t kStreamStack = 4;
+
 template <int ZMAX>
 __device__ __forceinline__ void draw_column(uint64_t seed, uint32_t stream, uint64_t j, int d, int zeta,
-                                            int (&rows)[ZMAX], uint32_t& negbits) {
+                                            int (&rows)[ZMAX], uint32_t& negbits, int kind = kUniform) {
     uint32_t w[ZMAX + 4];
 #pragma unroll
     for (int b = 0; b <= ZMAX / 4; ++b) {
@@ -63,16 +69,24 @@ __device__ __forceinline__ void draw_column(uint64_t seed, uint32_t stream, uint
             w[4 * b + 3] = blk.v[3];
         }
     }
-    // Floyd: for m = d-zeta .. d-1 draw t uniform in [0, m]; keep t unless already taken, else m.
+    if (kind == kStack) {
+        // one row per block of b rows: distinct by construction
+        const uint32_t b = uint32_t(d / zeta);
 #pragma unroll
-    for (int q = 0; q < ZMAX; ++q) {
-        if (q < zeta) {
-            const uint32_t m = uint32_t(d - zeta + q);
-            const int t = int(__umulhi(w[q], m + 1u));
-            bool taken = false;
+        for (int q = 0; q < ZMAX; ++q)
+            if (q < zeta) rows[q] = int(uint32_t(q) * b + __umulhi(w[q], b));
+    } else {
+        // Floyd: for m = d-zeta .. d-1 draw t uniform in [0, m]; keep t unless already taken, else m.
 #pragma unroll
-            for (int p = 0; p < q; ++p) taken |= (rows[p] == t);
-            rows[q] = taken ? int(m) : t;
+        for (int q = 0; q < ZMAX; ++q) {
+            if (q < zeta) {
+                const uint32_t m = uint32_t(d - zeta + q);
+                const int t = int(__umulhi(w[q], m + 1u));
+                bool taken = false;
+#pragma unroll
+                for (int p = 0; p < q; ++p) taken |= (rows[p] == t);
+                rows[q] = taken ? int(m) : t;
+            }
         }
     }
     uint32_t sb = 0;
@@ -84,12 +98,12 @@ __device__ __forceinline__ void draw_column(uint64_t seed, uint32_t stream, uint
 
 template <int ZMAX>
 __global__ void k_generate(int64_t n, int d, int zeta, uint64_t seed, uint32_t stream, int32_t* __restrict__ rows,
-                           uint32_t* __restrict__ signs) {
+                           uint32_t* __restrict__ signs, int kind) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int r[ZMAX];
     uint32_t nb;
-    draw_column<ZMAX>(seed, stream, uint64_t(j), d, zeta, r, nb);
+    draw_column<ZMAX>(seed, stream, uint64_t(j), d, zeta, r, nb, kind);
     if (rows) {
 #pragma unroll
         for (int q = 0; q < ZMAX; ++q)
@@ -120,7 +134,8 @@ __host__ __device__ inline IndexLayout index_layout(int d, int zeta) {
 
 template <int ZMAX>
 __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int zeta, uint64_t seed, uint32_t stream,
-                                                         uint16_t* __restrict__ offsets, uint16_t* __restrict__ entries) {
+                                                         int64_t col0, int kind, uint16_t* __restrict__ offsets,
+                                                         uint16_t* __restrict__ entries) {
     extern __shared__ __align__(16) uint8_t sm[];
     const IndexLayout L = index_layout(d, zeta);
     uint16_t* tgt = reinterpret_cast<uint16_t*>(sm + L.tgt_off);
@@ -138,11 +153,11 @@ __global__ void __launch_bounds__(kIndexThreads) k_index(int64_t n, int d, int z
     const int rows = int((n - j0) < C ? (n - j0) : C);
     const int nent = rows * zeta;
 
-    // 1. draw the chunk's columns
+    // 1. draw the chunk's columns (global column col0 + j0 + r of S)
     for (int r = tid; r < rows; r += kIndexThreads) {
         int rr[ZMAX];
         uint32_t nb;
-        draw_column<ZMAX>(seed, stream, uint64_t(j0 + r), d, zeta, rr, nb);
+        draw_column<ZMAX>(seed, stream, uint64_t(col0 + j0 + r), d, zeta, rr, nb, kind);
         if (ZMAX == 8 && zeta == 8) {
             uint4 pk;
             pk.x = uint32_t(rr[0]) | (uint32_t(rr[1 % ZMAX]) << 16);
@@ -468,6 +483,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
     Cursor cur, ahead;
     set_item(cur, int(blockIdx.x));
     ahead = cur;
+    // copies issued into / completed waits on each stage (the same in every thread), so that a CTA
+    // leaving early knows which stages may still receive bulk copies
+    uint32_t issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;
     if constexpr (TMA) {
         if (tid == 0) {
             rskd::mbar_init(&bars[0], 1);
@@ -476,10 +494,16 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
         }
         __syncthreads();
         // two chunks in flight: `ahead` always points two positions past `cur`
-        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage0, &bars[0]);
-        if (ahead.item < a.nitems) advance(ahead);
-        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage1, &bars[1]);
-        if (ahead.item < a.nitems) advance(ahead);
+        if (ahead.item < a.nitems) {
+            if (tid == 0) issue(ahead, stage0, &bars[0]);
+            ++issued0;
+            advance(ahead);
+        }
+        if (ahead.item < a.nitems) {
+            if (tid == 0) issue(ahead, stage1, &bars[1]);
+            ++issued1;
+            advance(ahead);
+        }
     }
 
     for (int it = 0; cur.item < a.nitems; ++it) {
@@ -492,6 +516,9 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
             // every thread waits on the stage's barrier itself (that is what makes the TMA writes
             // visible to it); a timeout skips the chunk and ends the loop at the barrier below
             ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
+            if (ok) {
+                if (st) ++waited1; else ++waited0;
+            }
             buf = st ? stage1 : stage0;
         } else {
             // A not TMA-compatible: plain loads into the single stage.
@@ -542,14 +569,26 @@ __global__ void __launch_bounds__(kApplyThreads, 1)
                 }
             }
         }
-        if (__syncthreads_or(!ok)) break;
+        if (__syncthreads_or(!ok)) {
+            if constexpr (TMA) {
+                // a wait ran out: before the CTA (and its shared memory) goes away, wait once more,
+                // bounded, for every copy still owed to a stage, so none lands after the exit
+                if (tid == 0) {
+                    if (issued0 > waited0) rskd::mbar_wait(&bars[0], waited0 & 1u, a.status);
+                    if (issued1 > waited1) rskd::mbar_wait(&bars[1], waited1 & 1u, a.status);
+                }
+                __syncthreads();
+            }
+            break;
+        }
         if constexpr (TMA) {
             if (ahead.item < a.nitems) {
+                const int st = it & 1;
                 if (tid == 0) {
                     rskd::fence_proxy_async();
-                    const int st = it & 1;
                     issue(ahead, st ? stage1 : stage0, &bars[st]);
                 }
+                if (st) ++issued1; else ++issued0;
                 advance(ahead);
             }
         }
@@ -604,6 +643,15 @@ rsk_status check_dims(rsk_handle* h, int64_t n, int64_t d, int32_t zeta) {
     return RSK_OK;
 }
 
+// SparseStack needs d to be a whole number of blocks: d = b * zeta.
+rsk_status check_stack_dims(rsk_handle* h, int64_t n, int64_t d, int32_t zeta) {
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    if (d % zeta != 0)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "SparseStack needs d = b * zeta (d=%lld, zeta=%d)", (long long)d, zeta);
+    return RSK_OK;
+}
+
 int64_t n_chunks_of(int64_t n, int zeta) { return (n + chunk_rows(zeta) - 1) / chunk_rows(zeta); }
 
 // Index storage: offsets (n_chunks rows of pitch entries, plus a tail so that any target-block
@@ -612,14 +660,14 @@ size_t offsets_count(int64_t n, int d, int zeta) { return size_t(n_chunks_of(n, 
 size_t entries_count(int64_t n, int zeta) { return size_t(n) * zeta + 16; }
 
 rsk_status launch_index(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed, uint32_t stream_id,
-                        uint16_t* offs, uint16_t* ents, cudaStream_t stream) {
+                        uint16_t* offs, uint16_t* ents, cudaStream_t stream, int64_t col0 = 0, int kind = kUniform) {
     const IndexLayout L = index_layout(d, zeta);
     if (L.total > 227 * 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "index build needs %zu B of shared memory", L.total);
     const int64_t nch = n_chunks_of(n, zeta);
     auto go = [&](auto kern) -> rsk_status {
         RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total)));
         const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_INDEX);
-        kern<<<unsigned(nch), kIndexThreads, L.total, stream>>>(n, d, zeta, seed, stream_id, offs, ents);
+        kern<<<unsigned(nch), kIndexThreads, L.total, stream>>>(n, d, zeta, seed, stream_id, col0, kind, offs, ents);
         rsk::prof_end(h, stream, pr);
         RSK_LAUNCH_CHECK(h);
         return RSK_OK;
@@ -776,6 +824,23 @@ rsk_status check_apply_args(rsk_handle* h, const void* A, int a_dt, int64_t k, i
     return RSK_OK;
 }
 
+rsk_status generate_kind(rsk_handle* h, int64_t n, int d, int zeta, uint64_t seed, uint32_t stream_id, int kind,
+                         int32_t* rows, uint32_t* signs, cudaStream_t stream) {
+    const unsigned grid = unsigned((n + 255) / 256);
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_GENERATE);
+    if (zeta <= 8) k_generate<8><<<grid, 256, 0, stream>>>(n, d, zeta, seed, stream_id, rows, signs, kind);
+    else if (zeta <= 16) k_generate<16><<<grid, 256, 0, stream>>>(n, d, zeta, seed, stream_id, rows, signs, kind);
+    else k_generate<32><<<grid, 256, 0, stream>>>(n, d, zeta, seed, stream_id, rows, signs, kind);
+    rsk::prof_end(h, stream, pr);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+// Index build + gather apply for the columns row0 .. row0 + n - 1 of a sketch of the given kind.
+rsk_status apply_kind(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                      int64_t row0, int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype,
+                      int64_t ldsa, cudaStream_t stream, uint32_t stream_id, int kind);
+
 }  // namespace
 
 struct rsk_sketch_plan {
@@ -799,6 +864,13 @@ rsk_status sketch_plan_apply_ws(rsk_handle* h, const rsk_sketch_plan* plan, cons
     const ApplyPlan p = plan_apply(h, plan->n, k, int(plan->d), plan->zeta, a_dt);
     return apply_with_index(h, plan->offs, plan->ents, A, a_dt, plan->n, k, lda, int(plan->d), plan->zeta, SA, sa_dt,
                             ldsa, partials, p, stream);
+}
+// Every argument check of rsk_sparse_sign_apply, without a launch (h may be null: no message).
+rsk_status sketch_check_args(rsk_handle* h, const void* A, rsk_dtype a_dt, int64_t n, int64_t k, int64_t lda,
+                             int64_t d, int zeta, const void* SA, rsk_dtype sa_dt, int64_t ldsa) {
+    rsk_status st = check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    return check_apply_args(h, A, a_dt, k, lda, SA, sa_dt, ldsa);
 }
 // Scratch bytes of one sparse sign apply when the inverted index and the partials are carved from a
 // single caller-provided buffer, and the apply that uses such a buffer.
@@ -899,9 +971,9 @@ rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64
     rsk_status st = check_dims(h, n, d, zeta);
     if (st != RSK_OK) return st;
     const unsigned grid = unsigned((n + 255) / 256);
-    if (zeta <= 8) k_generate<8><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs);
-    else if (zeta <= 16) k_generate<16><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs);
-    else k_generate<32><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs);
+    if (zeta <= 8) k_generate<8><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs, kUniform);
+    else if (zeta <= 16) k_generate<16><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs, kUniform);
+    else k_generate<32><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, stream_id, rows, signs, kUniform);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
@@ -916,13 +988,25 @@ rsk_status rsk_sparse_sign_generate(rsk_handle* h, int64_t n, int64_t d, int32_t
     if (st != RSK_OK) return st;
     if (!rows && !sign_bits) return RSK_OK;
     const unsigned grid = unsigned((n + 255) / 256);
-    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SKETCH_GENERATE);
-    if (zeta <= 8) k_generate<8><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, kStreamLeft, rows, sign_bits);
-    else if (zeta <= 16) k_generate<16><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, kStreamLeft, rows, sign_bits);
-    else k_generate<32><<<grid, 256, 0, stream>>>(n, int(d), zeta, seed, kStreamLeft, rows, sign_bits);
-    rsk::prof_end(h, stream, pr);
-    RSK_LAUNCH_CHECK(h);
-    return RSK_OK;
+    return generate_kind(h, n, int(d), zeta, seed, kStreamLeft, kUniform, rows, sign_bits, stream);
+}
+
+rsk_status rsk_sparse_stack_generate(rsk_handle* h, int64_t n, int64_t d, int32_t zeta, uint64_t seed, int32_t* rows,
+                                     uint32_t* sign_bits, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_stack_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    if (!rows && !sign_bits) return RSK_OK;
+    return generate_kind(h, n, int(d), zeta, seed, kStreamStack, kStack, rows, sign_bits, stream);
+}
+
+rsk_status rsk_sparse_stack_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                                  int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype, int64_t ldsa,
+                                  cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    rsk_status st = check_stack_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    return apply_kind(h, A, a_dtype, n, k, lda, 0, d, zeta, seed, SA, sa_dtype, ldsa, stream, kStreamStack, kStack);
 }
 
 rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows_out, int64_t* n_chunks,
@@ -949,10 +1033,28 @@ rsk_status rsk_sparse_sign_index(rsk_handle* h, int64_t n, int64_t d, int32_t ze
 rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
                                  int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype, int64_t ldsa,
                                  cudaStream_t stream) {
+    return rsk_sparse_sign_apply_rows(h, A, a_dtype, n, k, lda, 0, d, zeta, seed, SA, sa_dtype, ldsa, stream);
+}
+
+rsk_status rsk_sparse_sign_apply_rows(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
+                                      int64_t lda, int64_t row0, int64_t d, int32_t zeta, uint64_t seed, void* SA,
+                                      rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream) {
     if (!h) return RSK_ERR_INVALID_ARG;
     rsk_status st = check_dims(h, n, d, zeta);
     if (st != RSK_OK) return st;
-    st = check_apply_args(h, A, a_dtype, k, lda, SA, sa_dtype, ldsa);
+    return apply_kind(h, A, a_dtype, n, k, lda, row0, d, zeta, seed, SA, sa_dtype, ldsa, stream, kStreamLeft,
+                      kUniform);
+}
+
+}  // extern "C"
+
+namespace {
+rsk_status apply_kind(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                      int64_t row0, int64_t d, int32_t zeta, uint64_t seed, void* SA, rsk_dtype sa_dtype,
+                      int64_t ldsa, cudaStream_t stream, uint32_t stream_id, int kind) {
+    if (row0 < 0 || row0 + n >= (int64_t(1) << 31))
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "row0=%lld: need 0 <= row0 and row0 + n < 2^31", (long long)row0);
+    rsk_status st = check_apply_args(h, A, a_dtype, k, lda, SA, sa_dtype, ldsa);
     if (st != RSK_OK) return st;
     const ApplyPlan p = plan_apply(h, n, k, int(d), zeta, a_dtype);
     const size_t off_bytes = offsets_count(n, int(d), zeta) * 2;
@@ -965,10 +1067,33 @@ rsk_status rsk_sparse_sign_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype
     uint16_t* offs = cv.take<uint16_t>(offsets_count(n, int(d), zeta));
     uint16_t* ents = cv.take<uint16_t>(entries_count(n, zeta));
     void* partials = cv.take<char>(p.partial_bytes);
-    st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
+    st = launch_index(h, n, int(d), zeta, seed, stream_id, offs, ents, stream, row0, kind);
     if (st != RSK_OK) return st;
     return apply_with_index(h, offs, ents, A, a_dtype, n, k, lda, int(d), zeta, SA, sa_dtype, ldsa, partials, p,
                             stream);
+}
+}  // namespace
+
+extern "C" {
+
+rsk_status rsk_sketch_sum_partials(rsk_handle* h, const void* parts, rsk_dtype dtype, int32_t count,
+                                   int64_t part_stride, int64_t d, int64_t k, void* out, int64_t ldo,
+                                   cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!parts || !out) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (dtype != RSK_F32 && dtype != RSK_F64) return rsk::fail(h, RSK_ERR_INVALID_ARG, "dtype must be F32 or F64");
+    if (count < 1 || d < 1 || k < 1 || ldo < k || part_stride < d * k)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "need count, d, k >= 1, ldo >= k, part_stride >= d*k");
+    const int64_t total = d * k;
+    const unsigned grid = unsigned((total + 255) / 256);
+    if (dtype == RSK_F64)
+        k_sum_blocks<double><<<grid, 256, 0, stream>>>(static_cast<const double*>(parts), part_stride, count, int(d), k,
+                                                      static_cast<double*>(out), ldo);
+    else
+        k_sum_blocks<float><<<grid, 256, 0, stream>>>(static_cast<const float*>(parts), part_stride, count, int(d), k,
+                                                     static_cast<float*>(out), ldo);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
 }
 
 rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dtype a_dtype, int64_t n, int64_t k,
@@ -1004,36 +1129,42 @@ rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dty
     char* outs = cv.take<char>(size_t(nblk) * rsk::Carver::round(obytes));
     const size_t ostride = rsk::Carver::round(obytes);
     cudaStream_t cs = h->streams[1];  // copy stream
-    cudaEvent_t ev_ready, copied[2], freed[2];
-    RSK_CUDA_TRY(h, cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
-    for (int i = 0; i < 2; ++i) {
-        RSK_CUDA_TRY(h, cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming));
-        RSK_CUDA_TRY(h, cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming));
-    }
+    // every event created here is destroyed on every exit path below (a failed CUDA call only sets
+    // st and skips the remaining work)
+    cudaEvent_t ev_ready = nullptr, copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    auto cuda_ok = [&](cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return true;
+        st = rsk::fail(h, RSK_ERR_CUDA, "%s failed: %s", what, cudaGetErrorString(e));
+        return false;
+    };
+    bool good = cuda_ok(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming), "cudaEventCreate");
+    for (int i = 0; good && i < 2; ++i)
+        good = cuda_ok(cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming), "cudaEventCreate") &&
+               cuda_ok(cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming), "cudaEventCreate");
     // the copy stream starts after the caller's earlier work on `stream` (the workspace may be reused)
-    RSK_CUDA_TRY(h, cudaEventRecord(ev_ready, stream));
-    RSK_CUDA_TRY(h, cudaStreamWaitEvent(cs, ev_ready, 0));
-    st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
-    for (int64_t b = 0; st == RSK_OK && b < nblk; ++b) {
+    good = good && cuda_ok(cudaEventRecord(ev_ready, stream), "cudaEventRecord") &&
+           cuda_ok(cudaStreamWaitEvent(cs, ev_ready, 0), "cudaStreamWaitEvent");
+    if (good) st = launch_index(h, n, int(d), zeta, seed, kStreamLeft, offs, ents, stream);
+    for (int64_t b = 0; good && st == RSK_OK && b < nblk; ++b) {
         const int64_t r0 = b * brows, rows = std::min<int64_t>(brows, n - r0);
         char* buf = stage[b & 1];
-        if (b >= 2) RSK_CUDA_TRY(h, cudaStreamWaitEvent(cs, freed[b & 1], 0));
+        if (b >= 2 && !cuda_ok(cudaStreamWaitEvent(cs, freed[b & 1], 0), "cudaStreamWaitEvent")) break;
         const char* src = static_cast<const char*>(A_host) + size_t(r0) * size_t(lda) * es;
-        if (lda == k)
-            RSK_CUDA_TRY(h, cudaMemcpyAsync(buf, src, size_t(rows) * row_bytes, cudaMemcpyHostToDevice, cs));
-        else
-            RSK_CUDA_TRY(h, cudaMemcpy2DAsync(buf, size_t(row_bytes), src, size_t(lda) * es, size_t(row_bytes),
-                                              size_t(rows), cudaMemcpyHostToDevice, cs));
-        RSK_CUDA_TRY(h, cudaEventRecord(copied[b & 1], cs));
-        RSK_CUDA_TRY(h, cudaStreamWaitEvent(stream, copied[b & 1], 0));
+        const cudaError_t ce =
+            lda == k ? cudaMemcpyAsync(buf, src, size_t(rows) * row_bytes, cudaMemcpyHostToDevice, cs)
+                     : cudaMemcpy2DAsync(buf, size_t(row_bytes), src, size_t(lda) * es, size_t(row_bytes),
+                                         size_t(rows), cudaMemcpyHostToDevice, cs);
+        if (!cuda_ok(ce, "host-to-device copy of A") || !cuda_ok(cudaEventRecord(copied[b & 1], cs), "cudaEventRecord") ||
+            !cuda_ok(cudaStreamWaitEvent(stream, copied[b & 1], 0), "cudaStreamWaitEvent"))
+            break;
         // the block is whole chunks of the global index: its sub-index starts at chunk r0 / C
         const int64_t c0 = r0 / C;
         const ApplyPlan pb = plan_apply(h, rows, k, int(d), zeta, a_dtype);
         st = apply_with_index(h, offs + c0 * offsets_pitch(int(d)), ents + c0 * C * zeta, buf, a_dtype, rows, k, k,
                               int(d), zeta, outs + size_t(b) * ostride, sa_dtype, k, partials, pb, stream);
-        RSK_CUDA_TRY(h, cudaEventRecord(freed[b & 1], stream));
+        if (st == RSK_OK && !cuda_ok(cudaEventRecord(freed[b & 1], stream), "cudaEventRecord")) break;
     }
-    if (st == RSK_OK) {
+    if (good && st == RSK_OK) {
         // SA = sum of the block sketches, in block order
         const int64_t total = d * k;
         if (sa_dtype == RSK_F64)
@@ -1044,13 +1175,13 @@ rsk_status rsk_sparse_sign_apply_host(rsk_handle* h, const void* A_host, rsk_dty
             k_sum_blocks<float><<<unsigned((total + 255) / 256), 256, 0, stream>>>(
                 reinterpret_cast<const float*>(outs), int64_t(ostride / 4), int(nblk), int(d), k,
                 static_cast<float*>(SA), ldsa);
-        if (cudaGetLastError() != cudaSuccess) st = rsk::fail(h, RSK_ERR_CUDA, "block sum launch failed");
+        cuda_ok(cudaGetLastError(), "block sum launch");
     }
     // events may be destroyed while work is pending (the driver releases them on completion)
-    cudaEventDestroy(ev_ready);
+    if (ev_ready) cudaEventDestroy(ev_ready);
     for (int i = 0; i < 2; ++i) {
-        cudaEventDestroy(copied[i]);
-        cudaEventDestroy(freed[i]);
+        if (copied[i]) cudaEventDestroy(copied[i]);
+        if (freed[i]) cudaEventDestroy(freed[i]);
     }
     return st;
 }

@@ -159,11 +159,12 @@ __global__ void k_srtt_dbits(int64_t nwords, uint64_t seed, uint32_t* __restrict
 // D as the transform kernel reads it: per 2048-row block, word 2g + h holds the signs of rows
 // g + 32 (32h + x), x = 0..31, in bit x (a 32 x 32 bit transpose of the block's natural words
 // 32h .. 32h + 31, done with one ballot per bit).  One warp per (block, h).
-__global__ void k_srtt_dbits_t(int64_t nblocks, uint64_t seed, uint32_t* __restrict__ out) {
+// Block b of the output holds global block blk0 + b (row blocks of a row-sharded A).
+__global__ void k_srtt_dbits_t(int64_t nblocks, uint64_t seed, int64_t blk0, uint32_t* __restrict__ out) {
     const int lane = threadIdx.x & 31, h = threadIdx.x >> 5;
     const int64_t b = blockIdx.x;
     if (b >= nblocks) return;
-    const int64_t wd = b * (kBlk / 32) + 32 * h + lane;  // natural word index: rows 32 wd .. 32 wd + 31
+    const int64_t wd = (blk0 + b) * (kBlk / 32) + 32 * h + lane;  // natural word index: rows 32 wd .. 32 wd + 31
     const rskd::Block4 blk = rskd::philox_block(seed, kStreamD, uint64_t(wd >> 2), 0);
     const uint32_t word = blk.v[wd & 3];
     uint32_t mine = 0;
@@ -254,8 +255,9 @@ __global__ void __launch_bounds__(1024) k_srtt_deal(const int32_t* __restrict__ 
 struct SrttArgs {
     const void* A;          // used by the plain-load path
     int64_t lda;
-    int64_t n, k;
+    int64_t n, k;            // rows of this A (a row block of the transform when blk0 > 0), columns
     int d, nblocks, nslices, R, nitems;
+    int blk0;                // global index of this A's first 2048-row block
     const int32_t* prow;    // d selected rows
     const int32_t* slot_q;  // output row handled by slot tid + 256*j, or -1
     const uint32_t* dbits;  // nblocks * 64 words of D, transposed per block (k_srtt_dbits_t)
@@ -263,6 +265,10 @@ struct SrttArgs {
     int64_t pstride;        // d * kCols
     uint64_t seed;
     unsigned int* status;
+    // SparseRTT: xi > 0 positions per output row (slot s = output row s), spos[i * nslots + s] =
+    // position | (negative << 31); xi == 0 is the SRTT (one position per row, from prow/slot_q)
+    int xi, nslots;
+    const uint32_t* spos;
 };
 
 // Position in a CTA's sequence of (item, block): items blockIdx.x, + gridDim.x, ...
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
     float acc[QPT][kCols];
 #pragma unroll
     for (int j = 0; j < QPT; ++j) {
-        const int q = a.slot_q[tid + kThreads * j];
+        const int q = a.xi ? -1 : a.slot_q[tid + kThreads * j];
         const int p = q >= 0 ? a.prow[q] : 0;
         plo[j] = p & (kBlk - 1);
         phi[j] = p >> 11;
@@ -373,6 +379,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
     SrttCursor cur, ahead;
     cursor_item(a, cur, int(blockIdx.x));
     ahead = cur;
+    // copies issued into / completed waits on each stage (the same in every thread), so that a CTA
+    // leaving early knows which stages may still receive bulk copies
+    uint32_t issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;
     if constexpr (TMA) {
         if (tid == 0) {
             rskd::mbar_init(&bars[0], 1);
@@ -381,16 +390,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         }
         __syncthreads();
         // two blocks in flight: `ahead` always points two positions past `cur`
-        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage0, &bars[0]);
-        if (ahead.item < a.nitems) cursor_next(a, ahead);
-        if (tid == 0 && ahead.item < a.nitems) issue(ahead, stage1, &bars[1]);
-        if (ahead.item < a.nitems) cursor_next(a, ahead);
+        if (ahead.item < a.nitems) {
+            if (tid == 0) issue(ahead, stage0, &bars[0]);
+            ++issued0;
+            cursor_next(a, ahead);
+        }
+        if (ahead.item < a.nitems) {
+            if (tid == 0) issue(ahead, stage1, &bars[1]);
+            ++issued1;
+            cursor_next(a, ahead);
+        }
     }
     auto flush = [&](int item) {
         float* part = a.partials + int64_t(item) * a.pstride;
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
-            const int q = a.slot_q[tid + kThreads * j];
+            const int q = a.xi ? (tid + kThreads * j < a.d ? tid + kThreads * j : -1) : a.slot_q[tid + kThreads * j];
             if (q >= 0) {
                 float4* dst = reinterpret_cast<float4*>(part + int64_t(q) * kCols);
                 dst[0] = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
@@ -413,8 +428,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
         // D words of this block (transposed layout): staged with the block on the TMA path
         if (!TMA && tid < kBlk / 32) dwords[tid] = a.dbits[int64_t(blk) * (kBlk / 32) + tid];
         bool ok = true;
-        if constexpr (TMA) ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
-        if (__syncthreads_or(!ok)) break;
+        if constexpr (TMA) {
+            ok = rskd::mbar_wait(&bars[st], uint32_t((it >> 1) & 1), a.status);
+            if (ok) {
+                if (st) ++waited1; else ++waited0;
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if constexpr (TMA) {
+                // a wait ran out: before the CTA (and its shared memory) goes away, wait once more,
+                // bounded, for every copy still owed to a stage, so none lands after the exit
+                if (tid == 0) {
+                    if (issued0 > waited0) rskd::mbar_wait(&bars[0], waited0 & 1u, a.status);
+                    if (issued1 > waited1) rskd::mbar_wait(&bars[1], waited1 & 1u, a.status);
+                }
+                __syncthreads();
+            }
+            break;
+        }
         const uint32_t* dw = TMA ? dstage + st * (kBlk / 32) : dwords;
         const uint2 tw = *reinterpret_cast<const uint2*>(dw + 2 * g1);  // signs of rows g1 + 32x
         const T* raw = reinterpret_cast<const T*>(st ? stage1 : stage0);
@@ -445,6 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
                 rskd::fence_proxy_async();
                 issue(ahead, st ? stage1 : stage0, &bars[st]);
             }
+            if (st) ++issued1; else ++issued0;
             cursor_next(a, ahead);
         }
         // pass 2: stages on row bits 0..4
@@ -462,6 +494,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
                 Z[zel(32 * (g2 + 32 * h) + y + 1, c2)] = w[16 * h + (y >> 1)].y;
             }
         __syncthreads();
+        if (a.xi) {
+            // SparseRTT gather: Y[q] += sum_i rho_qi (-1)^{popcount(p_hi & blk)} Z[p_lo] over the xi
+            // positions p = s_qi of output row q (slot q)
+            const uint32_t gblk = uint32_t(a.blk0 + blk);
+#pragma unroll
+            for (int j = 0; j < QPT; ++j) {
+                const int slot = tid + kThreads * j;
+                if (slot >= a.d) continue;
+                float2 s0 = make_float2(acc[j][0], acc[j][1]), s1 = make_float2(acc[j][2], acc[j][3]);
+                float2 s2 = make_float2(acc[j][4], acc[j][5]), s3 = make_float2(acc[j][6], acc[j][7]);
+                for (int i = 0; i < a.xi; ++i) {
+                    const uint32_t w = __ldg(a.spos + int64_t(i) * a.nslots + slot);
+                    const int lo = int(w & uint32_t(kBlk - 1));
+                    const uint32_t hi = (w & 0x7fffffffu) >> 11;
+                    const uint32_t neg = (w >> 31) ^ (__popc(hi & gblk) & 1u);
+                    const float sg = neg ? -1.f : 1.f;
+                    const float2 sg2 = make_float2(sg, sg);
+                    const float4* zr = reinterpret_cast<const float4*>(Z + zoff(lo));
+                    const int sw = (lo >> 2) & 1;
+                    const float4 z0 = zr[sw], z1 = zr[sw ^ 1];
+                    s0 = __ffma2_rn(make_float2(z0.x, z0.y), sg2, s0);
+                    s1 = __ffma2_rn(make_float2(z0.z, z0.w), sg2, s1);
+                    s2 = __ffma2_rn(make_float2(z1.x, z1.y), sg2, s2);
+                    s3 = __ffma2_rn(make_float2(z1.z, z1.w), sg2, s3);
+                }
+                acc[j][0] = s0.x; acc[j][1] = s0.y; acc[j][2] = s1.x; acc[j][3] = s1.y;
+                acc[j][4] = s2.x; acc[j][5] = s2.y; acc[j][6] = s3.x; acc[j][7] = s3.y;
+            }
+        } else {
         // gather: Y[q] += (-1)^{popcount(p_hi & blk)} Z[p_lo]
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
@@ -469,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
             const int sw = (plo[j] >> 2) & 1;  // halves swapped for this row
             const float4 za = zr[sw], zb = zr[sw ^ 1];
             const float4 z0 = za, z1 = zb;
-            const float sg = (__popc(uint32_t(phi[j]) & uint32_t(blk)) & 1) ? -1.f : 1.f;
+            const float sg = (__popc(uint32_t(phi[j]) & uint32_t(a.blk0 + blk)) & 1) ? -1.f : 1.f;
             const float2 sg2 = make_float2(sg, sg);
             float2 t0 = __ffma2_rn(make_float2(z0.x, z0.y), sg2, make_float2(acc[j][0], acc[j][1]));
             float2 t1 = __ffma2_rn(make_float2(z0.z, z0.w), sg2, make_float2(acc[j][2], acc[j][3]));
@@ -477,6 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_srtt(const __grid_constant__ CU
             float2 t3 = __ffma2_rn(make_float2(z1.z, z1.w), sg2, make_float2(acc[j][6], acc[j][7]));
             acc[j][0] = t0.x; acc[j][1] = t0.y; acc[j][2] = t1.x; acc[j][3] = t1.y;
             acc[j][4] = t2.x; acc[j][5] = t2.y; acc[j][6] = t3.x; acc[j][7] = t3.y;
+        }
         }
         __syncthreads();
         const int done_item = cur.item;
@@ -499,6 +561,47 @@ __global__ void k_reduce_srtt(const float* __restrict__ partials, int64_t pstrid
     Y[i * ldy + col] = Out(double(sum) * scale);
 }
 
+// SparseCol positions of SparseRTT (Def. SparseCol): output row q (a column of S) takes xi distinct
+// positions of [0, n) by Floyd's algorithm with draws w_t = word(seed, 5, q, t), t < xi, and the
+// sign of its t-th position is -1 iff bit t of w_xi is set.  One thread per output row.
+constexpr uint32_t kStreamSparseCol = 5;
+__global__ void k_sparsecol_draw(int64_t n, int d, int xi, uint64_t seed, int nslots, uint32_t* __restrict__ spos,
+                                 int32_t* __restrict__ pos_out, uint32_t* __restrict__ signs_out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= d) return;
+    uint32_t w[36];
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        if (4 * b <= xi) {
+            const rskd::Block4 blk = rskd::philox_block(seed, kStreamSparseCol, uint64_t(q), uint32_t(b));
+            w[4 * b + 0] = blk.v[0];
+            w[4 * b + 1] = blk.v[1];
+            w[4 * b + 2] = blk.v[2];
+            w[4 * b + 3] = blk.v[3];
+        }
+    }
+    uint32_t sb = 0;
+#pragma unroll
+    for (int t = 0; t <= 32; ++t)
+        if (t == xi) sb = w[t];
+    uint32_t p[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        if (t < xi) {
+            const uint32_t m = uint32_t(n - xi + t);
+            const uint32_t v = uint32_t((uint64_t(w[t]) * (uint64_t(m) + 1)) >> 32);
+            bool taken = false;
+#pragma unroll
+            for (int r = 0; r < t; ++r) taken |= (p[r] == v);
+            p[t] = taken ? m : v;
+            const uint32_t neg = (sb >> t) & 1u;
+            spos[int64_t(t) * nslots + q] = p[t] | (neg << 31);
+            if (pos_out) pos_out[int64_t(q) * xi + t] = int32_t(p[t]);
+        }
+    }
+    if (signs_out) signs_out[q] = xi >= 32 ? sb : (sb & ((1u << xi) - 1u));
+}
+
 int hash_bits_for(int d) {
     int b = 1;
     while ((1 << b) < 2 * d) ++b;
@@ -512,6 +615,22 @@ rsk_status check_srtt(rsk_handle* h, int64_t n, int64_t d) {
         return rsk::fail(h, RSK_ERR_INVALID_ARG, "SRTT needs 1 <= d <= min(n, 8192) (got %lld)", (long long)d);
     return RSK_OK;
 }
+
+// SparseRTT: n = 2^m (the WHT), 1 <= xi <= min(n, 32) positions per output row, and at most 2048
+// output rows (the gather's register slots).
+rsk_status check_sparse_rtt(rsk_handle* h, int64_t n, int64_t d, int xi) {
+    if (n < 1 || n >= (int64_t(1) << 31) || (n & (n - 1)))
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "SparseRTT needs n = 2^m < 2^31 (got %lld)", (long long)n);
+    if (d < 1 || d > 8 * kThreads)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "SparseRTT needs 1 <= d <= %d (got %lld)", 8 * kThreads, (long long)d);
+    if (xi < 1 || xi > 32 || xi > n)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "SparseRTT needs 1 <= xi <= min(n, 32) (got %d)", xi);
+    return RSK_OK;
+}
+
+rsk_status srtt_impl(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n_rows, int64_t k, int64_t lda,
+                     int64_t row0, int64_t n, int64_t d, int xi, uint64_t seed, void* Y, rsk_dtype y_dtype,
+                     int64_t ldy, cudaStream_t stream);
 
 rsk_status launch_draw(rsk_handle* h, int64_t n, int d, uint64_t seed, int32_t* rows, int64_t* rows64,
                        cudaStream_t stream) {
@@ -570,9 +689,59 @@ rsk_status rsk_srtt_draw(rsk_handle* h, int64_t n, int64_t d, uint64_t seed, int
 
 rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
                           int64_t d, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream) {
+    return rsk_srtt_apply_rows(h, A, a_dtype, n, k, lda, 0, n, d, seed, Y, y_dtype, ldy, stream);
+}
+
+rsk_status rsk_srtt_apply_rows(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n_rows, int64_t k,
+                               int64_t lda, int64_t row0, int64_t n, int64_t d, uint64_t seed, void* Y,
+                               rsk_dtype y_dtype, int64_t ldy, cudaStream_t stream) {
     if (!h) return RSK_ERR_INVALID_ARG;
-    rsk_status st = check_srtt(h, n, d);
+    return srtt_impl(h, A, a_dtype, n_rows, k, lda, row0, n, d, 0, seed, Y, y_dtype, ldy, stream);
+}
+
+int32_t rsk_sparse_rtt_default_xi(int64_t d) {
+    if (d < 1) return 0;
+    const int xi = int(ceil(1.5 * log(double(d)) - 1e-12));
+    return xi < 1 ? 1 : (xi > 32 ? 32 : xi);
+}
+
+rsk_status rsk_sparse_rtt_draw(rsk_handle* h, int64_t n, int64_t d, int32_t xi, uint64_t seed, int32_t* positions,
+                               uint32_t* sign_bits, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (xi == 0) xi = rsk_sparse_rtt_default_xi(d);
+    rsk_status st = check_sparse_rtt(h, n, d, xi);
     if (st != RSK_OK) return st;
+    if (!positions && !sign_bits) return RSK_OK;
+    st = rsk::ensure_workspace(h, size_t(d) * xi * 4 + 256, stream);
+    if (st != RSK_OK) return st;
+    k_sparsecol_draw<<<unsigned((d + 127) / 128), 128, 0, stream>>>(n, int(d), xi, seed, int(d),
+                                                                    static_cast<uint32_t*>(h->ws), positions, sign_bits);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status rsk_sparse_rtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t lda,
+                                int64_t d, int32_t xi, uint64_t seed, void* Y, rsk_dtype y_dtype, int64_t ldy,
+                                cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (xi == 0) xi = rsk_sparse_rtt_default_xi(d);
+    rsk_status st = check_sparse_rtt(h, n, d, xi);
+    if (st != RSK_OK) return st;
+    return srtt_impl(h, A, a_dtype, n, k, lda, 0, n, d, xi, seed, Y, y_dtype, ldy, stream);
+}
+
+}  // extern "C"
+
+namespace {
+rsk_status srtt_impl(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n_rows, int64_t k, int64_t lda,
+                     int64_t row0, int64_t n, int64_t d, int xi, uint64_t seed, void* Y, rsk_dtype y_dtype,
+                     int64_t ldy, cudaStream_t stream) {
+    rsk_status st = xi ? RSK_OK : check_srtt(h, n, d);
+    if (st != RSK_OK) return st;
+    if (n_rows < 1 || row0 < 0 || row0 % kBlk != 0 || row0 + n_rows > n)
+        return rsk::fail(h, RSK_ERR_INVALID_ARG,
+                         "row block [%lld, %lld) must start at a multiple of %d and lie in [0, n = %lld)",
+                         (long long)row0, (long long)(row0 + n_rows), kBlk, (long long)n);
     if (!A || !Y) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null matrix pointer");
     if (a_dtype != RSK_F32 && a_dtype != RSK_BF16)
         return rsk::fail(h, RSK_ERR_UNSUPPORTED, "SRTT apply takes F32 or BF16 input");
@@ -584,10 +753,11 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     SrttArgs args;
     args.A = A;
     args.lda = lda;
-    args.n = n;
+    args.n = n_rows;
     args.k = k;
     args.d = int(d);
-    args.nblocks = int((n + kBlk - 1) / kBlk);
+    args.nblocks = int((n_rows + kBlk - 1) / kBlk);
+    args.blk0 = int(row0 / kBlk);
     args.nslices = int((k + kCols - 1) / kCols);
     // bands: R = num_sms / gcd(nslices, num_sms) makes nslices * R a multiple of the SM count
     int gg = args.nslices, hh = h->num_sms;
@@ -606,8 +776,11 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     // gather slots: kThreads x QPT, QPT the power of two launch_srtt picks for d
     const int qpt_need = (int(d) + kThreads - 1) / kThreads;
     const int nslots = kThreads * (qpt_need <= 1 ? 1 : qpt_need <= 2 ? 2 : qpt_need <= 4 ? 4 : 8);
+    args.xi = xi;
+    args.nslots = nslots;
     st = rsk::ensure_workspace(h, rsk::Carver::round(part_bytes) + rsk::Carver::round(size_t(d) * 4) +
-                                      rsk::Carver::round(size_t(ndw) * 4) + rsk::Carver::round(size_t(nslots) * 4) + 512,
+                                      rsk::Carver::round(size_t(ndw) * 4) + rsk::Carver::round(size_t(nslots) * 4) +
+                                      rsk::Carver::round(size_t(nslots) * size_t(xi) * 4) + 768,
                                stream);
     if (st != RSK_OK) return st;
     rsk::Carver cv(h->ws);
@@ -615,27 +788,36 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     args.partials = cv.take<float>(size_t(args.nitems) * args.pstride);
     uint32_t* dbits = cv.take<uint32_t>(size_t(ndw));
     int32_t* slot_q = cv.take<int32_t>(size_t(nslots));
-    k_srtt_dbits_t<<<unsigned(args.nblocks), 64, 0, stream>>>(args.nblocks, seed, dbits);
+    uint32_t* spos = cv.take<uint32_t>(size_t(nslots) * size_t(xi));
+    k_srtt_dbits_t<<<unsigned(args.nblocks), 64, 0, stream>>>(args.nblocks, seed, int64_t(args.blk0), dbits);
     args.dbits = dbits;
     args.prow = prow;
-    st = launch_draw(h, n, int(d), seed, prow, nullptr, stream);
-    if (st != RSK_OK) return st;
-    if (d <= 8 * kThreads) {
-        k_srtt_deal<<<1, 1024, 0, stream>>>(prow, int(d), nslots, slot_q);
+    args.spos = spos;
+    if (xi) {
+        // SparseRTT: xi SparseCol positions per output row; slot s is output row s
+        k_sparsecol_draw<<<unsigned((d + 127) / 128), 128, 0, stream>>>(n, int(d), xi, seed, nslots, spos, nullptr,
+                                                                        nullptr);
         RSK_LAUNCH_CHECK(h);
+    } else {
+        st = launch_draw(h, n, int(d), seed, prow, nullptr, stream);
+        if (st != RSK_OK) return st;
+        if (d <= 8 * kThreads) {
+            k_srtt_deal<<<1, 1024, 0, stream>>>(prow, int(d), nslots, slot_q);
+            RSK_LAUNCH_CHECK(h);
+        }
     }
     args.slot_q = slot_q;
 
     CUtensorMap map;
     memset(&map, 0, sizeof(map));
     const CUtensorMapDataType tdt = a_dtype == RSK_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    if (tma) tma = rsk::encode_2d(h, &map, tdt, A, uint64_t(k), uint64_t(n), uint64_t(lda) * es, kCols, kBoxRows);
+    if (tma) tma = rsk::encode_2d(h, &map, tdt, A, uint64_t(k), uint64_t(n_rows), uint64_t(lda) * es, kCols, kBoxRows);
     st = a_dtype == RSK_F32 ? launch_srtt<float>(h, map, args, tma, stream)
                             : launch_srtt<__nv_bfloat16>(h, map, args, tma, stream);
     if (st != RSK_OK) return st;
 
     const int64_t total = d * k;
-    const double scale = 1.0 / sqrt(double(d));
+    const double scale = 1.0 / sqrt(double(d) * double(xi ? xi : 1));
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_SRTT_REDUCE);
     if (y_dtype == RSK_F64)
         k_reduce_srtt<double><<<unsigned((total + 255) / 256), 256, 0, stream>>>(
@@ -648,4 +830,5 @@ rsk_status rsk_srtt_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64
     return RSK_OK;
 }
 
-}  // extern "C"
+}  // namespace
+

@@ -49,7 +49,7 @@ def test_argument_counts_match_header(lib):
 
 
 def test_host_only_calls(lib):
-    assert lib.rsk_version() == 100
+    assert lib.rsk_version() == 200
     c, m, p = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     args = (ctypes.byref(c), ctypes.byref(m), ctypes.byref(p))
     assert lib.rsk_sparse_sign_index_dims(20000, 400, 8, *args) == 0
@@ -62,3 +62,18 @@ def test_host_only_calls(lib):
     assert lib.rsk_sparse_sign_index_dims(100, 64, 33, *args) == 1
     assert lib.rsk_sparse_sign_apply(None, None, 0, 10, 1, 1, 4, 2, 0, None, 0, 1, None) == 1
     assert lib.rsk_destroy(None) == 1
+    assert lib.rsk_set_wait_limit(None, 1) == 1
+
+
+def test_noalloc_rejects_invalid_sizes_before_any_device_work(lib):
+    # every argument is validated before the fixed scratch array is sized or the device is touched:
+    # d that does not fit in 32 bits, zeta > d, d > 8192, an unknown dtype and lda < k all return
+    # RSK_ERR_INVALID_ARG (never a division by zero in the sizing, never RSK_ERR_UNSUPPORTED)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks come first
+    call = lib.rsk_sparse_sign_apply_noalloc
+    assert call(fake, 2, 1 << 20, 256, 256, (1 << 32) - 3, 8, 0, fake, 1, 256, None) == 1
+    assert call(fake, 2, 1 << 20, 256, 256, 4, 8, 0, fake, 1, 256, None) == 1
+    assert call(fake, 2, 1 << 20, 256, 256, 9000, 8, 0, fake, 1, 256, None) == 1
+    assert call(fake, 7, 1 << 20, 256, 256, 2048, 8, 0, fake, 1, 256, None) == 1
+    assert call(fake, 2, 1 << 20, 256, 100, 2048, 8, 0, fake, 1, 256, None) == 1
+    assert call(None, 2, 1 << 20, 256, 256, 2048, 8, 0, fake, 1, 256, None) == 1
