@@ -352,6 +352,59 @@ rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const 
                                             const rsk_lsq_opts* opts, rsk_lsq_info* infos, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Dense steps of the low-rank algorithms (Algs. 1, 2, 4, 5 name them svd_econ, qr_econ / orth,
+ * chol): FP32, column-major (column c of X at X + c * ldx), device pointers, asynchronous.
+ * ------------------------------------------------------------------------------------------- */
+/* Thin SVD A = U diag(s) V^T of A (m x q, m >= q) by one-sided block Jacobi (Hestenes): plane
+ * rotations of column pairs until no pair has |a_i . a_j| > 2 sqrt(m) u_32 ||a_i|| ||a_j|| (at most 40
+ * sweeps).  U m x q (ldu >= m), s[q] descending, V q x q (ldv >= q; may be NULL).  A is not
+ * modified.  Limits: q <= 1024, m <= 4096 (RSK_ERR_UNSUPPORTED beyond). */
+rsk_status rsk_svd_econ(rsk_handle* h, const float* A, int64_t m, int64_t q, int64_t lda, float* U, int64_t ldu,
+                        float* s, float* V, int64_t ldv, cudaStream_t stream);
+/* Thin QR X = Q R of X (m x q, m >= q) by shifted Cholesky QR3 (one round of Cholesky QR on X^T X +
+ * s I with s = 11 (m q + q (q + 1)) u_32 ||X||_F^2, then two plain rounds): Q m x q (ldq >= m) with
+ * orthonormal columns, R q x q upper triangular (leading dimension q; may be NULL).  Limits: q <= 330.
+ * A Cholesky pivot that is not positive is recorded in the device status word (rsk_sync_status). */
+rsk_status rsk_qr_econ(rsk_handle* h, const float* X, int64_t m, int64_t q, int64_t ldx, float* Q, int64_t ldq,
+                       float* R, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Randomized Nystrom approximation of a psd matrix (Alg. 2, Sec. 2.2) with a structured test matrix:
+ * Y = A Omega; nu = sqrt(n) eps ||Y||; Y_nu = Y + nu Omega; C = chol(Omega^T Y_nu);
+ * B = Y_nu C^{-1}; [U, Sigma, ~] = svd(B); Lambda = max(0, Sigma^2 - nu I), truncated to `rank`.
+ * Omega = S^T with S the k x n SparseStack (kind = 1, needs k % zeta == 0) or SparseUniform
+ * (kind = 0) sketch of this library (zeta nonzeros per row of Omega, drawn from `seed` exactly as
+ * rsk_sparse_stack_generate / rsk_sparse_sign_generate).  Readings: eps = 2^-24 (FP32 arithmetic)
+ * and ||Y|| the Frobenius norm (never smaller than the spectral norm).
+ * A: device FP32 n x n, symmetric positive semidefinite, row-major (lda >= n); only S A is formed,
+ * which the symmetry makes equal to Y^T (one pass over A).  U: device FP32 n x rank column-major
+ * (ldu >= n), orthonormal columns.  lambda: device FP32[rank], descending.  A ~ U diag(lambda) U^T.
+ * Limits: 1 <= rank <= k <= min(n, 330).  A failed Cholesky (A not psd) is recorded in the device
+ * status word (rsk_sync_status returns RSK_ERR_INTERNAL).  Asynchronous; allocates its buffers
+ * stream-ordered on `stream`. */
+rsk_status rsk_nystrom_psd(rsk_handle* h, const float* A, int64_t n, int64_t lda, int32_t k, int32_t rank, int32_t zeta,
+                           uint64_t seed, int32_t kind, float* U, int64_t ldu, float* lambda, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Generalized Nystrom approximation of a general A (Algs. 4 and 5, Sec. 2.4) with structured test
+ * matrices Omega (d x k) and Psi (n x p), k <= p (the paper recommends p = ceil(1.5 k)):
+ * Y = A Omega and X = A^T Psi, one pass over A each (the right and the left sparse sketch).
+ *   form 0 (Alg. 4, outer-product form): [U, Sigma, V] = svd(X^T Omega); r = #{sigma_i > 5 eps sigma_1};
+ *          F = Y V_r Sigma_r^{-1} (out1, n x k), G = X U_r (out2, d x k); A ~ F G^T (columns >= r zero).
+ *   form 1 (Alg. 5, SVD form): Q = qr(Y), [P, T] = qr(X), [U1, S1, V1] = svd(Psi^T Q),
+ *          C = V1_r S1_r^{-1} U1_r^T T^T, [Uh, Sigma, Vh] = svd(C); U = Q Uh (out1, n x k),
+ *          sigma (k, descending), V = P Vh (out2, d x k); A ~ U diag(sigma) V^T.
+ * Omega = S^T for the k x d sketch S of `seed`, Psi = S'^T for the p x n sketch S' of seed + 1, both of
+ * the given kind (0 SparseUniform, 1 SparseStack: k and p multiples of zeta).  eps = 2^-24.
+ * A: device FP32 n x d row-major (lda >= d).  out1, out2: device FP32 column-major (ld1 >= n,
+ * ld2 >= d).  rank: device int32, the numerical rank r.  The thin QRs are Cholesky QR2 with the Gram
+ * accumulated in FP64 (Y and X must have full numerical rank, kappa up to ~1e7).  Limits:
+ * 1 <= k <= p <= min(n, d), k <= 512, p <= 1024.  Asynchronous; allocates stream-ordered. */
+rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, int32_t k, int32_t p,
+                           int32_t zeta, uint64_t seed, int32_t kind, int32_t form, float* out1, int64_t ld1,
+                           float* sigma, float* out2, int64_t ld2, int32_t* rank, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
  * a9: randomized SVD with a sparse sign test matrix (Alg. 1, Sec. 2.1) and power_iters subspace
  * iterations (re-orthonormalising after every product; Alg. 1 itself has none).
  * A: device FP32 m x n row-major (lda >= n).  Omega (n x r) has zeta nonzeros +-zeta^{-1/2} per row,

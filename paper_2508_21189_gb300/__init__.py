@@ -373,6 +373,85 @@ def rsk_lstsq_sketch_precond_batched(As, bs, ds=None, zeta=8, seed=0, sketch_dty
     return xs, out
 
 
+def _colmajor(X, name):
+    """A CUDA FP32 matrix viewed column-major: X must be the transpose of a row-major tensor
+    (stride (1, ld)), i.e. X.t() contiguous."""
+    if not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2 or X.stride(0) != 1 or X.stride(1) < X.shape[0]:
+        raise ValueError(f"{name} must be a column-major CUDA float32 matrix (stride (1, ld))")
+    return X
+
+
+def rsk_svd_econ(A, stream=None):
+    """Thin SVD of a column-major CUDA FP32 matrix A (m x q, m >= q): returns (U, s, V), U and V
+    column-major (A = U diag(s) V^T)."""
+    _colmajor(A, "A")
+    m, q = A.shape
+    U = torch.empty(q, m, device=A.device).t()
+    V = torch.empty(q, q, device=A.device).t()
+    s = torch.empty(q, device=A.device)
+    h = handle(A.device)
+    _check(load().rsk_svd_econ(h, A.data_ptr(), m, q, A.stride(1), U.data_ptr(), U.stride(1), s.data_ptr(),
+                               V.data_ptr(), V.stride(1), _stream(stream)), h)
+    return U, s, V
+
+
+def rsk_qr_econ(X, stream=None):
+    """Thin QR of a column-major CUDA FP32 matrix X (m x q): returns (Q column-major, R upper q x q)."""
+    _colmajor(X, "X")
+    m, q = X.shape
+    Q = torch.empty(q, m, device=X.device).t()
+    R = torch.empty(q, q, device=X.device).t()
+    h = handle(X.device)
+    _check(load().rsk_qr_econ(h, X.data_ptr(), m, q, X.stride(1), Q.data_ptr(), Q.stride(1), R.data_ptr(),
+                              _stream(stream)), h)
+    return Q, R
+
+
+def rsk_nystrom_psd(A, k, rank=None, zeta=4, seed=0, kind="stack", stream=None):
+    """Nystrom approximation of a psd CUDA FP32 matrix A (n x n, row-major): (U [n, rank] column-major,
+    lambda [rank]) with A ~ U diag(lambda) U^T; kind "stack" (SparseStack) or "uniform"."""
+    _matrix(A, "A")
+    if A.dtype != torch.float32 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square float32 matrix")
+    n = A.shape[0]
+    rank = k if rank is None else rank
+    U = torch.empty(rank, n, device=A.device).t()
+    lam = torch.empty(rank, device=A.device)
+    h = handle(A.device)
+    _check(load().rsk_nystrom_psd(h, A.data_ptr(), n, A.stride(0), k, rank, zeta, seed,
+                                  {"uniform": 0, "stack": 1}[kind], U.data_ptr(), U.stride(1), lam.data_ptr(),
+                                  _stream(stream)), h)
+    return U, lam
+
+
+def rsk_gen_nystrom(A, k, p=None, zeta=4, seed=0, kind="stack", form="svd", stream=None):
+    """Generalized Nystrom approximation of a CUDA FP32 matrix A (n x d, row-major).
+    form "outer" (Alg. 4): returns (F [n, k], G [d, k], r) with A ~ F G^T;
+    form "svd" (Alg. 5): returns (U [n, k], sigma [k], V [d, k], r) with A ~ U diag(sigma) V^T.
+    Matrices are column-major; r is the numerical rank.  p defaults to ceil(1.5 k) (rounded up to a
+    multiple of zeta for SparseStack)."""
+    _matrix(A, "A")
+    if A.dtype != torch.float32:
+        raise TypeError("A must be float32")
+    n, d = A.shape
+    if p is None:
+        p = -(-3 * k // 2)
+        if kind == "stack":
+            p = -(-p // zeta) * zeta
+    out1 = torch.empty(k, n, device=A.device).t()
+    out2 = torch.empty(k, d, device=A.device).t()
+    sig = torch.empty(k, device=A.device)
+    r = torch.zeros(1, dtype=torch.int32, device=A.device)
+    h = handle(A.device)
+    fm = {"outer": 0, "svd": 1}[form]
+    _check(load().rsk_gen_nystrom(h, A.data_ptr(), n, d, A.stride(0), k, p, zeta, seed, {"uniform": 0, "stack": 1}[kind],
+                                  fm, out1.data_ptr(), out1.stride(1), sig.data_ptr(), out2.data_ptr(), out2.stride(1),
+                                  r.data_ptr(), _stream(stream)), h)
+    if fm == 0:
+        return out1, out2, int(r.item())
+    return out1, sig, out2, int(r.item())
+
+
 def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
     """Randomized SVD of a CUDA FP32 tensor A (m x n): returns (U [m, r] FP32, s [r] FP64, Vt [r, n] FP32)."""
     _matrix(A, "A")

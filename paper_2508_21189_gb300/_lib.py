@@ -48,6 +48,11 @@ SIGNATURES = {
     "rsk_split_pairs": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_p],
     "rsk_lstsq_sketch_precond": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p],
     "rsk_lstsq_sketch_precond_batched": [c_p, c_i32, c_p, c_p, c_p, c_p],
+    "rsk_svd_econ": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_p, c_p, c_i64, c_p],
+    "rsk_qr_econ": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_p, c_p],
+    "rsk_nystrom_psd": [c_p, c_p, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_i32, c_p, c_i64, c_p, c_p],
+    "rsk_gen_nystrom": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_i32, c_i32, c_p, c_i64, c_p, c_p,
+                        c_i64, c_p, c_p],
     "rsk_rsvd": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_p, c_p, c_p, c_p],
 }
 

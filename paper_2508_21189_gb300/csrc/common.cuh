@@ -97,6 +97,17 @@ rsk_status sketch_apply_scratch(rsk_handle* h, const void* A, rsk_dtype a_dt, in
 
 rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, uint32_t stream_id,
                            int32_t* rows, uint32_t* signs, cudaStream_t stream);
+// kind 0 = SparseUniform (Philox stream 0), 1 = SparseStack (stream 4): rows/signs of the n columns of
+// the d x n sketch, and S * A (the workspace of rsk_sparse_sign_apply: uses the handle's workspace).
+rsk_status sketch_generate_kind(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, int kind, int32_t* rows,
+                                uint32_t* signs, cudaStream_t stream);
+// Right sketch Y = A Omega = A S^T for A n x dc row-major FP32 and S the k x dc sketch of the kind: Y is
+// n x k column-major (ldy >= n).  Uses the handle's workspace for the inverted index of S.
+rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n, int64_t dc, int64_t lda, int64_t k,
+                              int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream);
+rsk_status sketch_apply_kind(rsk_handle* h, int kind, const void* A, rsk_dtype a_dt, int64_t n, int64_t k,
+                             int64_t lda, int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
+                             cudaStream_t stream);
 size_t sketch_index_bytes(int64_t n, int64_t d, int zeta);
 rsk_status sketch_build_index(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, void* index_mem,
                               cudaStream_t stream);
@@ -196,6 +207,36 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Bounded software grid barrier for persistent kernels whose CTAs are all resident (cooperative
+// launch).  count / gen are two zero-initialised words; returns false (and records
+// RSK_DEV_TIMEOUT) if the other CTAs did not arrive within `limit` polls.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, unsigned int nblocks,
+                                             unsigned int* status, uint32_t limit) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd(const_cast<unsigned int*>(gen), 1u);
+        } else {
+            uint32_t it = 0;
+            while (*gen == g) {
+                if (++it > limit) {
+                    atomicOr(status, RSK_DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (it > 64) __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
 }
 
 }  // namespace rskd

@@ -1,0 +1,744 @@
+// Small dense linear algebra for the low-rank consumers of the sketches: FP32, column-major.
+//
+// Kernels
+//   k_gram          X^T Y over a chunk of rows: 64 x 64 output tile per CTA, 4 x 4 per thread, the rows
+//                   staged 32 at a time; per-chunk partials summed in chunk order by k_gram_reduce.
+//   k_matmul_ts     C = X M for tall X: 128 x 64 output tile per CTA, K in steps of 16.
+//   k_cholesky      one CTA: right-looking Cholesky on the packed upper triangle in shared memory.
+//   k_trinv         one CTA per column j of R^{-1}: column-oriented back substitution.
+//   k_jacobi        one-sided block Jacobi (Hestenes) on a cooperative grid: the q columns are dealt
+//                   into nb = 2G blocks; in each of the nb - 1 rounds of a sweep CTA g takes one pair
+//                   of blocks (round-robin), copies their columns (and V's) into shared memory,
+//                   orthogonalises every pair of them with plane rotations (one warp per pair, the
+//                   pairs of a local round disjoint), and writes them back; a bounded grid barrier
+//                   separates the rounds.  Sweeps stop when one makes no rotation.
+//   k_svd_post      singular values = column norms, sorted descending; U = X / s, V permuted alike.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "dense.cuh"
+
+namespace {
+
+constexpr float kU32 = 5.9604645e-8f;  // 2^-24
+
+// ------------------------------------------------------------------------------------------
+// Gram matrix.
+// ------------------------------------------------------------------------------------------
+constexpr int kGT = 64;      // output tile
+constexpr int kGRows = 32;   // rows staged per step
+constexpr int kGChunk = 2048;
+constexpr int kGPitch = kGT + 4;
+
+template <typename Acc>
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ X, int64_t m, int p, int64_t ldx,
+                                             const float* __restrict__ Y, int q, int64_t ldy, bool sym, int ntq,
+                                             Acc* __restrict__ part, int64_t pstride, int pp) {
+    __shared__ __align__(16) float Xs[kGRows][kGPitch];
+    __shared__ __align__(16) float Ys[kGRows][kGPitch];
+    const int tile = blockIdx.x;
+    const int tp = tile / ntq, tq = tile - (tile / ntq) * ntq;
+    if (sym && tp > tq) return;
+    const int64_t r0 = int64_t(blockIdx.y) * kGChunk;
+    const int64_t r1 = min(m, r0 + kGChunk);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int p0 = tp * kGT, q0 = tq * kGT;
+    Acc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
+    for (int64_t rb = r0; rb < r1; rb += kGRows) {
+        // coalesced loads along rows: element e of the thread is (row = tid % 32, col = tid / 32 + 8 e)
+        const int rr = tid & 31;
+        const int64_t row = rb + rr;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int c = (tid >> 5) + 8 * e;
+            Xs[rr][c] = (row < r1 && p0 + c < p) ? X[int64_t(p0 + c) * ldx + row] : 0.f;
+            Ys[rr][c] = (row < r1 && q0 + c < q) ? Y[int64_t(q0 + c) * ldy + row] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < kGRows; ++r) {
+            const float4 a = *reinterpret_cast<const float4*>(&Xs[r][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Ys[r][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(Acc(av[i]), Acc(bv[j]), acc[i][j]);
+        }
+        __syncthreads();
+    }
+    Acc* out = part + int64_t(blockIdx.y) * pstride;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gi = p0 + ty * 4 + i, gj = q0 + tx * 4 + j;
+            out[int64_t(gj) * pp + gi] = acc[i][j];
+        }
+}
+
+// G[i, j] = sum over chunks (in order) of part[chunk][j * pp + i]; the symmetric case mirrors the
+// computed triangle (tiles with tp <= tq).
+template <typename Acc>
+__global__ void k_gram_reduce(const Acc* __restrict__ part, int64_t pstride, int nchunks, int p, int q, int pp,
+                              bool sym, Acc* __restrict__ G, int64_t ldg) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= int64_t(p) * q) return;
+    const int j = int(idx / p), i = int(idx - int64_t(j) * p);
+    int si = i, sj = j;
+    if (sym && (i / kGT) > (j / kGT)) {
+        si = j;
+        sj = i;
+    }
+    Acc s = Acc(0);
+    for (int c = 0; c < nchunks; ++c) s += part[int64_t(c) * pstride + int64_t(sj) * pp + si];
+    G[int64_t(j) * ldg + i] = s;
+}
+
+// ------------------------------------------------------------------------------------------
+// Tall-by-small product.
+// ------------------------------------------------------------------------------------------
+constexpr int kMR = 128, kMC = 64, kMK = 16;
+
+__global__ void __launch_bounds__(256) k_matmul_ts(const float* __restrict__ X, int64_t m, int p, int64_t ldx,
+                                                  const float* __restrict__ M, int q, int64_t ldm,
+                                                  float* __restrict__ C, int64_t ldc) {
+    __shared__ __align__(16) float Xs[kMK][kMR];
+    __shared__ __align__(16) float Ms[kMK][kMC];
+    const int64_t r0 = int64_t(blockIdx.x) * kMR;
+    const int c0 = blockIdx.y * kMC;
+    const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < p; k0 += kMK) {
+        // X tile: 16 columns x 128 rows, rows contiguous in memory
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int lin = tid + 256 * e;
+            const int rr = lin & (kMR - 1), kk = lin >> 7;
+            const int64_t row = r0 + rr;
+            Xs[kk][rr] = (row < m && k0 + kk < p) ? X[int64_t(k0 + kk) * ldx + row] : 0.f;
+        }
+        // M tile: 16 rows x 64 columns, rows of a column contiguous
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int lin = tid + 256 * e;
+            const int kk = lin & (kMK - 1), cc = lin >> 4;
+            Ms[kk][cc] = (k0 + kk < p && c0 + cc < q) ? M[int64_t(c0 + cc) * ldm + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kMK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&Xs[kk][tr * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Xs[kk][tr * 8 + 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Ms[kk][tc * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int col = c0 + tc * 4 + j;
+        if (col >= q) continue;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t row = r0 + tr * 8 + i;
+            if (row < m) C[int64_t(col) * ldc + row] = acc[i][j];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Cholesky (packed upper triangle in shared memory) and triangular inverse.
+// ------------------------------------------------------------------------------------------
+constexpr int kCholMax = 330;
+__device__ __forceinline__ int pk(int i, int j, int q) { return i * q - (i * (i - 1)) / 2 + (j - i); }
+
+__global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, int q, int64_t ldg, float shift_coeff,
+                                                  float* __restrict__ R, int64_t ldr, unsigned int* status) {
+    extern __shared__ __align__(16) float U[];
+    __shared__ float piv_s, trace_s;
+    __shared__ int fail_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    // trace for the shift (the Frobenius norm squared of the factored matrix when G = X^T X)
+    if (tid == 0) {
+        float t = 0.f;
+        for (int i = 0; i < q; ++i) t += G[int64_t(i) * ldg + i];
+        trace_s = t;
+        fail_s = 0;
+    }
+    __syncthreads();
+    const float shift = shift_coeff * trace_s;
+    for (int i = warp; i < q; i += nw)
+        for (int j = i + lane; j < q; j += 32) U[pk(i, j, q)] = G[int64_t(j) * ldg + i] + (i == j ? shift : 0.f);
+    __syncthreads();
+    for (int j = 0; j < q; ++j) {
+        if (tid == 0) {
+            const float d = U[pk(j, j, q)];
+            if (!(d > 0.f) || !isfinite(d)) fail_s = 1;
+            piv_s = fail_s ? 1.f : sqrtf(d);
+            U[pk(j, j, q)] = piv_s;
+        }
+        __syncthreads();
+        if (fail_s) break;
+        const float rinv = 1.f / piv_s;
+        for (int k = j + 1 + tid; k < q; k += blockDim.x) U[pk(j, k, q)] *= rinv;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < q; i += nw) {
+            const float uji = U[pk(j, i, q)];
+            for (int k = i + lane; k < q; k += 32) U[pk(i, k, q)] -= uji * U[pk(j, k, q)];
+        }
+        __syncthreads();
+    }
+    if (fail_s) {
+        if (tid == 0) atomicOr(status, RSK_DEV_BOUNDS);
+        return;
+    }
+    for (int j = warp; j < q; j += nw)
+        for (int i = lane; i < q; i += 32) R[int64_t(j) * ldr + i] = i <= j ? U[pk(i, j, q)] : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_trinv(const float* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri) {
+    extern __shared__ float x[];
+    const int j = blockIdx.x, tid = threadIdx.x;
+    for (int i = tid; i < q; i += blockDim.x) x[i] = (i == j) ? 1.f : 0.f;
+    __syncthreads();
+    for (int i = j; i >= 0; --i) {
+        const float xi = x[i] / R[int64_t(i) * ldr + i];
+        __syncthreads();
+        if (tid == 0) x[i] = xi;
+        for (int k = tid; k < i; k += blockDim.x) x[k] -= R[int64_t(i) * ldr + k] * xi;
+        __syncthreads();
+    }
+    for (int i = tid; i < q; i += blockDim.x) Ri[int64_t(j) * ldr + i] = x[i];
+}
+
+// FP64 variant for the accurate orthonormalisation: R (q x q column-major, ldr) holds G on entry
+// (upper triangle read) and its upper Cholesky factor on exit (zeros below); the shift is
+// shift_coeff * trace(G).  One CTA; the matrix stays in L2 (read through ld.cg).
+__global__ void __launch_bounds__(1024) k_cholesky64(double* __restrict__ R, int q, int64_t ldr, double shift_coeff,
+                                                    unsigned int* status) {
+    __shared__ double piv_s, shift_s;
+    __shared__ int fail_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < q; ++i) t += R[int64_t(i) * ldr + i];
+        shift_s = shift_coeff * t;
+        fail_s = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < q; i += blockDim.x) R[int64_t(i) * ldr + i] += shift_s;
+    __syncthreads();
+    for (int j = 0; j < q; ++j) {
+        if (tid == 0) {
+            const double d = __ldcg(R + int64_t(j) * ldr + j);
+            if (!(d > 0.0) || !isfinite(d)) fail_s = 1;
+            piv_s = fail_s ? 1.0 : sqrt(d);
+            __stcg(R + int64_t(j) * ldr + j, piv_s);
+        }
+        __syncthreads();
+        if (fail_s) break;
+        const double rinv = 1.0 / piv_s;
+        for (int k = j + 1 + tid; k < q; k += blockDim.x) __stcg(R + int64_t(k) * ldr + j, __ldcg(R + int64_t(k) * ldr + j) * rinv);
+        __threadfence_block();
+        __syncthreads();
+        // trailing update of the upper triangle: R(i, k) -= R(j, i) R(j, k) for j < i <= k; warps take
+        // columns k, lanes rows i (contiguous in memory)
+        for (int k = j + 1 + warp; k < q; k += nw) {
+            const double rjk = __ldcg(R + int64_t(k) * ldr + j);
+            for (int i = j + 1 + lane; i <= k; i += 32)
+                __stcg(R + int64_t(k) * ldr + i, __ldcg(R + int64_t(k) * ldr + i) - __ldcg(R + int64_t(i) * ldr + j) * rjk);
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+    if (fail_s) {
+        if (tid == 0) atomicOr(status, RSK_DEV_BOUNDS);
+        return;
+    }
+    for (int k = warp; k < q; k += nw)
+        for (int i = k + 1 + lane; i < q; i += 32) R[int64_t(k) * ldr + i] = 0.0;
+}
+
+// Ri (float, q x q, ldr) = R^{-1} for the FP64 upper triangular R: back substitution in FP64, one CTA
+// per column, the result rounded to FP32 for the FP32 product X R^{-1}.
+__global__ void __launch_bounds__(256) k_trinv64(const double* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri,
+                                                double* __restrict__ Ri64) {
+    extern __shared__ double x64[];
+    const int j = blockIdx.x, tid = threadIdx.x;
+    for (int i = tid; i < q; i += blockDim.x) x64[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int i = j; i >= 0; --i) {
+        const double xi = x64[i] / R[int64_t(i) * ldr + i];
+        __syncthreads();
+        if (tid == 0) x64[i] = xi;
+        for (int k = tid; k < i; k += blockDim.x) x64[k] -= R[int64_t(i) * ldr + k] * xi;
+        __syncthreads();
+    }
+    for (int i = tid; i < q; i += blockDim.x) {
+        Ri[int64_t(j) * ldr + i] = float(x64[i]);
+        if (Ri64) Ri64[int64_t(j) * ldr + i] = x64[i];
+    }
+}
+
+// C (FP64, q x q) = A (FP64 upper, q x q) * B (FP64 upper, q x q): product of two triangular factors.
+__global__ void k_trmm64(const double* __restrict__ A, const double* __restrict__ B, int q, double* __restrict__ C) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= int64_t(q) * q) return;
+    const int j = int(idx / q), i = int(idx - int64_t(j) * q);
+    double t = 0.0;
+    for (int l = i; l <= j; ++l) t += A[int64_t(l) * q + i] * B[int64_t(j) * q + l];
+    C[idx] = i <= j ? t : 0.0;
+}
+
+__global__ void k_to_f32(const double* __restrict__ X, int64_t count, float* __restrict__ Y) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < count) Y[i] = float(X[i]);
+}
+
+// ------------------------------------------------------------------------------------------
+// One-sided block Jacobi SVD.
+// ------------------------------------------------------------------------------------------
+struct JacobiArgs {
+    float* X;
+    int64_t ldx;
+    int m, q, nb, w;   // w = columns per block (the last ones may hold fewer)
+    float* V;
+    int64_t ldv;
+    float tol;
+    int max_sweeps;
+    unsigned int* flags;   // one word per sweep: set when the sweep rotated
+    unsigned int* bar;     // grid barrier (2 words)
+    unsigned int* status;
+    uint32_t limit;
+};
+
+// Block held by position p of the round-robin table in round r (position 0 fixed).
+__device__ __forceinline__ int rr_block(int pos, int r, int n) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (n - 1); }
+
+__global__ void __launch_bounds__(1024) k_jacobi(const JacobiArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int mv = a.V ? a.q : 0;          // rows of V's columns
+    const int cl = a.m + mv;               // floats per local column (X part, then V part)
+    __shared__ int cols_s[256];            // global column of each local column
+    __shared__ int nloc_s;
+    __shared__ int rot_s;
+    for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+        for (int r = 0; r < a.nb - 1; ++r) {
+            const int b0 = rr_block(g, r, a.nb), b1 = rr_block(a.nb - 1 - g, r, a.nb);
+            if (tid == 0) {
+                int n = 0;
+                for (int bb = 0; bb < 2; ++bb) {
+                    const int b = bb ? b1 : b0;
+                    const int c0 = b * a.w, c1 = min(a.q, c0 + a.w);
+                    for (int c = c0; c < c1; ++c) cols_s[n++] = c;
+                }
+                nloc_s = n;
+                rot_s = 0;
+            }
+            __syncthreads();
+            const int L = nloc_s;
+            // columns another CTA rotated in the previous round: read through L2 (ld.cg), never from
+            // a line this SM's L1 may still hold from an earlier round
+            for (int l = warp; l < L; l += nw) {
+                const int c = cols_s[l];
+                for (int i = lane; i < a.m; i += 32) sm[l * cl + i] = __ldcg(a.X + int64_t(c) * a.ldx + i);
+                for (int i = lane; i < mv; i += 32) sm[l * cl + a.m + i] = __ldcg(a.V + int64_t(c) * a.ldv + i);
+            }
+            __syncthreads();
+            // one local sweep over every pair of the L columns (round-robin on Le = L rounded up)
+            const int Le = L + (L & 1);
+            for (int lr = 0; lr < Le - 1; ++lr) {
+                for (int pi = warp; pi < Le / 2; pi += nw) {
+                    const int pa = rr_block(pi, lr, Le), pb = rr_block(Le - 1 - pi, lr, Le);
+                    if (pa >= L || pb >= L) continue;
+                    float* ca = sm + pa * cl;
+                    float* cb = sm + pb * cl;
+                    float al = 0.f, be = 0.f, ga = 0.f;
+                    for (int i = lane; i < a.m; i += 32) {
+                        const float x = ca[i], y = cb[i];
+                        al = fmaf(x, x, al);
+                        be = fmaf(y, y, be);
+                        ga = fmaf(x, y, ga);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    }
+                    if (ga == 0.f || !(fabsf(ga) > a.tol * sqrtf(al) * sqrtf(be))) continue;
+                    const float zeta = (be - al) / (2.f * ga);
+                    const float t = fabsf(zeta) > 1e15f ? 0.5f / zeta
+                                                        : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    const float c = rsqrtf(1.f + t * t), s = c * t;
+                    for (int i = lane; i < cl; i += 32) {
+                        const float x = ca[i], y = cb[i];
+                        ca[i] = c * x - s * y;
+                        cb[i] = s * x + c * y;
+                    }
+                    if (lane == 0) rot_s = 1;
+                }
+                __syncthreads();
+            }
+            for (int l = warp; l < L; l += nw) {
+                const int c = cols_s[l];
+                for (int i = lane; i < a.m; i += 32) __stcg(a.X + int64_t(c) * a.ldx + i, sm[l * cl + i]);
+                for (int i = lane; i < mv; i += 32) __stcg(a.V + int64_t(c) * a.ldv + i, sm[l * cl + a.m + i]);
+            }
+            if (tid == 0 && rot_s) atomicOr(a.flags + sweep, 1u);
+            if (!rskd::grid_barrier(a.bar, a.bar + 1, gridDim.x, a.status, a.limit)) return;
+        }
+        if (*static_cast<volatile unsigned int*>(a.flags + sweep) == 0u) return;  // converged
+    }
+}
+
+__global__ void k_identity(float* __restrict__ V, int q, int64_t ldv) {
+    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= int64_t(q) * q) return;
+    const int j = int(idx / q), i = int(idx - int64_t(j) * q);
+    V[int64_t(j) * ldv + i] = i == j ? 1.f : 0.f;
+}
+
+// Column norms of X (one warp per column).
+__global__ void k_colnorms(const float* __restrict__ X, int m, int q, int64_t ldx, float* __restrict__ s) {
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= q) return;
+    float t = 0.f;
+    for (int i = lane; i < m; i += 32) t = fmaf(X[int64_t(c) * ldx + i], X[int64_t(c) * ldx + i], t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) s[c] = sqrtf(t);
+}
+
+// Rank of each column by descending norm (ties by index), one thread per column.
+__global__ void k_rank(const float* __restrict__ s, int q, int* __restrict__ rank) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= q) return;
+    const float v = s[c];
+    int r = 0;
+    for (int o = 0; o < q; ++o) r += (s[o] > v) || (s[o] == v && o < c);
+    rank[c] = r;
+}
+
+// out[:, rank[c]] = X[:, c] * (scale ? 1 / s[c] : 1) (0 where s[c] == 0); s_out[rank[c]] = s[c].
+__global__ void k_permute_cols(const float* __restrict__ X, int m, int q, int64_t ldx, const int* __restrict__ rank,
+                               const float* __restrict__ s, bool scale, float* __restrict__ out, int64_t ldo,
+                               float* __restrict__ s_out) {
+    const int c = blockIdx.y;
+    const int rc = rank[c];
+    const float f = scale ? (s[c] > 0.f ? 1.f / s[c] : 0.f) : 1.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        out[int64_t(rc) * ldo + i] = X[int64_t(c) * ldx + i] * f;
+    if (s_out && blockIdx.x == 0 && threadIdx.x == 0) s_out[rc] = s[c];
+}
+
+__global__ void k_copy_cols(const float* __restrict__ src, int64_t lds, int m, int q, float* __restrict__ dst,
+                            int64_t ldd) {
+    const int c = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        dst[int64_t(c) * ldd + i] = src[int64_t(c) * lds + i];
+}
+
+struct JacobiPlan {
+    int G, nb, w;
+    size_t smem;
+};
+JacobiPlan jacobi_plan(int64_t m, int q, bool with_v, int num_sms) {
+    JacobiPlan p;
+    p.G = 8;
+    for (;;) {
+        p.nb = 2 * p.G;
+        p.w = (q + p.nb - 1) / p.nb;
+        p.smem = size_t(2 * p.w) * size_t(m + (with_v ? q : 0)) * 4;
+        if ((p.smem <= 200 * 1024 && 2 * p.w <= 256) || p.G >= 64) break;
+        p.G *= 2;
+    }
+    // blocks of at least one column, and no more CTAs than can be resident
+    while (p.G > 1 && (p.nb > q || p.G > num_sms)) {
+        p.G /= 2;
+        p.nb = 2 * p.G;
+        p.w = (q + p.nb - 1) / p.nb;
+        p.smem = size_t(2 * p.w) * size_t(m + (with_v ? q : 0)) * 4;
+    }
+    return p;
+}
+
+constexpr int kMaxSweeps = 40;
+
+}  // namespace
+
+namespace rsk {
+namespace dense {
+
+size_t gram_scratch_bytes(int64_t m, int p, int q) {
+    const int64_t nch = (m + kGChunk - 1) / kGChunk;
+    const int64_t pp = (p + kGT - 1) / kGT * kGT, qq = (q + kGT - 1) / kGT * kGT;
+    return size_t(nch) * size_t(pp * qq) * 4 + 256;
+}
+
+template <typename Acc>
+rsk_status gram_t(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* Y, int q, int64_t ldy,
+                  Acc* G, int64_t ldg, void* scratch, cudaStream_t stream) {
+    if (m < 1 || p < 1 || q < 1) return fail(h, RSK_ERR_INVALID_ARG, "gram: empty operand");
+    const int nch = int((m + kGChunk - 1) / kGChunk);
+    const int ntp = (p + kGT - 1) / kGT, ntq = (q + kGT - 1) / kGT;
+    const int pp = ntp * kGT;
+    const int64_t pstride = int64_t(pp) * (int64_t(ntq) * kGT);
+    const bool sym = (X == Y) && (p == q) && (ldx == ldy);
+    Acc* part = static_cast<Acc*>(scratch);
+    k_gram<Acc><<<dim3(unsigned(ntp * ntq), unsigned(nch)), 256, 0, stream>>>(X, m, p, ldx, Y, q, ldy, sym, ntq, part,
+                                                                              pstride, pp);
+    RSK_LAUNCH_CHECK(h);
+    const int64_t tot = int64_t(p) * q;
+    k_gram_reduce<Acc><<<unsigned((tot + 255) / 256), 256, 0, stream>>>(part, pstride, nch, p, q, pp, sym, G, ldg);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status gram(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* Y, int q, int64_t ldy,
+                float* G, int64_t ldg, void* scratch, cudaStream_t stream) {
+    return gram_t<float>(h, X, m, p, ldx, Y, q, ldy, G, ldg, scratch, stream);
+}
+
+rsk_status gram64(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* Y, int q, int64_t ldy,
+                  double* G, int64_t ldg, void* scratch, cudaStream_t stream) {
+    return gram_t<double>(h, X, m, p, ldx, Y, q, ldy, G, ldg, scratch, stream);
+}
+
+rsk_status matmul_ts(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* M, int q,
+                     int64_t ldm, float* C, int64_t ldc, cudaStream_t stream) {
+    if (m < 1 || p < 1 || q < 1) return fail(h, RSK_ERR_INVALID_ARG, "matmul: empty operand");
+    const dim3 grid(unsigned((m + kMR - 1) / kMR), unsigned((q + kMC - 1) / kMC));
+    k_matmul_ts<<<grid, 256, 0, stream>>>(X, m, p, ldx, M, q, ldm, C, ldc);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status cholesky(rsk_handle* h, const float* G, int q, int64_t ldg, float shift_coeff, float* R, int64_t ldr,
+                    cudaStream_t stream) {
+    if (q < 1 || q > kCholMax) return fail(h, RSK_ERR_UNSUPPORTED, "cholesky supports 1 <= q <= %d (got %d)", kCholMax, q);
+    const int smem = int((size_t(q) * (q + 1) / 2) * 4);
+    RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_cholesky<<<1, 1024, smem, stream>>>(G, q, ldg, shift_coeff, R, ldr, h->dev_status);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status trinv(rsk_handle* h, const float* R, int q, int64_t ldr, float* Ri, cudaStream_t stream) {
+    k_trinv<<<unsigned(q), 256, size_t(q) * 4, stream>>>(R, q, ldr, Ri);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+size_t svd_scratch_bytes(int64_t m, int q) {
+    return Carver::round(size_t(m) * q * 4) + Carver::round(size_t(q) * q * 4) + 2 * Carver::round(size_t(q) * 8) +
+           Carver::round(size_t(kMaxSweeps + 2) * 4) + 1024;
+}
+
+rsk_status svd(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* s, float* V, int64_t ldv, void* scratch,
+               cudaStream_t stream) {
+    if (q < 1 || q > 1024 || m < q || m > 4096)
+        return fail(h, RSK_ERR_UNSUPPORTED, "svd supports 1 <= q <= 1024, q <= m <= 4096 (got m=%lld, q=%d)",
+                    (long long)m, q);
+    Carver cv(scratch);
+    float* Ut = cv.take<float>(size_t(m) * q);
+    float* Vt = cv.take<float>(size_t(q) * q);
+    float* sn = cv.take<float>(size_t(q));
+    float* vn = cv.take<float>(size_t(q));
+    int* rank = cv.take<int>(size_t(q));
+    unsigned int* words = cv.take<unsigned int>(size_t(kMaxSweeps + 2));
+    // V starts as the identity (held in Vt), then rotates with X
+    const bool with_v = V != nullptr;
+    if (with_v) {
+        k_identity<<<unsigned((int64_t(q) * q + 255) / 256), 256, 0, stream>>>(Vt, q, q);
+        RSK_LAUNCH_CHECK(h);
+    }
+    RSK_CUDA_TRY(h, cudaMemsetAsync(words, 0, size_t(kMaxSweeps + 2) * 4, stream));
+    if (q > 1) {
+        const JacobiPlan jp = jacobi_plan(m, q, with_v, h->num_sms);
+        if (jp.smem > 227 * 1024 || 2 * jp.w > 256)
+            return fail(h, RSK_ERR_UNSUPPORTED, "svd: %lld x %d needs too much shared memory", (long long)m, q);
+        JacobiArgs ja;
+        ja.X = X;
+        ja.ldx = ldx;
+        ja.m = int(m);
+        ja.q = q;
+        ja.nb = jp.nb;
+        ja.w = jp.w;
+        ja.V = with_v ? Vt : nullptr;
+        ja.ldv = q;
+        ja.tol = 2.f * sqrtf(float(m)) * kU32;
+        ja.max_sweeps = kMaxSweeps;
+        ja.flags = words;
+        ja.bar = words + kMaxSweeps;
+        ja.status = h->dev_status;
+        ja.limit = h->wait_limit;
+        RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jp.smem)));
+        int per_sm = 0;
+        RSK_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 1024, jp.smem));
+        if (per_sm * h->num_sms < jp.G) return fail(h, RSK_ERR_UNSUPPORTED, "svd: %d CTAs cannot be resident", jp.G);
+        void* args[] = {&ja};
+        RSK_CUDA_TRY(h, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_jacobi), dim3(jp.G), dim3(1024), args,
+                                                    jp.smem, stream));
+    }
+    k_colnorms<<<unsigned((q + 7) / 8), 256, 0, stream>>>(X, int(m), q, ldx, sn);
+    k_rank<<<unsigned((q + 255) / 256), 256, 0, stream>>>(sn, q, rank);
+    RSK_LAUNCH_CHECK(h);
+    const unsigned gx = unsigned(std::min<int64_t>(8, (m + 255) / 256));
+    k_permute_cols<<<dim3(gx, unsigned(q)), 256, 0, stream>>>(X, int(m), q, ldx, rank, sn, true, Ut, m, s);
+    k_copy_cols<<<dim3(gx, unsigned(q)), 256, 0, stream>>>(Ut, m, int(m), q, X, ldx);
+    RSK_LAUNCH_CHECK(h);
+    if (with_v) {
+        // V's columns drift from unit length by the rounding of many FP32 rotations (their mutual
+        // orthogonality holds to a few u); renormalise them while permuting
+        k_colnorms<<<unsigned((q + 7) / 8), 256, 0, stream>>>(Vt, q, q, q, vn);
+        const unsigned gv = unsigned(std::min(8, (q + 255) / 256));
+        k_permute_cols<<<dim3(gv, unsigned(q)), 256, 0, stream>>>(Vt, q, q, q, rank, vn, true, V, ldv, nullptr);
+        RSK_LAUNCH_CHECK(h);
+    }
+    return RSK_OK;
+}
+
+size_t orth_scratch_bytes(int64_t m, int q) {
+    return 2 * Carver::round(gram_scratch_bytes(m, q, q)) + 4 * Carver::round(size_t(q) * q * 4) +
+           4 * Carver::round(size_t(q) * q * 8) + Carver::round(size_t(m) * q * 4) + 1024;
+}
+
+rsk_status orth_accurate(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* R, void* scratch,
+                         cudaStream_t stream) {
+    if (q < 1 || q > 1024 || m < q)
+        return fail(h, RSK_ERR_UNSUPPORTED, "orth supports 1 <= q <= 1024, m >= q (got m=%lld, q=%d)", (long long)m, q);
+    Carver cv(scratch);
+    void* gs = cv.take<char>(2 * gram_scratch_bytes(m, q, q));
+    double* G = cv.take<double>(size_t(q) * q);
+    double* R64 = cv.take<double>(size_t(q) * q);
+    double* Racc = cv.take<double>(size_t(q) * q);
+    double* Rtmp = cv.take<double>(size_t(q) * q);
+    float* Ri = cv.take<float>(size_t(q) * q);
+    float* T = cv.take<float>(size_t(m) * q);
+    // Cholesky QR2 with the Gram in FP64 (exact products of the FP32 entries, FP64 sums): a relative
+    // shift of 8 q u_64 keeps the first factorisation defined for kappa(X) up to ~1e7; the second
+    // round restores orthogonality to O(u_32)
+    const double coeff[2] = {8.0 * q * 1.1102230246251565e-16, 0.0};
+    for (int round = 0; round < 2; ++round) {
+        rsk_status st = gram64(h, X, m, q, ldx, X, q, ldx, G, q, gs, stream);
+        if (st != RSK_OK) return st;
+        RSK_CUDA_TRY(h, cudaMemcpyAsync(R64, G, size_t(q) * q * 8, cudaMemcpyDeviceToDevice, stream));
+        k_cholesky64<<<1, 1024, 0, stream>>>(R64, q, q, coeff[round], h->dev_status);
+        k_trinv64<<<unsigned(q), 256, size_t(q) * 8, stream>>>(R64, q, q, Ri, nullptr);
+        RSK_LAUNCH_CHECK(h);
+        st = matmul_ts(h, X, m, q, ldx, Ri, q, q, T, m, stream);
+        if (st != RSK_OK) return st;
+        const unsigned gx = unsigned(std::min<int64_t>(64, (m + 255) / 256));
+        k_copy_cols<<<dim3(gx, unsigned(q)), 256, 0, stream>>>(T, m, int(m), q, X, ldx);
+        RSK_LAUNCH_CHECK(h);
+        if (R) {
+            if (round == 0) {
+                RSK_CUDA_TRY(h, cudaMemcpyAsync(Racc, R64, size_t(q) * q * 8, cudaMemcpyDeviceToDevice, stream));
+            } else {
+                k_trmm64<<<unsigned((int64_t(q) * q + 255) / 256), 256, 0, stream>>>(R64, Racc, q, Rtmp);
+                RSK_LAUNCH_CHECK(h);
+                RSK_CUDA_TRY(h, cudaMemcpyAsync(Racc, Rtmp, size_t(q) * q * 8, cudaMemcpyDeviceToDevice, stream));
+            }
+        }
+    }
+    if (R) {
+        k_to_f32<<<unsigned((int64_t(q) * q + 255) / 256), 256, 0, stream>>>(Racc, int64_t(q) * q, R);
+        RSK_LAUNCH_CHECK(h);
+    }
+    return RSK_OK;
+}
+
+rsk_status orth(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* R, void* scratch, cudaStream_t stream) {
+    if (q < 1 || q > kCholMax || m < q)
+        return fail(h, RSK_ERR_UNSUPPORTED, "orth supports 1 <= q <= %d, m >= q (got m=%lld, q=%d)", kCholMax,
+                    (long long)m, q);
+    Carver cv(scratch);
+    void* gs = cv.take<char>(gram_scratch_bytes(m, q, q));
+    float* G = cv.take<float>(size_t(q) * q);
+    float* Rk = cv.take<float>(size_t(q) * q);
+    float* Ri = cv.take<float>(size_t(q) * q);
+    float* Racc = cv.take<float>(size_t(q) * q);
+    float* T = cv.take<float>(size_t(m) * q);
+    // shifted round first (Fukaya et al.: s = 11 (m q + q (q + 1)) u ||X||_2^2, with ||X||_F^2 = trace(G) >= ||X||_2^2)
+    const float coeff[3] = {11.f * (float(m) * q + float(q) * (q + 1)) * kU32, 0.f, 0.f};
+    for (int round = 0; round < 3; ++round) {
+        rsk_status st = gram(h, X, m, q, ldx, X, q, ldx, G, q, gs, stream);
+        if (st == RSK_OK) st = cholesky(h, G, q, q, coeff[round], Rk, q, stream);
+        if (st == RSK_OK) st = trinv(h, Rk, q, q, Ri, stream);
+        if (st == RSK_OK) st = matmul_ts(h, X, m, q, ldx, Ri, q, q, T, m, stream);
+        if (st != RSK_OK) return st;
+        const unsigned gx = unsigned(std::min<int64_t>(64, (m + 255) / 256));
+        k_copy_cols<<<dim3(gx, unsigned(q)), 256, 0, stream>>>(T, m, int(m), q, X, ldx);
+        RSK_LAUNCH_CHECK(h);
+        if (R) {
+            // R_total = Rk * R_total (upper triangular factors accumulate on the left)
+            if (round == 0) {
+                k_copy_cols<<<dim3(1, unsigned(q)), 256, 0, stream>>>(Rk, q, q, q, Racc, q);
+            } else {
+                st = matmul_ts(h, Rk, q, q, q, Racc, q, q, Ri, q, stream);  // Ri is free here
+                if (st != RSK_OK) return st;
+                k_copy_cols<<<dim3(1, unsigned(q)), 256, 0, stream>>>(Ri, q, q, q, Racc, q);
+            }
+            RSK_LAUNCH_CHECK(h);
+        }
+    }
+    if (R) {
+        k_copy_cols<<<dim3(1, unsigned(q)), 256, 0, stream>>>(Racc, q, q, q, R, q);
+        RSK_LAUNCH_CHECK(h);
+    }
+    return RSK_OK;
+}
+
+}  // namespace dense
+}  // namespace rsk
+
+extern "C" {
+
+rsk_status rsk_svd_econ(rsk_handle* h, const float* A, int64_t m, int64_t q, int64_t lda, float* U, int64_t ldu,
+                        float* s, float* V, int64_t ldv, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!A || !U || !s) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (q < 1 || m < q || lda < m || ldu < m || (V && ldv < q))
+        return rsk::fail(h, RSK_ERR_INVALID_ARG, "need 1 <= q <= m, lda >= m, ldu >= m, ldv >= q");
+    if (q > 1024 || m > 4096) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "svd_econ supports q <= 1024, m <= 4096");
+    const size_t need = rsk::dense::svd_scratch_bytes(m, int(q)) + 256;
+    rsk_status st = rsk::ensure_workspace(h, need, stream);
+    if (st != RSK_OK) return st;
+    RSK_CUDA_TRY(h, cudaMemcpy2DAsync(U, size_t(ldu) * 4, A, size_t(lda) * 4, size_t(m) * 4, size_t(q),
+                                      cudaMemcpyDeviceToDevice, stream));
+    return rsk::dense::svd(h, U, m, int(q), ldu, s, V, ldv, h->ws, stream);
+}
+
+rsk_status rsk_qr_econ(rsk_handle* h, const float* X, int64_t m, int64_t q, int64_t ldx, float* Q, int64_t ldq,
+                       float* R, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!X || !Q) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (q < 1 || m < q || ldx < m || ldq < m) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need 1 <= q <= m, ldx, ldq >= m");
+    if (q > 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "qr_econ supports q <= 1024");
+    rsk_status st = rsk::ensure_workspace(h, rsk::dense::orth_scratch_bytes(m, int(q)) + 256, stream);
+    if (st != RSK_OK) return st;
+    RSK_CUDA_TRY(h, cudaMemcpy2DAsync(Q, size_t(ldq) * 4, X, size_t(ldx) * 4, size_t(m) * 4, size_t(q),
+                                      cudaMemcpyDeviceToDevice, stream));
+    return rsk::dense::orth_accurate(h, Q, m, int(q), ldq, R, h->ws, stream);
+}
+
+}  // extern "C"

@@ -29,36 +29,6 @@ namespace {
 constexpr int kPassThreads = 256;      // fused normal-equation passes
 constexpr int kMaxK = 1024;
 
-// ------------------------------------------------------------------------------------------
-// Bounded software grid barrier for persistent kernels whose CTAs are all resident.
-// ------------------------------------------------------------------------------------------
-__device__ bool grid_barrier(unsigned int* count, volatile unsigned int* gen, unsigned int nblocks,
-                             unsigned int* status, uint32_t limit) {
-    __syncthreads();
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        const unsigned int g = *gen;
-        __threadfence();
-        if (atomicAdd(count, 1u) == nblocks - 1) {
-            *count = 0;
-            __threadfence();
-            atomicAdd(const_cast<unsigned int*>(gen), 1u);
-        } else {
-            uint32_t it = 0;
-            while (*gen == g) {
-                if (++it > limit) {
-                    atomicOr(status, RSK_DEV_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (it > 64) __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    return __syncthreads_and(ok) != 0;
-}
-
 __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -110,7 +80,7 @@ __global__ void __launch_bounds__(256) k_qr(double* W, int d, int k, double* tau
     const int cols = k + 1;
     if (blockIdx.x == 0) make_reflector(W, d, 0, tau, red);
     for (int j = 0; j < k; ++j) {
-        if (!grid_barrier(bar, bar + 1, G, status, limit)) return;
+        if (!rskd::grid_barrier(bar, bar + 1, G, status, limit)) return;
         // Reflector j was written by another CTA: read it through L2 (ld.cg), never from a line this
         // SM's L1 may hold from an earlier step.
         const double* v = W + size_t(j) * d;

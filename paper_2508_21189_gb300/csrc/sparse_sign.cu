@@ -633,6 +633,71 @@ __global__ void k_sum_blocks(const Out* __restrict__ outs, int64_t bstride, int 
 }
 
 // ------------------------------------------------------------------------------------------
+// Right sketch Y = A Omega = A S^T (A n x dc row-major, S k x dc): Y[i, c] = zeta^{-1/2} sum over the
+// entries (j, sign) of row c of S of sign * A[i, j].  One CTA per tile of 32 rows of A at a time;
+// per index chunk the tile's 32 x C block of A is staged transposed ([j][i], lane index XOR-swizzled
+// by j so that both the staging writes and the gathers are free of bank conflicts), and warp w
+// accumulates output columns w, w + 8, ... for its 32 rows (lane = row): every lane of a warp walks
+// the same entry list, so the gather does not diverge.  Chunks are summed in order (deterministic).
+// ------------------------------------------------------------------------------------------
+constexpr int kRightRows = 32;
+constexpr int kRightThreads = 256;
+
+template <int MAXC>
+__global__ void __launch_bounds__(kRightThreads, 2)
+    k_right(const float* __restrict__ A, int64_t n, int64_t dc, int64_t lda, int k, int zeta, int C, int pitch,
+            const uint16_t* __restrict__ offs, const uint16_t* __restrict__ ents, int nchunks, float scale,
+            float* __restrict__ Y, int64_t ldy) {
+    extern __shared__ __align__(16) uint8_t smr[];
+    float* tile = reinterpret_cast<float*>(smr);                                   // C x 32
+    uint16_t* es = reinterpret_cast<uint16_t*>(smr + size_t(C) * kRightRows * 4);  // C * zeta entries
+    uint16_t* os = es + size_t(C) * zeta;                                          // k + 1 offsets
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t ntiles = (n + kRightRows - 1) / kRightRows;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t i0 = t * kRightRows;
+        float acc[MAXC];
+#pragma unroll
+        for (int cc = 0; cc < MAXC; ++cc) acc[cc] = 0.f;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            const int64_t j0 = int64_t(ch) * C;
+            const int cols = int(min(int64_t(C), dc - j0));
+            for (int idx = tid; idx < kRightRows * cols; idx += kRightThreads) {
+                const int r = idx / cols, c = idx - r * cols;
+                const float v = (i0 + r < n) ? A[(i0 + r) * lda + j0 + c] : 0.f;
+                tile[c * kRightRows + (r ^ (c & 31))] = v;
+            }
+            const uint16_t* ce = ents + j0 * zeta;
+            for (int e = tid; e < cols * zeta; e += kRightThreads) es[e] = ce[e];
+            const uint16_t* co = offs + int64_t(ch) * pitch;
+            for (int e = tid; e <= k; e += kRightThreads) os[e] = co[e];
+            __syncthreads();
+#pragma unroll
+            for (int cc = 0; cc < MAXC; ++cc) {
+                const int c = warp + 8 * cc;
+                if (c < k) {
+                    const int b = os[c], end = os[c + 1];
+                    float a = acc[cc];
+                    for (int e = b; e < end; ++e) {
+                        const uint32_t v = es[e];
+                        const int j = int(v & 0x7fffu);
+                        const float x = tile[j * kRightRows + (lane ^ (j & 31))];
+                        a += (v & 0x8000u) ? -x : x;
+                    }
+                    acc[cc] = a;
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int cc = 0; cc < MAXC; ++cc) {
+            const int c = warp + 8 * cc;
+            if (c < k && i0 + lane < n) Y[int64_t(c) * ldy + i0 + lane] = acc[cc] * scale;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Host side.
 // ------------------------------------------------------------------------------------------
 rsk_status check_dims(rsk_handle* h, int64_t n, int64_t d, int32_t zeta) {
@@ -964,6 +1029,60 @@ rsk_status sketch_apply_vec_built(rsk_handle* h, const void* index_mem, int64_t 
     k_apply_vec_sum<<<unsigned((d + 127) / 128), 128, 0, stream>>>(scratch, int(d), nch, 1.0 / sqrt(double(zeta)), Sb);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
+}
+// Rows/signs of a SparseUniform (kind 0, stream 0) or SparseStack (kind 1, stream 4) sketch, and the
+// apply of either kind (used by the Nystrom approximations, whose test matrix is a caller's choice).
+rsk_status sketch_generate_kind(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, int kind, int32_t* rows,
+                                uint32_t* signs, cudaStream_t stream) {
+    rsk_status st = kind == kStack ? check_stack_dims(h, n, d, zeta) : check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    return generate_kind(h, n, int(d), zeta, seed, kind == kStack ? kStreamStack : kStreamLeft, kind, rows, signs,
+                         stream);
+}
+rsk_status sketch_apply_kind(rsk_handle* h, int kind, const void* A, rsk_dtype a_dt, int64_t n, int64_t k,
+                             int64_t lda, int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
+                             cudaStream_t stream) {
+    rsk_status st = kind == kStack ? check_stack_dims(h, n, d, zeta) : check_dims(h, n, d, zeta);
+    if (st != RSK_OK) return st;
+    return apply_kind(h, A, a_dt, n, k, lda, 0, d, zeta, seed, SA, sa_dt, ldsa, stream,
+                      kind == kStack ? kStreamStack : kStreamLeft, kind);
+}
+// Y = A Omega for Omega = S^T, S the k x dc sketch of the given kind: Y n x k column-major (ldy >= n).
+rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n, int64_t dc, int64_t lda, int64_t k,
+                              int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream) {
+    rsk_status st = kind == kStack ? check_stack_dims(h, dc, k, zeta) : check_dims(h, dc, k, zeta);
+    if (st != RSK_OK) return st;
+    if (!A || !Y) return fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (n < 1 || lda < dc || ldy < n) return fail(h, RSK_ERR_INVALID_ARG, "need n >= 1, lda >= dc, ldy >= n");
+    if (k > 512) return fail(h, RSK_ERR_UNSUPPORTED, "the right sketch supports k <= 512");
+    const size_t ib = sketch_index_bytes(dc, k, zeta);
+    st = ensure_workspace(h, ib + 256, stream);
+    if (st != RSK_OK) return st;
+    Carver cv(h->ws);
+    uint16_t* offs = cv.take<uint16_t>(offsets_count(dc, int(k), zeta));
+    uint16_t* ents = cv.take<uint16_t>(entries_count(dc, zeta));
+    st = launch_index(h, dc, int(k), zeta, seed, kind == kStack ? kStreamStack : kStreamLeft, offs, ents, stream, 0,
+                      kind);
+    if (st != RSK_OK) return st;
+    const int C = chunk_rows(zeta);
+    const int nch = int(n_chunks_of(dc, zeta));
+    const size_t smem = size_t(C) * kRightRows * 4 + size_t(C) * zeta * 2 + size_t(k + 8) * 2;
+    const int64_t ntiles = (n + kRightRows - 1) / kRightRows;
+    const unsigned grid = unsigned(std::min<int64_t>(ntiles, int64_t(h->num_sms) * 2));
+    const float scale = float(1.0 / sqrt(double(zeta)));
+    auto go = [&](auto kern) -> rsk_status {
+        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        const int pr = prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
+        kern<<<grid, kRightThreads, smem, stream>>>(A, n, dc, lda, int(k), zeta, C, offsets_pitch(int(k)), offs, ents,
+                                                    nch, scale, Y, ldy);
+        prof_end(h, stream, pr);
+        RSK_LAUNCH_CHECK(h);
+        return RSK_OK;
+    };
+    if (k <= 64) return go(k_right<8>);
+    if (k <= 128) return go(k_right<16>);
+    if (k <= 256) return go(k_right<32>);
+    return go(k_right<64>);
 }
 // Draw rows/signs of a sparse sign matrix from any Philox stream (the RSVD test matrix uses stream 3).
 rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, uint32_t stream_id,
