@@ -352,6 +352,39 @@ rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const 
                                             const rsk_lsq_opts* opts, rsk_lsq_info* infos, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Autotuning of launch parameters (not a step of the paper).  Knobs (kernel ids): 0 = the number of
+ * row ranges of the sparse gather apply (sparse sign, SparseStack, the solvers' sketches), 1 = the
+ * number of row bands of the SRTT / SparseRTT, 2 = the rows per work tile of the batched
+ * least-squares passes.  Tuned values live in a process-wide table keyed by (kernel, dtype, n, k, d,
+ * SM count) -- for kernel 2: (inner dtype, total rows, problem count, 0, SM count) -- and are used
+ * by every later call with that key; a tuned value regroups partial sums, so results are
+ * deterministic for a fixed table but may differ in the last bits from untuned ones.  If the
+ * environment variable RSK_TUNE_CACHE names a file, the table is read from it at the first lookup
+ * and written back after every autotune call.  File format: text lines
+ *     rsk-tune v1 kernel=<int> dtype=<int> n=<int> k=<int> d=<int> sms=<int> value=<int>
+ * ('#' starts a comment line; later lines override earlier ones).  The table calls are host-only
+ * and thread safe. */
+rsk_status rsk_tune_cache_load(const char* path);      /* merge a cache file into the table */
+rsk_status rsk_tune_cache_save(const char* path);      /* write the whole table */
+rsk_status rsk_tune_cache_clear(void);                 /* empty the table (and skip RSK_TUNE_CACHE) */
+rsk_status rsk_tune_cache_set(int32_t kernel, int32_t dtype, int64_t n, int64_t k, int64_t d, int32_t sms,
+                              int32_t value);
+/* *value = the tuned value for the key, 0 when none. */
+rsk_status rsk_tune_cache_get(int32_t kernel, int32_t dtype, int64_t n, int64_t k, int64_t d, int32_t sms,
+                              int32_t* value);
+/* Time the default rule and candidate values around it for kernel 0 (rsk_sparse_sign_apply) or 1
+ * (rsk_srtt_apply) on an n x k matrix of a_dtype with d sketch rows (zeta for kernel 0), keep the
+ * fastest in the table (0 = the default rule won; the key is then left untuned).  Allocates its
+ * buffers on `stream`; synchronous.  *chosen and *best_ms (may be NULL) are host outputs. */
+rsk_status rsk_autotune_sketch(rsk_handle* h, int32_t kernel, rsk_dtype a_dtype, int64_t n, int64_t k, int64_t d,
+                               int32_t zeta, int32_t* chosen, double* best_ms, cudaStream_t stream);
+/* Time the batched least-squares solver on the caller's problems with 1024, 2048, 4096 and 8192 rows
+ * per work tile (and the default), keep the fastest for this batch's key.  Synchronous; the
+ * problems' x are overwritten by the solves. */
+rsk_status rsk_autotune_batched(rsk_handle* h, int32_t count, const rsk_lsq_problem* probs, const rsk_lsq_opts* opts,
+                                int32_t* chosen, double* best_ms, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Dense steps of the low-rank algorithms (Algs. 1, 2, 4, 5 name them svd_econ, qr_econ / orth,
  * chol): FP32, column-major (column c of X at X + c * ldx), device pointers, asynchronous.
  * ------------------------------------------------------------------------------------------- */
@@ -403,6 +436,20 @@ rsk_status rsk_nystrom_psd(rsk_handle* h, const float* A, int64_t n, int64_t lda
 rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, int32_t k, int32_t p,
                            int32_t zeta, uint64_t seed, int32_t kind, int32_t form, float* out1, int64_t ld1,
                            float* sigma, float* out2, int64_t ld2, int32_t* rank, cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Injectivity and dilation on the adversarial subspace (Fig. 2, Sec. 1.5; discussed in Sec. 3):
+ * for Q = [e_1 ... e_r] and embedding dimension k, alpha = sigma_min^2(Omega^T Q) and
+ * beta = sigma_max^2(Omega^T Q), Omega^T Q being the first r columns S_r of the k x d sketch of the
+ * given kind (0 SparseUniform, 1 SparseStack with k % zeta == 0) drawn from `seed`.  Estimated by
+ * `iters` Lanczos steps on S_r^T S_r from v_1 = (1, ..., 1) / sqrt(r) (FP64 vectors, products with a
+ * deterministic CSR of S_r and with its columns as drawn), then bisection on the Lanczos tridiagonal:
+ * *alpha is the smallest Ritz value (>= the true alpha), *beta the largest (<= the true beta); with
+ * iters >= r they are the eigenvalues to rounding.  Host outputs; synchronous.  Limits: r, k < 2^31,
+ * r * zeta < 2^31, 1 <= zeta <= min(k, 32), 1 <= iters <= 100000.  Device memory: about
+ * r (8 zeta + 28) + 28 k bytes from the handle's workspace. */
+rsk_status rsk_osi_estimate(rsk_handle* h, int64_t r, int64_t k, int32_t zeta, uint64_t seed, int32_t kind,
+                            int32_t iters, double* alpha, double* beta, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
  * a9: randomized SVD with a sparse sign test matrix (Alg. 1, Sec. 2.1) and power_iters subspace

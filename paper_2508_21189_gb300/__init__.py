@@ -452,6 +452,17 @@ def rsk_gen_nystrom(A, k, p=None, zeta=4, seed=0, kind="stack", form="svd", stre
     return out1, sig, out2, int(r.item())
 
 
+def rsk_osi_estimate(r, k=None, zeta=8, seed=0, kind="stack", iters=300, device=None, stream=None):
+    """(alpha, beta): injectivity and dilation estimates of the sketch on Q = [e_1 ... e_r] (k = 2r by default)."""
+    k = 2 * r if k is None else k
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    h = handle(dev)
+    _check(load().rsk_osi_estimate(h, r, k, zeta, seed, {"uniform": 0, "stack": 1}[kind], iters, ctypes.byref(a),
+                                   ctypes.byref(b), _stream(stream)), h)
+    return a.value, b.value
+
+
 def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
     """Randomized SVD of a CUDA FP32 tensor A (m x n): returns (U [m, r] FP32, s [r] FP64, Vt [r, n] FP32)."""
     _matrix(A, "A")

@@ -53,6 +53,14 @@ SIGNATURES = {
     "rsk_nystrom_psd": [c_p, c_p, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_i32, c_p, c_i64, c_p, c_p],
     "rsk_gen_nystrom": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_i32, c_i32, c_p, c_i64, c_p, c_p,
                         c_i64, c_p, c_p],
+    "rsk_osi_estimate": [c_p, c_i64, c_i64, c_i32, c_u64, c_i32, c_i32, c_p, c_p, c_p],
+    "rsk_tune_cache_load": [ctypes.c_char_p],
+    "rsk_tune_cache_save": [ctypes.c_char_p],
+    "rsk_tune_cache_clear": [],
+    "rsk_tune_cache_set": [c_i32, c_i32, c_i64, c_i64, c_i64, c_i32, c_i32],
+    "rsk_tune_cache_get": [c_i32, c_i32, c_i64, c_i64, c_i64, c_i32, c_p],
+    "rsk_autotune_sketch": [c_p, c_i32, c_i32, c_i64, c_i64, c_i64, c_i32, c_p, c_p, c_p],
+    "rsk_autotune_batched": [c_p, c_i32, c_p, c_p, c_p, c_p, c_p],
     "rsk_rsvd": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_p, c_p, c_p, c_p],
 }
 

@@ -39,12 +39,26 @@ struct rsk_handle {
     // iteration limit of the bounded polls on global-memory flags (grid barrier, reflector-ready
     // flags); rsk_set_wait_limit changes it, 0 restores the default
     uint32_t wait_limit = 1u << 22;
+    // launch-parameter override used while the autotuner times a candidate: 0 = the tuning table, then
+    // the default rule; -1 = the default rule only; > 0 = this value
+    int tune_override = 0;
 };
 constexpr int kHostFlags = 8;
 
 namespace rsk {
 
 rsk_status fail(rsk_handle* h, rsk_status st, const char* fmt, ...);
+
+// Tuned launch parameters (tune.cu): the knob of `kernel` for a problem shape, or 0 when none is
+// tuned.  Kernels: 0 = sparse gather apply (row ranges), 1 = SRTT (row bands), 2 = batched solver
+// (rows per work tile).  The handle's tune_override takes precedence.
+enum TuneKernel { kTuneApply = 0, kTuneSrtt = 1, kTuneBatchTile = 2 };
+int tune_lookup(int kernel, int dtype, int64_t n, int64_t k, int64_t d, int sms);
+inline int tuned_value(const rsk_handle* h, int kernel, int dtype, int64_t n, int64_t k, int64_t d) {
+    if (h && h->tune_override > 0) return h->tune_override;
+    if (h && h->tune_override < 0) return 0;
+    return tune_lookup(kernel, dtype, n, k, d, h ? h->num_sms : 0);
+}
 
 // Make sure the handle owns at least `count` internal non-blocking streams.
 rsk_status ensure_streams(rsk_handle* h, int count);
@@ -105,6 +119,8 @@ rsk_status sketch_generate_kind(rsk_handle* h, int64_t n, int64_t d, int zeta, u
 // n x k column-major (ldy >= n).  Uses the handle's workspace for the inverted index of S.
 rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n, int64_t dc, int64_t lda, int64_t k,
                               int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream);
+rsk_status sketch_generate_large(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, int kind, int32_t* rows,
+                                 uint32_t* signs, cudaStream_t stream);
 rsk_status sketch_apply_kind(rsk_handle* h, int kind, const void* A, rsk_dtype a_dt, int64_t n, int64_t k,
                              int64_t lda, int64_t d, int zeta, uint64_t seed, void* SA, rsk_dtype sa_dt, int64_t ldsa,
                              cudaStream_t stream);

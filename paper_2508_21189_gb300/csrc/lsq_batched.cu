@@ -676,6 +676,11 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     size_t bytes = 0;
     auto add = [&](size_t b_) { bytes += Carver::round(b_); };
     size_t max_sketch_scratch = 0;
+    // rows per work tile: tuned for this batch (keyed by its total rows and problem count) or 2048
+    int64_t total_rows = 0;
+    for (int i = 0; i < count; ++i) total_rows += probs[i].n;
+    const int tuned_tile = rsk::tuned_value(h, rsk::kTuneBatchTile, int(opts->inner_dtype), total_rows, count, 0);
+    const int tile_rows = tuned_tile > 0 ? tuned_tile : kTileRows;
     for (int i = 0; i < count; ++i) {
         const rsk_lsq_problem& pr = probs[i];
         if (!pr.A || !pr.b || !pr.x) return fail(h, RSK_ERR_INVALID_ARG, "problem %d: null pointer", i);
@@ -697,12 +702,12 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         q.a_f32 = pr.a_dtype == RSK_F32;
         q.in_f32 = opts->inner_dtype == RSK_F32;
         q.tile0 = int(tiles.size());
-        q.ntiles = int((pr.n + kTileRows - 1) / kTileRows);
+        q.ntiles = int((pr.n + tile_rows - 1) / tile_rows);
         for (int t = 0; t < q.ntiles; ++t) {
             Tile T;
             T.p = i;
-            T.r0 = t * kTileRows;
-            T.r1 = int(std::min<int64_t>(pr.n, int64_t(t + 1) * kTileRows));
+            T.r0 = t * tile_rows;
+            T.r1 = int(std::min<int64_t>(pr.n, int64_t(t + 1) * tile_rows));
             T.pad = 0;
             tiles.push_back(T);
         }

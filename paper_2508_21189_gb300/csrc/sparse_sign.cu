@@ -776,6 +776,8 @@ ApplyPlan plan_apply(rsk_handle* h, int64_t n, int64_t k, int d, int zeta, rsk_d
         hh = t_;
     }
     int R = pairs >= h->num_sms ? 1 : h->num_sms / std::max(1, gg);
+    const int tuned = rsk::tuned_value(h, rsk::kTuneApply, int(dt), n, k, d);
+    if (tuned > 0) R = tuned;
     const int64_t cap = std::max<int64_t>(1, int64_t(512) * (1 << 20) / int64_t(p.pstride * acc));
     R = int(std::min<int64_t>(std::min<int64_t>(R, cap), p.nchunks));
     p.nranges = std::max(1, R);
@@ -1036,6 +1038,16 @@ rsk_status sketch_generate_kind(rsk_handle* h, int64_t n, int64_t d, int zeta, u
                                 uint32_t* signs, cudaStream_t stream) {
     rsk_status st = kind == kStack ? check_stack_dims(h, n, d, zeta) : check_dims(h, n, d, zeta);
     if (st != RSK_OK) return st;
+    return generate_kind(h, n, int(d), zeta, seed, kind == kStack ? kStreamStack : kStreamLeft, kind, rows, signs,
+                         stream);
+}
+// The same draw for any d < 2^31 (no inverted index is built, so the index's d <= 8192 limit does not
+// apply): rows int32[n * zeta], signs uint32[n].
+rsk_status sketch_generate_large(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, int kind, int32_t* rows,
+                                 uint32_t* signs, cudaStream_t stream) {
+    if (n < 1 || n >= (int64_t(1) << 31) || d < 1 || d >= (int64_t(1) << 31) || zeta < 1 || zeta > 32 || zeta > d ||
+        (kind == kStack && d % zeta != 0))
+        return fail(h, RSK_ERR_INVALID_ARG, "draw needs n, d < 2^31, 1 <= zeta <= min(d, 32)");
     return generate_kind(h, n, int(d), zeta, seed, kind == kStack ? kStreamStack : kStreamLeft, kind, rows, signs,
                          stream);
 }

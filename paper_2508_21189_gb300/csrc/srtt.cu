@@ -767,6 +767,8 @@ rsk_status srtt_impl(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n_
         hh = t_;
     }
     args.R = std::max(1, std::min(args.nblocks, h->num_sms / gg));
+    const int tuned = rsk::tuned_value(h, rsk::kTuneSrtt, int(a_dtype), n_rows, k, d);
+    if (tuned > 0) args.R = std::max(1, std::min(args.nblocks, tuned));
     args.nitems = args.nslices * args.R;
     args.pstride = int64_t(d) * kCols;
     args.seed = seed;
