@@ -18,6 +18,7 @@ S), the N partial d x k sketches are gathered over NCCL and summed in rank order
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -34,6 +35,9 @@ N_ROWS, K_COLS, D_SKETCH, ZETA = 1 << 22, 256, 2048, 8
 LSQ_N, LSQ_K, LSQ_D = 1 << 20, 500, 2000
 BATCH_COUNT = 512
 RSVD_M, RSVD_N, RSVD_R, RSVD_Q, RSVD_RANK = 262144, 8192, 300, 2, 400
+NYS_N, NYS_K, NYS_RANK = 32768, 300, 1000
+GEN_N, GEN_D, GEN_K, GEN_RANK = 131072, 40000, 200, 400
+OSI_R = (10 ** 5, 10 ** 6, 10 ** 7)
 FALLBACK_HBM_GBS = 6800.0
 APPLY_SOURCES = ["paper_2508_21189_gb300/csrc/sparse_sign.cu", "paper_2508_21189_gb300/csrc/common.cuh"]
 
@@ -60,6 +64,14 @@ def parse():
                    "captures)")
     p.add_argument("--profile-rsvd", action="store_true", help="open the CUDA profiler range around the timed RSVD "
                    "calls only (for ncu --profile-from-start off)")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch parameters for the headline "
+                   "shape instead of timing candidates first")
+    p.add_argument("--no-variants", action="store_true", help="skip the SparseStack / SparseRTT sketches")
+    p.add_argument("--no-nystrom", action="store_true", help="skip the Nystrom approximations")
+    p.add_argument("--no-osi", action="store_true", help="skip the injectivity/dilation estimator")
+    p.add_argument("--nystrom-n", type=int, default=NYS_N, help="order of the psd Nystrom matrix")
+    p.add_argument("--gen-rows", type=int, default=GEN_N, help="rows of the generalized Nystrom matrix")
+    p.add_argument("--gen-cols", type=int, default=GEN_D, help="columns of the generalized Nystrom matrix")
     return p.parse_args()
 
 
@@ -200,16 +212,96 @@ def oracle_sample(rows, seed):
     return time.perf_counter() - t0
 
 
+def _oracle_block(args):
+    """One worker's share of the all-core CPU baseline: the oracle's sketch of its own row block (the
+    sketch is additive over row blocks, so the blocks are independent work)."""
+    row0, rows, seed = args
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import sparse_sign as osk
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((rows, K_COLS)) * np.logspace(-3, 0, K_COLS)[None, :]
+    t0 = time.perf_counter()
+    osk.apply_block(A, row0, D_SKETCH, ZETA, seed)
+    return time.perf_counter() - t0
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_extras():
+    """Oracle timings of the other workloads on a bounded sample (single thread)."""
+    import numpy as np
+    from oracle import srtt as osr
+    from oracle import lsq as olsq
+    out = {}
+    rng = np.random.default_rng(5)
+    n = 1 << 17
+    A = rng.standard_normal((n, K_COLS))
+    t0 = time.perf_counter()
+    osr.apply(A, D_SKETCH, 3)
+    t = time.perf_counter() - t0
+    out["srtt"] = {"sample": f"{n} x {K_COLS} FP64 (of 2^22 rows), d={D_SKETCH}", "s": round(t, 3),
+                   "gbs_bf16_equiv": round(n * K_COLS * 2 / t / 1e9, 4)}
+    nl, kl = 1 << 15, 100
+    Q, _ = np.linalg.qr(rng.standard_normal((nl, kl)))
+    V, _ = np.linalg.qr(rng.standard_normal((kl, kl)))
+    Al = (Q * np.logspace(0, -8, kl)) @ V.T
+    bl = Al @ rng.standard_normal(kl) + 1e-6 * rng.standard_normal(nl)
+    t0 = time.perf_counter()
+    olsq.sketch_precond(Al, bl, 4 * kl, ZETA, 7)
+    t = time.perf_counter() - t0
+    out["lsq"] = {"sample": f"sketch-and-precondition (oracle: FP64 sketch, QR, LSQR refinement) on {nl} x {kl}, "
+                            "kappa=1e8 (reduced from 2^20 x 500)", "s": round(t, 3), "solves_per_s": round(1 / t, 4)}
+    return out
+
+
 def cpu_baseline(target_s=12.0, a_bytes=2):
     rows = 1 << 14
     t = oracle_sample(rows, 1)
     while t < target_s / 4 and rows < (1 << 20):
         rows *= 2
         t = oracle_sample(rows, 1)
-    gbs = rows * K_COLS * a_bytes / t / 1e9
-    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rows} of {N_ROWS} rows x {K_COLS} cols (FP64 oracle: Philox+Floyd draw of S, scipy CSR "
-                      f"product), {t:.2f} s; GB/s counted in BF16 bytes of A"}
+    single = rows * K_COLS * a_bytes / t / 1e9
+    cores = os.cpu_count() or 1
+    # all cores: one spawned worker per core, each sketching its own block of `rows` rows
+    import multiprocessing as mp
+    per = max(1 << 12, rows // 2)
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_block, [(0, 1 << 10, 1)] * cores)  # start-up and imports outside the timing
+            t0 = time.perf_counter()
+            pool.map(_oracle_block, [(g * per, per, 100 + g) for g in range(cores)])
+            tall = time.perf_counter() - t0
+        allc = cores * per * K_COLS * a_bytes / tall / 1e9
+    except (OSError, RuntimeError):
+        allc, tall = None, None
+    res = {"value": round(allc if allc else single, 4), "unit": "GB/s", "cores": cores if allc else 1, "kind": "oracle",
+           "single_thread": round(single, 4), "cpu_model": cpu_model(), "nproc": cores,
+           "sample": f"single thread: {rows} of {N_ROWS} rows x {K_COLS} cols in {t:.2f} s; all cores: {cores} spawned "
+                     f"workers x {per} rows in {tall:.2f} s (FP64 oracle: Philox+Floyd draw of S, scipy CSR product); "
+                     "GB/s counted in BF16 bytes of A" if tall else f"{rows} rows single thread"}
+    try:
+        res["other_workloads"] = cpu_extras()
+    except Exception as e:  # the extras are context only
+        res["other_workloads"] = {"error": str(e)[:200]}
+    return res
 
 
 def run_reference(args):
@@ -390,6 +482,135 @@ def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps, rows=RSVD_M, profi
                                        if gemm_ms > 0 else None)}
 
 
+def time_variants(rsk, A, out, steps, torch, dev):
+    """SparseStack (Def. SparseStack) and SparseRTT (Def. SparseRTT, xi = ceil(1.5 ln d)) on the headline A."""
+    a_bytes = A.numel() * A.element_size()
+    res = {}
+    for name, fn in (("sparse_stack", lambda s: rsk.rsk_sparse_stack_apply(A, D_SKETCH, ZETA, s, out=out)),
+                     ("sparse_rtt", lambda s: rsk.rsk_sparse_rtt_apply(A, D_SKETCH, s, out=out))):
+        for w in range(3):
+            fn(w)
+        rsk.rsk_profile_enable(True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for st in range(steps):
+            fn(50_000 + st)
+        ev1.record()
+        torch.cuda.synchronize()
+        kid = "sketch_apply" if name == "sparse_stack" else "srtt_apply"
+        ap = rsk.rsk_profile_read(kid)
+        rsk.rsk_profile_enable(False)
+        rsk.rsk_sync_status()
+        ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, device=dev)
+        apply_ms = ap[0] / max(1, ap[1])
+        res[name] = {"value": round(a_bytes / (ms / 1e3) / 1e9, 3), "unit": "GB/s", "ms_per_step": round(ms, 4),
+                     "apply_ms": round(apply_ms, 4),
+                     "apply_hbm_frac": round(a_bytes / (apply_ms / 1e3) / 1e9 / hbm_peak()[0], 4)}
+    res["sparse_rtt"]["xi"] = rsk.rsk_sparse_rtt_default_xi(D_SKETCH)
+    res["sparse_stack"]["workload"] = f"SparseStack d={D_SKETCH} zeta={ZETA} on A 2^22 x 256 BF16"
+    res["sparse_rtt"]["workload"] = f"SparseRTT d={D_SKETCH} (WHT, xi=ceil(1.5 ln d)) on A 2^22 x 256 BF16"
+    return res
+
+
+def spectral_norm(apply, n, torch, dev, iters=30, seed=9):
+    """||M||_2 of the operator x -> M x (M^T M by power iteration from a seeded start)."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.randn(n, 1, generator=g, device=dev, dtype=torch.float64)
+    lam = 0.0
+    for _ in range(iters):
+        y = apply(x)
+        lam = float(torch.linalg.norm(y))
+        x = y / max(lam, 1e-300)
+    return math.sqrt(lam)
+
+
+def bench_nystrom(rsk, torch, dev, reps, n=NYS_N):
+    """Alg. 2 on a psd A = U diag(j^-1, j <= 1000) U^T + 1e-6 I (n x n FP32), k = 300, SparseStack zeta = 4."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    U, _ = torch.linalg.qr(torch.randn(n, NYS_RANK, generator=g, device=dev, dtype=torch.float32))
+    lam = 1.0 / torch.arange(1, NYS_RANK + 1, device=dev, dtype=torch.float32)
+    A = (U * lam) @ U.T
+    A.diagonal().add_(1e-6)
+    A = 0.5 * (A + A.T)
+    del U
+    ms, (Un, ln) = timed_calls(lambda: rsk.rsk_nystrom_psd(A, NYS_K, zeta=4, seed=1), reps, torch, dev)
+    A64 = None
+    # ||A - U diag(l) U^T||_2 against the best rank-k error lambda_{k+1}
+    Ud, ld = Un.double(), ln.double()
+
+    def err_op(x):
+        y = (A.double() @ x) - Ud @ (ld[:, None] * (Ud.T @ x))
+        return (A.double() @ y) - Ud @ (ld[:, None] * (Ud.T @ y))
+    err = spectral_norm(err_op, n, torch, dev, iters=20)
+    best = 1.0 / (NYS_K + 1) + 1e-6
+    del A, Un, ln, Ud, ld, A64
+    torch.cuda.empty_cache()
+    return {"workload": f"psd Nystrom (Alg. 2): A = U diag(j^-1, j<=1000) U^T + 1e-6 I, {n} x {n} FP32, k={NYS_K}, "
+                        "SparseStack zeta=4",
+            "value": round(1e3 / ms, 3), "unit": "calls/s", "ms_per_call": round(ms, 3),
+            "spectral_error": err, "best_rank_k_error": best, "error_over_best": round(err / best, 4)}
+
+
+def bench_gen_nystrom(rsk, torch, dev, reps, n=GEN_N, d=GEN_D):
+    """Algs. 4 and 5 on A = U diag(0.95^j, j < 400) V^T + 1e-6 noise (n x d FP32), k = 200, p = 300,
+    SparseStack zeta = 4 (a stand-in for the paper's 131072 x 40000 simulation snapshots, whose
+    singular values decay fast; with a slow decay the Frobenius tail dominates every sketch's error)."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(88)
+    U = torch.randn(n, GEN_RANK, generator=g, device=dev) / math.sqrt(n)
+    V = torch.randn(d, GEN_RANK, generator=g, device=dev) / math.sqrt(d)
+    s = 0.95 ** torch.arange(GEN_RANK, device=dev, dtype=torch.float32)
+    A = (U * s) @ V.T
+    del U, V
+    A.add_(torch.randn(n, d, generator=g, device=dev), alpha=1e-6 / math.sqrt(max(n, d)))
+    k, p = GEN_K, 300
+    res = {"workload": f"generalized Nystrom (Algs. 4, 5): A {n} x {d} FP32 = rank-{GEN_RANK} (0.95^j) + 1e-6 noise, "
+                       f"k={k}, p={p}, SparseStack zeta=4",
+           "a_bytes": A.numel() * 4}
+    nA = spectral_norm(lambda x: A.T.double() @ (A.double() @ x), d, torch, dev, iters=15)
+    for form in ("outer", "svd"):
+        ms, out = timed_calls(lambda: rsk.rsk_gen_nystrom(A, k, p=p, zeta=4, seed=2, form=form), reps, torch, dev)
+        if form == "outer":
+            F, G, r = out
+            L, R = F.double(), G.double()
+        else:
+            Uo, so, Vo, r = out
+            L, R = Uo.double() * so.double(), Vo.double()
+
+        def op(x):
+            y = A.double() @ x - L @ (R.T @ x)
+            return A.T.double() @ y - R @ (L.T @ y)
+        err = spectral_norm(op, d, torch, dev, iters=15)
+        res[form] = {"ms_per_call": round(ms, 3), "calls_per_s": round(1e3 / ms, 3), "numerical_rank": r,
+                     "relative_spectral_error": err / nA,
+                     "sketch_pass_gbs": round(2 * res["a_bytes"] / (ms / 1e3) / 1e9, 1)}
+        del out, L, R
+    res["value"] = res["svd"]["calls_per_s"]
+    res["unit"] = "calls/s"
+    res["best_rank_k_relative_error"] = 0.95 ** k
+    del A
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_osi(rsk, torch, rs=OSI_R):
+    """Fig. 2's estimates for SparseStack zeta = 8, k = 2r, Q = [e_1 ... e_r] (300 Lanczos steps)."""
+    out = []
+    for r in rs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a, b = rsk.rsk_osi_estimate(r, zeta=8, seed=1, kind="stack", iters=300)
+        torch.cuda.synchronize()
+        out.append({"r": r, "alpha": round(a, 5), "beta": round(b, 5), "s": round(time.perf_counter() - t0, 3)})
+    return {"workload": "injectivity alpha / dilation beta of SparseStack zeta=8, k=2r, Q=[e_1..e_r], 300 Lanczos "
+                        "steps", "gaussian_asymptotes": [round((1 - 2 ** -0.5) ** 2, 5), round((1 + 2 ** -0.5) ** 2, 5)],
+            "estimates": out}
+
+
 def run_ours(args):
     import torch
     rank, world = dist_init("nccl")
@@ -412,11 +633,17 @@ def run_ours(args):
     # rows of this rank: the whole A on one GPU; a row block of it (2048-row aligned, so the SRTT
     # can use the same blocks) on several
     row0, n_local = row_partition(args.rows, world, 2048)[rank]
+    tuned = {}
     for name in names:
         dt = dts[name]
         A = synthetic.colscaled_gaussian(n_local, K_COLS, seed=2022 + rank, device=dev, dtype=dt)
         out = torch.empty(D_SKETCH, K_COLS, device=dev, dtype=torch.float32)
         a_bytes = args.rows * K_COLS * A.element_size()  # the whole A, over all ranks
+        if not args.no_autotune:
+            # launch parameters of this shape chosen by timing candidates (outside the timed region)
+            tuned[name] = {"sketch_row_ranges": rsk.rsk_autotune_sketch(0, A.dtype, n_local, K_COLS, D_SKETCH, ZETA),
+                           "srtt_bands": (rsk.rsk_autotune_sketch(1, A.dtype, n_local, K_COLS, D_SKETCH, ZETA)
+                                          if not args.no_srtt else None)}
         for w in range(args.warmup):
             sketch_step(rsk, A, out, w, row0, world)
         rsk.rsk_sync_status()
@@ -504,11 +731,20 @@ def run_ours(args):
                         "ms_per_step": round(e2e_ms, 4),
                         "h2d_copy_gbs": round(a_bytes / (copy_ms / 1e3) / 1e9, 3)}
             del A_host
+        if name == head and not args.no_variants and world == 1:
+            r["variants"] = time_variants(rsk, A, out, args.steps, torch, dev)
         result[name] = r
         del A
         torch.cuda.empty_cache()
     clocks = sampler.stop()
     extra = {}
+    if tuned:
+        extra["autotune"] = {"chosen": tuned, "note": "0 = the default rule was fastest"}
+    if not args.no_nystrom and world == 1:
+        extra["nystrom_psd"] = bench_nystrom(rsk, torch, dev, args.solve_reps, n=args.nystrom_n)
+        extra["gen_nystrom"] = bench_gen_nystrom(rsk, torch, dev, args.solve_reps, n=args.gen_rows, d=args.gen_cols)
+    if not args.no_osi and world == 1:
+        extra["osi"] = bench_osi(rsk, torch)
     if not args.no_lsq:
         extra["lsq"] = bench_lsq(rsk, synthetic, torch, dev, rank, world, args.solve_reps, args.lsq_rows)
         extra["lsq_batched"] = bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, args.solve_reps,
@@ -554,6 +790,8 @@ def run_ours(args):
                       "apply_ms": round(r["apply_ms"], 4),
                       "apply_frac": round((r["local_bytes"] + D_SKETCH * K_COLS * 4) / (r["apply_ms"] / 1e3) / 1e9
                                           / peak, 4)}
+    if "variants" in main:
+        line.update(main["variants"])
     line.update(extra)
     if args.rows != N_ROWS:
         line["config"]["n"] = args.rows

@@ -463,6 +463,17 @@ def rsk_osi_estimate(r, k=None, zeta=8, seed=0, kind="stack", iters=300, device=
     return a.value, b.value
 
 
+def rsk_autotune_sketch(kernel, dtype, n, k, d, zeta=8, device=None, stream=None):
+    """Time candidate launch parameters of kernel 0 (sparse gather apply) or 1 (SRTT) for this shape and
+    keep the fastest in the tuning table; returns the chosen value (0 = the default rule)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    chosen, ms = ctypes.c_int32(), ctypes.c_double()
+    h = handle(dev)
+    _check(load().rsk_autotune_sketch(h, kernel, _DT[dtype], n, k, d, zeta, ctypes.byref(chosen), ctypes.byref(ms),
+                                      _stream(stream)), h)
+    return chosen.value
+
+
 def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
     """Randomized SVD of a CUDA FP32 tensor A (m x n): returns (U [m, r] FP32, s [r] FP64, Vt [r, n] FP32)."""
     _matrix(A, "A")
