@@ -451,6 +451,16 @@ rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, int64_t d, 
 rsk_status rsk_osi_estimate(rsk_handle* h, int64_t r, int64_t k, int32_t zeta, uint64_t seed, int32_t kind,
                             int32_t iters, double* alpha, double* beta, cudaStream_t stream);
 
+/* D = A B^T on the BF16 tensor cores (tcgen05, FP32 accumulation in tensor memory): A device BF16
+ * M x K row-major (lda >= K), B device BF16 N x K row-major (ldb >= K) -- both K-major --, D device
+ * FP32 M x N column-major (ldd >= M).  The dense product step of Alg. 1 (Z = A^T Q, Y = A Z) with the
+ * rank as N.  1 <= N <= 512 (N rounded up to an even multiple of 16 internally: 2 x 16 .. 2 x 256);
+ * A, B 16-byte aligned with 16-byte row pitches.  nsplit > 1 splits K over that many CTAs per
+ * 128-row tile (the partials come from the handle's workspace and are summed in split order).
+ * Asynchronous. */
+rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B, int64_t N,
+                         int64_t ldb, float* D, int64_t ldd, int32_t nsplit, cudaStream_t stream);
+
 /* ---------------------------------------------------------------------------------------------
  * a9: randomized SVD with a sparse sign test matrix (Alg. 1, Sec. 2.1) and power_iters subspace
  * iterations (re-orthonormalising after every product; Alg. 1 itself has none).

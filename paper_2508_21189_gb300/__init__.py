@@ -474,6 +474,22 @@ def rsk_autotune_sketch(kernel, dtype, n, k, d, zeta=8, device=None, stream=None
     return chosen.value
 
 
+def rsk_gemm_bf16(A, B, nsplit=1, stream=None):
+    """D = A @ B.T on the tensor cores: A (M x K) and B (N x K) row-major CUDA BF16; D FP32 (M x N)
+    returned column-major."""
+    _matrix(A, "A")
+    _matrix(B, "B")
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or A.shape[1] != B.shape[1]:
+        raise ValueError("A and B must be bfloat16 with the same number of columns")
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty(N, M, device=A.device).t()
+    h = handle(A.device)
+    _check(load().rsk_gemm_bf16(h, A.data_ptr(), M, K, A.stride(0), B.data_ptr(), N, B.stride(0), D.data_ptr(),
+                                D.stride(1), nsplit, _stream(stream)), h)
+    return D
+
+
 def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
     """Randomized SVD of a CUDA FP32 tensor A (m x n): returns (U [m, r] FP32, s [r] FP64, Vt [r, n] FP32)."""
     _matrix(A, "A")

@@ -66,6 +66,19 @@ bool encode_2d(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const vo
     return r == CUDA_SUCCESS;
 }
 
+bool encode_2d_swz128(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                      uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner, uint32_t box_outer) {
+    if (!h->encode_tiled) return false;
+    auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(h->encode_tiled);
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_stride_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 static cudaEvent_t take_event(rsk_handle* h) {
     if (!h->event_pool.empty()) {
         cudaEvent_t e = h->event_pool.back();

@@ -95,6 +95,11 @@ bool encode_2d(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const vo
                uint64_t inner, uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner,
                uint32_t box_outer);
 
+// The same with the 128-byte swizzle (the K-major operand layout of the tensor-core GEMM); box_inner
+// times the element size must be at most 128 bytes.
+bool encode_2d_swz128(rsk_handle* h, CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                      uint64_t outer, uint64_t row_stride_bytes, uint32_t box_inner, uint32_t box_outer);
+
 // Sparse sign apply with caller-provided scratch for the per-range partials (used by solvers that
 // carve their own buffers out of the workspace).  sketch_partial_bytes gives the size needed.
 size_t sketch_partial_bytes(rsk_handle* h, int64_t n, int64_t k, int64_t d, int zeta, rsk_dtype a_dt);

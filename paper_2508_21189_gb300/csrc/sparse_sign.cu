@@ -308,9 +308,9 @@ struct AccF32 {
         reinterpret_cast<float4*>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
     }
 };
-// bf16 words are unpacked with the sign folded in: the low half becomes w*2^16 + s and the high
-// half (w & 0xffff0000) ^ s, where s is 0 or 0x80000000 (adding 2^31 modulo 2^32 flips the top bit),
-// then both halves are accumulated with one packed f32x2 add.
+// bf16 entries are accumulated with the mixed-precision FMA acc = x * s + acc (x and s bf16, acc
+// FP32), s = +-1 carrying the sign: the product is exact, so each step rounds once, exactly like an
+// FP32 add of the widened entry, at one instruction per element and no unpacking.
 struct AccBF16 {
     static constexpr int kVec = 8;
     using store_t = float;
@@ -319,15 +319,29 @@ struct AccBF16 {
 #pragma unroll
         for (int i = 0; i < 4; ++i) v[i] = make_float2(0.f, 0.f);
     }
-    __device__ __forceinline__ static float2 unpack(uint32_t w, uint32_t sm) {
-        return make_float2(__uint_as_float(w * 65536u + sm), __uint_as_float((w & 0xffff0000u) ^ sm));
+    // acc += (low or high bf16 half of w) * s, s the bf16 pattern in the low 16 bits of `one`
+    __device__ __forceinline__ static void fma_lo(float& acc, uint32_t w, uint32_t one) {
+        asm("{\n\t.reg .b16 lo, hi, s;\n\tmov.b32 {lo, hi}, %1;\n\tcvt.u16.u32 s, %2;\n\t"
+            "fma.rn.f32.bf16 %0, lo, s, %0;\n\t}"
+            : "+f"(acc)
+            : "r"(w), "r"(one));
+    }
+    __device__ __forceinline__ static void fma_hi(float& acc, uint32_t w, uint32_t one) {
+        asm("{\n\t.reg .b16 lo, hi, s;\n\tmov.b32 {lo, hi}, %1;\n\tcvt.u16.u32 s, %2;\n\t"
+            "fma.rn.f32.bf16 %0, hi, s, %0;\n\t}"
+            : "+f"(acc)
+            : "r"(w), "r"(one));
     }
     __device__ __forceinline__ void add(const uint4 x, uint32_t negative) {
-        const uint32_t sm = negative << 31;
-        v[0] = __fadd2_rn(v[0], unpack(x.x, sm));
-        v[1] = __fadd2_rn(v[1], unpack(x.y, sm));
-        v[2] = __fadd2_rn(v[2], unpack(x.z, sm));
-        v[3] = __fadd2_rn(v[3], unpack(x.w, sm));
+        const uint32_t one = 0x3f80u | (negative << 15);  // bf16 +1 or -1
+        fma_lo(v[0].x, x.x, one);
+        fma_hi(v[0].y, x.x, one);
+        fma_lo(v[1].x, x.y, one);
+        fma_hi(v[1].y, x.y, one);
+        fma_lo(v[2].x, x.z, one);
+        fma_hi(v[2].y, x.z, one);
+        fma_lo(v[3].x, x.w, one);
+        fma_hi(v[3].y, x.w, one);
     }
     __device__ __forceinline__ void store(float* dst) const {
         reinterpret_cast<float4*>(dst)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
