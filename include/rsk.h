@@ -87,6 +87,9 @@ typedef enum {
     RSK_KERNEL_SRTT_REDUCE = 5,
     RSK_KERNEL_DENSE = 6,          /* LSQ / RSVD dense helpers (QR, solves, matvecs) */
     RSK_KERNEL_GEMM = 7,           /* BF16 tensor-core GEMMs of the RSVD             */
+    RSK_KERNEL_FACTOR = 8,         /* small Cholesky factorisations and R^{-1}       */
+    RSK_KERNEL_SMALL_SVD = 9,      /* one-sided Jacobi SVD of a small matrix         */
+    RSK_KERNEL_CONVERT = 10,       /* BF16 conversions and three-term splits         */
     RSK_KERNEL_COUNT = 16
 } rsk_kernel_id;
 /* Turn recording on (on != 0) or off.  Turning it on clears earlier records. */
@@ -203,6 +206,17 @@ rsk_status rsk_sparse_stack_generate(rsk_handle* h, int64_t n, int64_t d, int32_
 rsk_status rsk_sparse_stack_apply(rsk_handle* h, const void* A, rsk_dtype a_dtype, int64_t n, int64_t k,
                                   int64_t lda, int64_t d, int32_t zeta, uint64_t seed, void* SA,
                                   rsk_dtype sa_dtype, int64_t ldsa, cudaStream_t stream);
+
+/* Right sketch Y = A Omega with Omega = S^T (Sec. 2: the test matrices of Algs. 1, 2, 4, 5 multiply A
+ * from the right), S the k x dc sparse sign of the given kind (0 SparseUniform, 1 SparseStack with
+ * k % zeta == 0) drawn from `seed` on Philox stream `philox_stream` (-1: the kind's own stream, 0 or 4;
+ * the RSVD test matrix is stream 3).  A device FP32 n x dc row-major (lda >= dc); Y device FP32 n x k
+ * column-major (ldy >= n): Y[i, c] = zeta^{-1/2} sum over the entries (j, sign) of row c of S of
+ * sign * A[i, j], summed in increasing j (deterministic).  Limits: k <= 512, 1 <= zeta <= min(k, 32).
+ * The inverted index of S comes from the handle's workspace.  Asynchronous. */
+rsk_status rsk_sparse_sign_apply_right(rsk_handle* h, int32_t kind, const float* A, int64_t n, int64_t dc,
+                                       int64_t lda, int64_t k, int32_t zeta, uint64_t seed, int32_t philox_stream,
+                                       float* Y, int64_t ldy, cudaStream_t stream);
 
 /* Plans keep the inverted index of one S for repeated application (e.g. to A and then to b).
  * The plan owns device memory allocated on `stream`; destroy it with rsk_sparse_sign_plan_destroy. */
@@ -400,6 +414,15 @@ rsk_status rsk_svd_econ(rsk_handle* h, const float* A, int64_t m, int64_t q, int
  * A Cholesky pivot that is not positive is recorded in the device status word (rsk_sync_status). */
 rsk_status rsk_qr_econ(rsk_handle* h, const float* X, int64_t m, int64_t q, int64_t ldx, float* Q, int64_t ldq,
                        float* R, cudaStream_t stream);
+/* Upper Cholesky factor (Alg. 2's chol): R^T R = sym(G) + s I with s = shift_coeff * trace(G), G
+ * read from its upper triangle, R q x q upper triangular with zeros below the diagonal.  Blocked
+ * right-looking factorisation in one CTA (q <= 330, RSK_ERR_UNSUPPORTED beyond).  A pivot that is not
+ * positive is recorded in the device status word (rsk_sync_status) and R is then undefined. */
+rsk_status rsk_cholesky(rsk_handle* h, const float* G, int64_t q, int64_t ldg, float shift_coeff, float* R,
+                        int64_t ldr, cudaStream_t stream);
+/* Ri = R^{-1} for an upper triangular R (q x q, ldr; Ri has leading dimension ldr, zeros below the
+ * diagonal): back substitution, one warp per column.  q <= 880 (RSK_ERR_UNSUPPORTED beyond). */
+rsk_status rsk_trinv(rsk_handle* h, const float* R, int64_t q, int64_t ldr, float* Ri, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Randomized Nystrom approximation of a psd matrix (Alg. 2, Sec. 2.2) with a structured test matrix:
@@ -460,6 +483,24 @@ rsk_status rsk_osi_estimate(rsk_handle* h, int64_t r, int64_t k, int32_t zeta, u
  * Asynchronous. */
 rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B, int64_t N,
                          int64_t ldb, float* D, int64_t ldd, int32_t nsplit, cudaStream_t stream);
+/* The same product with the operand and output layouts of the RSVD's steps: a_mn != 0 takes A
+ * MN-major, i.e. element (m, k) at A[k * lda + m] (lda >= M: A^T of a row-major K x M matrix, so that
+ * Z = A^T Q reads A in place); d_row_major != 0 stores D row-major (element (m, n) at D[m * ldd + n],
+ * ldd >= N) instead of column-major.  Alignment, limits and nsplit as rsk_gemm_bf16. */
+rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* A, int64_t M, int64_t K, int64_t lda,
+                            const void* B, int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t d_row_major,
+                            int32_t nsplit, cudaStream_t stream);
+/* D = A B^T for FP32 device A, B at FP32 accuracy on the BF16 tensor cores: each operand is split into
+ * three BF16 terms (x = x1 + x2 + x3 + O(2^-24 |x|)) and the six products x_i y_j with i + j <= 4
+ * accumulate in FP32 in tensor memory, the corrections first and x1 y1 last.  The tensor cores' FP32
+ * accumulation rounds toward zero, so a same-sign sum carries a relative bias of up to about 2^-24
+ * per 16-wide K step accumulated per split (ceil(K / nsplit / 16) steps); split K to bound it.  The
+ * products of the RSVD's orthonormalisation (Gram matrices X^T X, X R^{-1}) and of U = Q Uhat.  Layouts as rsk_gemm_bf16_ex (FP32 elements); any lda, ldb
+ * covering the operand.  The splits and the split-K partials come from the handle's workspace.
+ * Asynchronous. */
+rsk_status rsk_gemm_f32(rsk_handle* h, int32_t a_mn, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
+                        int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t d_row_major, int32_t nsplit,
+                        cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
  * a9: randomized SVD with a sparse sign test matrix (Alg. 1, Sec. 2.1) and power_iters subspace

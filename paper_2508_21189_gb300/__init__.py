@@ -247,6 +247,24 @@ def rsk_sparse_stack_apply(A, d, zeta, seed, out_dtype=torch.float32, out=None, 
     return out
 
 
+def rsk_sparse_sign_apply_right(A, k, zeta, seed, kind=0, philox_stream=-1, out=None, stream=None):
+    """Y = A @ S.T (n x k, returned as a column-major view) for S the k x dc sparse sign of `kind`
+    (0 SparseUniform, 1 SparseStack) on Philox stream `philox_stream` (-1: the kind's own)."""
+    _matrix(A, "A")
+    if A.dtype != torch.float32:
+        raise TypeError("the right sketch takes FP32 A")
+    n, dc = A.shape
+    if out is None:
+        out = torch.empty(k, n, dtype=torch.float32, device=A.device).t()
+    if out.shape != (n, k) or out.stride(0) != 1 or out.dtype != torch.float32:
+        raise ValueError("out must be an FP32 n x k column-major view")
+    h = handle(A.device)
+    st = load().rsk_sparse_sign_apply_right(h, kind, A.data_ptr(), n, dc, A.stride(0), k, zeta, seed, philox_stream,
+                                            out.data_ptr(), out.stride(1), _stream(stream))
+    _check(st, h)
+    return out
+
+
 def rsk_sparse_sign_apply_rows(A, row0, d, zeta, seed, out_dtype=torch.float32, out=None, stream=None):
     """Partial sketch S[:, row0:row0+n] @ A of a row block A (n x k) of a row-sharded matrix."""
     _matrix(A, "A")
@@ -395,6 +413,27 @@ def rsk_svd_econ(A, stream=None):
     return U, s, V
 
 
+def rsk_cholesky(G, shift_coeff=0.0, stream=None):
+    """Upper Cholesky factor R of sym(G) + shift_coeff * trace(G) I for a column-major CUDA FP32 G."""
+    _colmajor(G, "G")
+    q = G.shape[0]
+    R = torch.empty(q, q, device=G.device).t()
+    h = handle(G.device)
+    _check(load().rsk_cholesky(h, G.data_ptr(), q, G.stride(1), float(shift_coeff), R.data_ptr(), R.stride(1),
+                               _stream(stream)), h)
+    return R
+
+
+def rsk_trinv(R, stream=None):
+    """R^{-1} of an upper triangular column-major CUDA FP32 R."""
+    _colmajor(R, "R")
+    q = R.shape[0]
+    Ri = torch.empty(q, q, device=R.device).t()
+    h = handle(R.device)
+    _check(load().rsk_trinv(h, R.data_ptr(), q, R.stride(1), Ri.data_ptr(), _stream(stream)), h)
+    return Ri
+
+
 def rsk_qr_econ(X, stream=None):
     """Thin QR of a column-major CUDA FP32 matrix X (m x q): returns (Q column-major, R upper q x q)."""
     _colmajor(X, "X")
@@ -490,6 +529,47 @@ def rsk_gemm_bf16(A, B, nsplit=1, stream=None):
     return D
 
 
+def _gemm_operands(A, B, a_mn, dtype):
+    _matrix(A, "A")
+    _matrix(B, "B")
+    if A.dtype != dtype or B.dtype != dtype:
+        raise ValueError(f"A and B must be {dtype}")
+    # a_mn: the product's A operand is A.T (A given K x M row-major, read MN-major in place)
+    M, K = (A.shape[1], A.shape[0]) if a_mn else (A.shape[0], A.shape[1])
+    if B.shape[1] != K:
+        raise ValueError("B must have K columns")
+    return M, K, B.shape[0]
+
+
+def _gemm_out(M, N, row_major_out, device):
+    return torch.empty(M, N, device=device) if row_major_out else torch.empty(N, M, device=device).t()
+
+
+def rsk_gemm_bf16_ex(A, B, a_mn=False, row_major_out=False, nsplit=1, stream=None):
+    """D = op(A) @ B.T on the tensor cores, BF16 operands, FP32 D (M x N).  op(A) = A.T when a_mn (A is
+    K x M row-major, read in place as an MN-major operand), else A (M x K).  D row-major when
+    row_major_out, else a column-major view."""
+    M, K, N = _gemm_operands(A, B, a_mn, torch.bfloat16)
+    D = _gemm_out(M, N, row_major_out, A.device)
+    h = handle(A.device)
+    _check(load().rsk_gemm_bf16_ex(h, int(a_mn), A.data_ptr(), M, K, A.stride(0), B.data_ptr(), N, B.stride(0),
+                                   D.data_ptr(), D.stride(0) if row_major_out else D.stride(1), int(row_major_out),
+                                   nsplit, _stream(stream)), h)
+    return D
+
+
+def rsk_gemm_f32(A, B, a_mn=False, row_major_out=False, nsplit=1, stream=None):
+    """D = op(A) @ B.T for FP32 operands at FP32 accuracy (three-term BF16 splits on the tensor cores);
+    layouts as rsk_gemm_bf16_ex."""
+    M, K, N = _gemm_operands(A, B, a_mn, torch.float32)
+    D = _gemm_out(M, N, row_major_out, A.device)
+    h = handle(A.device)
+    _check(load().rsk_gemm_f32(h, int(a_mn), A.data_ptr(), M, K, A.stride(0), B.data_ptr(), N, B.stride(0),
+                               D.data_ptr(), D.stride(0) if row_major_out else D.stride(1), int(row_major_out), nsplit,
+                               _stream(stream)), h)
+    return D
+
+
 def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
     """Randomized SVD of a CUDA FP32 tensor A (m x n): returns (U [m, r] FP32, s [r] FP64, Vt [r, n] FP32)."""
     _matrix(A, "A")
@@ -508,7 +588,8 @@ def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
 
 # Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).
 KERNEL_IDS = {"sketch_index": 0, "sketch_apply": 1, "sketch_reduce": 2, "sketch_generate": 3,
-              "srtt_apply": 4, "srtt_reduce": 5, "dense": 6, "gemm": 7}
+              "srtt_apply": 4, "srtt_reduce": 5, "dense": 6, "gemm": 7, "factor": 8, "small_svd": 9,
+              "convert": 10}
 
 
 def rsk_profile_enable(on=True, device=None):

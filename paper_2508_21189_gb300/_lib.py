@@ -37,6 +37,8 @@ SIGNATURES = {
     "rsk_sparse_sign_apply_host": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_stack_generate": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p, c_p],
     "rsk_sparse_stack_apply": [c_p, c_p, c_i32, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_p, c_i32, c_i64, c_p],
+    "rsk_sparse_sign_apply_right": [c_p, c_i32, c_p, c_i64, c_i64, c_i64, c_i64, c_i32, c_u64, c_i32, c_p, c_i64,
+                                    c_p],
     "rsk_sparse_sign_plan_create": [c_p, c_i64, c_i64, c_i32, c_u64, c_p, c_p],
     "rsk_sparse_sign_plan_apply": [c_p, c_p, c_p, c_i32, c_i64, c_i64, c_p, c_i32, c_i64, c_p],
     "rsk_sparse_sign_plan_destroy": [c_p, c_p, c_p],
@@ -50,6 +52,8 @@ SIGNATURES = {
     "rsk_lstsq_sketch_precond_batched": [c_p, c_i32, c_p, c_p, c_p, c_p],
     "rsk_svd_econ": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_p, c_p, c_i64, c_p],
     "rsk_qr_econ": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_p, c_p],
+    "rsk_cholesky": [c_p, c_p, c_i64, c_i64, ctypes.c_float, c_p, c_i64, c_p],
+    "rsk_trinv": [c_p, c_p, c_i64, c_i64, c_p, c_p],
     "rsk_nystrom_psd": [c_p, c_p, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_i32, c_p, c_i64, c_p, c_p],
     "rsk_gen_nystrom": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_i32, c_i32, c_p, c_i64, c_p, c_p,
                         c_i64, c_p, c_p],
@@ -62,6 +66,8 @@ SIGNATURES = {
     "rsk_autotune_sketch": [c_p, c_i32, c_i32, c_i64, c_i64, c_i64, c_i32, c_p, c_p, c_p],
     "rsk_autotune_batched": [c_p, c_i32, c_p, c_p, c_p, c_p, c_p],
     "rsk_gemm_bf16": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_p],
+    "rsk_gemm_bf16_ex": [c_p, c_i32, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_i32, c_p],
+    "rsk_gemm_f32": [c_p, c_i32, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_i32, c_p],
     "rsk_rsvd": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_p, c_p, c_p, c_p],
 }
 

@@ -121,9 +121,11 @@ rsk_status sketch_generate(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64
 rsk_status sketch_generate_kind(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, int kind, int32_t* rows,
                                 uint32_t* signs, cudaStream_t stream);
 // Right sketch Y = A Omega = A S^T for A n x dc row-major FP32 and S the k x dc sketch of the kind: Y is
-// n x k column-major (ldy >= n).  Uses the handle's workspace for the inverted index of S.
+// n x k column-major (ldy >= n).  S comes from the kind's Philox stream, or from `stream_id` when it is
+// not ~0u.  Uses the handle's workspace for the inverted index of S.
 rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n, int64_t dc, int64_t lda, int64_t k,
-                              int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream);
+                              int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream,
+                              uint32_t stream_id = ~0u);
 rsk_status sketch_generate_large(rsk_handle* h, int64_t n, int64_t d, int zeta, uint64_t seed, int kind, int32_t* rows,
                                  uint32_t* signs, cudaStream_t stream);
 rsk_status sketch_apply_kind(rsk_handle* h, int kind, const void* A, rsk_dtype a_dt, int64_t n, int64_t k,

@@ -4,8 +4,10 @@
 //   k_gram          X^T Y over a chunk of rows: 64 x 64 output tile per CTA, 4 x 4 per thread, the rows
 //                   staged 32 at a time; per-chunk partials summed in chunk order by k_gram_reduce.
 //   k_matmul_ts     C = X M for tall X: 128 x 64 output tile per CTA, K in steps of 16.
-//   k_cholesky      one CTA: right-looking Cholesky on the packed upper triangle in shared memory.
-//   k_trinv         one CTA per column j of R^{-1}: column-oriented back substitution.
+//   k_cholesky      one CTA: blocked right-looking Cholesky on the packed upper triangle in shared
+//                   memory (16-row panels, register-tiled trailing update).
+//   k_trinv         one warp per column j of R^{-1}: column-oriented back substitution, the columns of
+//                   R staged 32 at a time through shared memory.
 //   k_jacobi        one-sided block Jacobi (Hestenes) on a cooperative grid: the q columns are dealt
 //                   into nb = 2G blocks; in each of the nb - 1 rounds of a sweep CTA g takes one pair
 //                   of blocks (round-robin), copies their columns (and V's) into shared memory,
@@ -166,42 +168,130 @@ __global__ void __launch_bounds__(256) k_matmul_ts(const float* __restrict__ X, 
 // ------------------------------------------------------------------------------------------
 // Cholesky (packed upper triangle in shared memory) and triangular inverse.
 // ------------------------------------------------------------------------------------------
-constexpr int kCholMax = 330;
+constexpr int kCholMax = 330;  // packed triangle + panel buffer within 227 KB of shared memory
 __device__ __forceinline__ int pk(int i, int j, int q) { return i * q - (i * (i - 1)) / 2 + (j - i); }
 
-__global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, int q, int64_t ldg, float shift_coeff,
+// Blocked right-looking Cholesky sym(G) + s I = R^T R (s = shift_coeff * trace(G)) in one CTA, the
+// upper triangle packed in shared memory.  Per panel of kCP rows (16; 8 when q > 320, so that the
+// triangle and the panel buffer fit in shared memory) (c0 .. c1-1):
+//   A  warp 0 factors the diagonal block in registers (a lane per column, shuffles for the rows);
+//   B  one thread per trailing column t >= c1 solves R_pp^T R(c0:c1, t) = U(c0:c1, t) (forward
+//      substitution against the just-factored block), into the panel buffer P and the triangle;
+//   C  the trailing upper triangle takes the rank-kCP update U(a, b) -= sum_k P(k, a) P(k, b), in
+//      4 x 4 register tiles (two 16-byte loads per k).
+// Three barriers per panel; R is written from the packed factor at the end.  A pivot that is not
+// positive (or not finite) stops the factorisation and sets RSK_DEV_BOUNDS.
+constexpr int kCholThreads = 512;  // 128 registers a thread: the 4 x 4 tiles and the solve stay in registers
+template <int kCP>
+__global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restrict__ G, int q, int64_t ldg, float shift_coeff,
                                                   float* __restrict__ R, int64_t ldr, unsigned int* status) {
     extern __shared__ __align__(16) float U[];
-    __shared__ float piv_s, trace_s;
+    const int qp = (q + 3) & ~3;                                 // panel buffer pitch (16-byte rows)
+    float* P = U + (q * (q + 1) / 2 + 3) / 4 * 4;                // kCP x qp
+    __shared__ float part[32];
+    __shared__ float Rpp[kCP * kCP];   // the panel's diagonal block, reciprocal pivots on the diagonal
     __shared__ int fail_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    // trace for the shift (the Frobenius norm squared of the factored matrix when G = X^T X)
-    if (tid == 0) {
-        float t = 0.f;
-        for (int i = 0; i < q; ++i) t += G[int64_t(i) * ldg + i];
-        trace_s = t;
-        fail_s = 0;
-    }
+    float t = 0.f;
+    for (int i = tid; i < q; i += blockDim.x) t += G[int64_t(i) * ldg + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) part[warp] = t;
+    if (tid == 0) fail_s = 0;
     __syncthreads();
-    const float shift = shift_coeff * trace_s;
-    for (int i = warp; i < q; i += nw)
-        for (int j = i + lane; j < q; j += 32) U[pk(i, j, q)] = G[int64_t(j) * ldg + i] + (i == j ? shift : 0.f);
+    float trace = 0.f;
+    for (int w = 0; w < nw; ++w) trace += part[w];
+    const float shift = shift_coeff * trace;
+    // the upper triangle column by column (coalesced: column j's rows 0 .. j are contiguous)
+    for (int j = warp; j < q; j += nw)
+#pragma unroll 4
+        for (int i = lane; i <= j; i += 32) U[pk(i, j, q)] = G[int64_t(j) * ldg + i] + (i == j ? shift : 0.f);
+    for (int e = tid; e < kCP * (qp - q); e += blockDim.x) P[(e / (qp - q)) * qp + q + e % (qp - q)] = 0.f;
     __syncthreads();
-    for (int j = 0; j < q; ++j) {
-        if (tid == 0) {
-            const float d = U[pk(j, j, q)];
-            if (!(d > 0.f) || !isfinite(d)) fail_s = 1;
-            piv_s = fail_s ? 1.f : sqrtf(d);
-            U[pk(j, j, q)] = piv_s;
+    for (int c0 = 0; c0 < q; c0 += kCP) {
+        const int c1 = min(q, c0 + kCP), nb = c1 - c0;
+        // A: the diagonal block, in registers: lane j < nb holds column j (a[i] = U(c0+i, c0+j), i <= j);
+        // at step k lane k's diagonal is broadcast, row k is scaled in place, and lane j >= i takes
+        // a[i] -= R(k, i) R(k, j) with R(k, i) broadcast from lane i.  The factor goes to R, to the
+        // packed triangle's block and, with reciprocal pivots, to Rpp for step B.
+        if (warp == 0) {
+            float a[kCP];
+#pragma unroll
+            for (int i = 0; i < kCP; ++i) a[i] = (lane < nb && i <= lane) ? U[pk(c0 + i, c0 + lane, q)] : 0.f;
+            bool bad = false;
+#pragma unroll
+            for (int k = 0; k < kCP; ++k) {
+                if (k < nb) {
+                    const float dk = __shfl_sync(0xffffffffu, a[k], k);
+                    bad = bad || !(dk > 0.f) || !isfinite(dk);
+                    const float rk = sqrtf(dk);
+                    if (lane == k) a[k] = rk;
+                    else if (lane > k) a[k] = a[k] / rk;
+#pragma unroll
+                    for (int i = k + 1; i < kCP; ++i) {
+                        const float rki = __shfl_sync(0xffffffffu, a[k], i);
+                        if (lane >= i) a[i] -= rki * a[k];
+                    }
+                }
+            }
+            if (lane < nb) {
+#pragma unroll
+                for (int i = 0; i < kCP; ++i)
+                    if (i <= lane) {
+                        U[pk(c0 + i, c0 + lane, q)] = a[i];
+                        Rpp[i * kCP + lane] = i == lane ? 1.f / a[i] : a[i];
+                    }
+            }
+            if (lane == 0 && bad) fail_s = 1;
         }
         __syncthreads();
         if (fail_s) break;
-        const float rinv = 1.f / piv_s;
-        for (int k = j + 1 + tid; k < q; k += blockDim.x) U[pk(j, k, q)] *= rinv;
+        // B: the panel's rows right of the block, one thread per column: R_pp^T x = U(c0:c1, t)
+        for (int tt = c1 + tid; tt < q; tt += blockDim.x) {
+            float x[kCP];
+#pragma unroll
+            for (int k = 0; k < kCP; ++k) {
+                if (k < nb) {
+                    float v = U[pk(c0 + k, tt, q)];
+#pragma unroll
+                    for (int i = 0; i < k; ++i) v -= Rpp[i * kCP + k] * x[i];
+                    x[k] = v * Rpp[k * kCP + k];
+                    P[k * qp + tt] = x[k];
+                    U[pk(c0 + k, tt, q)] = x[k];
+                }
+            }
+        }
+        for (int k = nb + warp; k < kCP; k += nw)   // rows of a short last panel: zero
+            for (int tt = lane; tt < qp; tt += 32) P[k * qp + tt] = 0.f;
         __syncthreads();
-        for (int i = j + 1 + warp; i < q; i += nw) {
-            const float uji = U[pk(j, i, q)];
-            for (int k = i + lane; k < q; k += 32) U[pk(i, k, q)] -= uji * U[pk(j, k, q)];
+        // C: trailing update in 4 x 4 tiles (a0 <= b0, both multiples of 4 from c1)
+        const int nt = (q - c1 + 3) / 4;
+        for (int e = tid; e < nt * nt; e += blockDim.x) {
+            const int ia = e / nt, ib = e - ia * nt;
+            if (ib < ia) continue;
+            const int a0 = c1 + 4 * ia, b0 = c1 + 4 * ib;
+            float acc[4][4] = {};
+#pragma unroll
+            for (int k = 0; k < kCP; ++k) {
+                const float4 pa = *reinterpret_cast<const float4*>(P + k * qp + a0);
+                const float4 pb = *reinterpret_cast<const float4*>(P + k * qp + b0);
+                const float va[4] = {pa.x, pa.y, pa.z, pa.w}, vb[4] = {pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] = fmaf(va[i], vb[j2], acc[i][j2]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int a = a0 + i;
+                if (a >= q) break;
+                const int base = pk(a, a, q) - a;
+#pragma unroll
+                for (int j2 = 0; j2 < 4; ++j2) {
+                    const int b = b0 + j2;
+                    if (b >= a && b < q) U[base + b] -= acc[i][j2];
+                }
+            }
         }
         __syncthreads();
     }
@@ -209,23 +299,54 @@ __global__ void __launch_bounds__(1024) k_cholesky(const float* __restrict__ G, 
         if (tid == 0) atomicOr(status, RSK_DEV_BOUNDS);
         return;
     }
-    for (int j = warp; j < q; j += nw)
-        for (int i = lane; i < q; i += 32) R[int64_t(j) * ldr + i] = i <= j ? U[pk(i, j, q)] : 0.f;
+    // R from the packed factor, column by column (coalesced), zeros below the diagonal
+    for (int c = warp; c < q; c += nw)
+#pragma unroll 4
+        for (int i = lane; i < q; i += 32) R[int64_t(c) * ldr + i] = i <= c ? U[pk(i, c, q)] : 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_trinv(const float* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri) {
-    extern __shared__ float x[];
-    const int j = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < q; i += blockDim.x) x[i] = (i == j) ? 1.f : 0.f;
-    __syncthreads();
-    for (int i = j; i >= 0; --i) {
-        const float xi = x[i] / R[int64_t(i) * ldr + i];
+// Ri = R^{-1} for an upper triangular R (column-major, ldr): warp w of CTA b solves R x = e_j for
+// j = 32 b + w by column-oriented back substitution (x_k = b_k / R_kk, then b_i -= R_ik x_k for i < k)
+// on its right-hand side in shared memory; the columns of R it reads are staged 32 at a time into
+// shared memory by the whole CTA, from the highest down, with the reciprocals of their pivots.
+constexpr int kTrinvCols = 32;
+constexpr int kTrinvMax = 880;  // (32 staged columns + 32 right-hand sides) x q floats within 227 KB
+__global__ void __launch_bounds__(1024) k_trinv(const float* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri) {
+    extern __shared__ __align__(16) float tsm[];
+    float* Rs = tsm;                        // kTrinvCols columns x q rows
+    float* bs = tsm + kTrinvCols * q;       // one right-hand side (q) per warp
+    __shared__ float rinv[kTrinvCols];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int j = blockIdx.x * kTrinvCols + warp;
+    float* b = bs + warp * q;
+    for (int i = lane; i < q; i += 32) b[i] = (i == j) ? 1.f : 0.f;
+    const int jmax = min(q - 1, blockIdx.x * kTrinvCols + kTrinvCols - 1);
+    for (int k0 = jmax / kTrinvCols * kTrinvCols; k0 >= 0; k0 -= kTrinvCols) {
+        const int k1 = min(k0 + kTrinvCols, jmax + 1);   // stage columns k0 .. k1-1, rows 0 .. k1-1
         __syncthreads();
-        if (tid == 0) x[i] = xi;
-        for (int k = tid; k < i; k += blockDim.x) x[k] -= R[int64_t(i) * ldr + k] * xi;
+#pragma unroll 4
+        for (int e = tid; e < (k1 - k0) * k1; e += blockDim.x) {   // column c = e / k1, rows < k1
+            const int c = e / k1, i = e - c * k1;
+            if (i <= k0 + c) Rs[c * q + i] = R[int64_t(k0 + c) * ldr + i];
+        }
+        if (tid < k1 - k0) rinv[tid] = 1.f / R[int64_t(k0 + tid) * ldr + k0 + tid];
         __syncthreads();
+        if (j < q) {
+            for (int k = min(k1 - 1, j); k >= k0; --k) {
+                const float* rc = Rs + (k - k0) * q;
+                // b[k] is final here (no later step touches it); x_k replaces it once every lane has
+                // read it (after the step's warp barrier), and the update touches only b[0 .. k-1]
+                const float xk = b[k] * rinv[k - k0];
+#pragma unroll 4
+                for (int i = lane; i < k; i += 32) b[i] -= rc[i] * xk;
+                __syncwarp();
+                if (lane == (k & 31)) b[k] = xk;
+            }
+        }
     }
-    for (int i = tid; i < q; i += blockDim.x) Ri[int64_t(j) * ldr + i] = x[i];
+    __syncwarp();
+    if (j < q)
+        for (int i = lane; i < q; i += 32) Ri[int64_t(j) * ldr + i] = i <= j ? b[i] : 0.f;
 }
 
 // FP64 variant for the accurate orthonormalisation: R (q x q column-major, ldr) holds G on entry
@@ -535,15 +656,22 @@ rsk_status matmul_ts(rsk_handle* h, const float* X, int64_t m, int p, int64_t ld
 rsk_status cholesky(rsk_handle* h, const float* G, int q, int64_t ldg, float shift_coeff, float* R, int64_t ldr,
                     cudaStream_t stream) {
     if (q < 1 || q > kCholMax) return fail(h, RSK_ERR_UNSUPPORTED, "cholesky supports 1 <= q <= %d (got %d)", kCholMax, q);
-    const int smem = int((size_t(q) * (q + 1) / 2) * 4);
-    RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_cholesky<<<1, 1024, smem, stream>>>(G, q, ldg, shift_coeff, R, ldr, h->dev_status);
-    RSK_LAUNCH_CHECK(h);
-    return RSK_OK;
+    const int panel = q <= 320 ? 16 : 8;
+    const int smem = int(((size_t(q) * (q + 1) / 2 + 3) / 4 * 4 + size_t(panel) * ((q + 3) & ~3)) * 4);
+    auto go = [&](auto kern) -> rsk_status {
+        RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        kern<<<1, kCholThreads, smem, stream>>>(G, q, ldg, shift_coeff, R, ldr, h->dev_status);
+        RSK_LAUNCH_CHECK(h);
+        return RSK_OK;
+    };
+    return panel == 16 ? go(k_cholesky<16>) : go(k_cholesky<8>);
 }
 
 rsk_status trinv(rsk_handle* h, const float* R, int q, int64_t ldr, float* Ri, cudaStream_t stream) {
-    k_trinv<<<unsigned(q), 256, size_t(q) * 4, stream>>>(R, q, ldr, Ri);
+    if (q < 1 || q > kTrinvMax) return fail(h, RSK_ERR_UNSUPPORTED, "trinv supports 1 <= q <= %d (got %d)", kTrinvMax, q);
+    const int smem = (kTrinvCols + 32) * q * 4;
+    RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_trinv<<<unsigned((q + kTrinvCols - 1) / kTrinvCols), 1024, smem, stream>>>(R, q, ldr, Ri);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
@@ -739,6 +867,27 @@ rsk_status rsk_qr_econ(rsk_handle* h, const float* X, int64_t m, int64_t q, int6
     RSK_CUDA_TRY(h, cudaMemcpy2DAsync(Q, size_t(ldq) * 4, X, size_t(ldx) * 4, size_t(m) * 4, size_t(q),
                                       cudaMemcpyDeviceToDevice, stream));
     return rsk::dense::orth_accurate(h, Q, m, int(q), ldq, R, h->ws, stream);
+}
+
+rsk_status rsk_cholesky(rsk_handle* h, const float* G, int64_t q, int64_t ldg, float shift_coeff, float* R,
+                        int64_t ldr, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!G || !R) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (q < 1 || ldg < q || ldr < q) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need q >= 1, ldg, ldr >= q");
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_FACTOR);
+    const rsk_status st = rsk::dense::cholesky(h, G, int(q), ldg, shift_coeff, R, ldr, stream);
+    rsk::prof_end(h, stream, pr);
+    return st;
+}
+
+rsk_status rsk_trinv(rsk_handle* h, const float* R, int64_t q, int64_t ldr, float* Ri, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!R || !Ri) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (q < 1 || ldr < q) return rsk::fail(h, RSK_ERR_INVALID_ARG, "need q >= 1, ldr >= q");
+    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_DENSE);
+    const rsk_status st = rsk::dense::trinv(h, R, int(q), ldr, Ri, stream);
+    rsk::prof_end(h, stream, pr);
+    return st;
 }
 
 }  // extern "C"

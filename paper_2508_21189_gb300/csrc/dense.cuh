@@ -22,10 +22,10 @@ rsk_status gram(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, co
 rsk_status matmul_ts(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* M, int q,
                      int64_t ldm, float* C, int64_t ldc, cudaStream_t stream);
 
-// Upper Cholesky factor R (q x q, ldr, zeros below the diagonal) of sym(G) + shift I, G read from
-// its upper triangle (q <= 330).  A pivot that is not positive (or not finite) sets RSK_DEV_BOUNDS
-// and R is then undefined.
-rsk_status cholesky(rsk_handle* h, const float* G, int q, int64_t ldg, float shift, float* R, int64_t ldr,
+// Upper Cholesky factor R (q x q, ldr, zeros below the diagonal) of sym(G) + s I, s = shift_coeff *
+// trace(G), G read from its upper triangle (q <= 330).  A pivot that is not positive (or not finite)
+// sets RSK_DEV_BOUNDS and R is then undefined.
+rsk_status cholesky(rsk_handle* h, const float* G, int q, int64_t ldg, float shift_coeff, float* R, int64_t ldr,
                     cudaStream_t stream);
 
 // Ri = R^{-1} for an upper triangular q x q R (both ldr; Ri upper, zeros below).

@@ -1,27 +1,28 @@
-// BF16 x BF16 -> FP32 GEMM on the fifth-generation tensor cores (tcgen05), both operands K-major:
-//     D (M x N, column-major, ldd) = A (M x K) * B (N x K)^T
-// the dense products of the randomized SVD (Alg. 1: Z = A^T Q, Y = A Z, B = Q^T A) with the
-// rank r <= 512 as the N dimension.
+// BF16 x BF16 -> FP32 products on the fifth-generation tensor cores (tcgen05): the dense products of
+// the randomized SVD (Alg. 1: Y = A Z, Z = A^T Q, B = Q^T A) with the rank r <= 512 as the N dimension,
+// and, through three-term BF16 splits, the FP32-accurate products of its orthonormalisation (Gram
+// matrices X^T X, X R^{-1}) and of U = Q Uhat.
 //
 // One CTA per 128-row tile of D (and per K split): 6 warps.
-//   warp 0, one thread   TMA producer: per 64-wide K block, the 128 x 64 tile of A and the N x 64 tile of
-//                        B (two boxes of N/2 rows) into one of 3 shared-memory stages (2 when N = 512; 128-byte swizzle),
-//                        completion counted on the stage's `full` mbarrier
+//   warp 0, one thread   TMA producer: per 64-wide K block (of every pass), the 128 x 64 tile of A (one
+//                        box for K-major A, two 64 x 64 boxes for MN-major A) and the N x 64 tile of B
+//                        (two boxes of N/2 rows) into one of 3 shared-memory stages (2 when N = 512;
+//                        128-byte swizzle), completion counted on the stage's `full` mbarrier
 //   warp 1, one thread   MMA issuer: per K block, 4 K-steps of 16, each two tcgen05.mma (M = 128,
 //                        N = N/2) into the TMEM accumulator (128 lanes x N FP32 columns); a tcgen05.commit
 //                        on the stage's `empty` barrier frees it, a last one on `tmem_full` hands the
 //                        accumulator to the epilogue.  Warp 1 also allocates and frees the TMEM.
 //   warps 2-5            epilogue: tcgen05.ld of their 32 lanes (rows), 32 columns at a time, stored to
-//                        D column by column (lanes = consecutive rows: coalesced).
+//                        D (column-major: lanes = consecutive rows, coalesced; row-major: each lane
+//                        writes 128 contiguous bytes of its row).
 // Every mbarrier wait is bounded; a wait that runs out records RSK_DEV_TIMEOUT, stops the roles, and
 // before the CTA leaves the producer waits (bounded) for the copies still owed to a stage and the
 // epilogue for the MMAs already issued, so no copy or MMA outlives the CTA's shared memory or TMEM.
-#include <cuda_bf16.h>
+#include "gemm_tc.cuh"
+
 #include <string.h>
 
 #include <algorithm>
-
-#include "common.cuh"
 
 namespace {
 
@@ -32,13 +33,17 @@ constexpr int stages_for() {
     return 3 * (kBM * kBK * 2 + 2 * NH * kBK * 2) <= 200 * 1024 ? 3 : 2;
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    // tcgen05 shared-memory matrix descriptor: K-major operand with the 128-byte swizzle: start address
-    // (bits 0-13, >> 4), leading byte offset 1 (unused for swizzled K-major), stride byte offset 1024 B
-    // between 8-row groups (bits 32-45, >> 4), descriptor version 1 (bits 46-47), swizzle mode 2 =
-    // 128-byte (bits 61-63)
+// tcgen05 shared-memory matrix descriptor, 128-byte swizzle: start address (bits 0-13, >> 4), leading
+// byte offset (bits 16-29, >> 4), stride byte offset (bits 32-45, >> 4), descriptor version 1
+// (bits 46-47), swizzle mode 2 = 128-byte (bits 61-63).
+//   K-major operand: rows of 64 BF16 (128 bytes) along K, 8-row groups 1024 bytes apart (the stride
+//   offset); the leading offset is unused (1).  A K-step of 16 advances the start by 32 bytes.
+//   MN-major operand: rows of 64 BF16 along M, one row per K index, 8-row (K) groups 1024 bytes apart
+//   (stride offset), the second 64-wide M group 8192 bytes further (leading offset).  A K-step of 16
+//   advances the start by two groups (2048 bytes).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo) {
     uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
-    d |= uint64_t(1) << 16;
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
     d |= uint64_t(1024 >> 4) << 32;
     d |= uint64_t(1) << 46;
     d |= uint64_t(2) << 61;
@@ -46,9 +51,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28).
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+// (bits 7-9 = 1, 10-12 = 1), A MN-major when bit 15 is set (B always K-major: bit 16 = 0), N >> 3
+// (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n, bool a_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn ? (1u << 15) : 0u) | (uint32_t(n >> 3) << 17) |
+           (uint32_t(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {
@@ -88,20 +95,28 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+struct GemmMaps {
+    CUtensorMap a[rsk::tc::kMaxOperands];
+    CUtensorMap b[rsk::tc::kMaxOperands];
+};
+
 struct GemmArgs {
     int64_t M, K;
     int N;             // columns of D stored (<= 2 * NH)
-    int kblocks;       // K blocks per split
-    int64_t nk_total;  // K blocks overall
+    int kblocks;       // K blocks per split (of one pass)
+    int64_t nk_total;  // K blocks of one pass overall
+    int npass;
+    uint8_t pa[rsk::tc::kMaxPasses], pb[rsk::tc::kMaxPasses];
     float* D;
     int64_t ldd;
+    int row_major;         // D row-major (only without split-K: partials are column-major)
     int64_t split_stride;  // elements between the splits' partial outputs (0: one split)
     unsigned int* status;
 };
 
-template <int NH>
+template <int NH, bool A_MN>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const GemmArgs a) {
+    k_gemm_tc(const __grid_constant__ GemmMaps maps, const GemmArgs a) {
     constexpr int kStages = stages_for<NH>();
     constexpr int kABytes = kBM * kBK * 2;          // 16 KB
     constexpr int kBBytes = 2 * NH * kBK * 2;       // N x 64 BF16
@@ -121,6 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int split = blockIdx.y;
     const int64_t kb0 = int64_t(split) * a.kblocks;
     const int nk = int(std::min<int64_t>(a.kblocks, a.nk_total - kb0));
+    const int total = nk > 0 ? nk * a.npass : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -141,19 +157,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int issued[kStages] = {};
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % kStages;
-                if (kb >= kStages && !rskd::mbar_wait(&empty[s], uint32_t(((kb / kStages) & 1) ^ 1), a.status)) {
+            for (int it = 0; it < total; ++it) {
+                const int s = it % kStages;
+                if (it >= kStages && !rskd::mbar_wait(&empty[s], uint32_t(((it / kStages) & 1) ^ 1), a.status)) {
                     *abort_flag = 1;
                     break;
                 }
                 if (*abort_flag) break;
+                const int pass = it / nk, kb = it - pass * nk;
+                const CUtensorMap* ma = &maps.a[a.pa[pass]];
+                const CUtensorMap* mb = &maps.b[a.pb[pass]];
                 uint8_t* st = sm + s * kStage;
                 const int kx = int((kb0 + kb) * kBK);
                 rskd::mbar_expect_tx(&full[s], uint32_t(kStage));
-                rskd::tma_load_2d(st, &ta, kx, int(m0), &full[s]);
-                rskd::tma_load_2d(st + kABytes, &tb, kx, 0, &full[s]);
-                rskd::tma_load_2d(st + kABytes + NH * kBK * 2, &tb, kx, NH, &full[s]);
+                if constexpr (A_MN) {
+                    rskd::tma_load_2d(st, ma, int(m0), kx, &full[s]);
+                    rskd::tma_load_2d(st + kABytes / 2, ma, int(m0) + 64, kx, &full[s]);
+                } else {
+                    rskd::tma_load_2d(st, ma, kx, int(m0), &full[s]);
+                }
+                rskd::tma_load_2d(st + kABytes, mb, kx, 0, &full[s]);
+                rskd::tma_load_2d(st + kABytes + NH * kBK * 2, mb, kx, NH, &full[s]);
                 ++issued[s];
             }
             // copies still owed to a stage (only after a timeout) land before the CTA leaves.  The MMA
@@ -166,10 +190,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = instr_desc(kBM, NH);
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % kStages;
-                if (*abort_flag || !rskd::mbar_wait(&full[s], uint32_t((kb / kStages) & 1), a.status)) {
+            constexpr uint32_t idesc = instr_desc(kBM, NH, A_MN);
+            for (int it = 0; it < total; ++it) {
+                const int s = it % kStages;
+                if (*abort_flag || !rskd::mbar_wait(&full[s], uint32_t((it / kStages) & 1), a.status)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -179,11 +203,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t sb = sa + kABytes;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
-                    const uint64_t ad = smem_desc(sa + kk * 32);
+                    const uint64_t ad = A_MN ? smem_desc(sa + kk * 2048, kABytes / 2) : smem_desc(sa + kk * 32, 16);
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) {
-                        const uint64_t bd = smem_desc(sb + hh * NH * kBK * 2 + kk * 32);
-                        tc_mma(tmem + uint32_t(hh * NH), ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+                        const uint64_t bd = smem_desc(sb + hh * NH * kBK * 2 + kk * 32, 16);
+                        tc_mma(tmem + uint32_t(hh * NH), ad, bd, idesc, (it | kk) != 0 ? 1u : 0u);
                     }
                 }
                 tc_commit(&empty[s]);
@@ -197,23 +221,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the TMEM loads below are warp-wide (.sync.aligned): the decision to run them is the warp's
         const bool ok = __all_sync(0xffffffffu, rskd::mbar_wait(tfull, 0u, a.status));
         tc_fence_after();
-        if (ok && !*abort_flag && nk > 0) {
-            const int64_t row = m0 + 32 * q + lane;
-            float* out = a.D + int64_t(split) * a.split_stride;
+        const int64_t row = m0 + 32 * q + lane;
+        float* out = a.D + int64_t(split) * a.split_stride;
+        if (ok && !*abort_flag && total > 0) {
             for (int c0 = 0; c0 < 2 * NH; c0 += 32) {
                 uint32_t v[32];
                 tc_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(c0), v);
-                if (row < a.M) {
+                if (row < a.M && c0 < a.N) {
+                    if (!a.row_major) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c0 + j < a.N) out[int64_t(c0 + j) * a.ldd + row] = __uint_as_float(v[j]);
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < a.N) out[int64_t(c0 + j) * a.ldd + row] = __uint_as_float(v[j]);
+                    } else if (c0 + 32 <= a.N && (a.ldd & 3) == 0) {
+                        float4* o4 = reinterpret_cast<float4*>(out + row * a.ldd + c0);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            o4[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                                                __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < a.N) out[row * a.ldd + c0 + j] = __uint_as_float(v[j]);
+                    }
                 }
             }
-        } else if (nk == 0 && 0 < a.N) {
-            const int64_t row = m0 + 32 * q + lane;
-            float* out = a.D + int64_t(split) * a.split_stride;
-            if (row < a.M)
-                for (int c = 0; c < a.N; ++c) out[int64_t(c) * a.ldd + row] = 0.f;
+        } else if (total == 0 && row < a.M) {
+            for (int c = 0; c < a.N; ++c) out[a.row_major ? row * a.ldd + c : int64_t(c) * a.ldd + row] = 0.f;
         }
     }
     tc_fence_before();
@@ -225,30 +258,86 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// D = sum over splits (in split order) of the partials.
+// D = sum over splits (in split order) of the column-major partials.
 __global__ void k_sum_splits(const float* __restrict__ part, int64_t stride, int nsplit, int64_t M, int N, int64_t ldd,
-                             float* __restrict__ D) {
+                             int row_major, float* __restrict__ D) {
     const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
     const int64_t c = idx / M, r = idx - c * M;
     float s = 0.f;
     for (int p = 0; p < nsplit; ++p) s += part[int64_t(p) * stride + c * M + r];
-    D[c * ldd + r] = s;
+    D[row_major ? r * ldd + c : c * ldd + r] = s;
 }
 
-template <int NH>
-rsk_status launch_gemm(rsk_handle* h, const CUtensorMap& ta, const CUtensorMap& tb, const GemmArgs& ga, int mtiles,
-                       int nsplit, cudaStream_t stream) {
+// Three-term BF16 split, column c of X at X + c * ldx: x1 = bf16(x), x2 = bf16(x - x1), x3 =
+// bf16(x - x1 - x2); both differences are exact in FP32 (each has at most 16 significant bits).
+__global__ void k_split3(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                         __nv_bfloat16* __restrict__ o1, __nv_bfloat16* __restrict__ o2,
+                         __nv_bfloat16* __restrict__ o3, int64_t ldt) {
+    for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+        for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+            const float x = X[c * ldx + r];
+            const __nv_bfloat16 b1 = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(b1);
+            const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(b2);
+            o1[c * ldt + r] = b1;
+            o2[c * ldt + r] = b2;
+            o3[c * ldt + r] = __float2bfloat16_rn(r2);
+        }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                          __nv_bfloat16* __restrict__ out, int64_t ldt) {
+    for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+        for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
+            out[c * ldt + r] = __float2bfloat16_rn(X[c * ldx + r]);
+}
+
+// Packed conversion (ldx == ldt == rows, count a multiple of 4, 16-byte aligned X): 4 elements a thread.
+__global__ void k_to_bf16_flat(const float4* __restrict__ X, int64_t n4, uint2* __restrict__ out) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 f = X[i];
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(f.x, f.y), hi = __floats2bfloat162_rn(f.z, f.w);
+        uint2 o;
+        o.x = *reinterpret_cast<const uint32_t*>(&lo);
+        o.y = *reinterpret_cast<const uint32_t*>(&hi);
+        out[i] = o;
+    }
+}
+
+template <int NH, bool A_MN>
+rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, const GemmArgs& ga, int mtiles, int nsplit,
+                       cudaStream_t stream) {
     constexpr int kStage = kBM * kBK * 2 + 2 * NH * kBK * 2;
     const int smem = stages_for<NH>() * kStage + 1024 + 256;
-    auto kern = k_gemm_tc<NH>;
+    auto kern = k_gemm_tc<NH, A_MN>;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_GEMM);
-    kern<<<dim3(unsigned(mtiles), unsigned(nsplit)), kThreads, smem, stream>>>(ta, tb, ga);
+    kern<<<dim3(unsigned(mtiles), unsigned(nsplit)), kThreads, smem, stream>>>(maps, ga);
     rsk::prof_end(h, stream, pr);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
+
+template <bool A_MN>
+rsk_status dispatch_nh(rsk_handle* h, int nh, const GemmMaps& maps, const GemmArgs& ga, int mtiles, int nsplit,
+                       cudaStream_t stream) {
+    switch (nh) {
+        case 16: return launch_gemm<16, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 32: return launch_gemm<32, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 48: return launch_gemm<48, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 64: return launch_gemm<64, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 96: return launch_gemm<96, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 128: return launch_gemm<128, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 160: return launch_gemm<160, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 192: return launch_gemm<192, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        case 256: return launch_gemm<256, A_MN>(h, maps, ga, mtiles, nsplit, stream);
+        default: return rsk::fail(h, RSK_ERR_UNSUPPORTED, "gemm: N half %d is not supported", nh);
+    }
+}
+
+bool aligned16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
 }  // namespace
 
@@ -259,73 +348,167 @@ size_t gemm_scratch_bytes(int64_t M, int N, int nsplit) {
     return nsplit > 1 ? size_t(nsplit) * size_t(M) * size_t(N) * 4 + 256 : 0;
 }
 
-// D (M x N column-major, ldd) = A (M x K, row-major = K-major, lda) * B (N x K, K-major, ldb)^T.
-// nsplit > 1 splits K over that many CTAs per row tile (partials in scratch, summed in order).
-rsk_status gemm_bf16(rsk_handle* h, const __nv_bfloat16* A, int64_t M, int64_t K, int64_t lda, const __nv_bfloat16* B,
-                     int N, int64_t ldb, float* D, int64_t ldd, int nsplit, float* scratch, cudaStream_t stream) {
-    if (M < 1 || K < 1 || N < 1 || N > 512 || ldd < M) return fail(h, RSK_ERR_INVALID_ARG, "gemm: bad shape");
-    if ((lda * 2) % 16 || (ldb * 2) % 16 || reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(B) % 16)
-        return fail(h, RSK_ERR_INVALID_ARG, "gemm: operands and row pitches must be 16-byte aligned");
+void set_split_passes(Product& p) {
+    // The tensor cores' FP32 accumulation rounds toward zero: every MMA into an accumulator loses up to
+    // one unit in the last place of the accumulator's current value.  The correction terms therefore
+    // go first, smallest first, while the accumulator is small, and the main term x1 y1 last: the
+    // bias is then that of the main term's own K steps alone.
+    static const uint8_t pa[kMaxPasses] = {2, 0, 1, 1, 0, 0}, pb[kMaxPasses] = {0, 2, 1, 0, 1, 0};
+    p.npass = kMaxPasses;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        p.pa[i] = pa[i];
+        p.pb[i] = pb[i];
+    }
+}
+
+rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream) {
+    if (p.M < 1 || p.K < 1 || p.N < 1 || p.N > 512 || p.ldd < (p.d_row_major ? p.N : p.M))
+        return fail(h, RSK_ERR_INVALID_ARG, "gemm: bad shape");
+    if (p.npass < 1 || p.npass > kMaxPasses || p.na < 1 || p.na > kMaxOperands || p.nb < 1 || p.nb > kMaxOperands)
+        return fail(h, RSK_ERR_INVALID_ARG, "gemm: bad pass list");
+    for (int i = 0; i < p.npass; ++i)
+        if (p.pa[i] >= p.na || p.pb[i] >= p.nb) return fail(h, RSK_ERR_INVALID_ARG, "gemm: pass names a missing operand");
+    if ((p.lda * 2) % 16 || (p.ldb * 2) % 16 || p.lda < (p.a_mn ? p.M : p.K) || p.ldb < p.K)
+        return fail(h, RSK_ERR_INVALID_ARG, "gemm: leading dimensions must cover the operand and be multiples of 8");
+    for (int i = 0; i < p.na; ++i)
+        if (!p.a[i] || !aligned16(p.a[i])) return fail(h, RSK_ERR_INVALID_ARG, "gemm: A operands must be 16-byte aligned");
+    for (int i = 0; i < p.nb; ++i)
+        if (!p.b[i] || !aligned16(p.b[i])) return fail(h, RSK_ERR_INVALID_ARG, "gemm: B operands must be 16-byte aligned");
     // N split into two halves of NH columns (a multiple of 16, the MMA's N step for M = 128)
-    const int nh = std::max(16, ((N + 1) / 2 + 15) / 16 * 16);
-    const int64_t nk = (K + kBK - 1) / kBK;
+    const int nh = std::max(16, ((p.N + 1) / 2 + 15) / 16 * 16);
+    const int64_t nk = (p.K + kBK - 1) / kBK;
     nsplit = int(std::max<int64_t>(1, std::min<int64_t>(nsplit, nk)));
     const int kblocks = int((nk + nsplit - 1) / nsplit);
     nsplit = int((nk + kblocks - 1) / kblocks);
-    CUtensorMap ta, tb;
-    memset(&ta, 0, sizeof(ta));
-    memset(&tb, 0, sizeof(tb));
-    if (!encode_2d_swz128(h, &ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, A, uint64_t(K), uint64_t(M), uint64_t(lda) * 2, kBK,
-                          kBM) ||
-        !encode_2d_swz128(h, &tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B, uint64_t(K), uint64_t(N), uint64_t(ldb) * 2, kBK,
-                          uint32_t(nh)))
-        return fail(h, RSK_ERR_UNSUPPORTED, "gemm: tensor map encoding failed");
+    GemmMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    for (int i = 0; i < p.na; ++i) {
+        const bool ok = p.a_mn ? encode_2d_swz128(h, &maps.a[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.a[i],
+                                                  uint64_t(p.M), uint64_t(p.K), uint64_t(p.lda) * 2, 64, 64)
+                               : encode_2d_swz128(h, &maps.a[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.a[i],
+                                                  uint64_t(p.K), uint64_t(p.M), uint64_t(p.lda) * 2, kBK, kBM);
+        if (!ok) return fail(h, RSK_ERR_UNSUPPORTED, "gemm: tensor map encoding failed (A)");
+    }
+    for (int i = 0; i < p.nb; ++i)
+        if (!encode_2d_swz128(h, &maps.b[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.b[i], uint64_t(p.K), uint64_t(p.N),
+                              uint64_t(p.ldb) * 2, kBK, uint32_t(nh)))
+            return fail(h, RSK_ERR_UNSUPPORTED, "gemm: tensor map encoding failed (B)");
     GemmArgs ga;
-    ga.M = M;
-    ga.K = K;
-    ga.N = N;
+    memset(&ga, 0, sizeof(ga));
+    ga.M = p.M;
+    ga.K = p.K;
+    ga.N = p.N;
     ga.kblocks = kblocks;
     ga.nk_total = nk;
+    ga.npass = p.npass;
+    for (int i = 0; i < p.npass; ++i) {
+        ga.pa[i] = p.pa[i];
+        ga.pb[i] = p.pb[i];
+    }
     ga.status = h->dev_status;
     if (nsplit > 1) {
         if (!scratch) return fail(h, RSK_ERR_INVALID_ARG, "gemm: split-K needs scratch");
         ga.D = scratch;
-        ga.ldd = M;
-        ga.split_stride = M * int64_t(N);
+        ga.ldd = p.M;
+        ga.row_major = 0;
+        ga.split_stride = p.M * int64_t(p.N);
     } else {
-        ga.D = D;
-        ga.ldd = ldd;
+        ga.D = p.D;
+        ga.ldd = p.ldd;
+        ga.row_major = p.d_row_major ? 1 : 0;
         ga.split_stride = 0;
     }
-    const int mtiles = int((M + kBM - 1) / kBM);
-    rsk_status st;
-    switch (nh) {
-        case 16: st = launch_gemm<16>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 32: st = launch_gemm<32>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 48: st = launch_gemm<48>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 64: st = launch_gemm<64>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 96: st = launch_gemm<96>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 128: st = launch_gemm<128>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 160: st = launch_gemm<160>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 192: st = launch_gemm<192>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        case 256: st = launch_gemm<256>(h, ta, tb, ga, mtiles, nsplit, stream); break;
-        default: return fail(h, RSK_ERR_UNSUPPORTED, "gemm: N = %d is not supported (half %d)", N, nh);
-    }
+    const int mtiles = int((p.M + kBM - 1) / kBM);
+    const rsk_status st = p.a_mn ? dispatch_nh<true>(h, nh, maps, ga, mtiles, nsplit, stream)
+                                 : dispatch_nh<false>(h, nh, maps, ga, mtiles, nsplit, stream);
     if (st != RSK_OK || nsplit == 1) return st;
-    k_sum_splits<<<unsigned((M * N + 255) / 256), 256, 0, stream>>>(scratch, M * int64_t(N), nsplit, M, N, ldd, D);
+    k_sum_splits<<<unsigned((p.M * p.N + 255) / 256), 256, 0, stream>>>(scratch, p.M * int64_t(p.N), nsplit, p.M, p.N,
+                                                                        p.ldd, p.d_row_major ? 1 : 0, p.D);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
+}
+
+static dim3 elementwise_grid(int64_t rows, int64_t cols) {
+    return dim3(unsigned(std::min<int64_t>((rows + 255) / 256, 64)), unsigned(std::min<int64_t>(cols, 16384)));
+}
+
+rsk_status split3(rsk_handle* h, const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* const* out,
+                  int64_t ldt, cudaStream_t stream) {
+    const int pr = prof_begin(h, stream, RSK_KERNEL_CONVERT);
+    k_split3<<<elementwise_grid(rows, cols), 256, 0, stream>>>(X, rows, cols, ldx, out[0], out[1], out[2], ldt);
+    prof_end(h, stream, pr);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+rsk_status to_bf16(rsk_handle* h, const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* out,
+                   int64_t ldt, cudaStream_t stream) {
+    const int64_t count = rows * cols;
+    const int pr = prof_begin(h, stream, RSK_KERNEL_CONVERT);
+    if (ldx == rows && ldt == rows && count % 4 == 0 && aligned16(X) && reinterpret_cast<uintptr_t>(out) % 8 == 0) {
+        const unsigned grid = unsigned(std::min<int64_t>((count / 4 + 255) / 256, int64_t(h->num_sms) * 16));
+        k_to_bf16_flat<<<grid, 256, 0, stream>>>(reinterpret_cast<const float4*>(X), count / 4,
+                                                 reinterpret_cast<uint2*>(out));
+    } else {
+        k_to_bf16<<<elementwise_grid(rows, cols), 256, 0, stream>>>(X, rows, cols, ldx, out, ldt);
+    }
+    prof_end(h, stream, pr);
+    RSK_LAUNCH_CHECK(h);
+    return RSK_OK;
+}
+
+size_t f32_product_scratch_bytes(bool a_mn, int64_t M, int64_t K, int N, int nsplit) {
+    const int64_t a_rows = a_mn ? M : K, a_cols = a_mn ? K : M;
+    return 3 * Carver::round(size_t(pad8(a_rows)) * size_t(a_cols) * 2) + 3 * Carver::round(size_t(pad8(K)) * size_t(N) * 2) +
+           Carver::round(gemm_scratch_bytes(M, N, nsplit) + 4) + 256;
+}
+
+rsk_status f32_product(rsk_handle* h, bool a_mn, const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
+                       int64_t K, int N, float* D, int64_t ldd, bool d_row_major, int nsplit, void* scratch,
+                       cudaStream_t stream) {
+    Carver cv(scratch);
+    // A's splits keep A's orientation: MN-major A is a column-major M x K matrix, K-major A a
+    // column-major K x M one
+    const int64_t a_rows = a_mn ? M : K, a_cols = a_mn ? K : M;
+    const int64_t lta = pad8(a_rows), ltb = pad8(K);
+    Product p;
+    p.a_mn = a_mn;
+    __nv_bfloat16* as[3];
+    __nv_bfloat16* bs[3];
+    for (int i = 0; i < 3; ++i) as[i] = cv.take<__nv_bfloat16>(size_t(lta) * size_t(a_cols));
+    for (int i = 0; i < 3; ++i) bs[i] = cv.take<__nv_bfloat16>(size_t(ltb) * size_t(N));
+    float* part = cv.take<float>(gemm_scratch_bytes(M, N, nsplit) / 4 + 1);
+    rsk_status st = split3(h, A, a_rows, a_cols, lda, as, lta, stream);
+    if (st == RSK_OK) st = split3(h, B, K, N, ldb, bs, ltb, stream);
+    if (st != RSK_OK) return st;
+    for (int i = 0; i < 3; ++i) {
+        p.a[i] = as[i];
+        p.b[i] = bs[i];
+    }
+    p.na = p.nb = 3;
+    p.lda = lta;
+    p.ldb = ltb;
+    set_split_passes(p);
+    p.M = M;
+    p.K = K;
+    p.N = N;
+    p.D = D;
+    p.ldd = ldd;
+    p.d_row_major = d_row_major;
+    return gemm(h, p, nsplit, part, stream);
 }
 
 }  // namespace tc
 }  // namespace rsk
 
-extern "C" rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B,
-                                    int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t nsplit, cudaStream_t stream) {
+extern "C" rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* A, int64_t M, int64_t K, int64_t lda,
+                                       const void* B, int64_t N, int64_t ldb, float* D, int64_t ldd,
+                                       int32_t d_row_major, int32_t nsplit, cudaStream_t stream) {
     if (!h) return RSK_ERR_INVALID_ARG;
     if (!A || !B || !D) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
-    if (M < 1 || K < 1 || N < 1 || N > 512 || lda < K || ldb < K || ldd < M)
-        return rsk::fail(h, RSK_ERR_INVALID_ARG, "need M, K >= 1, 1 <= N <= 512, lda, ldb >= K, ldd >= M");
+    if (M < 1 || K < 1 || N < 1 || N > 512 || lda < (a_mn ? M : K) || ldb < K || ldd < (d_row_major ? N : M))
+        return rsk::fail(h, RSK_ERR_INVALID_ARG,
+                         "need M, K >= 1, 1 <= N <= 512, lda >= (a_mn ? M : K), ldb >= K, ldd >= (row-major D ? N : M)");
     nsplit = std::max(1, nsplit);
     float* scratch = nullptr;
     if (nsplit > 1) {
@@ -333,6 +516,40 @@ extern "C" rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int
         if (st != RSK_OK) return st;
         scratch = static_cast<float*>(h->ws);
     }
-    return rsk::tc::gemm_bf16(h, static_cast<const __nv_bfloat16*>(A), M, K, lda, static_cast<const __nv_bfloat16*>(B),
-                              int(N), ldb, D, ldd, nsplit, scratch, stream);
+    rsk::tc::Product p;
+    p.a_mn = a_mn != 0;
+    p.a[0] = static_cast<const __nv_bfloat16*>(A);
+    p.na = 1;
+    p.lda = lda;
+    p.b[0] = static_cast<const __nv_bfloat16*>(B);
+    p.nb = 1;
+    p.ldb = ldb;
+    p.npass = 1;
+    p.M = M;
+    p.K = K;
+    p.N = int(N);
+    p.D = D;
+    p.ldd = ldd;
+    p.d_row_major = d_row_major != 0;
+    return rsk::tc::gemm(h, p, nsplit, scratch, stream);
+}
+
+extern "C" rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B,
+                                    int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t nsplit, cudaStream_t stream) {
+    return rsk_gemm_bf16_ex(h, 0, A, M, K, lda, B, N, ldb, D, ldd, 0, nsplit, stream);
+}
+
+extern "C" rsk_status rsk_gemm_f32(rsk_handle* h, int32_t a_mn, const float* A, int64_t M, int64_t K, int64_t lda,
+                                   const float* B, int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t d_row_major,
+                                   int32_t nsplit, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (!A || !B || !D) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
+    if (M < 1 || K < 1 || N < 1 || N > 512 || lda < (a_mn ? M : K) || ldb < K || ldd < (d_row_major ? N : M))
+        return rsk::fail(h, RSK_ERR_INVALID_ARG,
+                         "need M, K >= 1, 1 <= N <= 512, lda >= (a_mn ? M : K), ldb >= K, ldd >= (row-major D ? N : M)");
+    nsplit = std::max(1, nsplit);
+    rsk_status st = rsk::ensure_workspace(h, rsk::tc::f32_product_scratch_bytes(a_mn != 0, M, K, int(N), nsplit), stream);
+    if (st != RSK_OK) return st;
+    return rsk::tc::f32_product(h, a_mn != 0, A, lda, B, ldb, M, K, int(N), D, ldd, d_row_major != 0, nsplit, h->ws,
+                                stream);
 }

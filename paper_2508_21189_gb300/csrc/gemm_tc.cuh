@@ -1,0 +1,70 @@
+// Dense products on the fifth-generation tensor cores (tcgen05) for the low-rank algorithms.
+//
+//     D (M x N, FP32) = sum over passes p of  A_{pa[p]} (M x K) * B_{pb[p]} (N x K)^T
+//
+// A operands are BF16 and either K-major (element (m, k) at A[m * lda + k]) or MN-major (element
+// (m, k) at A[k * lda + m], i.e. the transpose of a row-major K x M matrix); B operands are BF16
+// K-major (element (n, j) at B[n * ldb + j]).  Several passes over the same K range accumulate into
+// one tensor-memory accumulator: with the three-term BF16 splits of two FP32 matrices this gives
+// products of FP32 accuracy (the six pairs whose split orders sum to at most four).  D is column-major
+// (element (m, n) at D[n * ldd + m]) or row-major (D[m * ldd + n]).  1 <= N <= 512.  Every pointer is
+// 16-byte aligned and every leading dimension a multiple of 8 elements (TMA row pitch).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace rsk {
+namespace tc {
+
+constexpr int kMaxOperands = 3;
+constexpr int kMaxPasses = 6;
+
+struct Product {
+    bool a_mn = false;  // A MN-major
+    const __nv_bfloat16* a[kMaxOperands] = {};
+    int na = 0;
+    int64_t lda = 0;
+    const __nv_bfloat16* b[kMaxOperands] = {};
+    int nb = 0;
+    int64_t ldb = 0;
+    int npass = 0;
+    uint8_t pa[kMaxPasses] = {}, pb[kMaxPasses] = {};
+    int64_t M = 0, K = 0;
+    int N = 0;
+    float* D = nullptr;
+    int64_t ldd = 0;
+    bool d_row_major = false;
+};
+
+// Scratch for split-K partials (nsplit > 1).
+size_t gemm_scratch_bytes(int64_t M, int N, int nsplit);
+// Runs the product with K split over nsplit CTAs per row tile (partials summed in split order).
+rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream);
+
+// The six split pairs (3,1), (1,3), (2,2), (2,1), (1,2), (1,1) of two three-term splits, in that
+// order.  The accumulation truncates: a same-sign sum's relative bias grows by up to about 2^-24 per
+// 16-wide K step a split accumulates (nsplit bounds it).
+void set_split_passes(Product& p);
+
+// X (rows x cols FP32, column c at X + c * ldx) -> three BF16 terms X = X1 + X2 + X3 + O(2^-24 |X|),
+// each rows x cols with column c at Xt + c * ldt (ldt >= rows, a multiple of 8), written to out[0..2].
+rsk_status split3(rsk_handle* h, const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* const* out,
+                  int64_t ldt, cudaStream_t stream);
+// X (FP32, same layout) -> bf16(X) with leading dimension ldt.
+rsk_status to_bf16(rsk_handle* h, const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* out,
+                   int64_t ldt, cudaStream_t stream);
+
+// Product of FP32 matrices at FP32 accuracy: A (M x K; MN-major when a_mn, i.e. element (m, k) at
+// A[k * lda + m], else A[m * lda + k]), B (N x K, element (n, j) at B[n * ldb + j]); the splits and the
+// partials come from `scratch` (f32_product_scratch_bytes).
+size_t f32_product_scratch_bytes(bool a_mn, int64_t M, int64_t K, int N, int nsplit);
+rsk_status f32_product(rsk_handle* h, bool a_mn, const float* A, int64_t lda, const float* B, int64_t ldb, int64_t M,
+                       int64_t K, int N, float* D, int64_t ldd, bool d_row_major, int nsplit, void* scratch,
+                       cudaStream_t stream);
+
+inline int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
+
+}  // namespace tc
+}  // namespace rsk

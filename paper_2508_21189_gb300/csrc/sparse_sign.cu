@@ -1075,7 +1075,7 @@ rsk_status sketch_apply_kind(rsk_handle* h, int kind, const void* A, rsk_dtype a
 }
 // Y = A Omega for Omega = S^T, S the k x dc sketch of the given kind: Y n x k column-major (ldy >= n).
 rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n, int64_t dc, int64_t lda, int64_t k,
-                              int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream) {
+                              int zeta, uint64_t seed, float* Y, int64_t ldy, cudaStream_t stream, uint32_t stream_id) {
     rsk_status st = kind == kStack ? check_stack_dims(h, dc, k, zeta) : check_dims(h, dc, k, zeta);
     if (st != RSK_OK) return st;
     if (!A || !Y) return fail(h, RSK_ERR_INVALID_ARG, "null pointer");
@@ -1087,8 +1087,8 @@ rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n
     Carver cv(h->ws);
     uint16_t* offs = cv.take<uint16_t>(offsets_count(dc, int(k), zeta));
     uint16_t* ents = cv.take<uint16_t>(entries_count(dc, zeta));
-    st = launch_index(h, dc, int(k), zeta, seed, kind == kStack ? kStreamStack : kStreamLeft, offs, ents, stream, 0,
-                      kind);
+    if (stream_id == ~0u) stream_id = kind == kStack ? kStreamStack : kStreamLeft;
+    st = launch_index(h, dc, int(k), zeta, seed, stream_id, offs, ents, stream, 0, kind);
     if (st != RSK_OK) return st;
     const int C = chunk_rows(zeta);
     const int nch = int(n_chunks_of(dc, zeta));
@@ -1152,6 +1152,16 @@ rsk_status rsk_sparse_stack_apply(rsk_handle* h, const void* A, rsk_dtype a_dtyp
     rsk_status st = check_stack_dims(h, n, d, zeta);
     if (st != RSK_OK) return st;
     return apply_kind(h, A, a_dtype, n, k, lda, 0, d, zeta, seed, SA, sa_dtype, ldsa, stream, kStreamStack, kStack);
+}
+
+rsk_status rsk_sparse_sign_apply_right(rsk_handle* h, int32_t kind, const float* A, int64_t n, int64_t dc,
+                                       int64_t lda, int64_t k, int32_t zeta, uint64_t seed, int32_t philox_stream,
+                                       float* Y, int64_t ldy, cudaStream_t stream) {
+    if (!h) return RSK_ERR_INVALID_ARG;
+    if (kind != kUniform && kind != kStack) return rsk::fail(h, RSK_ERR_INVALID_ARG, "kind must be 0 or 1");
+    if (philox_stream < -1) return rsk::fail(h, RSK_ERR_INVALID_ARG, "philox_stream must be -1 or a stream number");
+    return rsk::sketch_apply_right(h, kind, A, n, dc, lda, k, zeta, seed, Y, ldy, stream,
+                              philox_stream < 0 ? ~0u : uint32_t(philox_stream));
 }
 
 rsk_status rsk_sparse_sign_index_dims(int64_t n, int64_t d, int32_t zeta, int64_t* chunk_rows_out, int64_t* n_chunks,

@@ -69,3 +69,45 @@ def test_qr_econ_orthonormal(rsk, m, q, cond_exp, seed):
     assert np.abs(Q.T @ Q - np.eye(q)).max() <= 1e-5
     assert np.allclose(np.tril(R, -1), 0)
     assert np.abs(Q @ R - X).max() <= 1e-5 * np.linalg.norm(X, 2)
+
+
+@pytest.mark.parametrize("q,cond_exp,shift", [(1, 0, 0.0), (17, 1, 0.0), (300, 3, 0.0), (320, 2, 3e-5), (330, 1, 0.0),
+                                               (100, 6, 3e-5)])
+def test_cholesky_matches_lapack(rsk, q, cond_exp, shift):
+    """R^T R = G + shift trace(G) I: R matches LAPACK's factor of the same FP32 matrix to FP32 accuracy
+    (relative to the factor's norm, times the condition number)."""
+    rng = np.random.default_rng(q)
+    Vq, _ = np.linalg.qr(rng.standard_normal((q, q)))
+    G = ((Vq * np.logspace(0, -cond_exp, q)) @ Vq.T).astype(np.float32).astype(np.float64)
+    G = 0.5 * (G + G.T)
+    R = rsk.rsk_cholesky(colmajor(G), shift_coeff=shift)
+    torch.cuda.synchronize()
+    rsk.rsk_sync_status()
+    R = R.double().cpu().numpy()
+    Gs = G + np.float32(shift) * np.float32(np.trace(G.astype(np.float32))) * np.eye(q)
+    ref = np.linalg.cholesky(Gs).T
+    assert np.allclose(np.tril(R, -1), 0)
+    assert np.abs(R.T @ R - Gs).max() <= 64 * q * U32 * np.abs(Gs).max()
+    assert np.abs(R - ref).max() <= 1e-5 * 10 ** cond_exp * np.abs(ref).max() * max(1, q / 64)
+
+
+def test_cholesky_not_psd(rsk):
+    G = np.eye(40)
+    G[7, 7] = -1.0
+    rsk.rsk_cholesky(colmajor(G))
+    torch.cuda.synchronize()
+    with pytest.raises(rsk.RskError):
+        rsk.rsk_sync_status()
+
+
+@pytest.mark.parametrize("q", [1, 31, 32, 33, 300, 330, 880])
+def test_trinv_matches_solve(rsk, q):
+    rng = np.random.default_rng(q + 1)
+    # well conditioned: unit-order diagonal, off-diagonal entries of size q^-1/2 (kappa ~ 10)
+    R = np.triu(rng.standard_normal((q, q)), 1) / (2 * q ** 0.5) + np.diag(1.0 + rng.random(q))
+    R = R.astype(np.float32).astype(np.float64)
+    Ri = rsk.rsk_trinv(colmajor(R))
+    torch.cuda.synchronize()
+    Ri = Ri.double().cpu().numpy()
+    assert np.allclose(np.tril(Ri, -1), 0)
+    assert np.abs(R @ Ri - np.eye(q)).max() <= 1e-5 * max(1, q / 64)

@@ -31,3 +31,74 @@ def test_gemm_matches_fp64(rsk, M, K, N, nsplit):
     scale = A.double().abs() @ B.double().abs().T
     err = (D.double() - ref).abs()
     assert bool((err <= 1e-5 * scale + 1e-30).all()), float((err / scale.clamp_min(1e-30)).max())
+
+
+@pytest.mark.parametrize("M,K,N,nsplit,row_major", [(128, 64, 32, 1, False), (256, 192, 96, 1, True),
+                                                    (1000, 1000, 300, 1, False), (8192, 20000, 300, 3, False),
+                                                    (333, 4104, 45, 1, True), (8192, 8192, 320, 2, True)])
+def test_gemm_mn_major_a(rsk, M, K, N, nsplit, row_major):
+    """op(A) = A^T read in place (A given K x M row-major), column- or row-major D."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7 * M + K + N)
+    At = torch.randn(K, M + (8 - M % 8) % 8, generator=g, device="cuda").to(torch.bfloat16)[:, :M]
+    B = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+    D = rsk.rsk_gemm_bf16_ex(At, B, a_mn=True, row_major_out=row_major, nsplit=nsplit)
+    torch.cuda.synchronize()
+    rsk.rsk_sync_status()
+    ref = At.double().T @ B.double().T
+    scale = At.double().abs().T @ B.double().abs().T
+    err = (D.double() - ref).abs()
+    assert bool((err <= 1e-5 * scale + 1e-30).all()), float((err / scale.clamp_min(1e-30)).max())
+
+
+def test_gemm_row_major_out(rsk):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    A = torch.randn(1000, 640, generator=g, device="cuda").to(torch.bfloat16)
+    B = torch.randn(300, 640, generator=g, device="cuda").to(torch.bfloat16)
+    D = rsk.rsk_gemm_bf16_ex(A, B, row_major_out=True)
+    Dc = rsk.rsk_gemm_bf16(A, B)
+    torch.cuda.synchronize()
+    assert D.is_contiguous() and torch.equal(D, Dc)        # the same accumulation, stored transposed
+
+
+@pytest.mark.parametrize("a_mn,M,K,N,nsplit", [(False, 300, 262144, 300, 48), (False, 300, 20000, 300, 8),
+                                               (True, 20000, 300, 300, 1), (True, 8192, 300, 256, 1),
+                                               (False, 1000, 300, 77, 1), (True, 4100, 1000, 300, 2)])
+def test_gemm_f32_accuracy(rsk, a_mn, M, K, N, nsplit):
+    """Three-term BF16 splits: within FP32 rounding of the exact product of the FP32 inputs (the
+    neglected split products are O(2^-24) relative; FP32 accumulation over K adds K u |A||B|)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(M + 3 * K + N)
+    A = torch.randn(K, M, generator=g, device="cuda") if a_mn else torch.randn(M, K, generator=g, device="cuda")
+    B = torch.randn(N, K, generator=g, device="cuda")
+    D = rsk.rsk_gemm_f32(A, B, a_mn=a_mn, nsplit=nsplit)
+    torch.cuda.synchronize()
+    rsk.rsk_sync_status()
+    Aop = A.double().T if a_mn else A.double()
+    ref = Aop @ B.double().T
+    scale = Aop.abs() @ B.double().abs().T
+    rel = ((D.double() - ref).abs() / scale).max().item()
+    # FP32 accumulation: a few u_32 per term in the worst case; typically ~sqrt(K) u_32
+    assert rel <= 64 * 2.0 ** -24 * max(1.0, K ** 0.5 / 8), rel
+    # and far beyond what one BF16 product could give
+    assert rel <= 1e-5
+
+
+def test_gemm_f32_gram_symmetric_orthogonal(rsk):
+    """X^T X of an orthonormal X (QR of a Gaussian, FP32) is I to FP32 accuracy."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    X, _ = torch.linalg.qr(torch.randn(50000, 300, generator=g, device="cuda", dtype=torch.float64))
+    Xc = X.float().T.contiguous()          # column-major X = row-major X^T (300 x 50000)
+    ref = X.float().double().T @ X.float().double()
+    errs = {}
+    for nsplit in (16, 160):
+        G = rsk.rsk_gemm_f32(Xc, Xc, nsplit=nsplit)
+        torch.cuda.synchronize()
+        errs[nsplit] = (G.double() - ref).abs().max().item()
+    # the accumulation truncates: the diagonal's bias follows the main term's K steps per split, up to
+    # about 2^-24 each (nsplit 16: 196 steps, measured 7.7e-6; nsplit 160: 20 steps, 1.1e-6), plus the
+    # round-to-nearest sum of the partials
+    assert errs[16] <= 196 * 2.0 ** -24, errs
+    assert errs[160] <= 2e-6, errs
