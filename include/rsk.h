@@ -486,10 +486,13 @@ rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int
 /* The same product with the operand and output layouts of the RSVD's steps: a_mn != 0 takes A
  * MN-major, i.e. element (m, k) at A[k * lda + m] (lda >= M: A^T of a row-major K x M matrix, so that
  * Z = A^T Q reads A in place); d_row_major != 0 stores D row-major (element (m, n) at D[m * ldd + n],
- * ldd >= N) instead of column-major.  Alignment, limits and nsplit as rsk_gemm_bf16. */
+ * ldd >= N) instead of column-major.  cluster = 1, 2 or 4 row tiles per thread-block cluster share the
+ * B tile (each CTA loads its part and multicasts it: B's traffic from L2 falls by that factor; 4 only
+ * when N rounds to 256, 320 or 512 columns), 0 takes 2 with at least 8 row tiles, else 1.  Alignment,
+ * limits and nsplit as rsk_gemm_bf16. */
 rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* A, int64_t M, int64_t K, int64_t lda,
                             const void* B, int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t d_row_major,
-                            int32_t nsplit, cudaStream_t stream);
+                            int32_t nsplit, int32_t cluster, cudaStream_t stream);
 /* D = A B^T for FP32 device A, B at FP32 accuracy on the BF16 tensor cores: each operand is split into
  * three BF16 terms (x = x1 + x2 + x3 + O(2^-24 |x|)) and the six products x_i y_j with i + j <= 4
  * accumulate in FP32 in tensor memory, the corrections first and x1 y1 last.  The tensor cores' FP32

@@ -545,16 +545,16 @@ def _gemm_out(M, N, row_major_out, device):
     return torch.empty(M, N, device=device) if row_major_out else torch.empty(N, M, device=device).t()
 
 
-def rsk_gemm_bf16_ex(A, B, a_mn=False, row_major_out=False, nsplit=1, stream=None):
+def rsk_gemm_bf16_ex(A, B, a_mn=False, row_major_out=False, nsplit=1, cluster=0, stream=None):
     """D = op(A) @ B.T on the tensor cores, BF16 operands, FP32 D (M x N).  op(A) = A.T when a_mn (A is
     K x M row-major, read in place as an MN-major operand), else A (M x K).  D row-major when
-    row_major_out, else a column-major view."""
+    row_major_out, else a column-major view.  cluster: row tiles sharing the B tile (0 automatic)."""
     M, K, N = _gemm_operands(A, B, a_mn, torch.bfloat16)
     D = _gemm_out(M, N, row_major_out, A.device)
     h = handle(A.device)
     _check(load().rsk_gemm_bf16_ex(h, int(a_mn), A.data_ptr(), M, K, A.stride(0), B.data_ptr(), N, B.stride(0),
                                    D.data_ptr(), D.stride(0) if row_major_out else D.stride(1), int(row_major_out),
-                                   nsplit, _stream(stream)), h)
+                                   nsplit, cluster, _stream(stream)), h)
     return D
 
 

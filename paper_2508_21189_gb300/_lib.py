@@ -66,7 +66,8 @@ SIGNATURES = {
     "rsk_autotune_sketch": [c_p, c_i32, c_i32, c_i64, c_i64, c_i64, c_i32, c_p, c_p, c_p],
     "rsk_autotune_batched": [c_p, c_i32, c_p, c_p, c_p, c_p, c_p],
     "rsk_gemm_bf16": [c_p, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_p],
-    "rsk_gemm_bf16_ex": [c_p, c_i32, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_i32, c_p],
+    "rsk_gemm_bf16_ex": [c_p, c_i32, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_i32, c_i32,
+                         c_p],
     "rsk_gemm_f32": [c_p, c_i32, c_p, c_i64, c_i64, c_i64, c_p, c_i64, c_i64, c_p, c_i64, c_i32, c_i32, c_p],
     "rsk_rsvd": [c_p, c_p, c_i64, c_i64, c_i64, c_i32, c_i32, c_i32, c_u64, c_p, c_p, c_p, c_p],
 }

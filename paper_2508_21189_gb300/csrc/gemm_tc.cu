@@ -6,8 +6,9 @@
 // One CTA per 128-row tile of D (and per K split): 6 warps.
 //   warp 0, one thread   TMA producer: per 64-wide K block (of every pass), the 128 x 64 tile of A (one
 //                        box for K-major A, two 64 x 64 boxes for MN-major A) and the N x 64 tile of B
-//                        (two boxes of N/2 rows) into one of 3 shared-memory stages (2 when N = 512;
-//                        128-byte swizzle), completion counted on the stage's `full` mbarrier
+//                        (two boxes of N/2 rows; with a cluster of 2 or 4 row tiles, this CTA's share of
+//                        it, multicast to the cluster) into one of up to 4 shared-memory stages (128-byte
+//                        swizzle), completion counted on the stage's `full` mbarrier
 //   warp 1, one thread   MMA issuer: per K block, 4 K-steps of 16, each two tcgen05.mma (M = 128,
 //                        N = N/2) into the TMEM accumulator (128 lanes x N FP32 columns); a tcgen05.commit
 //                        on the stage's `empty` barrier frees it, a last one on `tmem_full` hands the
@@ -27,10 +28,10 @@
 namespace {
 
 constexpr int kBM = 128, kBK = 64, kThreads = 192;
-// pipeline depth: 3 stages while they fit in 200 KB of shared memory, else 2
+// pipeline depth: as many stages (at most 4) as fit in 227 KB of shared memory with the barriers
 template <int NH>
 constexpr int stages_for() {
-    return 3 * (kBM * kBK * 2 + 2 * NH * kBK * 2) <= 200 * 1024 ? 3 : 2;
+    return std::min(4, (227 * 1024 - 1024 - 256) / (kBM * kBK * 2 + 2 * NH * kBK * 2));
 }
 
 // tcgen05 shared-memory matrix descriptor, 128-byte swizzle: start address (bits 0-13, >> 4), leading
@@ -82,6 +83,32 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                      rskd::smem_u32(bar))
                  : "memory");
 }
+// The same arrive on the barrier at this offset in every CTA of `mask` (thread-block cluster).
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     rskd::smem_u32(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+// 2-D tiled TMA load delivered to the same shared-memory offset in every CTA of `mask`, completion
+// counted on the barrier at the same offset in each of them.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3}], [%4], %5;" ::"r"(rskd::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(rskd::smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // 32 lanes x 32 consecutive FP32 columns: thread t of the warp receives lane (base lane + t).
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
@@ -114,7 +141,11 @@ struct GemmArgs {
     unsigned int* status;
 };
 
-template <int NH, bool A_MN>
+// CL > 1: the CTAs of a cluster (consecutive row tiles) share the B tile: CTA rank c loads rows
+// [c 2NH/CL, (c+1) 2NH/CL) of it and multicasts them to the whole cluster, so each stage's `full`
+// barrier counts the own A tile plus the CL pieces, and a stage is free again only when every CTA's
+// MMAs are done with it (its `empty` barrier takes one multicast commit from each CTA).
+template <int NH, bool A_MN, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmMaps maps, const GemmArgs a) {
     constexpr int kStages = stages_for<NH>();
@@ -138,10 +169,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nk = int(std::min<int64_t>(a.kblocks, a.nk_total - kb0));
     const int total = nk > 0 ? nk * a.npass : 0;
 
+    constexpr uint16_t kMask = uint16_t((1u << CL) - 1);
+    constexpr int kPieceRows = 2 * NH / CL;                // rows of B each CTA of the cluster loads
+    const int rank = CL > 1 ? int(cluster_rank()) : 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             rskd::mbar_init(&full[s], 1);
-            rskd::mbar_init(&empty[s], 1);
+            rskd::mbar_init(&empty[s], CL);
             consumed[s] = 0;
         }
         rskd::mbar_init(tfull, 1);
@@ -151,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) tc_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
+    if constexpr (CL > 1) cluster_sync();   // every CTA's barriers exist before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -176,9 +211,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
                     rskd::tma_load_2d(st, ma, kx, int(m0), &full[s]);
                 }
-                rskd::tma_load_2d(st + kABytes, mb, kx, 0, &full[s]);
-                rskd::tma_load_2d(st + kABytes + NH * kBK * 2, mb, kx, NH, &full[s]);
+                if constexpr (CL == 1) {
+                    rskd::tma_load_2d(st + kABytes, mb, kx, 0, &full[s]);
+                    rskd::tma_load_2d(st + kABytes + NH * kBK * 2, mb, kx, NH, &full[s]);
+                } else {
+                    tma_load_2d_mc(st + kABytes + rank * kPieceRows * kBK * 2, mb, kx, rank * kPieceRows, &full[s],
+                                   kMask);
+                }
                 ++issued[s];
+            }
+            if constexpr (CL > 1) {
+                // every CTA's last release of every stage: after it no remote arrive or multicast
+                // write targets this CTA's shared memory (skipped after a timeout: the bounded waits
+                // of the other CTAs outlast their copies in flight)
+                if (!*abort_flag)
+                    for (int s = 0; s < kStages && s < total; ++s) {
+                        const int last = (total - 1 - s) / kStages;   // use number of the stage's last fill
+                        rskd::mbar_wait(&empty[s], uint32_t(last & 1), a.status);
+                    }
             }
             // copies still owed to a stage (only after a timeout) land before the CTA leaves.  The MMA
             // thread advances consumed[s] concurrently: one read decides both whether a copy is owed
@@ -210,7 +260,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tc_mma(tmem + uint32_t(hh * NH), ad, bd, idesc, (it | kk) != 0 ? 1u : 0u);
                     }
                 }
-                tc_commit(&empty[s]);
+                if constexpr (CL == 1) tc_commit(&empty[s]);
+                else tc_commit_mc(&empty[s], kMask);
             }
             // the accumulator is complete (or the issued MMAs are done, after a timeout)
             tc_commit(tfull);
@@ -256,6 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         tc_dealloc(tmem, kTmemCols);
     }
+    if constexpr (CL > 1) cluster_sync();   // no CTA leaves while another may still signal it
 }
 
 // D = sum over splits (in split order) of the column-major partials.
@@ -287,6 +339,31 @@ __global__ void k_split3(const float* __restrict__ X, int64_t rows, int64_t cols
         }
 }
 
+// The same split, four consecutive rows a thread (rows, ldx, ldt multiples of 4; X 16-byte and the
+// outputs 8-byte aligned): one 16-byte load and three 8-byte stores.
+__global__ void k_split3_v4(const float* __restrict__ X, int64_t rows4, int64_t cols, int64_t ldx,
+                            __nv_bfloat16* __restrict__ o1, __nv_bfloat16* __restrict__ o2,
+                            __nv_bfloat16* __restrict__ o3, int64_t ldt) {
+    for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+        for (int64_t r4 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r4 < rows4;
+             r4 += int64_t(gridDim.x) * blockDim.x) {
+            const float4 x = *reinterpret_cast<const float4*>(X + c * ldx + 4 * r4);
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+            __nv_bfloat16 b1[4], b2[4], b3[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                b1[i] = __float2bfloat16_rn(xs[i]);
+                const float r1 = xs[i] - __bfloat162float(b1[i]);
+                b2[i] = __float2bfloat16_rn(r1);
+                b3[i] = __float2bfloat16_rn(r1 - __bfloat162float(b2[i]));
+            }
+            const int64_t o = c * ldt + 4 * r4;
+            *reinterpret_cast<uint2*>(o1 + o) = *reinterpret_cast<const uint2*>(b1);
+            *reinterpret_cast<uint2*>(o2 + o) = *reinterpret_cast<const uint2*>(b2);
+            *reinterpret_cast<uint2*>(o3 + o) = *reinterpret_cast<const uint2*>(b3);
+        }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                           __nv_bfloat16* __restrict__ out, int64_t ldt) {
     for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
@@ -306,34 +383,62 @@ __global__ void k_to_bf16_flat(const float4* __restrict__ X, int64_t n4, uint2* 
     }
 }
 
-template <int NH, bool A_MN>
+template <int NH, bool A_MN, int CL>
 rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, const GemmArgs& ga, int mtiles, int nsplit,
                        cudaStream_t stream) {
     constexpr int kStage = kBM * kBK * 2 + 2 * NH * kBK * 2;
     const int smem = stages_for<NH>() * kStage + 1024 + 256;
-    auto kern = k_gemm_tc<NH, A_MN>;
+    auto kern = k_gemm_tc<NH, A_MN, CL>;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned((mtiles + CL - 1) / CL * CL), unsigned(nsplit));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_GEMM);
-    kern<<<dim3(unsigned(mtiles), unsigned(nsplit)), kThreads, smem, stream>>>(maps, ga);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, ga);
     rsk::prof_end(h, stream, pr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return rsk::fail(h, RSK_ERR_CUDA, "gemm launch: %s", cudaGetErrorString(e));
+    }
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
 
-template <bool A_MN>
+// Clusters of 4 are built for the N halves of the RSVD's ranks (128, 160, 256) only.
+constexpr bool cluster4_nh(int nh) { return nh == 128 || nh == 160 || nh == 256; }
+
+template <bool A_MN, int CL>
 rsk_status dispatch_nh(rsk_handle* h, int nh, const GemmMaps& maps, const GemmArgs& ga, int mtiles, int nsplit,
                        cudaStream_t stream) {
-    switch (nh) {
-        case 16: return launch_gemm<16, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 32: return launch_gemm<32, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 48: return launch_gemm<48, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 64: return launch_gemm<64, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 96: return launch_gemm<96, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 128: return launch_gemm<128, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 160: return launch_gemm<160, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 192: return launch_gemm<192, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        case 256: return launch_gemm<256, A_MN>(h, maps, ga, mtiles, nsplit, stream);
-        default: return rsk::fail(h, RSK_ERR_UNSUPPORTED, "gemm: N half %d is not supported", nh);
+    if constexpr (CL == 4) {
+        switch (nh) {
+            case 128: return launch_gemm<128, A_MN, 4>(h, maps, ga, mtiles, nsplit, stream);
+            case 160: return launch_gemm<160, A_MN, 4>(h, maps, ga, mtiles, nsplit, stream);
+            case 256: return launch_gemm<256, A_MN, 4>(h, maps, ga, mtiles, nsplit, stream);
+            default: return rsk::fail(h, RSK_ERR_UNSUPPORTED, "gemm: clusters of 4 need N half 128, 160 or 256");
+        }
+    } else {
+        switch (nh) {
+            case 16: return launch_gemm<16, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 32: return launch_gemm<32, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 48: return launch_gemm<48, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 64: return launch_gemm<64, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 96: return launch_gemm<96, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 128: return launch_gemm<128, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 160: return launch_gemm<160, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 192: return launch_gemm<192, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 256: return launch_gemm<256, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            default: return rsk::fail(h, RSK_ERR_UNSUPPORTED, "gemm: N half %d is not supported", nh);
+        }
     }
 }
 
@@ -361,7 +466,7 @@ void set_split_passes(Product& p) {
     }
 }
 
-rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream) {
+rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream, int cluster) {
     if (p.M < 1 || p.K < 1 || p.N < 1 || p.N > 512 || p.ldd < (p.d_row_major ? p.N : p.M))
         return fail(h, RSK_ERR_INVALID_ARG, "gemm: bad shape");
     if (p.npass < 1 || p.npass > kMaxPasses || p.na < 1 || p.na > kMaxOperands || p.nb < 1 || p.nb > kMaxOperands)
@@ -380,6 +485,15 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
     nsplit = int(std::max<int64_t>(1, std::min<int64_t>(nsplit, nk)));
     const int kblocks = int((nk + nsplit - 1) / nsplit);
     nsplit = int((nk + kblocks - 1) / kblocks);
+    const int mtiles = int((p.M + kBM - 1) / kBM);
+    // row tiles per cluster sharing the B tile (multicast): automatic = 2 with at least 8 row tiles
+    // (measured on the RSVD's 262144 x 8192 x 300 products: pairs 6% faster than single tiles, fours no
+    // faster than pairs), else 1
+    if (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4)
+        return fail(h, RSK_ERR_INVALID_ARG, "gemm: cluster must be 0 (automatic), 1, 2 or 4");
+    if (cluster == 4 && !cluster4_nh(nh))
+        return fail(h, RSK_ERR_UNSUPPORTED, "gemm: clusters of 4 need N half 128, 160 or 256 (have %d)", nh);
+    const int cl = cluster ? cluster : mtiles >= 8 ? 2 : 1;
     GemmMaps maps;
     memset(&maps, 0, sizeof(maps));
     for (int i = 0; i < p.na; ++i) {
@@ -391,7 +505,7 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
     }
     for (int i = 0; i < p.nb; ++i)
         if (!encode_2d_swz128(h, &maps.b[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.b[i], uint64_t(p.K), uint64_t(p.N),
-                              uint64_t(p.ldb) * 2, kBK, uint32_t(nh)))
+                              uint64_t(p.ldb) * 2, kBK, uint32_t(cl == 4 ? nh / 2 : nh)))
             return fail(h, RSK_ERR_UNSUPPORTED, "gemm: tensor map encoding failed (B)");
     GemmArgs ga;
     memset(&ga, 0, sizeof(ga));
@@ -418,9 +532,16 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
         ga.row_major = p.d_row_major ? 1 : 0;
         ga.split_stride = 0;
     }
-    const int mtiles = int((p.M + kBM - 1) / kBM);
-    const rsk_status st = p.a_mn ? dispatch_nh<true>(h, nh, maps, ga, mtiles, nsplit, stream)
-                                 : dispatch_nh<false>(h, nh, maps, ga, mtiles, nsplit, stream);
+    rsk_status st;
+    if (cl == 4)
+        st = p.a_mn ? dispatch_nh<true, 4>(h, nh, maps, ga, mtiles, nsplit, stream)
+                    : dispatch_nh<false, 4>(h, nh, maps, ga, mtiles, nsplit, stream);
+    else if (cl == 2)
+        st = p.a_mn ? dispatch_nh<true, 2>(h, nh, maps, ga, mtiles, nsplit, stream)
+                    : dispatch_nh<false, 2>(h, nh, maps, ga, mtiles, nsplit, stream);
+    else
+        st = p.a_mn ? dispatch_nh<true, 1>(h, nh, maps, ga, mtiles, nsplit, stream)
+                    : dispatch_nh<false, 1>(h, nh, maps, ga, mtiles, nsplit, stream);
     if (st != RSK_OK || nsplit == 1) return st;
     k_sum_splits<<<unsigned((p.M * p.N + 255) / 256), 256, 0, stream>>>(scratch, p.M * int64_t(p.N), nsplit, p.M, p.N,
                                                                         p.ldd, p.d_row_major ? 1 : 0, p.D);
@@ -435,7 +556,13 @@ static dim3 elementwise_grid(int64_t rows, int64_t cols) {
 rsk_status split3(rsk_handle* h, const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* const* out,
                   int64_t ldt, cudaStream_t stream) {
     const int pr = prof_begin(h, stream, RSK_KERNEL_CONVERT);
-    k_split3<<<elementwise_grid(rows, cols), 256, 0, stream>>>(X, rows, cols, ldx, out[0], out[1], out[2], ldt);
+    bool v4 = rows % 4 == 0 && ldx % 4 == 0 && ldt % 4 == 0 && aligned16(X);
+    for (int i = 0; i < 3; ++i) v4 = v4 && reinterpret_cast<uintptr_t>(out[i]) % 8 == 0;
+    if (v4)
+        k_split3_v4<<<elementwise_grid(rows / 4, cols), 256, 0, stream>>>(X, rows / 4, cols, ldx, out[0], out[1], out[2],
+                                                                          ldt);
+    else
+        k_split3<<<elementwise_grid(rows, cols), 256, 0, stream>>>(X, rows, cols, ldx, out[0], out[1], out[2], ldt);
     prof_end(h, stream, pr);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
@@ -503,7 +630,7 @@ rsk_status f32_product(rsk_handle* h, bool a_mn, const float* A, int64_t lda, co
 
 extern "C" rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* A, int64_t M, int64_t K, int64_t lda,
                                        const void* B, int64_t N, int64_t ldb, float* D, int64_t ldd,
-                                       int32_t d_row_major, int32_t nsplit, cudaStream_t stream) {
+                                       int32_t d_row_major, int32_t nsplit, int32_t cluster, cudaStream_t stream) {
     if (!h) return RSK_ERR_INVALID_ARG;
     if (!A || !B || !D) return rsk::fail(h, RSK_ERR_INVALID_ARG, "null pointer");
     if (M < 1 || K < 1 || N < 1 || N > 512 || lda < (a_mn ? M : K) || ldb < K || ldd < (d_row_major ? N : M))
@@ -531,12 +658,12 @@ extern "C" rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* 
     p.D = D;
     p.ldd = ldd;
     p.d_row_major = d_row_major != 0;
-    return rsk::tc::gemm(h, p, nsplit, scratch, stream);
+    return rsk::tc::gemm(h, p, nsplit, scratch, stream, cluster);
 }
 
 extern "C" rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B,
                                     int64_t N, int64_t ldb, float* D, int64_t ldd, int32_t nsplit, cudaStream_t stream) {
-    return rsk_gemm_bf16_ex(h, 0, A, M, K, lda, B, N, ldb, D, ldd, 0, nsplit, stream);
+    return rsk_gemm_bf16_ex(h, 0, A, M, K, lda, B, N, ldb, D, ldd, 0, nsplit, 0, stream);
 }
 
 extern "C" rsk_status rsk_gemm_f32(rsk_handle* h, int32_t a_mn, const float* A, int64_t M, int64_t K, int64_t lda,

@@ -41,7 +41,9 @@ struct Product {
 // Scratch for split-K partials (nsplit > 1).
 size_t gemm_scratch_bytes(int64_t M, int N, int nsplit);
 // Runs the product with K split over nsplit CTAs per row tile (partials summed in split order).
-rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream);
+// cluster: row tiles per thread-block cluster that share (multicast) the B tile, 1, 2 or 4 (4 for N
+// halves 128, 160, 256 only); 0 picks 2 with at least 8 row tiles, else 1.
+rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream, int cluster = 0);
 
 // The six split pairs (3,1), (1,3), (2,2), (2,1), (1,2), (1,1) of two three-term splits, in that
 // order.  The accumulation truncates: a same-sign sum's relative bias grows by up to about 2^-24 per

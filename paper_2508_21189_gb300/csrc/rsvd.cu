@@ -83,9 +83,10 @@ namespace rsk {
 
 // Partials of a split-K product with M x N output.
 static int gram_splits(int64_t K) {
-    // at most 8 K blocks (32 accumulation steps of the main term) per accumulator
+    // at most 16 K blocks (64 accumulation steps of the main term) per accumulator: the truncated
+    // accumulation's relative bias stays below ~64 x 2^-24 ~ 4e-6
     const int64_t nk = (K + 63) / 64;
-    return int(std::max<int64_t>(1, (nk + 7) / 8));
+    return int(std::max<int64_t>(1, (nk + 15) / 16));
 }
 
 // X (rows x r, ld ldx) <- orthonormal basis of range(X) by `rounds` Cholesky QR rounds (the first
@@ -93,8 +94,8 @@ static int gram_splits(int64_t K) {
 // receives the accumulated upper factor with X_in = Q Racc.
 static rsk_status orth_tc(rsk_handle* h, float** X, float** Xalt, int64_t rows, int r, int64_t ldx, int rounds,
                           float* Racc, Ws& w, cudaStream_t s) {
-    // Shift of the first round: the split Gram's relative error is ~1e-6 (truncated accumulation over
-    // at most 32 steps per split plus the rounded sum of the partials); 3e-5 trace(G) keeps G + shift
+    // Shift of the first round: the split Gram's relative error is a few 1e-6 (truncated accumulation
+    // over at most 64 steps per split plus the rounded sum of the partials); 3e-5 trace(G) keeps G + shift
     // positive definite for any kappa(X) and leaves kappa(X R^{-1}) <= ~1 / sqrt(3e-5) for the plain
     // rounds that follow (Fukaya et al.'s shifted Cholesky QR with this Gram's error level).
     const float coeff0 = 3e-5f;

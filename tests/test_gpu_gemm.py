@@ -64,7 +64,8 @@ def test_gemm_row_major_out(rsk):
 
 @pytest.mark.parametrize("a_mn,M,K,N,nsplit", [(False, 300, 262144, 300, 48), (False, 300, 20000, 300, 8),
                                                (True, 20000, 300, 300, 1), (True, 8192, 300, 256, 1),
-                                               (False, 1000, 300, 77, 1), (True, 4100, 1000, 300, 2)])
+                                               (False, 1000, 300, 77, 1), (True, 4100, 1000, 300, 2),
+                                               (True, 1001, 301, 45, 1), (False, 333, 1001, 7, 2)])
 def test_gemm_f32_accuracy(rsk, a_mn, M, K, N, nsplit):
     """Three-term BF16 splits: within FP32 rounding of the exact product of the FP32 inputs (the
     neglected split products are O(2^-24) relative; FP32 accumulation over K adds K u |A||B|)."""
@@ -102,3 +103,36 @@ def test_gemm_f32_gram_symmetric_orthogonal(rsk):
     # round-to-nearest sum of the partials
     assert errs[16] <= 196 * 2.0 ** -24, errs
     assert errs[160] <= 2e-6, errs
+
+
+@pytest.mark.parametrize("a_mn,M,K,N,nsplit", [(False, 1000, 1000, 300, 1), (True, 1000, 4096, 300, 2),
+                                               (False, 4100, 640, 256, 1), (True, 8192, 8192, 300, 2),
+                                               (False, 777, 4104, 512, 3)])
+@pytest.mark.parametrize("cluster", [2, 4])
+def test_gemm_cluster_multicast(rsk, a_mn, M, K, N, nsplit, cluster):
+    """Row tiles in clusters of 2 or 4 share the B tile by multicast: the same accumulation as the
+    unclustered product, so the results are identical; a row-tile count that is not a multiple of the
+    cluster adds tiles beyond M that write nothing."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(M + K + N + cluster)
+    A = torch.randn(K, M + (8 - M % 8) % 8, generator=g, device="cuda").to(torch.bfloat16)[:, :M] if a_mn else \
+        torch.randn(M, K, generator=g, device="cuda").to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+    D1 = rsk.rsk_gemm_bf16_ex(A, B, a_mn=a_mn, nsplit=nsplit, cluster=1)
+    Dc = rsk.rsk_gemm_bf16_ex(A, B, a_mn=a_mn, nsplit=nsplit, cluster=cluster)
+    torch.cuda.synchronize()
+    rsk.rsk_sync_status()
+    assert torch.equal(D1, Dc)
+    Aop = A.double().T if a_mn else A.double()
+    ref = Aop @ B.double().T
+    scale = Aop.abs() @ B.double().abs().T
+    assert bool(((Dc.double() - ref).abs() <= 1e-5 * scale + 1e-30).all())
+
+
+def test_gemm_cluster_invalid(rsk):
+    A = torch.zeros(256, 64, device="cuda", dtype=torch.bfloat16)
+    B = torch.zeros(48, 64, device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(rsk.RskError):
+        rsk.rsk_gemm_bf16_ex(A, B, cluster=3)
+    with pytest.raises(rsk.RskError):
+        rsk.rsk_gemm_bf16_ex(A, B, cluster=4)       # N half 32: no cluster of 4 is built
