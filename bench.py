@@ -35,6 +35,7 @@ N_ROWS, K_COLS, D_SKETCH, ZETA = 1 << 22, 256, 2048, 8
 LSQ_N, LSQ_K, LSQ_D = 1 << 20, 500, 2000
 BATCH_COUNT = 512
 RSVD_M, RSVD_N, RSVD_R, RSVD_Q, RSVD_RANK = 262144, 8192, 300, 2, 400
+RSVD_TWIN = (16384, 2048, 100, 75)  # m, n, spectrum rank, r of the reduced twin the oracle also runs
 NYS_N, NYS_K, NYS_RANK = 32768, 300, 1000
 GEN_N, GEN_D, GEN_K, GEN_RANK = 131072, 40000, 200, 400
 OSI_R = (10 ** 5, 10 ** 6, 10 ** 7)
@@ -269,6 +270,15 @@ def cpu_extras():
     t = time.perf_counter() - t0
     out["lsq"] = {"sample": f"sketch-and-precondition (oracle: FP64 sketch, QR, LSQR refinement) on {nl} x {kl}, "
                             "kappa=1e8 (reduced from 2^20 x 500)", "s": round(t, 3), "solves_per_s": round(1 / t, 4)}
+    import synthetic
+    from oracle import rsvd as orsvd
+    m_t, n_t, rank_t, r_t = RSVD_TWIN
+    At = synthetic.lowrank_plus_noise(m_t, n_t, rank_t, seed=m_t + n_t, noise=1e-4, device="cpu").double().numpy()
+    t0 = time.perf_counter()
+    Q = orsvd.range_finder(At, r_t, RSVD_Q, ZETA, 5)
+    t = time.perf_counter() - t0
+    out["rsvd_twin"] = {"sample": f"range finder (Alg. 1 + {RSVD_Q} power iterations, FP64) on {m_t} x {n_t}, r={r_t}",
+                        "s": round(t, 3), "oracle_spectral_error": orsvd.spectral_error(At, Q, iters=30, seed=1)}
     return out
 
 
@@ -448,14 +458,34 @@ def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH
             "mixed": res["mixed"], "fp64": res["fp64"]}
 
 
+def spectral_error_gpu(torch, A, U, iters=20, seed=3):
+    """||A - U U^T A||_2 by the power method in FP64 on the GPU (plain torch: a measurement, not the
+    library's path)."""
+    g = torch.Generator(device=A.device)
+    g.manual_seed(seed)
+    Ad, Ud = A.double(), U.double()
+    v = torch.randn(A.shape[1], generator=g, device=A.device, dtype=torch.float64)
+    v /= v.norm()
+    est = 0.0
+    for _ in range(iters):
+        y = Ad @ v
+        y = y - Ud @ (Ud.T @ y)
+        est = y.norm().item()
+        v = Ad.T @ y
+        v /= v.norm()
+    del Ad, Ud
+    return est
+
+
 def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps, rows=RSVD_M, profiler_range=False):
-    """RSVD of A 262144 x 8192 FP32 (rank-400 spectrum j^-2 plus 1e-4 noise), r = 300, q = 2.
-    profiler_range: open the CUDA profiler range (cudaProfilerStart/Stop) around the timed calls only,
-    so that a capture with --profile-from-start off skips the warm-up call's GEMM autotuning."""
+    """RSVD of A 262144 x 8192 FP32 (rank-400 spectrum j^-2 plus 1e-4 noise), r = 300, q = 2, on this
+    library's kernels: time per call, per-phase device time, the big BF16 products against the BF16
+    and HBM rooflines, and the spectral error ||A - U U^T A||_2 at full size (FP64 power method) and on
+    the reduced twin that the FP64 oracle also runs (its error is filled in from the CPU leg).
+    profiler_range: open the CUDA profiler range (cudaProfilerStart/Stop) around the timed calls only."""
     A = synthetic.lowrank_plus_noise(rows, RSVD_N, RSVD_RANK, seed=2025 + rank, noise=1e-4, device=dev)
 
     def after_warmup():
-        # profiling starts after the warm-up call, which also loads the GEMM library's kernels
         rsk.rsk_profile_enable(True)
         if profiler_range:
             torch.cuda.synchronize()
@@ -465,21 +495,56 @@ def bench_rsvd(rsk, synthetic, torch, dev, rank, world, reps, rows=RSVD_M, profi
                                  reps, torch, dev, after_warmup=after_warmup)
     if profiler_range:
         torch.cuda.profiler.stop()
-    gemm = rsk.rsk_profile_read("gemm")
+    phases = {k: rsk.rsk_profile_read(k) for k in ("gemm", "gemm_split", "factor", "small_svd", "convert",
+                                                   "sketch_generate")}
     rsk.rsk_profile_enable(False)
-    rp = (RSVD_R + 7) // 8 * 8  # the library pads the GEMM dimension to a multiple of 8
-    flops = (2 + 2 * RSVD_Q) * 2 * rows * RSVD_N * rp
-    gemm_ms = gemm[0] / reps
+    calls = reps + 0  # the profile covers the timed calls only
+    big = 2 + 2 * RSVD_Q                    # Y = A Omega, q x (Z = A^T Q, Y = A Z), Z = A^T Q
+    flops = big * 2 * rows * RSVD_N * RSVD_R
+    gemm_ms = phases["gemm"][0] / calls
+    bf16, bf16_kind = bf16_peak()
+    sustained = bf16_sustained()
+    hbm, hbm_kind = hbm_peak()
+    a_bf16_bytes = rows * RSVD_N * 2        # each big product streams the BF16 copy of A once
+    err = spectral_error_gpu(torch, A, U)
+    floor = 1e-4 * (math.sqrt(rows) + math.sqrt(RSVD_N))
+    sg = s.cpu()
     del A, U, s, Vt
     torch.cuda.empty_cache()
+    m_t, n_t, rank_t, r_t = RSVD_TWIN
+    At = synthetic.lowrank_plus_noise(m_t, n_t, rank_t, seed=m_t + n_t, noise=1e-4, device="cpu").to(dev)
+    Ut, _, _ = rsk.rsk_rsvd(At, r_t, power_iters=RSVD_Q, zeta=ZETA, seed=5)
+    err_t = spectral_error_gpu(torch, At, Ut)
+    del At, Ut
+    torch.cuda.empty_cache()
+    gemm_tf = flops / (gemm_ms / 1e3) / 1e12 if gemm_ms > 0 else None
     return {"workload": f"RSVD A {rows} x {RSVD_N} FP32 (rank-400 spectrum j^-2 + 1e-4 noise), r=300, q=2, "
                         "sparse sign Omega zeta=8",
             "value": round(world * 1e3 / ms, 3), "unit": "calls/s", "ms_per_call": round(ms, 3),
-            "gemm_ms_per_call": round(gemm_ms, 3), "gemm_launches_per_call": gemm[1] // max(1, reps),
-            "gemm_flops_per_call": flops,
-            "gemm_tflops": round(flops / (gemm_ms / 1e3) / 1e12, 1) if gemm_ms > 0 else None,
-            "gemm_frac_of_bf16_peak": (round(flops / (gemm_ms / 1e3) / 1e12 / bf16_peak()[0], 4)
-                                       if gemm_ms > 0 else None)}
+            "phases_ms_per_call": {k: round(v[0] / calls, 3) for k, v in phases.items()},
+            "launches_per_call": {k: v[1] // max(1, calls) for k, v in phases.items()},
+            "gemm_big_products": {"count": big, "flops_per_call": flops, "ms_per_call": round(gemm_ms, 3),
+                                  "tflops": round(gemm_tf, 1) if gemm_tf else None,
+                                  "frac_of_bf16_burst": round(gemm_tf / bf16, 4) if gemm_tf else None,
+                                  "frac_of_bf16_sustained": round(gemm_tf / sustained, 4) if gemm_tf else None,
+                                  "peak_kind": bf16_kind,
+                                  "a_stream_gbs": round(big * a_bf16_bytes / (gemm_ms / 1e3) / 1e9, 1) if gemm_ms else None,
+                                  "frac_of_hbm": round(big * a_bf16_bytes / (gemm_ms / 1e3) / 1e9 / hbm, 4)
+                                  if gemm_ms else None, "hbm_kind": hbm_kind},
+            "spectral_error": {"value": err, "method": "FP64 power method, 20 iterations, on the GPU",
+                               "noise_floor": floor, "best_rank_r_noise_free": (RSVD_R + 1) ** -2.0,
+                               "sigma_1": float(sg[0])},
+            "twin": {"workload": f"A {m_t} x {n_t} (rank-{rank_t} j^-2 + 1e-4 noise), r={r_t}, q={RSVD_Q}, "
+                                 "Omega seed 5 (the FP64 oracle's reduced twin)",
+                     "spectral_error": err_t}}
+
+
+def bf16_sustained():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except (OSError, ValueError, KeyError):
+        return 1700.0
 
 
 def time_variants(rsk, A, out, steps, torch, dev):
@@ -798,6 +863,11 @@ def run_ours(args):
         line["config"]["workload"] += f" (reduced to {args.rows} rows for profiling)"
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        twin = line["cpu_baseline"].get("other_workloads", {}).get("rsvd_twin")
+        if twin and "rsvd" in line:
+            e_o = twin["oracle_spectral_error"]
+            line["rsvd"]["twin"]["oracle_spectral_error"] = e_o
+            line["rsvd"]["twin"]["ratio_to_oracle"] = round(line["rsvd"]["twin"]["spectral_error"] / e_o, 4)
     print(json.dumps(line), flush=True)
 
 

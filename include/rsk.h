@@ -90,6 +90,7 @@ typedef enum {
     RSK_KERNEL_FACTOR = 8,         /* small Cholesky factorisations and R^{-1}       */
     RSK_KERNEL_SMALL_SVD = 9,      /* one-sided Jacobi SVD of a small matrix         */
     RSK_KERNEL_CONVERT = 10,       /* BF16 conversions and three-term splits         */
+    RSK_KERNEL_GEMM_SPLIT = 11,    /* FP32-accurate products from split operands     */
     RSK_KERNEL_COUNT = 16
 } rsk_kernel_id;
 /* Turn recording on (on != 0) or off.  Turning it on clears earlier records. */

@@ -457,7 +457,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const JacobiArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int mv = a.V ? a.q : 0;          // rows of V's columns
-    const int cl = a.m + mv;               // floats per local column (X part, then V part)
+    // a local column: the X part padded to a multiple of 4 floats, then the V part likewise (zeros in
+    // the padding stay zero under rotations), so both parts are 16-byte aligned float4 runs
+    const int mp = (a.m + 3) & ~3, vp = (mv + 3) & ~3, cl = mp + vp;
     __shared__ int cols_s[256];            // global column of each local column
     __shared__ int nloc_s;
     __shared__ int rot_s;
@@ -478,10 +480,14 @@ __global__ void __launch_bounds__(1024) k_jacobi(const JacobiArgs a) {
             const int L = nloc_s;
             // columns another CTA rotated in the previous round: read through L2 (ld.cg), never from
             // a line this SM's L1 may still hold from an earlier round
-            for (int l = warp; l < L; l += nw) {
-                const int c = cols_s[l];
-                for (int i = lane; i < a.m; i += 32) sm[l * cl + i] = __ldcg(a.X + int64_t(c) * a.ldx + i);
-                for (int i = lane; i < mv; i += 32) sm[l * cl + a.m + i] = __ldcg(a.V + int64_t(c) * a.ldv + i);
+            // (all threads over the L x cl floats, so that many loads are in flight at once)
+#pragma unroll 4
+            for (int e = tid; e < L * cl; e += blockDim.x) {
+                const int l = e / cl, i = e - l * cl, c = cols_s[l];
+                float v = 0.f;
+                if (i < a.m) v = __ldcg(a.X + int64_t(c) * a.ldx + i);
+                else if (i >= mp && i - mp < mv) v = __ldcg(a.V + int64_t(c) * a.ldv + (i - mp));
+                sm[e] = v;
             }
             __syncthreads();
             // one local sweep over every pair of the L columns (round-robin on Le = L rounded up)
@@ -490,14 +496,14 @@ __global__ void __launch_bounds__(1024) k_jacobi(const JacobiArgs a) {
                 for (int pi = warp; pi < Le / 2; pi += nw) {
                     const int pa = rr_block(pi, lr, Le), pb = rr_block(Le - 1 - pi, lr, Le);
                     if (pa >= L || pb >= L) continue;
-                    float* ca = sm + pa * cl;
-                    float* cb = sm + pb * cl;
+                    float4* ca = reinterpret_cast<float4*>(sm + pa * cl);
+                    float4* cb = reinterpret_cast<float4*>(sm + pb * cl);
                     float al = 0.f, be = 0.f, ga = 0.f;
-                    for (int i = lane; i < a.m; i += 32) {
-                        const float x = ca[i], y = cb[i];
-                        al = fmaf(x, x, al);
-                        be = fmaf(y, y, be);
-                        ga = fmaf(x, y, ga);
+                    for (int i = lane; i < mp / 4; i += 32) {
+                        const float4 x = ca[i], y = cb[i];
+                        al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+                        be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+                        ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -510,19 +516,19 @@ __global__ void __launch_bounds__(1024) k_jacobi(const JacobiArgs a) {
                     const float t = fabsf(zeta) > 1e15f ? 0.5f / zeta
                                                         : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
                     const float c = rsqrtf(1.f + t * t), s = c * t;
-                    for (int i = lane; i < cl; i += 32) {
-                        const float x = ca[i], y = cb[i];
-                        ca[i] = c * x - s * y;
-                        cb[i] = s * x + c * y;
+                    for (int i = lane; i < cl / 4; i += 32) {
+                        const float4 x = ca[i], y = cb[i];
+                        ca[i] = make_float4(c * x.x - s * y.x, c * x.y - s * y.y, c * x.z - s * y.z, c * x.w - s * y.w);
+                        cb[i] = make_float4(s * x.x + c * y.x, s * x.y + c * y.y, s * x.z + c * y.z, s * x.w + c * y.w);
                     }
                     if (lane == 0) rot_s = 1;
                 }
                 __syncthreads();
             }
-            for (int l = warp; l < L; l += nw) {
-                const int c = cols_s[l];
-                for (int i = lane; i < a.m; i += 32) __stcg(a.X + int64_t(c) * a.ldx + i, sm[l * cl + i]);
-                for (int i = lane; i < mv; i += 32) __stcg(a.V + int64_t(c) * a.ldv + i, sm[l * cl + a.m + i]);
+            for (int e = tid; e < L * cl; e += blockDim.x) {
+                const int l = e / cl, i = e - l * cl, c = cols_s[l];
+                if (i < a.m) __stcg(a.X + int64_t(c) * a.ldx + i, sm[e]);
+                else if (i >= mp && i - mp < mv) __stcg(a.V + int64_t(c) * a.ldv + (i - mp), sm[e]);
             }
             if (tid == 0 && rot_s) atomicOr(a.flags + sweep, 1u);
             if (!rskd::grid_barrier(a.bar, a.bar + 1, gridDim.x, a.status, a.limit)) return;
@@ -582,14 +588,18 @@ struct JacobiPlan {
     int G, nb, w;
     size_t smem;
 };
+// Columns per block about 10: a local sweep then has ~10 independent pairs per step for a CTA's
+// warps, and the sweep's 2G - 1 rounds (each ending in a grid barrier) stay few enough; more blocks
+// only while a CTA's 2w columns do not fit in shared memory.
 JacobiPlan jacobi_plan(int64_t m, int q, bool with_v, int num_sms) {
     JacobiPlan p;
-    p.G = 8;
+    const size_t cl = size_t((m + 3) & ~int64_t(3)) + size_t(with_v ? (q + 3) & ~3 : 0);
+    p.G = std::max(8, (q + 19) / 20);
     for (;;) {
         p.nb = 2 * p.G;
         p.w = (q + p.nb - 1) / p.nb;
-        p.smem = size_t(2 * p.w) * size_t(m + (with_v ? q : 0)) * 4;
-        if ((p.smem <= 200 * 1024 && 2 * p.w <= 256) || p.G >= 64) break;
+        p.smem = size_t(2 * p.w) * cl * 4;
+        if ((p.smem <= 200 * 1024 && 2 * p.w <= 256) || p.G >= 128) break;
         p.G *= 2;
     }
     // blocks of at least one column, and no more CTAs than can be resident
@@ -597,7 +607,7 @@ JacobiPlan jacobi_plan(int64_t m, int q, bool with_v, int num_sms) {
         p.G /= 2;
         p.nb = 2 * p.G;
         p.w = (q + p.nb - 1) / p.nb;
-        p.smem = size_t(2 * p.w) * size_t(m + (with_v ? q : 0)) * 4;
+        p.smem = size_t(2 * p.w) * cl * 4;
     }
     return p;
 }

@@ -402,7 +402,7 @@ rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, const GemmArgs& ga, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const int pr = rsk::prof_begin(h, stream, RSK_KERNEL_GEMM);
+    const int pr = rsk::prof_begin(h, stream, ga.npass > 1 ? RSK_KERNEL_GEMM_SPLIT : RSK_KERNEL_GEMM);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, ga);
     rsk::prof_end(h, stream, pr);
     if (e != cudaSuccess) {
