@@ -442,8 +442,11 @@ def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH
     for name, (As, dt) in {"mixed": (As32, torch.float32), "fp64": (As64, torch.float64)}.items():
         ms, (xs, infos) = timed_calls(lambda: rsk.rsk_lstsq_sketch_precond_batched(As, bs, zeta=ZETA, seed=9,
                                                                                      sketch_dtype=dt, inner_dtype=dt),
-                                      reps, torch, dev)
+                                      reps, torch, dev, after_warmup=lambda: rsk.rsk_profile_enable(True))
+        phases = {k: rsk.rsk_profile_read("batch_" + k)[0] / reps for k in ("sketch", "qr", "resid", "cg")}
+        rsk.rsk_profile_enable(False)
         res[name] = {"solves_per_s": round(world * count * 1e3 / ms, 3), "ms_per_batch": round(ms, 3),
+                     "phases_ms": {k: round(v, 3) for k, v in phases.items()},
                      "max_backward_err": max(f["backward_err"] for f in infos),
                      "max_refine_steps": max(f["refine_steps"] for f in infos)}
     rows = sum(ns)

@@ -91,6 +91,10 @@ typedef enum {
     RSK_KERNEL_SMALL_SVD = 9,      /* one-sided Jacobi SVD of a small matrix         */
     RSK_KERNEL_CONVERT = 10,       /* BF16 conversions and three-term splits         */
     RSK_KERNEL_GEMM_SPLIT = 11,    /* FP32-accurate products from split operands     */
+    RSK_KERNEL_BATCH_SKETCH = 12,  /* batched solver phase: all problems' sketches   */
+    RSK_KERNEL_BATCH_QR = 13,      /* batched solver phase: QR, R^{-1}, warm start   */
+    RSK_KERNEL_BATCH_RESID = 14,   /* batched solver phase: residual passes + eta    */
+    RSK_KERNEL_BATCH_CG = 15,      /* batched solver phase: CG graph replays         */
     RSK_KERNEL_COUNT = 16
 } rsk_kernel_id;
 /* Turn recording on (on != 0) or off.  Turning it on clears earlier records. */

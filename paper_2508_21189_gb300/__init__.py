@@ -589,7 +589,8 @@ def rsk_rsvd(A, r, power_iters=2, zeta=8, seed=0, stream=None):
 # Kernel ids of rsk_profile_read (rsk_kernel_id in rsk.h).
 KERNEL_IDS = {"sketch_index": 0, "sketch_apply": 1, "sketch_reduce": 2, "sketch_generate": 3,
               "srtt_apply": 4, "srtt_reduce": 5, "dense": 6, "gemm": 7, "factor": 8, "small_svd": 9,
-              "convert": 10, "gemm_split": 11}
+              "convert": 10, "gemm_split": 11, "batch_sketch": 12, "batch_qr": 13, "batch_resid": 14,
+              "batch_cg": 15}
 
 
 def rsk_profile_enable(on=True, device=None):

@@ -629,12 +629,17 @@ __global__ void k_to_colmajor_b(const S* __restrict__ SA, const double* __restri
     W[idx] = c < k ? double(SA[int64_t(i) * k + c]) : Sb[i];
 }
 
-__global__ void k_split_vec(const double* __restrict__ b, int64_t n, float2* __restrict__ out) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double v = b[i];
-    const float h = float(v);
-    out[i] = make_float2(h, float(v - double(h)));
+// b as double-float pairs (hi = float(b), lo = float(b - hi)) for every problem in one launch
+// (blockIdx.y = problem).
+__global__ void k_split_vec_b(const BProb* __restrict__ P) {
+    const BProb& q = P[blockIdx.y];
+    float2* out = const_cast<float2*>(q.bsplit);
+    if (!out) return;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < q.n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double v = q.b[i];
+        const float h = float(v);
+        out[i] = make_float2(h, float(v - double(h)));
+    }
 }
 
 __global__ void k_f32_to_f64(const float* __restrict__ A, int64_t n, int k, int64_t lda, double* __restrict__ B) {
@@ -797,6 +802,8 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         return double(hp[a].d) * hp[a].k * hp[a].k > double(hp[b_].d) * hp[b_].k * hp[b_].k;
     });
     RSK_CUDA_TRY(h, cudaMemcpyAsync(dorder, order.data(), 4 * size_t(count), cudaMemcpyHostToDevice, main_s));
+    // the sketch phase as a whole (forked from and joined back to main_s), for phase timing
+    const int prs = prof_begin(h, main_s, RSK_KERNEL_BATCH_SKETCH);
     RSK_CUDA_TRY(h, cudaEventRecord(ev_done, main_s));
 
     // ---- sketches, spread over the stream pool
@@ -828,8 +835,6 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
             k_f64_to_f32<<<cgrid, 256, 0, s>>>((const double*)pr.A, pr.n, q.k, pr.lda, (float*)const_cast<void*>(q.Ain));
             RSK_LAUNCH_CHECK(h);
         }
-        k_split_vec<<<unsigned((pr.n + 255) / 256), 256, 0, s>>>(pr.b, pr.n, const_cast<float2*>(q.bsplit));
-        RSK_LAUNCH_CHECK(h);
         st = sketch_build_index(h, pr.n, q.d, zeta, opts->seed + uint64_t(i), index, s);
         if (st == RSK_OK)
             st = sketch_apply_built(h, index, pr.n, q.d, zeta, A_sk, sa_dt, pr.k, lda_sk, SA,
@@ -842,13 +847,17 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         else k_to_colmajor_b<float><<<gw, 256, 0, s>>>(reinterpret_cast<float*>(SA), Sb, q.d, q.k, q.W);
         RSK_LAUNCH_CHECK(h);
     }
+    // the double-float split of every b (for the residual passes), one launch for the whole batch
+    k_split_vec_b<<<dim3(64, unsigned(count)), 256, 0, main_s>>>(dP);
+    RSK_LAUNCH_CHECK(h);
     for (int si = 1; si <= kStreams; ++si) {
         RSK_CUDA_TRY(h, cudaEventRecord(ev_done, h->streams[si]));
         RSK_CUDA_TRY(h, cudaStreamWaitEvent(main_s, ev_done, 0));
     }
+    prof_end(h, main_s, prs);
 
     // ---- QR, R^{-1}, warm start
-    const int pr0 = prof_begin(h, main_s, RSK_KERNEL_DENSE);
+    const int pr0 = prof_begin(h, main_s, RSK_KERNEL_BATCH_QR);
     RSK_CUDA_TRY(h, cudaMemsetAsync(dqueue + 16, 0, 4, main_s));
     k_qr_b<<<std::min(count, h->num_sms), 1024, 0, main_s>>>(dP, dorder, count, dqueue + 16);
     k_rinv_b<<<count, 512, 0, main_s>>>(dP);
@@ -875,7 +884,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         // precision is FP32 (mixed form); the all-FP64 form uses FP64 arithmetic throughout
         bool all_f32 = true;
         for (int i = 0; i < count; ++i) all_f32 = all_f32 && hp[i].a_f32;
-        const int pr1 = prof_begin(h, main_s, RSK_KERNEL_DENSE);
+        const int pr1 = prof_begin(h, main_s, RSK_KERNEL_BATCH_RESID);
         if (df_resid && all_f32) launch_pass_b<3>(dP, dT, ntiles, dqueue, dactive, step == 0, grid, maxk, main_s);
         else launch_pass_b<2>(dP, dT, ntiles, dqueue, dactive, step == 0, grid, maxk, main_s);
         k_reduce_b<<<count, 256, 0, main_s>>>(dP, dactive, 1, 1, 0, step == 0);
@@ -924,7 +933,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
             RSK_CUDA_TRY(h, cudaGraphInstantiate(&cg_exec, graph, 0));
             cudaGraphDestroy(graph);
         }
-        const int pr2 = prof_begin(h, main_s, RSK_KERNEL_DENSE);
+        const int pr2 = prof_begin(h, main_s, RSK_KERNEL_BATCH_CG);
         // replay until no problem's CG is running; the count is copied to pinned memory at the end
         // of each replay, and the host reads it two replays behind so the GPU never waits for it
         for (int it = 0; it < max_inner; ++it) {
