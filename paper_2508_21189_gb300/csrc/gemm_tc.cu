@@ -21,9 +21,12 @@
 // epilogue for the MMAs already issued, so no copy or MMA outlives the CTA's shared memory or TMEM.
 #include "gemm_tc.cuh"
 
+#include "dense.cuh"
+
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 
 namespace {
 
@@ -479,8 +482,16 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
         if (!p.a[i] || !aligned16(p.a[i])) return fail(h, RSK_ERR_INVALID_ARG, "gemm: A operands must be 16-byte aligned");
     for (int i = 0; i < p.nb; ++i)
         if (!p.b[i] || !aligned16(p.b[i])) return fail(h, RSK_ERR_INVALID_ARG, "gemm: B operands must be 16-byte aligned");
-    // N split into two halves of NH columns (a multiple of 16, the MMA's N step for M = 128)
-    const int nh = std::max(16, ((p.N + 1) / 2 + 15) / 16 * 16);
+    // N split into two halves of NH columns (a multiple of 16, the MMA's N step for M = 128), rounded up
+    // to a half width the kernel is built for (the extra rows of B are zero-filled by the copies and the
+    // extra columns of D are not stored)
+    static const int kHalves[] = {16, 32, 48, 64, 96, 128, 160, 192, 256};
+    int nh = 256;
+    for (int c : kHalves)
+        if (2 * c >= p.N) {
+            nh = c;
+            break;
+        }
     const int64_t nk = (p.K + kBK - 1) / kBK;
     nsplit = int(std::max<int64_t>(1, std::min<int64_t>(nsplit, nk)));
     const int kblocks = int((nk + nsplit - 1) / nsplit);
@@ -623,6 +634,94 @@ rsk_status f32_product(rsk_handle* h, bool a_mn, const float* A, int64_t lda, co
     p.ldd = ldd;
     p.d_row_major = d_row_major;
     return gemm(h, p, nsplit, part, stream);
+}
+
+// Accumulators of at most 16 K blocks (64 main-term steps) for a Gram over K rows: the truncated
+// accumulation's relative bias stays below ~64 x 2^-24 ~ 4e-6.
+static int gram_splits(int64_t K) {
+    const int64_t nk = (K + 63) / 64;
+    return int(std::max<int64_t>(1, (nk + 15) / 16));
+}
+
+size_t orth_scratch_bytes(int64_t rows, int r) {
+    return 3 * Carver::round(size_t(pad8(rows)) * size_t(r) * 2) + 3 * Carver::round(size_t(pad8(r)) * size_t(r) * 2) +
+           4 * Carver::round(size_t(r) * size_t(r) * 4) + Carver::round(gemm_scratch_bytes(r, r, gram_splits(rows)) + 4) +
+           1024;
+}
+
+rsk_status orth(rsk_handle* h, float** X, float** Xalt, int64_t rows, int r, int64_t ldx, int rounds, int shifted,
+                float* Racc, void* scratch, cudaStream_t s) {
+    if (r < 1 || r > 330 || rows < r || ldx < rows || ldx % 8)
+        return fail(h, RSK_ERR_UNSUPPORTED, "orth: need 1 <= r <= 330, rows >= r, ldx >= rows a multiple of 8");
+    Carver cv(scratch);
+    const int64_t lds = pad8(rows), ldr = pad8(r);
+    __nv_bfloat16* S[3];
+    __nv_bfloat16* Rs[3];
+    for (int i = 0; i < 3; ++i) S[i] = cv.take<__nv_bfloat16>(size_t(lds) * r);
+    for (int i = 0; i < 3; ++i) Rs[i] = cv.take<__nv_bfloat16>(size_t(ldr) * r);
+    float* G = cv.take<float>(size_t(r) * r);
+    float* R = cv.take<float>(size_t(r) * r);
+    float* Ri = cv.take<float>(size_t(r) * r);
+    float* Rtmp = cv.take<float>(size_t(r) * r);
+    const int gs = gram_splits(rows);
+    float* part = cv.take<float>(gemm_scratch_bytes(r, r, gs) / 4 + 1);
+    const float coeff0 = 3e-5f;
+    for (int round = 0; round < rounds; ++round) {
+        rsk_status st = split3(h, *X, rows, r, ldx, S, lds, s);
+        if (st != RSK_OK) return st;
+        // G = X^T X: A = B = X^T, K-major (column c of X = row c of X^T), K = rows
+        Product g;
+        for (int i = 0; i < 3; ++i) {
+            g.a[i] = S[i];
+            g.b[i] = S[i];
+        }
+        g.na = g.nb = 3;
+        g.lda = g.ldb = lds;
+        set_split_passes(g);
+        g.M = r;
+        g.K = rows;
+        g.N = r;
+        g.D = G;
+        g.ldd = r;
+        st = gemm(h, g, gs, part, s);
+        const int pr = prof_begin(h, s, RSK_KERNEL_FACTOR);
+        if (st == RSK_OK) st = dense::cholesky(h, G, r, r, round < shifted ? coeff0 : 0.f, R, r, s);
+        if (st == RSK_OK) st = dense::trinv(h, R, r, r, Ri, s);
+        prof_end(h, s, pr);
+        if (st == RSK_OK) st = split3(h, Ri, r, r, r, Rs, ldr, s);
+        if (st != RSK_OK) return st;
+        // X R^{-1}: A = X (MN-major: column k of X holds (m, k) for all m), B_op[n][k] = Rinv[k][n] =
+        // column n of Rinv (column-major)
+        Product p;
+        p.a_mn = true;
+        for (int i = 0; i < 3; ++i) {
+            p.a[i] = S[i];
+            p.b[i] = Rs[i];
+        }
+        p.na = p.nb = 3;
+        p.lda = lds;
+        p.ldb = ldr;
+        set_split_passes(p);
+        p.M = rows;
+        p.K = r;
+        p.N = r;
+        p.D = *Xalt;
+        p.ldd = ldx;
+        st = gemm(h, p, 1, nullptr, s);
+        if (st != RSK_OK) return st;
+        std::swap(*X, *Xalt);
+        if (Racc) {
+            // R_total = R_round * R_total (upper triangular factors accumulate on the left)
+            if (round == 0) {
+                RSK_CUDA_TRY(h, cudaMemcpyAsync(Racc, R, size_t(r) * r * 4, cudaMemcpyDeviceToDevice, s));
+            } else {
+                st = dense::matmul_ts(h, R, r, r, r, Racc, r, r, Rtmp, r, s);
+                if (st != RSK_OK) return st;
+                RSK_CUDA_TRY(h, cudaMemcpyAsync(Racc, Rtmp, size_t(r) * r * 4, cudaMemcpyDeviceToDevice, s));
+            }
+        }
+    }
+    return RSK_OK;
 }
 
 }  // namespace tc

@@ -68,5 +68,18 @@ rsk_status f32_product(rsk_handle* h, bool a_mn, const float* A, int64_t lda, co
 
 inline int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
 
+// Orthonormal basis of range(X) for a tall FP32 X (rows x r, column-major, ldx a multiple of 8 >= rows,
+// r <= 330) by `rounds` Cholesky QR rounds: per round the three-term BF16 split of X, G = X^T X as
+// split products (K split into accumulators of at most 16 K blocks), the Cholesky factor R of
+// G + s I (s = 3e-5 trace(G) in the first `shifted` rounds, 0 after), R^{-1}, and X <- X R^{-1} as
+// split products.  The result is in *X on return (the routine swaps *X and *Xalt, an rows x r
+// buffer of the same leading dimension, as it goes).  Racc (r x r, column-major), when not null,
+// receives the accumulated upper factor with X_in = Q Racc.  The shift suits a Gram accurate to a few
+// 1e-6: each shifted round divides kappa by ~1 / sqrt(3e-5) ~ 180, and the plain rounds that follow
+// need kappa below ~1e3.  A Cholesky pivot that is not positive sets RSK_DEV_BOUNDS.
+size_t orth_scratch_bytes(int64_t rows, int r);
+rsk_status orth(rsk_handle* h, float** X, float** Xalt, int64_t rows, int r, int64_t ldx, int rounds, int shifted,
+                float* Racc, void* scratch, cudaStream_t stream);
+
 }  // namespace tc
 }  // namespace rsk

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "gemm_tc.cuh"
 
 namespace {
 
@@ -127,17 +128,25 @@ extern "C" rsk_status rsk_nystrom_psd(rsk_handle* h, const float* A, int64_t n, 
     using rsk::Carver;
     const size_t nk = size_t(n) * k;
     const int nparts = 256;
-    const size_t bytes = 2 * Carver::round(nk * 4) + Carver::round(nk * 4) + 5 * Carver::round(size_t(k) * k * 4) +
+    // the tensor-core path (split products, Cholesky QR on the tensor cores) needs k within the
+    // Cholesky kernel's 330; B is kept with a leading dimension that is a multiple of 8
+    const bool tcp = k <= 330;
+    const int64_t ldb = rsk::tc::pad8(n);
+    const size_t bk = size_t(ldb) * k;
+    const size_t scr = std::max({rsk::dense::orth_scratch_bytes(n, k), rsk::dense::svd_scratch_bytes(k, k),
+                                 tcp ? rsk::tc::orth_scratch_bytes(n, k) : 0,
+                                 tcp ? rsk::tc::f32_product_scratch_bytes(true, n, k, k, 1) : 0});
+    const size_t bytes = 2 * Carver::round(nk * 4) + 2 * Carver::round(bk * 4) + 5 * Carver::round(size_t(k) * k * 4) +
                          Carver::round(size_t(n) * zeta * 4) + Carver::round(size_t(n) * 4) + Carver::round(nparts * 8) +
-                         Carver::round(size_t(k) * 4) + 256 +
-                         std::max(rsk::dense::orth_scratch_bytes(n, k), rsk::dense::svd_scratch_bytes(k, k)) + 256;
+                         Carver::round(size_t(k) * 4) + 256 + scr + 256;
     DevBuf buf;
     rsk_status st = buf.alloc(h, bytes, stream);
     if (st != RSK_OK) return st;
     Carver cv(buf.p);
     float* Yt = cv.take<float>(nk);     // Y^T (k x n row-major) = Y column-major, then Y_nu, then Q_B
     float* Yrm = cv.take<float>(nk);    // Y_nu row-major (n x k)
-    float* B = cv.take<float>(nk);      // B = Y_nu C^{-1} (n x k column-major)
+    float* B = cv.take<float>(bk);      // B = Y_nu C^{-1} (n x k column-major, leading dimension ldb)
+    float* B2 = cv.take<float>(bk);     // the orthonormalisation's second buffer
     float* M = cv.take<float>(size_t(k) * k);
     float* Ms = cv.take<float>(size_t(k) * k);
     float* C = cv.take<float>(size_t(k) * k);
@@ -148,7 +157,7 @@ extern "C" rsk_status rsk_nystrom_psd(rsk_handle* h, const float* A, int64_t n, 
     double* part = cv.take<double>(nparts);
     float* sv = cv.take<float>(size_t(k));
     float* nu = cv.take<float>(1);
-    void* scratch = cv.take<char>(std::max(rsk::dense::orth_scratch_bytes(n, k), rsk::dense::svd_scratch_bytes(k, k)));
+    void* scratch = cv.take<char>(scr);
 
     // Y^T = S A (one pass over A)
     st = rsk::sketch_apply_kind(h, kind, A, RSK_F32, n, n, lda, k, zeta, seed, Yt, RSK_F32, n, stream);
@@ -170,11 +179,25 @@ extern "C" rsk_status rsk_nystrom_psd(rsk_handle* h, const float* A, int64_t n, 
     // C = chol(Omega^T Y_nu) (upper), B = Y_nu C^{-1}
     st = rsk::dense::cholesky(h, Ms, k, k, 0.f, C, k, stream);
     if (st == RSK_OK) st = rsk::dense::trinv(h, C, k, k, Ci, stream);
-    if (st == RSK_OK) st = rsk::dense::matmul_ts(h, Yt, n, k, n, Ci, k, k, B, n, stream);
-    // svd(B): B = Q_B R_B, R_B = U_R Sigma V_R^T, U = Q_B U_R
-    if (st == RSK_OK) st = rsk::dense::orth_accurate(h, B, n, k, n, RB, scratch, stream);
-    if (st == RSK_OK) st = rsk::dense::svd(h, RB, k, k, k, sv, nullptr, 0, scratch, stream);
-    if (st == RSK_OK) st = rsk::dense::matmul_ts(h, B, n, k, n, RB, rank, k, U, ldu, stream);
+    if (st != RSK_OK) return st;
+    if (tcp) {
+        // B = Y_nu C^{-1} as a split product (Y_nu column-major is the MN-major operand; column c of the
+        // column-major C^{-1} is row c of the K-major one); svd(B): B = Q_B R_B by Cholesky QR on the
+        // tensor cores (kappa(B) = kappa(A_hat)^{1/2}: one shifted round, two plain), R_B = U_R Sigma
+        // V_R^T, U = Q_B U_R as a split product
+        st = rsk::tc::f32_product(h, true, Yt, n, Ci, k, n, k, k, B, ldb, false, 1, scratch, stream);
+        float* Bq = B;
+        float* Balt = B2;
+        if (st == RSK_OK) st = rsk::tc::orth(h, &Bq, &Balt, n, k, ldb, 3, 1, RB, scratch, stream);
+        if (st == RSK_OK) st = rsk::dense::svd(h, RB, k, k, k, sv, nullptr, 0, scratch, stream);
+        if (st == RSK_OK) st = rsk::tc::f32_product(h, true, Bq, ldb, RB, k, n, k, rank, U, ldu, false, 1, scratch, stream);
+    } else {
+        st = rsk::dense::matmul_ts(h, Yt, n, k, n, Ci, k, k, B, ldb, stream);
+        // svd(B): B = Q_B R_B (FP64 Gram), R_B = U_R Sigma V_R^T, U = Q_B U_R
+        if (st == RSK_OK) st = rsk::dense::orth_accurate(h, B, n, k, ldb, RB, scratch, stream);
+        if (st == RSK_OK) st = rsk::dense::svd(h, RB, k, k, k, sv, nullptr, 0, scratch, stream);
+        if (st == RSK_OK) st = rsk::dense::matmul_ts(h, B, n, k, ldb, RB, rank, k, U, ldu, stream);
+    }
     if (st != RSK_OK) return st;
     k_lambda<<<unsigned((rank + 255) / 256), 256, 0, stream>>>(sv, nu, rank, lambda);
     RSK_LAUNCH_CHECK(h);
@@ -226,11 +249,15 @@ extern "C" rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, 
     if (k > 512 || p > 1024) return rsk::fail(h, RSK_ERR_UNSUPPORTED, "k <= 512 and p <= 1024");
     using rsk::Carver;
     const size_t nk = size_t(n) * k, pd = size_t(p) * d;
+    // tensor-core QRs (Alg. 5) where the Cholesky kernel's limit and the leading dimensions allow
+    const bool tcq = form == 1 && k <= 330 && p <= 330 && n % 8 == 0 && d % 8 == 0;
     const size_t scr = std::max({rsk::dense::orth_scratch_bytes(n, k), rsk::dense::orth_scratch_bytes(d, p),
-                                 rsk::dense::svd_scratch_bytes(p, k)});
+                                 rsk::dense::svd_scratch_bytes(p, k), rsk::tc::f32_product_scratch_bytes(true, n, k, k, 1),
+                                 rsk::tc::f32_product_scratch_bytes(true, d, p, k, 1),
+                                 tcq ? rsk::tc::orth_scratch_bytes(std::max(n, d), std::max(k, p)) : 0});
     const size_t bytes = 2 * Carver::round(nk * 4) + Carver::round(pd * 4) + 3 * Carver::round(size_t(p) * k * 4) +
                          3 * Carver::round(size_t(k) * k * 4) + Carver::round(size_t(p) * p * 4) +
-                         2 * Carver::round(size_t(k) * 4) + Carver::round(scr) + 1024;
+                         2 * Carver::round(size_t(k) * 4) + Carver::round(scr) + (tcq ? Carver::round(pd * 4) : 0) + 1024;
     DevBuf buf;
     rsk_status st = buf.alloc(h, bytes, stream);
     if (st != RSK_OK) return st;
@@ -248,6 +275,7 @@ extern "C" rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, 
     float* s1 = cv.take<float>(size_t(k));
     float* s2 = cv.take<float>(size_t(k));
     void* scratch = cv.take<char>(scr);
+    float* Xalt = tcq ? cv.take<float>(pd) : nullptr;   // second buffer of X's orthonormalisation
 
     // sketches: Y = A Omega (Omega = S^T, S k x d from seed), X^T = Psi^T A (Psi = S'^T, S' p x n from seed + 1)
     st = rsk::sketch_apply_right(h, kind, A, n, d, lda, k, zeta, seed, Y, n, stream);
@@ -263,14 +291,32 @@ extern "C" rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, 
         k_scale_trunc<<<dim3(1, unsigned(k)), 256, 0, stream>>>(V1, k, k, k, s1, rank, true);
         k_scale_trunc<<<dim3(4, unsigned(k)), 256, 0, stream>>>(W, p, k, p, s1, rank, false);
         RSK_LAUNCH_CHECK(h);
-        st = rsk::dense::matmul_ts(h, Y, n, k, n, V1, k, k, out1, ld1, stream);
-        if (st == RSK_OK) st = rsk::dense::matmul_ts(h, Xt, d, p, d, W, k, p, out2, ld2, stream);
+        // F = Y (V Sigma^{-1})_r, G = X U_r as split products (column c of the column-major right factor
+        // is row c of the K-major operand)
+        st = rsk::tc::f32_product(h, true, Y, n, V1, k, n, k, k, out1, ld1, false, 1, scratch, stream);
+        if (st == RSK_OK) st = rsk::tc::f32_product(h, true, Xt, d, W, p, d, p, k, out2, ld2, false, 1, scratch, stream);
         return st;
     }
     // Alg. 5: Q = qr(Y); [P, T] = qr(X); [U1, S1, V1] = svd(Psi^T Q); C = V1_r S1_r^{-1} U1_r^T T^T;
     // [Uh, Sigma, Vh] = svd(C); U = Q Uh; V = P Vh.  C is k x p, so svd(C^T) = (Vh, Sigma, Uh) is taken.
-    st = rsk::dense::orth_accurate(h, Y, n, k, n, nullptr, scratch, stream);
-    if (st == RSK_OK) st = rsk::dense::orth_accurate(h, Xt, d, p, d, T, scratch, stream);
+    if (tcq) {
+        // Cholesky QR on the tensor cores: two shifted rounds and two plain ones (kappa(A Omega) can be
+        // large: each shifted round divides it by ~180); the results are copied back when they end in
+        // the second buffer (Q row-major's storage serves Y, which is written only later)
+        float* Yq = Y;
+        float* Yalt = Qrm;
+        st = rsk::tc::orth(h, &Yq, &Yalt, n, k, n, 4, 2, nullptr, scratch, stream);
+        if (st == RSK_OK && Yq != Y)
+            RSK_CUDA_TRY(h, cudaMemcpyAsync(Y, Yq, nk * 4, cudaMemcpyDeviceToDevice, stream));
+        float* Xq = Xt;
+        float* Xa = Xalt;
+        if (st == RSK_OK) st = rsk::tc::orth(h, &Xq, &Xa, d, p, d, 4, 2, T, scratch, stream);
+        if (st == RSK_OK && Xq != Xt)
+            RSK_CUDA_TRY(h, cudaMemcpyAsync(Xt, Xq, pd * 4, cudaMemcpyDeviceToDevice, stream));
+    } else {
+        st = rsk::dense::orth_accurate(h, Y, n, k, n, nullptr, scratch, stream);
+        if (st == RSK_OK) st = rsk::dense::orth_accurate(h, Xt, d, p, d, T, scratch, stream);
+    }
     if (st != RSK_OK) return st;
     k_transpose<<<dim3(unsigned((n + 31) / 32), unsigned((k + 31) / 32)), tb, 0, stream>>>(Y, k, n, Qrm);
     RSK_LAUNCH_CHECK(h);
@@ -291,8 +337,8 @@ extern "C" rsk_status rsk_gen_nystrom(rsk_handle* h, const float* A, int64_t n, 
     st = rsk::dense::matmul_ts(h, E, p, k, p, Vt, k, k, Z, p, stream);
     // svd(C^T) = Vh Sigma Uh^T: Z -> Vh (p x k), V2 = Uh (k x k)
     if (st == RSK_OK) st = rsk::dense::svd(h, Z, p, k, p, s2, V2, k, scratch, stream);
-    if (st == RSK_OK) st = rsk::dense::matmul_ts(h, Y, n, k, n, V2, k, k, out1, ld1, stream);
-    if (st == RSK_OK) st = rsk::dense::matmul_ts(h, Xt, d, p, d, Z, k, p, out2, ld2, stream);
+    if (st == RSK_OK) st = rsk::tc::f32_product(h, true, Y, n, V2, k, n, k, k, out1, ld1, false, 1, scratch, stream);
+    if (st == RSK_OK) st = rsk::tc::f32_product(h, true, Xt, d, Z, p, d, p, k, out2, ld2, false, 1, scratch, stream);
     if (st != RSK_OK) return st;
     RSK_CUDA_TRY(h, cudaMemcpyAsync(sigma, s2, size_t(k) * 4, cudaMemcpyDeviceToDevice, stream));
     return RSK_OK;

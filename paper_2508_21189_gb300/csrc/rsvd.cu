@@ -65,13 +65,10 @@ struct Ws {
     float *Z, *Z2;           // n x r, ld ldn
     int64_t ldm, ldn;
     __nv_bfloat16* Qbf;      // bf16 of the current basis, max(m, n) x r
-    __nv_bfloat16* S[3];     // three-term split of the basis being orthonormalised
-    __nv_bfloat16* Rs[3];    // three-term split of R^{-1} (r x r, ld ldr)
-    int64_t ldr;
-    float *G, *R, *Ri, *Racc, *Rtmp, *Xs, *Vj, *sv;  // r x r (ld r), sv r
-    float* part;             // split-K partials
+    float *Racc, *Xs, *Vj, *sv;  // r x r (ld r), sv r
+    float* part;             // split-K partials of the big products
     size_t part_bytes;
-    void* fscratch;          // scratch of the final split products (aliases S)
+    void* oscratch;          // the orthonormalisations' scratch, then the final split products'
     void* svd_scratch;
     int32_t* orow;
     uint32_t* osgn;
@@ -80,85 +77,6 @@ struct Ws {
 }  // namespace
 
 namespace rsk {
-
-// Partials of a split-K product with M x N output.
-static int gram_splits(int64_t K) {
-    // at most 16 K blocks (64 accumulation steps of the main term) per accumulator: the truncated
-    // accumulation's relative bias stays below ~64 x 2^-24 ~ 4e-6
-    const int64_t nk = (K + 63) / 64;
-    return int(std::max<int64_t>(1, (nk + 15) / 16));
-}
-
-// X (rows x r, ld ldx) <- orthonormal basis of range(X) by `rounds` Cholesky QR rounds (the first
-// shifted), result in *X (the routine swaps *X and *Xalt as it goes).  Racc (r x r), when not null,
-// receives the accumulated upper factor with X_in = Q Racc.
-static rsk_status orth_tc(rsk_handle* h, float** X, float** Xalt, int64_t rows, int r, int64_t ldx, int rounds,
-                          float* Racc, Ws& w, cudaStream_t s) {
-    // Shift of the first round: the split Gram's relative error is a few 1e-6 (truncated accumulation
-    // over at most 64 steps per split plus the rounded sum of the partials); 3e-5 trace(G) keeps G + shift
-    // positive definite for any kappa(X) and leaves kappa(X R^{-1}) <= ~1 / sqrt(3e-5) for the plain
-    // rounds that follow (Fukaya et al.'s shifted Cholesky QR with this Gram's error level).
-    const float coeff0 = 3e-5f;
-    const int64_t lds = tc::pad8(rows);
-    for (int round = 0; round < rounds; ++round) {
-        rsk_status st = tc::split3(h, *X, rows, r, ldx, w.S, lds, s);
-        if (st != RSK_OK) return st;
-        // G = X^T X: A = B = X^T, K-major (column c of X = row c of X^T), K = rows
-        tc::Product g;
-        for (int i = 0; i < 3; ++i) {
-            g.a[i] = w.S[i];
-            g.b[i] = w.S[i];
-        }
-        g.na = g.nb = 3;
-        g.lda = g.ldb = lds;
-        tc::set_split_passes(g);
-        g.M = r;
-        g.K = rows;
-        g.N = r;
-        g.D = w.G;
-        g.ldd = r;
-        const int gs = gram_splits(rows);
-        if (tc::gemm_scratch_bytes(r, r, gs) > w.part_bytes) return fail(h, RSK_ERR_INTERNAL, "rsvd: partials too small");
-        st = tc::gemm(h, g, gs, w.part, s);
-        const int pr = prof_begin(h, s, RSK_KERNEL_FACTOR);
-        if (st == RSK_OK) st = dense::cholesky(h, w.G, r, r, round == 0 ? coeff0 : 0.f, w.R, r, s);
-        if (st == RSK_OK) st = dense::trinv(h, w.R, r, r, w.Ri, s);
-        prof_end(h, s, pr);
-        if (st == RSK_OK) st = tc::split3(h, w.Ri, r, r, r, w.Rs, w.ldr, s);
-        if (st != RSK_OK) return st;
-        // X R^{-1}: A = X (MN-major: column k of X holds (m, k) for all m), B_op[n][k] = Rinv[k][n] =
-        // column n of Rinv (column-major)
-        tc::Product p;
-        p.a_mn = true;
-        for (int i = 0; i < 3; ++i) {
-            p.a[i] = w.S[i];
-            p.b[i] = w.Rs[i];
-        }
-        p.na = p.nb = 3;
-        p.lda = lds;
-        p.ldb = w.ldr;
-        tc::set_split_passes(p);
-        p.M = rows;
-        p.K = r;
-        p.N = r;
-        p.D = *Xalt;
-        p.ldd = ldx;
-        st = tc::gemm(h, p, 1, nullptr, s);
-        if (st != RSK_OK) return st;
-        std::swap(*X, *Xalt);
-        if (Racc) {
-            // R_total = R_round * R_total (upper triangular factors accumulate on the left)
-            if (round == 0) {
-                RSK_CUDA_TRY(h, cudaMemcpyAsync(Racc, w.R, size_t(r) * r * 4, cudaMemcpyDeviceToDevice, s));
-            } else {
-                st = dense::matmul_ts(h, w.R, r, r, r, Racc, r, r, w.Rtmp, r, s);
-                if (st != RSK_OK) return st;
-                RSK_CUDA_TRY(h, cudaMemcpyAsync(Racc, w.Rtmp, size_t(r) * r * 4, cudaMemcpyDeviceToDevice, s));
-            }
-        }
-    }
-    return RSK_OK;
-}
 
 // D (M x r, column-major ld ldd) = A (BF16) * Bt^T for Bt = bf16 of a column-major K x r basis (its
 // column c is row c of the K-major operand).
@@ -203,15 +121,13 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     w.lda_bf = tc::pad8(n);
     w.ldm = tc::pad8(m);
     w.ldn = tc::pad8(n);
-    w.ldr = tc::pad8(r);
     const int64_t mx = std::max(w.ldm, w.ldn);
-    // split-K partials: the Gram of the m-row basis, or one wave of the K-split big product
+    // split-K partials: one wave of the K-split big product (Z = A^T Q)
     const int64_t mtiles_n = (n + 127) / 128;
-    const size_t part_bytes = std::max(tc::gemm_scratch_bytes(r, r, gram_splits(std::max(m, n))),
-                                       tc::gemm_scratch_bytes(n, r, int(std::max<int64_t>(1, std::min<int64_t>(
-                                                                           8, h->num_sms / mtiles_n)))));
+    const size_t part_bytes =
+        tc::gemm_scratch_bytes(n, r, int(std::max<int64_t>(1, std::min<int64_t>(8, h->num_sms / mtiles_n))));
     const size_t fbytes = std::max(tc::f32_product_scratch_bytes(true, std::max(m, n), r, r, 1),
-                                   3 * Carver::round(size_t(mx) * r * 2) + 1024);
+                                   tc::orth_scratch_bytes(mx, r));
     size_t bytes = 0;
     auto add = [&](size_t b_) { bytes += Carver::round(b_); };
     add(size_t(m) * w.lda_bf * 2);                  // A bf16
@@ -219,9 +135,8 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     add(size_t(w.ldm) * r * 4 * 2);                 // Y, Y2
     add(size_t(w.ldn) * r * 4 * 2);                 // Z, Z2
     add(size_t(mx) * r * 2);                        // Qbf
-    add(fbytes);                                    // splits / final products' scratch
-    add(size_t(w.ldr) * r * 2 * 3);                 // R^{-1} splits
-    add(size_t(r) * r * 4 * 8 + size_t(r) * 8);     // small matrices, pivots
+    add(fbytes);                                    // orthonormalisation / final products' scratch
+    add(size_t(r) * r * 4 * 3 + size_t(r) * 4);     // small matrices
     add(part_bytes);
     add(dense::svd_scratch_bytes(r, r));
     add(size_t(n) * zeta * 4 + size_t(n) * 4);
@@ -235,17 +150,8 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     w.Z = cv.take<float>(size_t(w.ldn) * r);
     w.Z2 = cv.take<float>(size_t(w.ldn) * r);
     w.Qbf = cv.take<__nv_bfloat16>(size_t(mx) * r);
-    w.fscratch = cv.take<char>(fbytes);
-    {
-        Carver sc(w.fscratch);
-        for (int i = 0; i < 3; ++i) w.S[i] = sc.take<__nv_bfloat16>(size_t(mx) * r);
-    }
-    for (int i = 0; i < 3; ++i) w.Rs[i] = cv.take<__nv_bfloat16>(size_t(w.ldr) * r);
-    w.G = cv.take<float>(size_t(r) * r);
-    w.R = cv.take<float>(size_t(r) * r);
-    w.Ri = cv.take<float>(size_t(r) * r);
+    w.oscratch = cv.take<char>(fbytes);
     w.Racc = cv.take<float>(size_t(r) * r);
-    w.Rtmp = cv.take<float>(size_t(r) * r);
     w.Xs = cv.take<float>(size_t(r) * r);
     w.Vj = cv.take<float>(size_t(r) * r);
     w.sv = cv.take<float>(size_t(r));
@@ -270,22 +176,22 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     float* Z = w.Z;
     float* Z2 = w.Z2;
     st = big_product(h, false, w.Abf, w.lda_bf, m, n, w.Ot, w.lda_bf, r, Y, w.ldm, w, stream);  // Y = A Omega
-    if (st == RSK_OK) st = orth_tc(h, &Y, &Y2, m, r, w.ldm, power_iters > 0 ? 2 : 3, nullptr, w, stream);
+    if (st == RSK_OK) st = tc::orth(h, &Y, &Y2, m, r, w.ldm, power_iters > 0 ? 2 : 3, 1, nullptr, w.oscratch, stream);
     for (int it = 0; st == RSK_OK && it < power_iters; ++it) {
         st = tc::to_bf16(h, Y, m, r, w.ldm, w.Qbf, w.ldm, stream);
         if (st == RSK_OK)                                                                       // Z = A^T Q
             st = big_product(h, true, w.Abf, w.lda_bf, n, m, w.Qbf, w.ldm, r, Z, w.ldn, w, stream);
-        if (st == RSK_OK) st = orth_tc(h, &Z, &Z2, n, r, w.ldn, 2, nullptr, w, stream);
+        if (st == RSK_OK) st = tc::orth(h, &Z, &Z2, n, r, w.ldn, 2, 1, nullptr, w.oscratch, stream);
         if (st == RSK_OK) st = tc::to_bf16(h, Z, n, r, w.ldn, w.Qbf, w.ldn, stream);
         if (st == RSK_OK)                                                                       // Y = A Z
             st = big_product(h, false, w.Abf, w.lda_bf, m, n, w.Qbf, w.ldn, r, Y, w.ldm, w, stream);
-        if (st == RSK_OK) st = orth_tc(h, &Y, &Y2, m, r, w.ldm, it + 1 < power_iters ? 2 : 3, nullptr, w, stream);
+        if (st == RSK_OK) st = tc::orth(h, &Y, &Y2, m, r, w.ldm, it + 1 < power_iters ? 2 : 3, 1, nullptr, w.oscratch, stream);
     }
     if (st != RSK_OK) return st;
     // ---- B = Q^T A = Z^T with Z = A^T Q; Z = Q_z R_z
     st = tc::to_bf16(h, Y, m, r, w.ldm, w.Qbf, w.ldm, stream);
     if (st == RSK_OK) st = big_product(h, true, w.Abf, w.lda_bf, n, m, w.Qbf, w.ldm, r, Z, w.ldn, w, stream);
-    if (st == RSK_OK) st = orth_tc(h, &Z, &Z2, n, r, w.ldn, 3, w.Racc, w, stream);
+    if (st == RSK_OK) st = tc::orth(h, &Z, &Z2, n, r, w.ldn, 3, 1, w.Racc, w.oscratch, stream);
     if (st != RSK_OK) return st;
     // ---- B = Z^T = R_z^T Q_z^T;  svd(R_z^T) = U_j Sigma V_j^T (one-sided Jacobi, U_j overwrites Xs):
     // Uhat = U_j
@@ -301,7 +207,7 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     RSK_LAUNCH_CHECK(h);
     // ---- U = Q Uhat (row-major m x r); V = Q_z V_j, column-major n x r = row-major V^T (r x n)
     // (B_op[c][k] = Uhat[k][c]: column c of the column-major Uhat, and likewise for V_j)
-    st = tc::f32_product(h, true, Y, w.ldm, w.Xs, r, m, r, r, U, r, true, 1, w.fscratch, stream);
-    if (st == RSK_OK) st = tc::f32_product(h, true, Z, w.ldn, w.Vj, r, n, r, r, Vt, n, false, 1, w.fscratch, stream);
+    st = tc::f32_product(h, true, Y, w.ldm, w.Xs, r, m, r, r, U, r, true, 1, w.oscratch, stream);
+    if (st == RSK_OK) st = tc::f32_product(h, true, Z, w.ldn, w.Vj, r, n, r, r, Vt, n, false, 1, w.oscratch, stream);
     return st;
 }

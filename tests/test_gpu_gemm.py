@@ -18,7 +18,8 @@ def rsk():
 
 @pytest.mark.parametrize("M,K,N,nsplit", [(128, 64, 32, 1), (256, 128, 64, 1), (128, 64, 320, 1), (1000, 1000, 300, 1),
                                           (4096, 2048, 300, 1), (777, 4104, 45, 1), (1024, 16384, 320, 4),
-                                          (8192, 8192, 300, 2), (300, 512, 512, 1)])
+                                          (8192, 8192, 300, 2), (300, 512, 512, 1), (1000, 640, 200, 1),
+                                          (513, 256, 450, 1), (640, 128, 161, 2)])
 def test_gemm_matches_fp64(rsk, M, K, N, nsplit):
     g = torch.Generator(device="cuda")
     g.manual_seed(M + K + N)
