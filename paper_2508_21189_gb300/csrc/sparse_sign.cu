@@ -650,7 +650,7 @@ __global__ void k_sum_blocks(const Out* __restrict__ outs, int64_t bstride, int 
 // Right sketch Y = A Omega = A S^T (A n x dc row-major, S k x dc): Y[i, c] = zeta^{-1/2} sum over the
 // entries (j, sign) of row c of S of sign * A[i, j].  One CTA per tile of 32 rows of A at a time;
 // per index chunk the tile's 32 x C block of A is staged transposed ([j][i], lane index XOR-swizzled
-// by j so that both the staging writes and the gathers are free of bank conflicts), and warp w
+// by j so that the gathers are free of bank conflicts; rows read with 16-byte loads), and warp w
 // accumulates output columns w, w + 8, ... for its 32 rows (lane = row): every lane of a warp walks
 // the same entry list, so the gather does not diverge.  Chunks are summed in order (deterministic).
 // ------------------------------------------------------------------------------------------
@@ -661,7 +661,7 @@ template <int MAXC>
 __global__ void __launch_bounds__(kRightThreads, 2)
     k_right(const float* __restrict__ A, int64_t n, int64_t dc, int64_t lda, int k, int zeta, int C, int pitch,
             const uint16_t* __restrict__ offs, const uint16_t* __restrict__ ents, int nchunks, float scale,
-            float* __restrict__ Y, int64_t ldy) {
+            float* __restrict__ Y, int64_t ldy, int vec4) {
     extern __shared__ __align__(16) uint8_t smr[];
     float* tile = reinterpret_cast<float*>(smr);                                   // C x 32
     uint16_t* es = reinterpret_cast<uint16_t*>(smr + size_t(C) * kRightRows * 4);  // C * zeta entries
@@ -676,10 +676,36 @@ __global__ void __launch_bounds__(kRightThreads, 2)
         for (int ch = 0; ch < nchunks; ++ch) {
             const int64_t j0 = int64_t(ch) * C;
             const int cols = int(min(int64_t(C), dc - j0));
-            for (int idx = tid; idx < kRightRows * cols; idx += kRightThreads) {
-                const int r = idx / cols, c = idx - r * cols;
-                const float v = (i0 + r < n) ? A[(i0 + r) * lda + j0 + c] : 0.f;
-                tile[c * kRightRows + (r ^ (c & 31))] = v;
+            if (vec4) {
+                // warp w stages rows w, w + 8, ...; lanes take 16-byte column groups (coalesced rows)
+                const int c4n = (cols + 3) >> 2;
+                for (int r = warp; r < kRightRows; r += kRightThreads / 32) {
+                    const bool live = i0 + r < n;
+                    const float* arow = A + (i0 + r) * lda + j0;
+#pragma unroll 4
+                    for (int c4 = lane; c4 < c4n; c4 += 32) {
+                        const int c = 4 * c4;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (live) {
+                            if (c + 4 <= cols) v = *reinterpret_cast<const float4*>(arow + c);
+                            else {
+                                v.x = arow[c];
+                                if (c + 1 < cols) v.y = arow[c + 1];
+                                if (c + 2 < cols) v.z = arow[c + 2];
+                            }
+                        }
+                        tile[c * kRightRows + (r ^ (c & 31))] = v.x;
+                        tile[(c + 1) * kRightRows + (r ^ ((c + 1) & 31))] = v.y;
+                        tile[(c + 2) * kRightRows + (r ^ ((c + 2) & 31))] = v.z;
+                        tile[(c + 3) * kRightRows + (r ^ ((c + 3) & 31))] = v.w;
+                    }
+                }
+            } else {
+                for (int idx = tid; idx < kRightRows * cols; idx += kRightThreads) {
+                    const int r = idx / cols, c = idx - r * cols;
+                    const float v = (i0 + r < n) ? A[(i0 + r) * lda + j0 + c] : 0.f;
+                    tile[c * kRightRows + (r ^ (c & 31))] = v;
+                }
             }
             const uint16_t* ce = ents + j0 * zeta;
             for (int e = tid; e < cols * zeta; e += kRightThreads) es[e] = ce[e];
@@ -1099,8 +1125,10 @@ rsk_status sketch_apply_right(rsk_handle* h, int kind, const float* A, int64_t n
     auto go = [&](auto kern) -> rsk_status {
         RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         const int pr = prof_begin(h, stream, RSK_KERNEL_SKETCH_APPLY);
+        // 16-byte staging loads when every row and every chunk start is 16-byte aligned
+        const int vec4 = (reinterpret_cast<uintptr_t>(A) % 16 == 0 && lda % 4 == 0 && C % 4 == 0) ? 1 : 0;
         kern<<<grid, kRightThreads, smem, stream>>>(A, n, dc, lda, int(k), zeta, C, offsets_pitch(int(k)), offs, ents,
-                                                    nch, scale, Y, ldy);
+                                                    nch, scale, Y, ldy, vec4);
         prof_end(h, stream, pr);
         RSK_LAUNCH_CHECK(h);
         return RSK_OK;
