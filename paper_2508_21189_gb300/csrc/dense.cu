@@ -18,6 +18,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -537,6 +539,119 @@ __global__ void __launch_bounds__(1024) k_jacobi(const JacobiArgs a) {
     }
 }
 
+// The same one-sided block Jacobi on one thread-block cluster whose CTAs keep their column blocks in
+// shared memory: CTA g holds the blocks at positions g and nb - 1 - g of the round-robin table (nb = 2G
+// blocks of w columns, zero columns past q), orthogonalises every pair of its 2w columns, and between
+// rounds every block moves to its next position (position 0 fixed, 1..nb-1 rotating: every pair of
+// blocks meets once per sweep) through distributed shared memory into the next holder's second buffer,
+// between two cluster barriers.  A sweep's "anything rotated" flag is OR-ed into CTA 0's shared memory
+// and read by every CTA between two barriers.  No waits other than the cluster barriers.
+struct JacobiCArgs {
+    float* X;
+    int64_t ldx;
+    int m, q, w;
+    float* V;
+    int64_t ldv;
+    float tol;
+    int max_sweeps;
+};
+
+constexpr int kJacobiSweepsMax = 40;
+
+__global__ void __launch_bounds__(1024) k_jacobi_cluster(const JacobiCArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) float smc[];
+    __shared__ int rot_flags[kJacobiSweepsMax];  // CTA 0's copy is the cluster's
+    __shared__ int ids[2][2];                    // block id per [buffer][slot]
+    __shared__ int rot_s;
+    const int G = int(cluster.num_blocks()), g = int(cluster.block_rank()), nb = 2 * G;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int mv = a.V ? a.q : 0;
+    const int mp = (a.m + 3) & ~3, vp = (mv + 3) & ~3, cl = mp + vp;
+    const int W = a.w;
+    const int slot = W * cl;                     // floats per block
+    float* buf[2] = {smc, smc + 2 * slot};      // per buffer: slot 0 (position g), slot 1 (position nb - 1 - g)
+    for (int i = tid; i < kJacobiSweepsMax; i += blockDim.x) rot_flags[i] = 0;
+    if (tid < 2) ids[0][tid] = tid == 0 ? g : nb - 1 - g;
+    for (int e = tid; e < 2 * slot; e += blockDim.x) {
+        const int sl = e / slot, rem = e - sl * slot, l = rem / cl, i = rem - l * cl;
+        const int c = (sl == 0 ? g : nb - 1 - g) * W + l;
+        float v = 0.f;
+        if (c < a.q) {
+            if (i < a.m) v = a.X[int64_t(c) * a.ldx + i];
+            else if (i >= mp && i - mp < mv) v = a.V[int64_t(c) * a.ldv + (i - mp)];
+        }
+        buf[0][e] = v;
+    }
+    cluster.sync();
+    int cur = 0;
+    const int Le = 2 * W;
+    for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+        if (tid == 0) rot_s = 0;
+        __syncthreads();
+        for (int r = 0; r < nb - 1; ++r) {
+            float* smx = buf[cur];
+            for (int lr = 0; lr < Le - 1; ++lr) {
+                for (int pi = warp; pi < Le / 2; pi += nw) {
+                    const int pa = rr_block(pi, lr, Le), pb = rr_block(Le - 1 - pi, lr, Le);
+                    float4* ca = reinterpret_cast<float4*>(smx + pa * cl);
+                    float4* cb = reinterpret_cast<float4*>(smx + pb * cl);
+                    float al = 0.f, be = 0.f, ga = 0.f;
+                    for (int i = lane; i < mp / 4; i += 32) {
+                        const float4 x = ca[i], y = cb[i];
+                        al = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, al))));
+                        be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+                        ga = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, ga))));
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                    }
+                    if (ga == 0.f || !(fabsf(ga) > a.tol * sqrtf(al) * sqrtf(be))) continue;
+                    const float zeta = (be - al) / (2.f * ga);
+                    const float t = fabsf(zeta) > 1e15f ? 0.5f / zeta
+                                                        : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    const float c = rsqrtf(1.f + t * t), sn = c * t;
+                    for (int i = lane; i < cl / 4; i += 32) {
+                        const float4 x = ca[i], y = cb[i];
+                        ca[i] = make_float4(c * x.x - sn * y.x, c * x.y - sn * y.y, c * x.z - sn * y.z, c * x.w - sn * y.w);
+                        cb[i] = make_float4(sn * x.x + c * y.x, sn * x.y + c * y.y, sn * x.z + c * y.z, sn * x.w + c * y.w);
+                    }
+                    if (lane == 0) rot_s = 1;
+                }
+                __syncthreads();
+            }
+            // both blocks to their next positions, into the next holder's other buffer
+            for (int sl = 0; sl < 2; ++sl) {
+                const int p = sl == 0 ? g : nb - 1 - g;
+                const int pn = p == 0 ? 0 : (p == nb - 1 ? 1 : p + 1);
+                const int dcta = pn < G ? pn : nb - 1 - pn, dslot = pn < G ? 0 : 1;
+                float4* dst = reinterpret_cast<float4*>(cluster.map_shared_rank(buf[cur ^ 1], dcta) + dslot * slot);
+                const float4* src = reinterpret_cast<const float4*>(smx + sl * slot);
+                for (int e = tid; e < slot / 4; e += blockDim.x) dst[e] = src[e];
+                if (tid == 0) cluster.map_shared_rank(&ids[cur ^ 1][0], dcta)[dslot] = ids[cur][sl];
+            }
+            cluster.sync();
+            cur ^= 1;
+        }
+        if (tid == 0 && rot_s) atomicOr(cluster.map_shared_rank(&rot_flags[sweep], 0), 1);
+        cluster.sync();
+        const int any = *cluster.map_shared_rank(&rot_flags[sweep], 0);
+        cluster.sync();   // every CTA has read the flag before any leaves
+        if (!any) break;
+    }
+    for (int e = tid; e < 2 * slot; e += blockDim.x) {
+        const int sl = e / slot, rem = e - sl * slot, l = rem / cl, i = rem - l * cl;
+        const int c = ids[cur][sl] * W + l;
+        if (c >= a.q) continue;
+        if (i < a.m) a.X[int64_t(c) * a.ldx + i] = buf[cur][e];
+        else if (i >= mp && i - mp < mv) a.V[int64_t(c) * a.ldv + (i - mp)] = buf[cur][e];
+    }
+}
+
 __global__ void k_identity(float* __restrict__ V, int q, int64_t ldv) {
     const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= int64_t(q) * q) return;
@@ -710,7 +825,50 @@ rsk_status svd(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* s,
         RSK_LAUNCH_CHECK(h);
     }
     RSK_CUDA_TRY(h, cudaMemsetAsync(words, 0, size_t(kMaxSweeps + 2) * 4, stream));
+    bool done = false;
     if (q > 1) {
+        // one cluster of G <= 16 CTAs (about 10 columns per block) when the columns fit in their shared
+        // memory (two buffers of two blocks per CTA)
+        const int64_t clw = ((m + 3) & ~int64_t(3)) + (with_v ? ((q + 3) & ~3) : 0);
+        for (int G : {std::min(16, std::max(2, (q + 19) / 20)), 8}) {
+            if (done || 2 * G > q) continue;
+            const int w = (q + 2 * G - 1) / (2 * G);
+            const size_t smem = size_t(4) * w * size_t(clw) * 4;
+            if (smem > 200 * 1024) continue;
+            RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            if (G > 8) RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(unsigned(G));
+            cfg.blockDim = dim3(1024);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = unsigned(G);
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_jacobi_cluster, &cfg) != cudaSuccess || clusters < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            JacobiCArgs ca;
+            ca.X = X;
+            ca.ldx = ldx;
+            ca.m = int(m);
+            ca.q = q;
+            ca.w = w;
+            ca.V = with_v ? Vt : nullptr;
+            ca.ldv = q;
+            ca.tol = 2.f * sqrtf(float(m)) * kU32;
+            ca.max_sweeps = std::min(kMaxSweeps, kJacobiSweepsMax);
+            RSK_CUDA_TRY(h, cudaLaunchKernelEx(&cfg, k_jacobi_cluster, ca));
+            done = true;
+        }
+    }
+    if (q > 1 && !done) {
         const JacobiPlan jp = jacobi_plan(m, q, with_v, h->num_sms);
         if (jp.smem > 227 * 1024 || 2 * jp.w > 256)
             return fail(h, RSK_ERR_UNSUPPORTED, "svd: %lld x %d needs too much shared memory", (long long)m, q);
