@@ -2,7 +2,8 @@
 //
 // Kernels
 //   k_gram          X^T Y over a chunk of rows: 64 x 64 output tile per CTA, 4 x 4 per thread, the rows
-//                   staged 32 at a time; per-chunk partials summed in chunk order by k_gram_reduce.
+//                   staged 32 at a time, FP64 accumulation; per-chunk partials summed in chunk order by
+//                   k_gram_reduce.
 //   k_matmul_ts     C = X M for tall X: 128 x 64 output tile per CTA, K in steps of 16.
 //   k_cholesky      one CTA: blocked right-looking Cholesky on the packed upper triangle in shared
 //                   memory (16-row panels, register-tiled trailing update).
@@ -14,6 +15,9 @@
 //                   orthogonalises every pair of them with plane rotations (one warp per pair, the
 //                   pairs of a local round disjoint), and writes them back; a bounded grid barrier
 //                   separates the rounds.  Sweeps stop when one makes no rotation.
+//   k_jacobi_cluster the same sweeps on one thread-block cluster when the columns fit in its shared
+//                   memory: blocks stay on chip and move between rounds through distributed shared
+//                   memory, cluster barriers instead of the grid barrier.
 //   k_svd_post      singular values = column norms, sorted descending; U = X / s, V permuted alike.
 #include <math.h>
 #include <string.h>
@@ -759,11 +763,6 @@ rsk_status gram_t(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, 
     return RSK_OK;
 }
 
-rsk_status gram(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* Y, int q, int64_t ldy,
-                float* G, int64_t ldg, void* scratch, cudaStream_t stream) {
-    return gram_t<float>(h, X, m, p, ldx, Y, q, ldy, G, ldg, scratch, stream);
-}
-
 rsk_status gram64(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* Y, int q, int64_t ldy,
                   double* G, int64_t ldg, void* scratch, cudaStream_t stream) {
     return gram_t<double>(h, X, m, p, ldx, Y, q, ldy, G, ldg, scratch, stream);
@@ -958,47 +957,6 @@ rsk_status orth_accurate(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx,
     }
     if (R) {
         k_to_f32<<<unsigned((int64_t(q) * q + 255) / 256), 256, 0, stream>>>(Racc, int64_t(q) * q, R);
-        RSK_LAUNCH_CHECK(h);
-    }
-    return RSK_OK;
-}
-
-rsk_status orth(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* R, void* scratch, cudaStream_t stream) {
-    if (q < 1 || q > kCholMax || m < q)
-        return fail(h, RSK_ERR_UNSUPPORTED, "orth supports 1 <= q <= %d, m >= q (got m=%lld, q=%d)", kCholMax,
-                    (long long)m, q);
-    Carver cv(scratch);
-    void* gs = cv.take<char>(gram_scratch_bytes(m, q, q));
-    float* G = cv.take<float>(size_t(q) * q);
-    float* Rk = cv.take<float>(size_t(q) * q);
-    float* Ri = cv.take<float>(size_t(q) * q);
-    float* Racc = cv.take<float>(size_t(q) * q);
-    float* T = cv.take<float>(size_t(m) * q);
-    // shifted round first (Fukaya et al.: s = 11 (m q + q (q + 1)) u ||X||_2^2, with ||X||_F^2 = trace(G) >= ||X||_2^2)
-    const float coeff[3] = {11.f * (float(m) * q + float(q) * (q + 1)) * kU32, 0.f, 0.f};
-    for (int round = 0; round < 3; ++round) {
-        rsk_status st = gram(h, X, m, q, ldx, X, q, ldx, G, q, gs, stream);
-        if (st == RSK_OK) st = cholesky(h, G, q, q, coeff[round], Rk, q, stream);
-        if (st == RSK_OK) st = trinv(h, Rk, q, q, Ri, stream);
-        if (st == RSK_OK) st = matmul_ts(h, X, m, q, ldx, Ri, q, q, T, m, stream);
-        if (st != RSK_OK) return st;
-        const unsigned gx = unsigned(std::min<int64_t>(64, (m + 255) / 256));
-        k_copy_cols<<<dim3(gx, unsigned(q)), 256, 0, stream>>>(T, m, int(m), q, X, ldx);
-        RSK_LAUNCH_CHECK(h);
-        if (R) {
-            // R_total = Rk * R_total (upper triangular factors accumulate on the left)
-            if (round == 0) {
-                k_copy_cols<<<dim3(1, unsigned(q)), 256, 0, stream>>>(Rk, q, q, q, Racc, q);
-            } else {
-                st = matmul_ts(h, Rk, q, q, q, Racc, q, q, Ri, q, stream);  // Ri is free here
-                if (st != RSK_OK) return st;
-                k_copy_cols<<<dim3(1, unsigned(q)), 256, 0, stream>>>(Ri, q, q, q, Racc, q);
-            }
-            RSK_LAUNCH_CHECK(h);
-        }
-    }
-    if (R) {
-        k_copy_cols<<<dim3(1, unsigned(q)), 256, 0, stream>>>(Racc, q, q, q, R, q);
         RSK_LAUNCH_CHECK(h);
     }
     return RSK_OK;

@@ -1,6 +1,6 @@
 // Small dense linear algebra on the GPU for the low-rank consumers of the sketches (the Nystrom
-// approximations and the randomized SVD): tall Gram matrices, tall-by-small products, Cholesky,
-// triangular inverses, a one-sided Jacobi SVD and shifted Cholesky QR.  FP32 storage and
+// approximations and the randomized SVD): FP64-accumulated Gram matrices, tall-by-small products,
+// Cholesky, triangular inverses, a one-sided Jacobi SVD and FP64-Gram Cholesky QR.  FP32 storage and
 // arithmetic, column-major matrices (column c of X at X + c * ldx).  Every routine is asynchronous
 // on `stream`, carves its scratch from the caller's buffer and reports device-side failures (a
 // Cholesky pivot that is not positive, a bounded wait that ran out) in the handle's status word.
@@ -11,12 +11,8 @@
 namespace rsk {
 namespace dense {
 
-// Scratch bytes gram() needs for an m x p by m x q product.
+// Scratch bytes gram64() needs (per precision word) for an m x p by m x q product.
 size_t gram_scratch_bytes(int64_t m, int p, int q);
-// G (p x q, leading dimension ldg) = X^T Y for X m x p (ldx) and Y m x q (ldy).  Row chunks are
-// summed in chunk order (deterministic).  X == Y with p == q computes one triangle and mirrors it.
-rsk_status gram(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* Y, int q, int64_t ldy,
-                float* G, int64_t ldg, void* scratch, cudaStream_t stream);
 
 // C (m x q, ldc) = X (m x p, ldx) * M (p x q, ldm).  C must not alias X or M.
 rsk_status matmul_ts(rsk_handle* h, const float* X, int64_t m, int p, int64_t ldx, const float* M, int q,
@@ -38,16 +34,12 @@ size_t svd_scratch_bytes(int64_t m, int q);
 rsk_status svd(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* s, float* V, int64_t ldv,
                void* scratch, cudaStream_t stream);
 
-// Q = orth(X) for X m x q (ldx, m >= q) by shifted Cholesky QR3 (Fukaya et al.: one round of
-// Cholesky QR on X^T X + shift I, two plain rounds), in place; R (q x q, upper) receives the
-// accumulated factor with X_in = Q R when R is not null.  scratch: orth_scratch_bytes(m, q).
+// Q = orth(X) for X m x q (ldx, m >= q), in place; R (q x q, upper) receives the accumulated factor
+// with X_in = Q R when R is not null.  scratch: orth_scratch_bytes(m, q).
 size_t orth_scratch_bytes(int64_t m, int q);
-rsk_status orth(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* R, void* scratch,
-                cudaStream_t stream);
-// The same Q (and R) by Cholesky QR2 with the Gram accumulated in FP64 from the FP32 entries and the
-// Cholesky factor and its inverse in FP64: orthonormal to O(u_32) for kappa(X) up to ~1e7 (the
-// FP32 shifted form needs kappa(X) well below u_32^{-1/2} once m q is large).  q <= 1024.  Same
-// scratch size.
+// By Cholesky QR2 with the Gram accumulated in FP64 from the FP32 entries and the Cholesky factor and
+// its inverse in FP64: orthonormal to O(u_32) for kappa(X) up to ~1e7.  q <= 1024.  (The tensor-core
+// Cholesky QR of gemm_tc.cuh is the fast form for q <= 330.)
 rsk_status orth_accurate(rsk_handle* h, float* X, int64_t m, int q, int64_t ldx, float* R, void* scratch,
                          cudaStream_t stream);
 // G (FP64) = X^T Y with FP64 accumulation of the FP32 products; scratch: 2 * gram_scratch_bytes.
