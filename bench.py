@@ -170,6 +170,18 @@ def bf16_peak():
         return 1900.0, "fallback"
 
 
+def alu_add_peak(torch, dev):
+    """FP32 adds per second derived from the unit counts and the clock: SMs x 128 FP32 lanes x the
+    maximum SM clock (one add per lane per cycle; MEASURED_PEAKS.json's sm_max_mhz, else 2070 MHz)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, kind = float(json.load(f)["sm_max_mhz"]), "derived: SMs x 128 lanes x measured max SM clock"
+    except (OSError, ValueError, KeyError):
+        mhz, kind = 2070.0, "derived: SMs x 128 lanes x 2070 MHz (nominal)"
+    return sms * 128 * mhz * 1e6, kind
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -843,14 +855,20 @@ def run_ours(args):
                       "reduce": round(main["reduce_ms"], 4)},
         "clocks": clocks,
     }
+    alu_peak, alu_kind = alu_add_peak(torch, dev)
     for name in names:
         r = result[name]
         if "srtt" in r:
             sr = r["srtt"]
             key = "srtt" if name == head else f"srtt_{name}"
+            # ~12 FP32 adds per element: 11 butterfly stages of the 2048-point transform + the gather
+            adds = 12.0 * r["local_bytes"] / (2 if name == "bf16" else 4)
             line[key] = {"value": round(sr["value"], 3), "unit": "GB/s", "ms_per_step": round(sr["ms_per_step"], 4),
                          "apply_ms": round(sr["apply_ms"], 4), "draw_ms": round(sr["draw_ms"], 4),
                          "apply_hbm_frac": round(r["local_bytes"] / (sr["apply_ms"] / 1e3) / 1e9 / peak, 4),
+                         "alu": {"adds_per_launch": adds, "achieved_tadds_per_s": round(adds / (sr["apply_ms"] / 1e3) / 1e12, 3),
+                                 "peak_tadds_per_s": round(alu_peak / 1e12, 2), "peak_kind": alu_kind,
+                                 "frac": round(adds / (sr["apply_ms"] / 1e3) / alu_peak, 4)},
                          "workload": f"SRTT d={D_SKETCH} (WHT, n=2^22), A {name}"}
     for name in names[1:]:
         r = result[name]
