@@ -363,8 +363,10 @@ typedef struct {
  * rsk_lstsq_sketch_precond; opts->sketch_dtype must be F64 or F32.  The fused passes of all
  * problems run in one persistent launch over (problem, 2048-row block) tiles taken from a work
  * queue; per-problem results are reduced in tile order (deterministic).  One CG iteration is a
- * captured CUDA graph.  With inner_dtype F32 and FP32 storage, the FP64-accuracy residual passes
- * use double-float (FP32 pair) arithmetic.  probs and infos are host arrays of `count` entries;
+ * captured CUDA graph.  The Householder QR of [S A_i | S b_i] runs in the inner precision (FP32
+ * when inner_dtype is F32, else FP64); R_i and Q_i^T S b_i are then used in FP64.  With inner_dtype
+ * F32 and FP32 storage, the FP64-accuracy residual passes use double-float (FP32 pair) arithmetic.
+ * probs and infos are host arrays of `count` entries;
  * synchronous; RSK_ERR_NOT_CONVERGED if any problem stays above tol_backward (infos[i].status says
  * which). */
 rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t count, const rsk_lsq_problem* probs,

@@ -1,7 +1,9 @@
 // Batched sketch-and-precondition least squares (row a8): many problems of uneven n_i and k_i
-// solved together.  Per problem the steps are those of rsk_lstsq_sketch_precond (sketch, FP64
+// solved together.  Per problem the steps are those of rsk_lstsq_sketch_precond (sketch,
 // Householder QR, warm start, refinement on the FP64 normal-equation residual with CG on
-// M_i = A_i R_i^{-1}); across problems the work is batched:
+// M_i = A_i R_i^{-1}); the QR runs in the inner precision (FP32 in the mixed form, whose sketch is
+// FP32 already; FP64 otherwise) and R_i, Q_i^T S b_i go to FP64 for the triangular steps.  Across
+// problems the work is batched:
 //   * sketches: the inverted index is built once per problem and applied to A_i and b_i, spread
 //     over a small pool of streams;
 //   * k_qr_b / k_rinv_b / k_trmv_b / k_cg_*_b: one CTA per problem;
@@ -35,6 +37,7 @@ struct BProb {
     int64_t n, lda, lda_in;
     int k, d, a_f32, in_f32;
     double* W;          // d x (k+1) column-major
+    float* W32;         // the same in FP32 for the inner-precision QR of the mixed form, else null
     double* tau;        // k
     double* Rinv;       // k x k column-major
     double* v;          // x g c z res p s t | stats[3] (8k + 8)
@@ -50,26 +53,37 @@ struct Tile {
     int p, r0, r1, pad;
 };
 
-__device__ __forceinline__ double block_sum_b(double v, double* red) {
+template <typename T>
+__device__ __forceinline__ T block_sum_b(T v, T* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) red[w] = v;
     __syncthreads();
-    double s = 0.0;
+    T s = T(0);
     for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
     return s;
 }
 
-// ---- FP64 Householder QR, one CTA per problem ---------------------------------------------
-__device__ void qr_one(const BProb& q, double* red);
+// ---- Householder QR of W = [S A | S b], one CTA per problem, in FP64 (T = double, on W) or FP32
+// (T = float, on W32) --------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T* qr_buf(const BProb& q);
+template <>
+__device__ __forceinline__ double* qr_buf<double>(const BProb& q) { return q.W; }
+template <>
+__device__ __forceinline__ float* qr_buf<float>(const BProb& q) { return q.W32; }
+
+template <typename T>
+__device__ void qr_one(const BProb& q, T* red);
 
 // Persistent: one CTA per SM pulls problems from a queue ordered by decreasing work (d k^2), so
 // the largest factorizations start first and the small ones fill in behind them (LPT order).
+template <typename T>
 __global__ void __launch_bounds__(1024) k_qr_b(BProb* P, const int* __restrict__ order, int count,
                                               unsigned int* queue) {
-    __shared__ double red[32];
+    __shared__ T red[32];
     __shared__ int next_s;
     for (;;) {
         if (threadIdx.x == 0) next_s = int(atomicAdd(queue, 1u));
@@ -77,45 +91,60 @@ __global__ void __launch_bounds__(1024) k_qr_b(BProb* P, const int* __restrict__
         const int slot = next_s;
         __syncthreads();
         if (slot >= count) break;
-        qr_one(P[order[slot]], red);
+        qr_one<T>(P[order[slot]], red);
     }
 }
 
-__device__ void qr_one(const BProb& q, double* red) {
+// Reflector j: v = (1, W[j+1:, j] / (alpha - beta)), tau = (beta - alpha) / beta, R_jj = beta; the
+// reflector is applied to the columns right of j (the last one is S b, so Q^T S b builds up there).
+template <typename T>
+__device__ void qr_one(const BProb& q, T* red) {
     const int d = q.d, k = q.k, cols = k + 1;
-    double* W = q.W;
+    T* W = qr_buf<T>(q);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = 0; j < k; ++j) {
-        double* colj = W + size_t(j) * d;
-        double s = 0.0;
+        T* colj = W + size_t(j) * d;
+        T s = T(0);
         for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) s += colj[i] * colj[i];
-        const double sigma = block_sum_b(s, red);
-        const double alpha = colj[j];
-        double tau = 0.0, beta = alpha, scale = 1.0;
-        if (sigma > 0.0) {
-            const double nrm = sqrt(alpha * alpha + sigma);
-            beta = alpha > 0.0 ? -nrm : nrm;
+        const T sigma = block_sum_b<T>(s, red);
+        const T alpha = colj[j];
+        T tau = T(0), beta = alpha, scale = T(1);
+        if (sigma > T(0)) {
+            const T nrm = sqrt(alpha * alpha + sigma);
+            beta = alpha > T(0) ? -nrm : nrm;
             tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
+            scale = T(1) / (alpha - beta);
             for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) colj[i] *= scale;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             colj[j] = beta;
-            q.tau[j] = tau;
+            q.tau[j] = double(tau);
         }
         __syncthreads();
         for (int c = j + 1 + warp; c < cols; c += nw) {
-            double* col = W + size_t(c) * d;
-            double t = 0.0;
+            T* col = W + size_t(c) * d;
+            T t = T(0);
             for (int i = j + 1 + lane; i < d; i += 32) t += colj[i] * col[i];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            const double w = tau * (col[j] + t);
+            const T w = tau * (col[j] + t);
             if (lane == 0) col[j] -= w;
             for (int i = j + 1 + lane; i < d; i += 32) col[i] -= w * colj[i];
         }
         __syncthreads();
+    }
+}
+
+// After the FP32 QR: rows 0..k-1 of every column of W32 (R and the leading k entries of Q^T S b) to
+// the FP64 W that k_rinv_b and k_trmv_b read.
+__global__ void k_qr32_to_w_b(BProb* P) {
+    const BProb& q = P[blockIdx.x];
+    if (!q.W32) return;
+    const int k = q.k, d = q.d;
+    for (int idx = threadIdx.x; idx < k * (k + 1); idx += blockDim.x) {
+        const int c = idx / k, i = idx - c * k;
+        q.W[size_t(c) * d + i] = double(q.W32[size_t(c) * d + i]);
     }
 }
 
@@ -620,13 +649,13 @@ __global__ void k_finish_b(BProb* P) {
     for (int j = threadIdx.x; j < q.k; j += blockDim.x) q.xout[j] = q.v[j];
 }
 
-template <typename S>
+template <typename S, typename T>
 __global__ void k_to_colmajor_b(const S* __restrict__ SA, const double* __restrict__ Sb, int d, int k,
-                                double* __restrict__ W) {
+                                T* __restrict__ W) {
     const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (idx >= int64_t(d) * (k + 1)) return;
     const int c = int(idx / d), i = int(idx - int64_t(c) * d);
-    W[idx] = c < k ? double(SA[int64_t(i) * k + c]) : Sb[i];
+    W[idx] = c < k ? T(SA[int64_t(i) * k + c]) : T(Sb[i]);
 }
 
 // b as double-float pairs (hi = float(b), lo = float(b - hi)) for every problem in one launch
@@ -718,6 +747,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         }
         maxk = std::max(maxk, q.k);
         add(size_t(d) * (q.k + 1) * 8);
+        if (opts->inner_dtype == RSK_F32) add(size_t(d) * (q.k + 1) * 4);
         add(size_t(q.k) * 8);
         add(size_t(q.k) * q.k * 8);
         add((size_t(8) * q.k + 8) * 8);
@@ -755,6 +785,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         BProb& q = hp[i];
         const rsk_lsq_problem& pr = probs[i];
         q.W = cv.take<double>(size_t(q.d) * (q.k + 1));
+        q.W32 = q.in_f32 ? cv.take<float>(size_t(q.d) * (q.k + 1)) : nullptr;
         q.tau = cv.take<double>(size_t(q.k));
         q.Rinv = cv.take<double>(size_t(q.k) * q.k);
         q.v = cv.take<double>(size_t(8) * q.k + 8);
@@ -843,8 +874,14 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         if (st == RSK_OK) st = sketch_apply_vec_built(h, index, pr.n, q.d, zeta, pr.b, Sb, static_cast<double*>(parts), s);
         if (st != RSK_OK) return st;
         const unsigned gw = unsigned((int64_t(q.d) * (q.k + 1) + 255) / 256);
-        if (sa_dt == RSK_F64) k_to_colmajor_b<double><<<gw, 256, 0, s>>>(SA, Sb, q.d, q.k, q.W);
-        else k_to_colmajor_b<float><<<gw, 256, 0, s>>>(reinterpret_cast<float*>(SA), Sb, q.d, q.k, q.W);
+        const float* SA32 = reinterpret_cast<const float*>(SA);
+        if (q.W32) {
+            if (sa_dt == RSK_F64) k_to_colmajor_b<double, float><<<gw, 256, 0, s>>>(SA, Sb, q.d, q.k, q.W32);
+            else k_to_colmajor_b<float, float><<<gw, 256, 0, s>>>(SA32, Sb, q.d, q.k, q.W32);
+        } else {
+            if (sa_dt == RSK_F64) k_to_colmajor_b<double, double><<<gw, 256, 0, s>>>(SA, Sb, q.d, q.k, q.W);
+            else k_to_colmajor_b<float, double><<<gw, 256, 0, s>>>(SA32, Sb, q.d, q.k, q.W);
+        }
         RSK_LAUNCH_CHECK(h);
     }
     // the double-float split of every b (for the residual passes), one launch for the whole batch
@@ -859,7 +896,12 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     // ---- QR, R^{-1}, warm start
     const int pr0 = prof_begin(h, main_s, RSK_KERNEL_BATCH_QR);
     RSK_CUDA_TRY(h, cudaMemsetAsync(dqueue + 16, 0, 4, main_s));
-    k_qr_b<<<std::min(count, h->num_sms), 1024, 0, main_s>>>(dP, dorder, count, dqueue + 16);
+    if (opts->inner_dtype == RSK_F32) {
+        k_qr_b<float><<<std::min(count, h->num_sms), 1024, 0, main_s>>>(dP, dorder, count, dqueue + 16);
+        k_qr32_to_w_b<<<count, 256, 0, main_s>>>(dP);
+    } else {
+        k_qr_b<double><<<std::min(count, h->num_sms), 1024, 0, main_s>>>(dP, dorder, count, dqueue + 16);
+    }
     k_rinv_b<<<count, 512, 0, main_s>>>(dP);
     k_trmv_b<<<count, 256, 0, main_s>>>(dP, 0, -1, 0, 0);
     prof_end(h, main_s, pr0);
