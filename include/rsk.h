@@ -485,9 +485,11 @@ rsk_status rsk_osi_estimate(rsk_handle* h, int64_t r, int64_t k, int32_t zeta, u
  * M x K row-major (lda >= K), B device BF16 N x K row-major (ldb >= K) -- both K-major --, D device
  * FP32 M x N column-major (ldd >= M).  The dense product step of Alg. 1 (Z = A^T Q, Y = A Z) with the
  * rank as N.  1 <= N <= 512 (N rounded up to an even multiple of 16 internally: 2 x 16 .. 2 x 256);
- * A, B 16-byte aligned with 16-byte row pitches.  nsplit > 1 splits K over that many CTAs per
- * 128-row tile (the partials come from the handle's workspace and are summed in split order).
- * Asynchronous. */
+ * A, B 16-byte aligned with 16-byte row pitches.  nsplit > 1 splits K that many ways for every
+ * 128-row tile (the partials come from the handle's workspace and are summed in split order); nsplit
+ * 0 chooses: K splits that keep the SMs busiest, and without a split a last round of row tiles that
+ * would leave more than half the SMs idle is split over K instead (those rows summed from partials).
+ * The kernel is persistent: one CTA per SM, the row tiles dealt round-robin.  Asynchronous. */
 rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B, int64_t N,
                          int64_t ldb, float* D, int64_t ldd, int32_t nsplit, cudaStream_t stream);
 /* The same product with the operand and output layouts of the RSVD's steps: a_mn != 0 takes A

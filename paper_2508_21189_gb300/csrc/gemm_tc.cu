@@ -32,9 +32,9 @@ namespace {
 
 constexpr int kBM = 128, kBK = 64, kThreads = 192;
 // pipeline depth: as many stages (at most 4) as fit in 227 KB of shared memory with the barriers
-template <int NH>
+template <int NH, int NH2>
 constexpr int stages_for() {
-    return std::min(4, (227 * 1024 - 1024 - 256) / (kBM * kBK * 2 + 2 * NH * kBK * 2));
+    return std::min(4, (227 * 1024 - 1024 - 256) / (kBM * kBK * 2 + (NH + NH2) * kBK * 2));
 }
 
 // tcgen05 shared-memory matrix descriptor, 128-byte swizzle: start address (bits 0-13, >> 4), leading
@@ -125,55 +125,100 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// b: B with a box of the first half's rows (NH; NH / 2 for clusters of 4); b2: the same B with a box of
+// the second half's rows (NH2).
 struct GemmMaps {
     CUtensorMap a[rsk::tc::kMaxOperands];
     CUtensorMap b[rsk::tc::kMaxOperands];
+    CUtensorMap b2[rsk::tc::kMaxOperands];
 };
 
+// Work items of the persistent kernel, counted in cluster units (CL consecutive row tiles that share
+// the B tile): items [0, n_full) are the row-tile groups g = item over all of K, written to D; items
+// [n_full, n_full + part_groups * nsplit) are (group, split) pairs, group = part_group0 + j % part_groups
+// and split = j / part_groups for j = item - n_full, over K blocks [split * kb_part, ...), written to the
+// column-major partials P + split * pstride (rows from prow0, leading dimension pld).
 struct GemmArgs {
     int64_t M, K;
-    int N;             // columns of D stored (<= 2 * NH)
-    int kblocks;       // K blocks per split (of one pass)
+    int N;             // columns of D stored (<= NH + NH2)
     int64_t nk_total;  // K blocks of one pass overall
     int npass;
     uint8_t pa[rsk::tc::kMaxPasses], pb[rsk::tc::kMaxPasses];
     float* D;
     int64_t ldd;
-    int row_major;         // D row-major (only without split-K: partials are column-major)
-    int64_t split_stride;  // elements between the splits' partial outputs (0: one split)
+    int row_major;     // D row-major
+    int n_full, part_groups, part_group0, nsplit, kb_part, nitems;
+    float* P;
+    int64_t pstride, prow0, pld;
     unsigned int* status;
 };
 
-// CL > 1: the CTAs of a cluster (consecutive row tiles) share the B tile: CTA rank c loads rows
-// [c 2NH/CL, (c+1) 2NH/CL) of it and multicasts them to the whole cluster, so each stage's `full`
-// barrier counts the own A tile plus the CL pieces, and a stage is free again only when every CTA's
-// MMAs are done with it (its `empty` barrier takes one multicast commit from each CTA).
-template <int NH, bool A_MN, int CL>
+struct ItemRange {
+    int group, kb0, nk;
+    bool partial;
+    int split;
+};
+__device__ __forceinline__ ItemRange decode_item(const GemmArgs& a, int item) {
+    ItemRange r;
+    if (item < a.n_full) {
+        r.group = item;
+        r.kb0 = 0;
+        r.nk = int(a.nk_total);
+        r.partial = false;
+        r.split = 0;
+    } else {
+        const int j = item - a.n_full;
+        r.split = j / a.part_groups;
+        r.group = a.part_group0 + (j - r.split * a.part_groups);
+        r.kb0 = r.split * a.kb_part;
+        r.nk = int(min(int64_t(a.kb_part), a.nk_total - r.kb0));
+        r.partial = true;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rskd::smem_u32(bar)) : "memory");
+}
+
+// The N columns of the tile are two MMAs' worth: the first NH, then NH2 <= NH (each a multiple of 16,
+// the MMA's N step for M = 128), accumulated side by side in tensor memory.
+// Persistent: cluster c takes items c, c + C, c + 2C, ... (C clusters in the grid); CTA rank r of the
+// cluster computes row tile CL * group + r of each.  The operand ring runs on across items: the
+// producer fills stages for the next item while the MMAs of the current one finish and the epilogue
+// drains its accumulator; the first MMA of an item waits until the epilogue has read the previous
+// accumulator out of tensor memory (`tempty`), the epilogue waits for the item's last MMA (`tfull`).
+// CL > 1: the CTAs of a cluster share the B tile: with CL = 2 CTA rank c loads half c of it, with
+// CL = 4 (NH2 = NH only) rows [c NH/2, (c+1) NH/2), and multicasts its piece to the whole cluster, so
+// each stage's `full` barrier counts the own A tile plus the CL pieces, and a stage is free again only
+// when every CTA's MMAs are done with it (its `empty` barrier takes one multicast commit from each CTA).
+template <int NH, int NH2, bool A_MN, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ GemmMaps maps, const GemmArgs a) {
-    constexpr int kStages = stages_for<NH>();
+    static_assert(NH2 <= NH && NH2 % 16 == 0 && NH2 >= 16, "second half: a multiple of 16, at most NH");
+    static_assert(CL != 4 || NH2 == NH, "clusters of 4 split equal halves");
+    constexpr int kStages = stages_for<NH, NH2>();
     constexpr int kABytes = kBM * kBK * 2;          // 16 KB
-    constexpr int kBBytes = 2 * NH * kBK * 2;       // N x 64 BF16
+    constexpr int kBBytes = (NH + NH2) * kBK * 2;   // N x 64 BF16
     constexpr int kStage = kABytes + kBBytes;       // multiple of 1024
-    constexpr uint32_t kTmemCols = (2 * NH <= 32) ? 32 : (2 * NH <= 64) ? 64 : (2 * NH <= 128) ? 128 : (2 * NH <= 256) ? 256 : 512;
+    constexpr int kNT = NH + NH2;
+    constexpr uint32_t kTmemCols = (kNT <= 32) ? 32 : (kNT <= 64) ? 64 : (kNT <= 128) ? 128 : (kNT <= 256) ? 256 : 512;
     extern __shared__ uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * kStage);
     uint64_t* empty = full + kStages;
     uint64_t* tfull = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tfull + 1);
+    uint64_t* tempty = tfull + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* consumed = abort_flag + 1;  // K blocks the MMA thread has waited for, per stage
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = int64_t(blockIdx.x) * kBM;
-    const int split = blockIdx.y;
-    const int64_t kb0 = int64_t(split) * a.kblocks;
-    const int nk = int(std::min<int64_t>(a.kblocks, a.nk_total - kb0));
-    const int total = nk > 0 ? nk * a.npass : 0;
+    const int nclusters = int(gridDim.x) / CL;
+    const int cluster_id = int(blockIdx.x) / CL;
 
     constexpr uint16_t kMask = uint16_t((1u << CL) - 1);
-    constexpr int kPieceRows = 2 * NH / CL;                // rows of B each CTA of the cluster loads
+    constexpr int kPieceRows = CL == 4 ? NH / 2 : NH;      // B rows between consecutive CTAs' pieces
     const int rank = CL > 1 ? int(cluster_rank()) : 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -182,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             consumed[s] = 0;
         }
         rskd::mbar_init(tfull, 1);
+        rskd::mbar_init(tempty, 4);   // one arrive per epilogue warp
         *abort_flag = 0;
         rskd::fence_mbar_init();
     }
@@ -195,41 +241,48 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int issued[kStages] = {};
-            for (int it = 0; it < total; ++it) {
-                const int s = it % kStages;
-                if (it >= kStages && !rskd::mbar_wait(&empty[s], uint32_t(((it / kStages) & 1) ^ 1), a.status)) {
-                    *abort_flag = 1;
-                    break;
+            int it = 0;
+            for (int item = cluster_id; item < a.nitems && !*abort_flag; item += nclusters) {
+                const ItemRange ir = decode_item(a, item);
+                const int64_t m0 = (int64_t(ir.group) * CL + rank) * kBM;
+                const int total = ir.nk * a.npass;
+                for (int t = 0; t < total; ++t, ++it) {
+                    const int s = it % kStages;
+                    if (it >= kStages && !rskd::mbar_wait(&empty[s], uint32_t(((it / kStages) & 1) ^ 1), a.status)) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    const int pass = t / ir.nk, kb = t - pass * ir.nk;
+                    const CUtensorMap* ma = &maps.a[a.pa[pass]];
+                    const CUtensorMap* mb = &maps.b[a.pb[pass]];
+                    const CUtensorMap* mb2 = &maps.b2[a.pb[pass]];
+                    uint8_t* st = sm + s * kStage;
+                    const int kx = (ir.kb0 + kb) * kBK;
+                    rskd::mbar_expect_tx(&full[s], uint32_t(kStage));
+                    if constexpr (A_MN) {
+                        rskd::tma_load_2d(st, ma, int(m0), kx, &full[s]);
+                        rskd::tma_load_2d(st + kABytes / 2, ma, int(m0) + 64, kx, &full[s]);
+                    } else {
+                        rskd::tma_load_2d(st, ma, kx, int(m0), &full[s]);
+                    }
+                    if constexpr (CL == 1) {
+                        rskd::tma_load_2d(st + kABytes, mb, kx, 0, &full[s]);
+                        rskd::tma_load_2d(st + kABytes + NH * kBK * 2, mb2, kx, NH, &full[s]);
+                    } else {
+                        tma_load_2d_mc(st + kABytes + rank * kPieceRows * kBK * 2, (CL == 2 && rank == 1) ? mb2 : mb,
+                                       kx, rank * kPieceRows, &full[s], kMask);
+                    }
+                    ++issued[s];
                 }
-                if (*abort_flag) break;
-                const int pass = it / nk, kb = it - pass * nk;
-                const CUtensorMap* ma = &maps.a[a.pa[pass]];
-                const CUtensorMap* mb = &maps.b[a.pb[pass]];
-                uint8_t* st = sm + s * kStage;
-                const int kx = int((kb0 + kb) * kBK);
-                rskd::mbar_expect_tx(&full[s], uint32_t(kStage));
-                if constexpr (A_MN) {
-                    rskd::tma_load_2d(st, ma, int(m0), kx, &full[s]);
-                    rskd::tma_load_2d(st + kABytes / 2, ma, int(m0) + 64, kx, &full[s]);
-                } else {
-                    rskd::tma_load_2d(st, ma, kx, int(m0), &full[s]);
-                }
-                if constexpr (CL == 1) {
-                    rskd::tma_load_2d(st + kABytes, mb, kx, 0, &full[s]);
-                    rskd::tma_load_2d(st + kABytes + NH * kBK * 2, mb, kx, NH, &full[s]);
-                } else {
-                    tma_load_2d_mc(st + kABytes + rank * kPieceRows * kBK * 2, mb, kx, rank * kPieceRows, &full[s],
-                                   kMask);
-                }
-                ++issued[s];
             }
             if constexpr (CL > 1) {
                 // every CTA's last release of every stage: after it no remote arrive or multicast
                 // write targets this CTA's shared memory (skipped after a timeout: the bounded waits
                 // of the other CTAs outlast their copies in flight)
                 if (!*abort_flag)
-                    for (int s = 0; s < kStages && s < total; ++s) {
-                        const int last = (total - 1 - s) / kStages;   // use number of the stage's last fill
+                    for (int s = 0; s < kStages && s < it; ++s) {
+                        const int last = (it - 1 - s) / kStages;   // use number of the stage's last fill
                         rskd::mbar_wait(&empty[s], uint32_t(last & 1), a.status);
                     }
             }
@@ -243,64 +296,99 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = instr_desc(kBM, NH, A_MN);
-            for (int it = 0; it < total; ++it) {
-                const int s = it % kStages;
-                if (*abort_flag || !rskd::mbar_wait(&full[s], uint32_t((it / kStages) & 1), a.status)) {
+            constexpr uint32_t idesc = instr_desc(kBM, NH, A_MN), idesc2 = instr_desc(kBM, NH2, A_MN);
+            int it = 0, j = 0;
+            for (int item = cluster_id; item < a.nitems && !*abort_flag; item += nclusters, ++j) {
+                const ItemRange ir = decode_item(a, item);
+                const int total = ir.nk * a.npass;
+                // the epilogue has read the previous item's accumulator
+                if (j > 0 && !rskd::mbar_wait(tempty, uint32_t((j - 1) & 1), a.status)) {
                     *abort_flag = 1;
                     break;
                 }
-                consumed[s] = consumed[s] + 1;
                 tc_fence_after();
-                const uint32_t sa = rskd::smem_u32(sm + s * kStage);
-                const uint32_t sb = sa + kABytes;
-#pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
-                    const uint64_t ad = A_MN ? smem_desc(sa + kk * 2048, kABytes / 2) : smem_desc(sa + kk * 32, 16);
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {
-                        const uint64_t bd = smem_desc(sb + hh * NH * kBK * 2 + kk * 32, 16);
-                        tc_mma(tmem + uint32_t(hh * NH), ad, bd, idesc, (it | kk) != 0 ? 1u : 0u);
+                bool stop = false;
+                for (int t = 0; t < total; ++t, ++it) {
+                    const int s = it % kStages;
+                    if (*abort_flag || !rskd::mbar_wait(&full[s], uint32_t((it / kStages) & 1), a.status)) {
+                        *abort_flag = 1;
+                        stop = true;
+                        break;
                     }
+                    consumed[s] = consumed[s] + 1;
+                    tc_fence_after();
+                    const uint32_t sa = rskd::smem_u32(sm + s * kStage);
+                    const uint32_t sb = sa + kABytes;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t ad = A_MN ? smem_desc(sa + kk * 2048, kABytes / 2) : smem_desc(sa + kk * 32, 16);
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const uint64_t bd = smem_desc(sb + hh * NH * kBK * 2 + kk * 32, 16);
+                            tc_mma(tmem + uint32_t(hh * NH), ad, bd, hh ? idesc2 : idesc, (t | kk) != 0 ? 1u : 0u);
+                        }
+                    }
+                    if constexpr (CL == 1) tc_commit(&empty[s]);
+                    else tc_commit_mc(&empty[s], kMask);
                 }
-                if constexpr (CL == 1) tc_commit(&empty[s]);
-                else tc_commit_mc(&empty[s], kMask);
+                // the item's accumulator is complete (or, after a timeout, the issued MMAs are done)
+                tc_commit(tfull);
+                if (stop) break;
             }
-            // the accumulator is complete (or the issued MMAs are done, after a timeout)
-            tc_commit(tfull);
         }
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, i.e. rows m0 + 32 (w % 4) + lane
         const int q = warp & 3;
-        // the TMEM loads below are warp-wide (.sync.aligned): the decision to run them is the warp's
-        const bool ok = __all_sync(0xffffffffu, rskd::mbar_wait(tfull, 0u, a.status));
-        tc_fence_after();
-        const int64_t row = m0 + 32 * q + lane;
-        float* out = a.D + int64_t(split) * a.split_stride;
-        if (ok && !*abort_flag && total > 0) {
-            for (int c0 = 0; c0 < 2 * NH; c0 += 32) {
+        int j = 0;
+        for (int item = cluster_id; item < a.nitems; item += nclusters, ++j) {
+            // the TMEM loads below are warp-wide (.sync.aligned): the decision to run them is the warp's
+            const bool ok = __all_sync(0xffffffffu, rskd::mbar_wait(tfull, uint32_t(j & 1), a.status));
+            if (!ok || *abort_flag) {
+                if (lane == 0) *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const ItemRange ir = decode_item(a, item);
+            const int64_t row = (int64_t(ir.group) * CL + rank) * kBM + 32 * q + lane;
+            float* out;
+            int64_t ld, orow;
+            bool rm;
+            if (ir.partial) {
+                out = a.P + int64_t(ir.split) * a.pstride;
+                ld = a.pld;
+                orow = row - a.prow0;
+                rm = false;
+            } else {
+                out = a.D;
+                ld = a.ldd;
+                orow = row;
+                rm = a.row_major != 0;
+            }
+            for (int c0 = 0; c0 < kNT; c0 += 32) {
                 uint32_t v[32];
                 tc_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(c0), v);
                 if (row < a.M && c0 < a.N) {
-                    if (!a.row_major) {
+                    if (!rm) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (c0 + j < a.N) out[int64_t(c0 + j) * a.ldd + row] = __uint_as_float(v[j]);
-                    } else if (c0 + 32 <= a.N && (a.ldd & 3) == 0) {
-                        float4* o4 = reinterpret_cast<float4*>(out + row * a.ldd + c0);
+                        for (int jj = 0; jj < 32; ++jj)
+                            if (c0 + jj < a.N) out[int64_t(c0 + jj) * ld + orow] = __uint_as_float(v[jj]);
+                    } else if (c0 + 32 <= a.N && (ld & 3) == 0) {
+                        float4* o4 = reinterpret_cast<float4*>(out + orow * ld + c0);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            o4[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
-                                                __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+                        for (int jj = 0; jj < 8; ++jj)
+                            o4[jj] = make_float4(__uint_as_float(v[4 * jj]), __uint_as_float(v[4 * jj + 1]),
+                                                 __uint_as_float(v[4 * jj + 2]), __uint_as_float(v[4 * jj + 3]));
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (c0 + j < a.N) out[row * a.ldd + c0 + j] = __uint_as_float(v[j]);
+                        for (int jj = 0; jj < 32; ++jj)
+                            if (c0 + jj < a.N) out[orow * ld + c0 + jj] = __uint_as_float(v[jj]);
                     }
                 }
             }
-        } else if (total == 0 && row < a.M) {
-            for (int c = 0; c < a.N; ++c) out[a.row_major ? row * a.ldd + c : int64_t(c) * a.ldd + row] = 0.f;
+            // this warp's reads of the accumulator are complete: hand tensor memory back to the MMAs
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty);
         }
     }
     tc_fence_before();
@@ -313,15 +401,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     if constexpr (CL > 1) cluster_sync();   // no CTA leaves while another may still signal it
 }
 
-// D = sum over splits (in split order) of the column-major partials.
-__global__ void k_sum_splits(const float* __restrict__ part, int64_t stride, int nsplit, int64_t M, int N, int64_t ldd,
-                             int row_major, float* __restrict__ D) {
+// Rows row0 + r (0 <= r < rows) of D = sum over splits (in split order) of the column-major partials
+// (element (r, c) of split p at part[p * stride + c * rows + r]).
+__global__ void k_sum_splits(const float* __restrict__ part, int64_t stride, int nsplit, int64_t row0, int64_t rows,
+                             int N, int64_t ldd, int row_major, float* __restrict__ D) {
     const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= M * N) return;
-    const int64_t c = idx / M, r = idx - c * M;
+    if (idx >= rows * N) return;
+    const int64_t c = idx / rows, r = idx - c * rows;
     float s = 0.f;
-    for (int p = 0; p < nsplit; ++p) s += part[int64_t(p) * stride + c * M + r];
-    D[row_major ? r * ldd + c : c * ldd + r] = s;
+    for (int p = 0; p < nsplit; ++p) s += part[int64_t(p) * stride + c * rows + r];
+    const int64_t row = row0 + r;
+    D[row_major ? row * ldd + c : c * ldd + row] = s;
 }
 
 // Three-term BF16 split, column c of X at X + c * ldx: x1 = bf16(x), x2 = bf16(x - x1), x3 =
@@ -386,15 +476,79 @@ __global__ void k_to_bf16_flat(const float4* __restrict__ X, int64_t n4, uint2* 
     }
 }
 
-template <int NH, bool A_MN, int CL>
-rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, const GemmArgs& ga, int mtiles, int nsplit,
-                       cudaStream_t stream) {
-    constexpr int kStage = kBM * kBK * 2 + 2 * NH * kBK * 2;
-    const int smem = stages_for<NH>() * kStage + 1024 + 256;
-    auto kern = k_gemm_tc<NH, A_MN, CL>;
+// Co-resident clusters of a kernel instance (at most one CTA per SM: the shared memory is the limit);
+// 0 if the query fails.
+int resident_clusters(const void* kern, cudaLaunchConfig_t cfg) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    return n;
+}
+
+// How the row-tile groups become work items: nsplit > 1 splits every group's K range; otherwise, with
+// split_last and enough scratch, a last round of items that would leave more than half the clusters
+// idle is split over K instead (2 to 4 ways, as many as fill the clusters).  sum_row0 / sum_splits
+// (out) say which rows of D come from partials (sum_splits 0: none).
+struct ItemPlan {
+    int groups, cl, nsplit, kblocks;
+    float* scratch;
+    size_t scratch_bytes;
+    bool split_last;
+    int64_t sum_row0;
+    int sum_splits;
+};
+
+void plan_items(GemmArgs& ga, ItemPlan& ip, int nc) {
+    ga.P = ip.scratch;
+    ip.sum_splits = 0;
+    ip.sum_row0 = 0;
+    if (ip.nsplit > 1) {
+        ga.n_full = 0;
+        ga.part_groups = ip.groups;
+        ga.part_group0 = 0;
+        ga.nsplit = ip.nsplit;
+        ga.kb_part = ip.kblocks;
+        ga.prow0 = 0;
+        ga.pld = ga.M;
+        ga.pstride = ga.M * int64_t(ga.N);
+        ip.sum_splits = ip.nsplit;
+    } else {
+        ga.n_full = ip.groups;
+        ga.part_groups = 0;
+        ga.nsplit = 1;
+        const int rem = nc > 0 ? ip.groups % nc : 0;
+        if (ip.split_last && ip.scratch && ip.groups > nc && rem > 0 && 2 * rem <= nc && ga.nk_total >= 32) {
+            int S = std::max(2, std::min(4, nc / rem));
+            const int kb = int((ga.nk_total + S - 1) / S);
+            S = int((ga.nk_total + kb - 1) / kb);
+            const int64_t prow0 = int64_t(ip.groups - rem) * ip.cl * kBM;
+            const int64_t pld = ga.M - prow0;
+            if (pld > 0 && size_t(S) * size_t(pld) * size_t(ga.N) * 4 <= ip.scratch_bytes) {
+                ga.n_full = ip.groups - rem;
+                ga.part_groups = rem;
+                ga.part_group0 = ga.n_full;
+                ga.nsplit = S;
+                ga.kb_part = kb;
+                ga.prow0 = prow0;
+                ga.pld = pld;
+                ga.pstride = pld * int64_t(ga.N);
+                ip.sum_row0 = prow0;
+                ip.sum_splits = S;
+            }
+        }
+    }
+    ga.nitems = ga.n_full + ga.part_groups * ga.nsplit;
+}
+
+template <int NH, int NH2, bool A_MN, int CL>
+rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, GemmArgs ga, ItemPlan& ip, cudaStream_t stream) {
+    constexpr int kStage = kBM * kBK * 2 + (NH + NH2) * kBK * 2;
+    const int smem = stages_for<NH, NH2>() * kStage + 1024 + 256;
+    auto kern = k_gemm_tc<NH, NH2, A_MN, CL>;
     RSK_CUDA_TRY(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned((mtiles + CL - 1) / CL * CL), unsigned(nsplit));
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = size_t(smem);
     cfg.stream = stream;
@@ -405,6 +559,16 @@ rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, const GemmArgs& ga, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // persistent grid: as many clusters as can be resident together (no more than there are items);
+    // the items are dealt round-robin, so a smaller grid is only slower, never wrong
+    static int resident = -1;   // per kernel instance
+    if (resident < 0) {
+        cfg.gridDim = dim3(unsigned(CL));
+        resident = resident_clusters(reinterpret_cast<const void*>(kern), cfg);
+    }
+    const int cap = resident > 0 ? resident : std::max(1, h->num_sms / CL);
+    plan_items(ga, ip, cap);
+    cfg.gridDim = dim3(unsigned(std::min(ga.nitems, cap) * CL));
     const int pr = rsk::prof_begin(h, stream, ga.npass > 1 ? RSK_KERNEL_GEMM_SPLIT : RSK_KERNEL_GEMM);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, ga);
     rsk::prof_end(h, stream, pr);
@@ -419,27 +583,36 @@ rsk_status launch_gemm(rsk_handle* h, const GemmMaps& maps, const GemmArgs& ga, 
 // Clusters of 4 are built for the N halves of the RSVD's ranks (128, 160, 256) only.
 constexpr bool cluster4_nh(int nh) { return nh == 128 || nh == 160 || nh == 256; }
 
+// the N halves (nh, nh2): nh2 = nh, or nh - 16 (clusters of 1 or 2)
+template <int NH, bool A_MN, int CL>
+rsk_status launch_halves(rsk_handle* h, int nh2, const GemmMaps& maps, const GemmArgs& ga, ItemPlan& ip, cudaStream_t stream) {
+    if constexpr (CL != 4 && NH >= 32) {
+        if (nh2 == NH - 16) return launch_gemm<NH, NH - 16, A_MN, CL>(h, maps, ga, ip, stream);
+    }
+    if (nh2 != NH) return rsk::fail(h, RSK_ERR_INTERNAL, "gemm: N halves %d + %d are not built", NH, nh2);
+    return launch_gemm<NH, NH, A_MN, CL>(h, maps, ga, ip, stream);
+}
+
 template <bool A_MN, int CL>
-rsk_status dispatch_nh(rsk_handle* h, int nh, const GemmMaps& maps, const GemmArgs& ga, int mtiles, int nsplit,
-                       cudaStream_t stream) {
+rsk_status dispatch_nh(rsk_handle* h, int nh, int nh2, const GemmMaps& maps, const GemmArgs& ga, ItemPlan& ip, cudaStream_t stream) {
     if constexpr (CL == 4) {
         switch (nh) {
-            case 128: return launch_gemm<128, A_MN, 4>(h, maps, ga, mtiles, nsplit, stream);
-            case 160: return launch_gemm<160, A_MN, 4>(h, maps, ga, mtiles, nsplit, stream);
-            case 256: return launch_gemm<256, A_MN, 4>(h, maps, ga, mtiles, nsplit, stream);
+            case 128: return launch_halves<128, A_MN, 4>(h, nh2, maps, ga, ip, stream);
+            case 160: return launch_halves<160, A_MN, 4>(h, nh2, maps, ga, ip, stream);
+            case 256: return launch_halves<256, A_MN, 4>(h, nh2, maps, ga, ip, stream);
             default: return rsk::fail(h, RSK_ERR_UNSUPPORTED, "gemm: clusters of 4 need N half 128, 160 or 256");
         }
     } else {
         switch (nh) {
-            case 16: return launch_gemm<16, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 32: return launch_gemm<32, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 48: return launch_gemm<48, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 64: return launch_gemm<64, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 96: return launch_gemm<96, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 128: return launch_gemm<128, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 160: return launch_gemm<160, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 192: return launch_gemm<192, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
-            case 256: return launch_gemm<256, A_MN, CL>(h, maps, ga, mtiles, nsplit, stream);
+            case 16: return launch_halves<16, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 32: return launch_halves<32, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 48: return launch_halves<48, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 64: return launch_halves<64, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 96: return launch_halves<96, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 128: return launch_halves<128, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 160: return launch_halves<160, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 192: return launch_halves<192, A_MN, CL>(h, nh2, maps, ga, ip, stream);
+            case 256: return launch_halves<256, A_MN, CL>(h, nh2, maps, ga, ip, stream);
             default: return rsk::fail(h, RSK_ERR_UNSUPPORTED, "gemm: N half %d is not supported", nh);
         }
     }
@@ -456,6 +629,28 @@ size_t gemm_scratch_bytes(int64_t M, int N, int nsplit) {
     return nsplit > 1 ? size_t(nsplit) * size_t(M) * size_t(N) * 4 + 256 : 0;
 }
 
+int wave_splits(int64_t M, int64_t K, int num_sms, int max_split) {
+    const int64_t mtiles = (M + kBM - 1) / kBM;
+    const int64_t tiles = mtiles >= 8 ? (mtiles + 1) / 2 * 2 : mtiles;   // the automatic cluster of 2
+    const int64_t nk = (K + kBK - 1) / kBK;
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= max_split && s <= nk; ++s) {
+        const int64_t kb = (nk + s - 1) / s;
+        const int64_t splits = (nk + kb - 1) / kb;
+        const int64_t ctas = tiles * splits;
+        const int64_t waves = (ctas + num_sms - 1) / num_sms;
+        // busy fraction of the SMs over the waves, times the share of a CTA's time spent in its K loop
+        // (about 12 K blocks' worth of setup, pipeline fill and epilogue per CTA)
+        const double eff = double(ctas) / double(waves * num_sms) * double(kb) / double(kb + 12);
+        if (eff > best_eff * 1.005) {
+            best_eff = eff;
+            best = int(splits);
+        }
+    }
+    return best;
+}
+
 void set_split_passes(Product& p) {
     // The tensor cores' FP32 accumulation rounds toward zero: every MMA into an accumulator loses up to
     // one unit in the last place of the accumulator's current value.  The correction terms therefore
@@ -469,7 +664,8 @@ void set_split_passes(Product& p) {
     }
 }
 
-rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream, int cluster) {
+rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream, int cluster,
+                size_t scratch_bytes, bool split_last) {
     if (p.M < 1 || p.K < 1 || p.N < 1 || p.N > 512 || p.ldd < (p.d_row_major ? p.N : p.M))
         return fail(h, RSK_ERR_INVALID_ARG, "gemm: bad shape");
     if (p.npass < 1 || p.npass > kMaxPasses || p.na < 1 || p.na > kMaxOperands || p.nb < 1 || p.nb > kMaxOperands)
@@ -484,7 +680,8 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
         if (!p.b[i] || !aligned16(p.b[i])) return fail(h, RSK_ERR_INVALID_ARG, "gemm: B operands must be 16-byte aligned");
     // N split into two halves of NH columns (a multiple of 16, the MMA's N step for M = 128), rounded up
     // to a half width the kernel is built for (the extra rows of B are zero-filled by the copies and the
-    // extra columns of D are not stored)
+    // extra columns of D are not stored); the second half is 16 columns narrower when that still covers
+    // N (N = 300: 160 + 144 = 304 columns computed instead of 320)
     static const int kHalves[] = {16, 32, 48, 64, 96, 128, 160, 192, 256};
     int nh = 256;
     for (int c : kHalves)
@@ -505,6 +702,7 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
     if (cluster == 4 && !cluster4_nh(nh))
         return fail(h, RSK_ERR_UNSUPPORTED, "gemm: clusters of 4 need N half 128, 160 or 256 (have %d)", nh);
     const int cl = cluster ? cluster : mtiles >= 8 ? 2 : 1;
+    const int nh2 = (cl != 4 && nh >= 32 && 2 * nh - 16 >= p.N) ? nh - 16 : nh;
     GemmMaps maps;
     memset(&maps, 0, sizeof(maps));
     for (int i = 0; i < p.na; ++i) {
@@ -516,14 +714,15 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
     }
     for (int i = 0; i < p.nb; ++i)
         if (!encode_2d_swz128(h, &maps.b[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.b[i], uint64_t(p.K), uint64_t(p.N),
-                              uint64_t(p.ldb) * 2, kBK, uint32_t(cl == 4 ? nh / 2 : nh)))
+                              uint64_t(p.ldb) * 2, kBK, uint32_t(cl == 4 ? nh / 2 : nh)) ||
+            !encode_2d_swz128(h, &maps.b2[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.b[i], uint64_t(p.K), uint64_t(p.N),
+                              uint64_t(p.ldb) * 2, kBK, uint32_t(cl == 4 ? nh / 2 : nh2)))
             return fail(h, RSK_ERR_UNSUPPORTED, "gemm: tensor map encoding failed (B)");
     GemmArgs ga;
     memset(&ga, 0, sizeof(ga));
     ga.M = p.M;
     ga.K = p.K;
     ga.N = p.N;
-    ga.kblocks = kblocks;
     ga.nk_total = nk;
     ga.npass = p.npass;
     for (int i = 0; i < p.npass; ++i) {
@@ -531,31 +730,35 @@ rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cud
         ga.pb[i] = p.pb[i];
     }
     ga.status = h->dev_status;
-    if (nsplit > 1) {
-        if (!scratch) return fail(h, RSK_ERR_INVALID_ARG, "gemm: split-K needs scratch");
-        ga.D = scratch;
-        ga.ldd = p.M;
-        ga.row_major = 0;
-        ga.split_stride = p.M * int64_t(p.N);
-    } else {
-        ga.D = p.D;
-        ga.ldd = p.ldd;
-        ga.row_major = p.d_row_major ? 1 : 0;
-        ga.split_stride = 0;
-    }
+    ga.D = p.D;
+    ga.ldd = p.ldd;
+    ga.row_major = p.d_row_major ? 1 : 0;
+    if (nsplit > 1 && !scratch) return fail(h, RSK_ERR_INVALID_ARG, "gemm: split-K needs scratch");
+    ItemPlan ip;
+    ip.groups = (mtiles + cl - 1) / cl;
+    ip.cl = cl;
+    ip.nsplit = nsplit;
+    ip.kblocks = kblocks;
+    ip.scratch = scratch;
+    ip.scratch_bytes = scratch_bytes;
+    ip.split_last = split_last;
+    ip.sum_row0 = 0;
+    ip.sum_splits = 0;
     rsk_status st;
     if (cl == 4)
-        st = p.a_mn ? dispatch_nh<true, 4>(h, nh, maps, ga, mtiles, nsplit, stream)
-                    : dispatch_nh<false, 4>(h, nh, maps, ga, mtiles, nsplit, stream);
+        st = p.a_mn ? dispatch_nh<true, 4>(h, nh, nh2, maps, ga, ip, stream)
+                    : dispatch_nh<false, 4>(h, nh, nh2, maps, ga, ip, stream);
     else if (cl == 2)
-        st = p.a_mn ? dispatch_nh<true, 2>(h, nh, maps, ga, mtiles, nsplit, stream)
-                    : dispatch_nh<false, 2>(h, nh, maps, ga, mtiles, nsplit, stream);
+        st = p.a_mn ? dispatch_nh<true, 2>(h, nh, nh2, maps, ga, ip, stream)
+                    : dispatch_nh<false, 2>(h, nh, nh2, maps, ga, ip, stream);
     else
-        st = p.a_mn ? dispatch_nh<true, 1>(h, nh, maps, ga, mtiles, nsplit, stream)
-                    : dispatch_nh<false, 1>(h, nh, maps, ga, mtiles, nsplit, stream);
-    if (st != RSK_OK || nsplit == 1) return st;
-    k_sum_splits<<<unsigned((p.M * p.N + 255) / 256), 256, 0, stream>>>(scratch, p.M * int64_t(p.N), nsplit, p.M, p.N,
-                                                                        p.ldd, p.d_row_major ? 1 : 0, p.D);
+        st = p.a_mn ? dispatch_nh<true, 1>(h, nh, nh2, maps, ga, ip, stream)
+                    : dispatch_nh<false, 1>(h, nh, nh2, maps, ga, ip, stream);
+    if (st != RSK_OK || ip.sum_splits == 0) return st;
+    const int64_t rows = p.M - ip.sum_row0;
+    k_sum_splits<<<unsigned((rows * p.N + 255) / 256), 256, 0, stream>>>(scratch, rows * int64_t(p.N), ip.sum_splits,
+                                                                         ip.sum_row0, rows, p.N, p.ldd,
+                                                                         p.d_row_major ? 1 : 0, p.D);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
@@ -735,10 +938,15 @@ extern "C" rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* 
     if (M < 1 || K < 1 || N < 1 || N > 512 || lda < (a_mn ? M : K) || ldb < K || ldd < (d_row_major ? N : M))
         return rsk::fail(h, RSK_ERR_INVALID_ARG,
                          "need M, K >= 1, 1 <= N <= 512, lda >= (a_mn ? M : K), ldb >= K, ldd >= (row-major D ? N : M)");
-    nsplit = std::max(1, nsplit);
+    // nsplit 0: automatic (K splits that fill the SMs, and a last round of row tiles split over K)
+    const bool automatic = nsplit == 0;
+    nsplit = automatic ? rsk::tc::wave_splits(M, K, h->num_sms) : std::max(1, nsplit);
     float* scratch = nullptr;
-    if (nsplit > 1) {
-        rsk_status st = rsk::ensure_workspace(h, rsk::tc::gemm_scratch_bytes(M, int(N), nsplit), stream);
+    // the split last round needs at most 4 splits of fewer than M rows
+    const size_t bytes = std::max(rsk::tc::gemm_scratch_bytes(M, int(N), nsplit),
+                                  automatic ? rsk::tc::gemm_scratch_bytes(M, int(N), 4) : size_t(0));
+    if (bytes > 0) {
+        rsk_status st = rsk::ensure_workspace(h, bytes, stream);
         if (st != RSK_OK) return st;
         scratch = static_cast<float*>(h->ws);
     }
@@ -757,7 +965,7 @@ extern "C" rsk_status rsk_gemm_bf16_ex(rsk_handle* h, int32_t a_mn, const void* 
     p.D = D;
     p.ldd = ldd;
     p.d_row_major = d_row_major != 0;
-    return rsk::tc::gemm(h, p, nsplit, scratch, stream, cluster);
+    return rsk::tc::gemm(h, p, nsplit, scratch, stream, cluster, bytes, automatic);
 }
 
 extern "C" rsk_status rsk_gemm_bf16(rsk_handle* h, const void* A, int64_t M, int64_t K, int64_t lda, const void* B,

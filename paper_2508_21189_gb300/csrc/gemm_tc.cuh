@@ -40,10 +40,19 @@ struct Product {
 
 // Scratch for split-K partials (nsplit > 1).
 size_t gemm_scratch_bytes(int64_t M, int N, int nsplit);
-// Runs the product with K split over nsplit CTAs per row tile (partials summed in split order).
+// K splits (at most max_split) that keep the SMs busiest for an M x K product with the automatic
+// cluster: the fraction of SM time in full waves, discounted by each CTA's fixed cost (setup,
+// pipeline fill, epilogue) relative to its K loop.  A 262144-row product gets 1, an 8192-row product
+// with K = 262144 gets 7 (448 CTAs: 98% of three waves on 152 SMs, against 84% of one with 2).
+int wave_splits(int64_t M, int64_t K, int num_sms, int max_split = 16);
+// Runs the product with K split nsplit ways for every row tile (partials summed in split order).
 // cluster: row tiles per thread-block cluster that share (multicast) the B tile, 1, 2 or 4 (4 for N
-// halves 128, 160, 256 only); 0 picks 2 with at least 8 row tiles, else 1.
-rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream, int cluster = 0);
+// halves 128, 160, 256 only); 0 picks 2 with at least 8 row tiles, else 1.  The kernel is persistent
+// (one cluster per group of SMs, tiles dealt round-robin).  split_last (nsplit = 1, scratch of
+// scratch_bytes): a last round of tiles that would leave more than half the clusters idle is split
+// over K instead, its rows summed from partials.
+rsk_status gemm(rsk_handle* h, const Product& p, int nsplit, float* scratch, cudaStream_t stream, int cluster = 0,
+                size_t scratch_bytes = 0, bool split_last = false);
 
 // The six split pairs (3,1), (1,3), (2,2), (2,1), (1,2), (1,1) of two three-term splits, in that
 // order.  The accumulation truncates: a same-sign sum's relative bias grows by up to about 2^-24 per

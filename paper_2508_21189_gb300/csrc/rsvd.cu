@@ -97,11 +97,10 @@ static rsk_status big_product(rsk_handle* h, bool a_mn, const __nv_bfloat16* A, 
     p.N = r;
     p.D = D;
     p.ldd = ldd;
-    // one wave of CTAs: split K when the row tiles alone leave SMs idle
-    const int64_t tiles = (M + 127) / 128;
-    int nsplit = int(std::max<int64_t>(1, std::min<int64_t>(8, int64_t(h->num_sms) / tiles)));
+    // split K when the row tiles alone leave SMs idle
+    int nsplit = tc::wave_splits(M, K, h->num_sms);
     while (nsplit > 1 && tc::gemm_scratch_bytes(M, r, nsplit) > w.part_bytes) --nsplit;
-    return tc::gemm(h, p, nsplit, w.part, s);
+    return tc::gemm(h, p, nsplit, w.part, s, 0, w.part_bytes, true);
 }
 
 }  // namespace rsk
@@ -122,10 +121,9 @@ extern "C" rsk_status rsk_rsvd(rsk_handle* h, const float* A, int64_t m, int64_t
     w.ldm = tc::pad8(m);
     w.ldn = tc::pad8(n);
     const int64_t mx = std::max(w.ldm, w.ldn);
-    // split-K partials: one wave of the K-split big product (Z = A^T Q)
-    const int64_t mtiles_n = (n + 127) / 128;
-    const size_t part_bytes =
-        tc::gemm_scratch_bytes(n, r, int(std::max<int64_t>(1, std::min<int64_t>(8, h->num_sms / mtiles_n))));
+    // split-K partials of the K-split big products (Z = A^T Q; Y = A Z when m is small)
+    const size_t part_bytes = std::max(tc::gemm_scratch_bytes(n, r, tc::wave_splits(n, m, h->num_sms)),
+                                       tc::gemm_scratch_bytes(m, r, tc::wave_splits(m, n, h->num_sms)));
     const size_t fbytes = std::max(tc::f32_product_scratch_bytes(true, std::max(m, n), r, r, 1),
                                    tc::orth_scratch_bytes(mx, r));
     size_t bytes = 0;

@@ -3,6 +3,8 @@
 D = A B^T with FP32 accumulation: every element within 1e-5 (|A| |B|^T) + 1e-30 of the FP64 product
 (FP32 accumulation over K terms, in tensor-core order).  Shapes span one tile, ragged M, K and N
 (out-of-bounds rows and columns are zero-filled by the copies), the RSVD's N = 300, and split K.
+N runs as two MMA halves, the second up to 16 columns narrower than the first (N = 300: 160 + 144, N =
+304 exactly, N = 305: 160 + 160; N = 45: 32 + 16), alone, in pairs and in fours of row tiles.
 """
 import pytest
 import torch
@@ -19,7 +21,8 @@ def rsk():
 @pytest.mark.parametrize("M,K,N,nsplit", [(128, 64, 32, 1), (256, 128, 64, 1), (128, 64, 320, 1), (1000, 1000, 300, 1),
                                           (4096, 2048, 300, 1), (777, 4104, 45, 1), (1024, 16384, 320, 4),
                                           (8192, 8192, 300, 2), (300, 512, 512, 1), (1000, 640, 200, 1),
-                                          (513, 256, 450, 1), (640, 128, 161, 2)])
+                                          (513, 256, 450, 1), (640, 128, 161, 2), (1024, 1024, 304, 1),
+                                          (1024, 1024, 305, 1), (100, 640, 45, 3)])
 def test_gemm_matches_fp64(rsk, M, K, N, nsplit):
     g = torch.Generator(device="cuda")
     g.manual_seed(M + K + N)
@@ -36,7 +39,8 @@ def test_gemm_matches_fp64(rsk, M, K, N, nsplit):
 
 @pytest.mark.parametrize("M,K,N,nsplit,row_major", [(128, 64, 32, 1, False), (256, 192, 96, 1, True),
                                                     (1000, 1000, 300, 1, False), (8192, 20000, 300, 3, False),
-                                                    (333, 4104, 45, 1, True), (8192, 8192, 320, 2, True)])
+                                                    (333, 4104, 45, 1, True), (8192, 8192, 320, 2, True),
+                                                    (8192, 32768, 300, 7, False)])
 def test_gemm_mn_major_a(rsk, M, K, N, nsplit, row_major):
     """op(A) = A^T read in place (A given K x M row-major), column- or row-major D."""
     g = torch.Generator(device="cuda")
@@ -50,6 +54,37 @@ def test_gemm_mn_major_a(rsk, M, K, N, nsplit, row_major):
     scale = At.double().abs().T @ B.double().abs().T
     err = (D.double() - ref).abs()
     assert bool((err <= 1e-5 * scale + 1e-30).all()), float((err / scale.clamp_min(1e-30)).max())
+
+
+@pytest.mark.parametrize("a_mn,M,K,N,row_major", [(False, 63488, 2048, 300, False), (False, 63488, 2048, 300, True),
+                                                  (True, 8192, 16384, 300, False), (False, 40000, 640, 161, False)])
+def test_gemm_automatic_splits(rsk, a_mn, M, K, N, row_major):
+    """nsplit 0: 63488 rows are 248 pairs of row tiles; with up to 76 pairs resident (152 SMs) the
+    rounds leave a last one of at most 40 pairs, which runs split over K (its rows summed from
+    partials); the 8192-row MN-major product splits K.  Every element within the FP32-accumulation
+    bound of the FP64 product; rows before the last 40 pairs are computed as without splits and are
+    bit-identical to the nsplit = 1 result."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(M + K + N + int(a_mn))
+    if a_mn:
+        A = torch.randn(K, M, generator=g, device="cuda").to(torch.bfloat16)
+        Aop = A.double().T
+    else:
+        A = torch.randn(M, K, generator=g, device="cuda").to(torch.bfloat16)
+        Aop = A.double()
+    B = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+    D = rsk.rsk_gemm_bf16_ex(A, B, a_mn=a_mn, row_major_out=row_major, nsplit=0)
+    D1 = rsk.rsk_gemm_bf16_ex(A, B, a_mn=a_mn, row_major_out=row_major, nsplit=1)
+    torch.cuda.synchronize()
+    rsk.rsk_sync_status()
+    ref = Aop @ B.double().T
+    scale = Aop.abs() @ B.double().abs().T
+    for X in (D, D1):
+        err = (X.double() - ref).abs()
+        assert bool((err <= 1e-5 * scale + 1e-30).all()), float((err / scale.clamp_min(1e-30)).max())
+    if M == 63488:
+        first = (248 - 40) * 256
+        assert torch.equal(D[:first], D1[:first])
 
 
 def test_gemm_row_major_out(rsk):
