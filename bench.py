@@ -442,7 +442,9 @@ def bench_lsq(rsk, synthetic, torch, dev, rank, world, reps, rows=LSQ_N):
 def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH_COUNT):
     """512 uneven problems (n_i log-uniform [4096, 262144], k_i uniform [16, 256], Gaussian A_i x
     logspace(-6, 0) column scales, Gaussian b_i, d_i = 4 k_i, zeta = 8) in one batched call: FP32
-    storage with FP32 sketch and inner CG against FP64 storage with FP64 sketch and inner CG."""
+    storage with FP32 sketch and inner CG against FP64 storage with FP64 sketch and inner CG, both
+    with the FP64 QR of the sketch; `mixed_qr_f32` is the mixed form with the QR in FP32 (an option
+    of the library, not the configured workload)."""
     ns, ks = synthetic.batched_sizes(count, seed=404 + rank)
     As32, As64, bs = [], [], []
     for i, (n, k) in enumerate(zip(ns, ks)):
@@ -451,9 +453,12 @@ def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH
         As32.append(A.float())
         bs.append(b)
     res = {}
-    for name, (As, dt) in {"mixed": (As32, torch.float32), "fp64": (As64, torch.float64)}.items():
+    forms = {"mixed": (As32, torch.float32, torch.float64), "fp64": (As64, torch.float64, torch.float64),
+             "mixed_qr_f32": (As32, torch.float32, torch.float32)}
+    for name, (As, dt, qdt) in forms.items():
         ms, (xs, infos) = timed_calls(lambda: rsk.rsk_lstsq_sketch_precond_batched(As, bs, zeta=ZETA, seed=9,
-                                                                                     sketch_dtype=dt, inner_dtype=dt),
+                                                                                     sketch_dtype=dt, inner_dtype=dt,
+                                                                                     qr_dtype=qdt),
                                       reps, torch, dev, after_warmup=lambda: rsk.rsk_profile_enable(True))
         phases = {k: rsk.rsk_profile_read("batch_" + k)[0] / reps for k in ("sketch", "qr", "resid", "cg")}
         rsk.rsk_profile_enable(False)
@@ -470,7 +475,7 @@ def bench_lsq_batched(rsk, synthetic, torch, dev, rank, world, reps, count=BATCH
             "total_rows": rows, "total_elements": elems,
             "value": res["mixed"]["solves_per_s"], "unit": "solves/s",
             "speedup_vs_fp64": round(res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"], 3),
-            "mixed": res["mixed"], "fp64": res["fp64"]}
+            "mixed": res["mixed"], "fp64": res["fp64"], "mixed_qr_f32": res["mixed_qr_f32"]}
 
 
 def spectral_error_gpu(torch, A, U, iters=20, seed=3):

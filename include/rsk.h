@@ -329,6 +329,8 @@ typedef struct {
     int32_t max_refine;      /* refinement steps; 0 returns the warm start x0; < 0 selects 20 */
     int32_t max_inner_iters; /* CG iterations per step (default 50 when <= 0) */
     double inner_tol;        /* relative CG residual reduction per step (default 1e-6 when <= 0) */
+    rsk_dtype qr_dtype;      /* precision of the batched solver's Householder QR of the sketch: F64 (the
+                                default, 0) or F32; the single solve always factors in FP64 */
 } rsk_lsq_opts;
 
 typedef struct {
@@ -363,9 +365,9 @@ typedef struct {
  * rsk_lstsq_sketch_precond; opts->sketch_dtype must be F64 or F32.  The fused passes of all
  * problems run in one persistent launch over (problem, 2048-row block) tiles taken from a work
  * queue; per-problem results are reduced in tile order (deterministic).  One CG iteration is a
- * captured CUDA graph.  The Householder QR of [S A_i | S b_i] runs in the inner precision (FP32
- * when inner_dtype is F32, else FP64); R_i and Q_i^T S b_i are then used in FP64.  With inner_dtype
- * F32 and FP32 storage, the FP64-accuracy residual passes use double-float (FP32 pair) arithmetic.
+ * captured CUDA graph.  The Householder QR of [S A_i | S b_i] runs in FP64, or in FP32 when
+ * opts->qr_dtype is F32 (R_i and Q_i^T S b_i are then used in FP64).  With inner_dtype F32 and FP32
+ * storage, the FP64-accuracy residual passes use double-float (FP32 pair) arithmetic.
  * probs and infos are host arrays of `count` entries;
  * synchronous; RSK_ERR_NOT_CONVERGED if any problem stays above tol_backward (infos[i].status says
  * which). */

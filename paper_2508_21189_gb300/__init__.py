@@ -365,9 +365,11 @@ def rsk_lstsq_sketch_precond(A, b, d, zeta=8, seed=0, sketch_dtype=torch.bfloat1
 
 def rsk_lstsq_sketch_precond_batched(As, bs, ds=None, zeta=8, seed=0, sketch_dtype=torch.float32,
                                      inner_dtype=torch.float32, tol=1e-10, max_refine=20, max_inner=50,
-                                     inner_tol=1e-6, xs=None, stream=None, raise_on_nonconvergence=True):
+                                     inner_tol=1e-6, xs=None, stream=None, raise_on_nonconvergence=True,
+                                     qr_dtype=torch.float64):
     """Batched sketch-and-precondition: lists of CUDA A_i (n_i x k_i) and b_i (FP64); returns
-    (list of x_i, list of info dicts).  Problem i uses seed + i and d_i = ds[i] (default 4 k_i)."""
+    (list of x_i, list of info dicts).  Problem i uses seed + i and d_i = ds[i] (default 4 k_i).
+    qr_dtype: precision of the sketch's Householder QR (float64 default, or float32)."""
     count = len(As)
     if xs is None:
         xs = [torch.empty(A.shape[1], dtype=torch.float64, device=A.device) for A in As]
@@ -378,7 +380,8 @@ def rsk_lstsq_sketch_precond_batched(As, bs, ds=None, zeta=8, seed=0, sketch_dty
             raise ValueError("each b must be a contiguous float64 vector of length n")
         d = 0 if ds is None else int(ds[i])
         arr[i] = LsqProblem(A.data_ptr(), _dt(A), A.shape[0], A.shape[1], A.stride(0), d, b.data_ptr(), x.data_ptr())
-    opts = LsqOpts(0, zeta, seed, _DT[sketch_dtype], _DT[inner_dtype], tol, max_refine, max_inner, inner_tol)
+    opts = LsqOpts(0, zeta, seed, _DT[sketch_dtype], _DT[inner_dtype], tol, max_refine, max_inner, inner_tol,
+                   _DT[qr_dtype])
     infos = (LsqInfo * count)()
     h = handle(As[0].device)
     st = load().rsk_lstsq_sketch_precond_batched(h, count, arr, ctypes.byref(opts), infos, _stream(stream))

@@ -84,7 +84,8 @@ class LsqOpts(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int64), ("zeta", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("sketch_dtype", ctypes.c_int32), ("inner_dtype", ctypes.c_int32),
                 ("tol_backward", ctypes.c_double), ("max_refine", ctypes.c_int32),
-                ("max_inner_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+                ("max_inner_iters", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("qr_dtype", ctypes.c_int32)]
 
 
 class LsqInfo(ctypes.Structure):

@@ -1,9 +1,8 @@
 // Batched sketch-and-precondition least squares (row a8): many problems of uneven n_i and k_i
 // solved together.  Per problem the steps are those of rsk_lstsq_sketch_precond (sketch,
 // Householder QR, warm start, refinement on the FP64 normal-equation residual with CG on
-// M_i = A_i R_i^{-1}); the QR runs in the inner precision (FP32 in the mixed form, whose sketch is
-// FP32 already; FP64 otherwise) and R_i, Q_i^T S b_i go to FP64 for the triangular steps.  Across
-// problems the work is batched:
+// M_i = A_i R_i^{-1}); the QR runs in FP64, or in FP32 on request (R_i and Q_i^T S b_i then go to
+// FP64 for the triangular steps).  Across problems the work is batched:
 //   * sketches: the inverted index is built once per problem and applied to A_i and b_i, spread
 //     over a small pool of streams;
 //   * k_qr_b / k_rinv_b / k_trmv_b / k_cg_*_b: one CTA per problem;
@@ -37,7 +36,7 @@ struct BProb {
     int64_t n, lda, lda_in;
     int k, d, a_f32, in_f32;
     double* W;          // d x (k+1) column-major
-    float* W32;         // the same in FP32 for the inner-precision QR of the mixed form, else null
+    float* W32;         // the same in FP32 when the QR runs in FP32, else null
     double* tau;        // k
     double* Rinv;       // k x k column-major
     double* v;          // x g c z res p s t | stats[3] (8k + 8)
@@ -703,6 +702,9 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         return fail(h, RSK_ERR_INVALID_ARG, "inner dtype must be F64 or F32");
     if (opts->sketch_dtype != RSK_F64 && opts->sketch_dtype != RSK_F32)
         return fail(h, RSK_ERR_INVALID_ARG, "batched sketch dtype must be F64 or F32");
+    if (opts->qr_dtype != RSK_F64 && opts->qr_dtype != RSK_F32)
+        return fail(h, RSK_ERR_INVALID_ARG, "QR dtype must be F64 or F32");
+    const bool qr32 = opts->qr_dtype == RSK_F32;
     const int zeta = opts->zeta;
     std::vector<BProb> hp(count);
     std::vector<Tile> tiles;
@@ -747,7 +749,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         }
         maxk = std::max(maxk, q.k);
         add(size_t(d) * (q.k + 1) * 8);
-        if (opts->inner_dtype == RSK_F32) add(size_t(d) * (q.k + 1) * 4);
+        if (qr32) add(size_t(d) * (q.k + 1) * 4);
         add(size_t(q.k) * 8);
         add(size_t(q.k) * q.k * 8);
         add((size_t(8) * q.k + 8) * 8);
@@ -785,7 +787,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
         BProb& q = hp[i];
         const rsk_lsq_problem& pr = probs[i];
         q.W = cv.take<double>(size_t(q.d) * (q.k + 1));
-        q.W32 = q.in_f32 ? cv.take<float>(size_t(q.d) * (q.k + 1)) : nullptr;
+        q.W32 = qr32 ? cv.take<float>(size_t(q.d) * (q.k + 1)) : nullptr;
         q.tau = cv.take<double>(size_t(q.k));
         q.Rinv = cv.take<double>(size_t(q.k) * q.k);
         q.v = cv.take<double>(size_t(8) * q.k + 8);
@@ -896,7 +898,7 @@ extern "C" rsk_status rsk_lstsq_sketch_precond_batched(rsk_handle* h, int32_t co
     // ---- QR, R^{-1}, warm start
     const int pr0 = prof_begin(h, main_s, RSK_KERNEL_BATCH_QR);
     RSK_CUDA_TRY(h, cudaMemsetAsync(dqueue + 16, 0, 4, main_s));
-    if (opts->inner_dtype == RSK_F32) {
+    if (qr32) {
         k_qr_b<float><<<std::min(count, h->num_sms), 1024, 0, main_s>>>(dP, dorder, count, dqueue + 16);
         k_qr32_to_w_b<<<count, 256, 0, main_s>>>(dP);
     } else {

@@ -54,7 +54,7 @@ def test_reflector_flag_wait_times_out(fresh_handle):
     lib, h = fresh_handle
     A, b = synthetic.batched_problem(20000, 64, seed=11, device="cuda", dtype=torch.float32)
     x = torch.empty(64, dtype=torch.float64, device="cuda")
-    opts = rsk.LsqOpts(256, 8, 0, rsk.RSK_F32, rsk.RSK_F32, 1e-10, 4, 50, 1e-6)
+    opts = rsk.LsqOpts(256, 8, 0, rsk.RSK_F32, rsk.RSK_F32, 1e-10, 4, 50, 1e-6, rsk.RSK_F64)
     info = rsk.LsqInfo()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 

@@ -53,10 +53,10 @@ def test_batched_backward_error(rsk, sketch, inner, kind):
 
 @pytest.mark.parametrize("lo_exp", [-6.0, -10.0])
 def test_batched_fp32_qr_preconditioner(rsk, lo_exp):
-    # The mixed form factors [S A | S b] in FP32.  Householder QR is column-wise backward stable, so
+    # qr_dtype float32 factors [S A | S b] in FP32.  Householder QR is column-wise backward stable, so
     # for column-scaled A (scales 10^lo_exp .. 1) A R^{-1} stays well conditioned however small the
-    # scales: the FP32-QR form (from an FP32 or an FP64 sketch) needs no more refinement steps and CG
-    # iterations than the FP64-QR form, up to a small slack, and reaches the same eta.
+    # scales: with the same sketch and inner precision, the FP32-QR solve needs no more refinement steps
+    # and CG iterations than the FP64-QR solve, up to a small slack, and reaches the same eta.
     ns, ks = synthetic.batched_sizes(10, 6, n_lo=2000, n_hi=16000, k_lo=16, k_hi=200)
     As, bs = [], []
     for i, (n, k) in enumerate(zip(ns, ks)):
@@ -64,17 +64,18 @@ def test_batched_fp32_qr_preconditioner(rsk, lo_exp):
         As.append(A.cuda())
         bs.append(b.cuda())
     runs = {}
-    for sk, inner in [(torch.float32, torch.float32), (torch.float64, torch.float32), (torch.float64, torch.float64)]:
-        xs, infos = rsk.rsk_lstsq_sketch_precond_batched(As, bs, sketch_dtype=sk, inner_dtype=inner, seed=13)
-        for A, b, x, info in zip(As, bs, xs, infos):
-            eta = olsq.backward_error(A.double().cpu().numpy(), b.cpu().numpy(), x.cpu().numpy())
-            assert eta <= 1e-10, (sk, inner, eta, info)
-        runs[(sk, inner)] = infos
-    ref = runs[(torch.float64, torch.float64)]
-    for key in [(torch.float32, torch.float32), (torch.float64, torch.float32)]:
-        for info, r in zip(runs[key], ref):
-            assert info["refine_steps"] <= r["refine_steps"] + 2, (key, info, r)
-            assert info["inner_iters"] <= 2 * r["inner_iters"] + 20, (key, info, r)
+    for sk in (torch.float32, torch.float64):
+        for qr in (torch.float64, torch.float32):
+            xs, infos = rsk.rsk_lstsq_sketch_precond_batched(As, bs, sketch_dtype=sk, inner_dtype=torch.float32,
+                                                             qr_dtype=qr, seed=13)
+            for A, b, x, info in zip(As, bs, xs, infos):
+                eta = olsq.backward_error(A.double().cpu().numpy(), b.cpu().numpy(), x.cpu().numpy())
+                assert eta <= 1e-10, (sk, qr, eta, info)
+            runs[(sk, qr)] = infos
+    for sk in (torch.float32, torch.float64):
+        for info, r in zip(runs[(sk, torch.float32)], runs[(sk, torch.float64)]):
+            assert info["refine_steps"] <= r["refine_steps"] + 2, (sk, info, r)
+            assert info["inner_iters"] <= 2 * r["inner_iters"] + 20, (sk, info, r)
 
 
 def test_batched_matches_single(rsk):
@@ -112,6 +113,10 @@ def test_batched_invalid(rsk):
     b = torch.zeros(10, dtype=torch.float64, device="cuda")
     with pytest.raises(rsk.RskError):
         rsk.rsk_lstsq_sketch_precond_batched([A], [b])
+    A = torch.zeros(100, 10, device="cuda")
+    b = torch.zeros(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(rsk.RskError):   # the QR runs in FP64 or FP32 only
+        rsk.rsk_lstsq_sketch_precond_batched([A], [b], qr_dtype=torch.bfloat16)
 
 
 def test_batched_full_size_workload(rsk):
