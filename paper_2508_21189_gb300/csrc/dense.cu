@@ -6,9 +6,10 @@
 //                   k_gram_reduce.
 //   k_matmul_ts     C = X M for tall X: 128 x 64 output tile per CTA, K in steps of 16.
 //   k_cholesky      one CTA: blocked right-looking Cholesky on the packed upper triangle in shared
-//                   memory (16-row panels, register-tiled trailing update).
-//   k_trinv         one warp per column j of R^{-1}: column-oriented back substitution, the columns of
-//                   R staged 32 at a time through shared memory.
+//                   memory (16-row panels, the diagonal block inverted for the panel solve,
+//                   register-tiled trailing update).
+//   k_trinv_diag,   R^{-1} blocked over 32 x 32 blocks: the diagonal blocks inverted one warp each, then
+//   k_trinv_blk     each block column by block back substitution (small products in shared memory).
 //   k_jacobi        one-sided block Jacobi (Hestenes) on a cooperative grid: the q columns are dealt
 //                   into nb = 2G blocks; in each of the nb - 1 rounds of a sweep CTA g takes one pair
 //                   of blocks (round-robin), copies their columns (and V's) into shared memory,
@@ -180,11 +181,14 @@ __device__ __forceinline__ int pk(int i, int j, int q) { return i * q - (i * (i 
 // Blocked right-looking Cholesky sym(G) + s I = R^T R (s = shift_coeff * trace(G)) in one CTA, the
 // upper triangle packed in shared memory.  Per panel of kCP rows (16; 8 when q > 320, so that the
 // triangle and the panel buffer fit in shared memory) (c0 .. c1-1):
-//   A  warp 0 factors the diagonal block in registers (a lane per column, shuffles for the rows);
-//   B  one thread per trailing column t >= c1 solves R_pp^T R(c0:c1, t) = U(c0:c1, t) (forward
-//      substitution against the just-factored block), into the panel buffer P and the triangle;
+//   A  warp 0 factors the diagonal block in registers (a lane per column, shuffles for the rows; the
+//      pivots' reciprocal square roots scale the rows), then inverts it (W = R_pp^{-1}, lane c taking
+//      column c by back substitution against the block's rows in shared memory);
+//   B  one thread per trailing column t >= c1 forms R(c0:c1, t) = W^T U(c0:c1, t), into the panel
+//      buffer P and the triangle (a product: no dependent chain);
 //   C  the trailing upper triangle takes the rank-kCP update U(a, b) -= sum_k P(k, a) P(k, b), in
-//      4 x 4 register tiles (two 16-byte loads per k).
+//      4 x 4 register tiles (two 16-byte loads per k), warp w taking tile rows w, w + 16, ... and its
+//      lanes the tiles right of the diagonal.
 // Three barriers per panel; R is written from the packed factor at the end.  A pivot that is not
 // positive (or not finite) stops the factorisation and sets RSK_DEV_BOUNDS.
 constexpr int kCholThreads = 512;  // 128 registers a thread: the 4 x 4 tiles and the solve stay in registers
@@ -195,7 +199,8 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
     const int qp = (q + 3) & ~3;                                 // panel buffer pitch (16-byte rows)
     float* P = U + (q * (q + 1) / 2 + 3) / 4 * 4;                // kCP x qp
     __shared__ float part[32];
-    __shared__ float Rpp[kCP * kCP];   // the panel's diagonal block, reciprocal pivots on the diagonal
+    __shared__ float Rpp[kCP * kCP];   // the panel's diagonal block R(c0 + i, c0 + j), i <= j
+    __shared__ float Wpp[kCP * kCP];   // its inverse W(i, j), zero for i > j
     __shared__ int fail_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     float t = 0.f;
@@ -217,22 +222,27 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
     for (int c0 = 0; c0 < q; c0 += kCP) {
         const int c1 = min(q, c0 + kCP), nb = c1 - c0;
         // A: the diagonal block, in registers: lane j < nb holds column j (a[i] = U(c0+i, c0+j), i <= j);
-        // at step k lane k's diagonal is broadcast, row k is scaled in place, and lane j >= i takes
-        // a[i] -= R(k, i) R(k, j) with R(k, i) broadcast from lane i.  The factor goes to R, to the
-        // packed triangle's block and, with reciprocal pivots, to Rpp for step B.
+        // at step k lane k's diagonal d is broadcast, row k is scaled by d^{-1/2} (lane k keeps d^{1/2}
+        // and d^{-1/2}), and lane j >= i takes a[i] -= R(k, i) R(k, j) with R(k, i) broadcast from lane i.
         if (warp == 0) {
             float a[kCP];
 #pragma unroll
             for (int i = 0; i < kCP; ++i) a[i] = (lane < nb && i <= lane) ? U[pk(c0 + i, c0 + lane, q)] : 0.f;
             bool bad = false;
+            float inv_own = 1.f;
 #pragma unroll
             for (int k = 0; k < kCP; ++k) {
                 if (k < nb) {
                     const float dk = __shfl_sync(0xffffffffu, a[k], k);
-                    bad = bad || !(dk > 0.f) || !isfinite(dk);
-                    const float rk = sqrtf(dk);
-                    if (lane == k) a[k] = rk;
-                    else if (lane > k) a[k] = a[k] / rk;
+                    const bool ok = dk > 0.f && isfinite(dk);
+                    bad = bad || !ok;
+                    const float inv = ok ? rsqrtf(dk) : 1.f;
+                    if (lane == k) {
+                        a[k] = dk * inv;
+                        inv_own = inv;
+                    } else if (lane > k) {
+                        a[k] *= inv;
+                    }
 #pragma unroll
                     for (int i = k + 1; i < kCP; ++i) {
                         const float rki = __shfl_sync(0xffffffffu, a[k], i);
@@ -245,25 +255,43 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
                 for (int i = 0; i < kCP; ++i)
                     if (i <= lane) {
                         U[pk(c0 + i, c0 + lane, q)] = a[i];
-                        Rpp[i * kCP + lane] = i == lane ? 1.f / a[i] : a[i];
+                        Rpp[i * kCP + lane] = a[i];
                     }
+            }
+            __syncwarp();
+            // W = R_pp^{-1}: lane c, column c, rows i = kCP-1 .. 0:
+            //   W(i, c) = (delta_ic - sum_{l > i} R(i, l) W(l, c)) / R(i, i),  W(l, c) = 0 for l > c
+            float w[kCP];
+#pragma unroll
+            for (int i = kCP - 1; i >= 0; --i) {
+                float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+                for (int l = i + 1; l < kCP; ++l)
+                    if (l < nb) s -= Rpp[i * kCP + l] * w[l];
+                const float ri = __shfl_sync(0xffffffffu, inv_own, i);
+                w[i] = (i <= lane && lane < nb) ? s * ri : 0.f;
+            }
+            if (lane < nb) {
+#pragma unroll
+                for (int i = 0; i < kCP; ++i) Wpp[i * kCP + lane] = w[i];
             }
             if (lane == 0 && bad) fail_s = 1;
         }
         __syncthreads();
         if (fail_s) break;
-        // B: the panel's rows right of the block, one thread per column: R_pp^T x = U(c0:c1, t)
+        // B: the panel's rows right of the block, one thread per column: x = W^T U(c0:c1, t)
         for (int tt = c1 + tid; tt < q; tt += blockDim.x) {
-            float x[kCP];
+            float u[kCP];
+#pragma unroll
+            for (int k = 0; k < kCP; ++k) u[k] = k < nb ? U[pk(c0 + k, tt, q)] : 0.f;
 #pragma unroll
             for (int k = 0; k < kCP; ++k) {
                 if (k < nb) {
-                    float v = U[pk(c0 + k, tt, q)];
+                    float x = 0.f;
 #pragma unroll
-                    for (int i = 0; i < k; ++i) v -= Rpp[i * kCP + k] * x[i];
-                    x[k] = v * Rpp[k * kCP + k];
-                    P[k * qp + tt] = x[k];
-                    U[pk(c0 + k, tt, q)] = x[k];
+                    for (int i = 0; i <= k; ++i) x = fmaf(Wpp[i * kCP + k], u[i], x);
+                    P[k * qp + tt] = x;
+                    U[pk(c0 + k, tt, q)] = x;
                 }
             }
         }
@@ -272,30 +300,31 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
         __syncthreads();
         // C: trailing update in 4 x 4 tiles (a0 <= b0, both multiples of 4 from c1)
         const int nt = (q - c1 + 3) / 4;
-        for (int e = tid; e < nt * nt; e += blockDim.x) {
-            const int ia = e / nt, ib = e - ia * nt;
-            if (ib < ia) continue;
-            const int a0 = c1 + 4 * ia, b0 = c1 + 4 * ib;
-            float acc[4][4] = {};
+        for (int ia = warp; ia < nt; ia += nw) {
+            const int a0 = c1 + 4 * ia;
+            for (int ib = ia + lane; ib < nt; ib += 32) {
+                const int b0 = c1 + 4 * ib;
+                float acc[4][4] = {};
 #pragma unroll
-            for (int k = 0; k < kCP; ++k) {
-                const float4 pa = *reinterpret_cast<const float4*>(P + k * qp + a0);
-                const float4 pb = *reinterpret_cast<const float4*>(P + k * qp + b0);
-                const float va[4] = {pa.x, pa.y, pa.z, pa.w}, vb[4] = {pb.x, pb.y, pb.z, pb.w};
+                for (int k = 0; k < kCP; ++k) {
+                    const float4 pa = *reinterpret_cast<const float4*>(P + k * qp + a0);
+                    const float4 pb = *reinterpret_cast<const float4*>(P + k * qp + b0);
+                    const float va[4] = {pa.x, pa.y, pa.z, pa.w}, vb[4] = {pb.x, pb.y, pb.z, pb.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] = fmaf(va[i], vb[j2], acc[i][j2]);
-            }
+                        for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] = fmaf(va[i], vb[j2], acc[i][j2]);
+                }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int a = a0 + i;
-                if (a >= q) break;
-                const int base = pk(a, a, q) - a;
+                for (int i = 0; i < 4; ++i) {
+                    const int a = a0 + i;
+                    if (a >= q) break;
+                    const int base = pk(a, a, q) - a;
 #pragma unroll
-                for (int j2 = 0; j2 < 4; ++j2) {
-                    const int b = b0 + j2;
-                    if (b >= a && b < q) U[base + b] -= acc[i][j2];
+                    for (int j2 = 0; j2 < 4; ++j2) {
+                        const int b = b0 + j2;
+                        if (b >= a && b < q) U[base + b] -= acc[i][j2];
+                    }
                 }
             }
         }
@@ -311,48 +340,142 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
         for (int i = lane; i < q; i += 32) R[int64_t(c) * ldr + i] = i <= c ? U[pk(i, c, q)] : 0.f;
 }
 
-// Ri = R^{-1} for an upper triangular R (column-major, ldr): warp w of CTA b solves R x = e_j for
-// j = 32 b + w by column-oriented back substitution (x_k = b_k / R_kk, then b_i -= R_ik x_k for i < k)
-// on its right-hand side in shared memory; the columns of R it reads are staged 32 at a time into
-// shared memory by the whole CTA, from the highest down, with the reciprocals of their pivots.
-constexpr int kTrinvCols = 32;
-constexpr int kTrinvMax = 880;  // (32 staged columns + 32 right-hand sides) x q floats within 227 KB
-__global__ void __launch_bounds__(1024) k_trinv(const float* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri) {
-    extern __shared__ __align__(16) float tsm[];
-    float* Rs = tsm;                        // kTrinvCols columns x q rows
-    float* bs = tsm + kTrinvCols * q;       // one right-hand side (q) per warp
-    __shared__ float rinv[kTrinvCols];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int j = blockIdx.x * kTrinvCols + warp;
-    float* b = bs + warp * q;
-    for (int i = lane; i < q; i += 32) b[i] = (i == j) ? 1.f : 0.f;
-    const int jmax = min(q - 1, blockIdx.x * kTrinvCols + kTrinvCols - 1);
-    for (int k0 = jmax / kTrinvCols * kTrinvCols; k0 >= 0; k0 -= kTrinvCols) {
-        const int k1 = min(k0 + kTrinvCols, jmax + 1);   // stage columns k0 .. k1-1, rows 0 .. k1-1
-        __syncthreads();
-#pragma unroll 4
-        for (int e = tid; e < (k1 - k0) * k1; e += blockDim.x) {   // column c = e / k1, rows < k1
-            const int c = e / k1, i = e - c * k1;
-            if (i <= k0 + c) Rs[c * q + i] = R[int64_t(k0 + c) * ldr + i];
-        }
-        if (tid < k1 - k0) rinv[tid] = 1.f / R[int64_t(k0 + tid) * ldr + k0 + tid];
-        __syncthreads();
-        if (j < q) {
-            for (int k = min(k1 - 1, j); k >= k0; --k) {
-                const float* rc = Rs + (k - k0) * q;
-                // b[k] is final here (no later step touches it); x_k replaces it once every lane has
-                // read it (after the step's warp barrier), and the update touches only b[0 .. k-1]
-                const float xk = b[k] * rinv[k - k0];
-#pragma unroll 4
-                for (int i = lane; i < k; i += 32) b[i] -= rc[i] * xk;
-                __syncwarp();
-                if (lane == (k & 31)) b[k] = xk;
-            }
-        }
+// Ri = R^{-1} for an upper triangular R (column-major, ldr), blocked over 32 x 32 blocks: k_trinv_diag
+// inverts the diagonal blocks (W_II), then k_trinv_blk forms each block column J above its diagonal
+// block by block back substitution, X_IJ = -W_II sum_{K=I+1..J} R_IK X_KJ for I = J-1 .. 0 (X_JJ =
+// W_JJ): small products without a dependent chain longer than one block.
+constexpr int kTB = 32;
+constexpr int kXS = kTB * (kTB + 1);   // one 32 x 32 block, column pitch 33
+constexpr int kTrinvMax = 880;         // (q / 32) blocks of 4.2 KB of shared memory per CTA
+
+// One warp per diagonal block I (the last one may be partial: padded with the identity): lane c takes
+// column c of W_II by back substitution against the block's rows in shared memory (broadcast reads);
+// the block goes to Ri's diagonal block, zeros below its diagonal.
+__global__ void __launch_bounds__(32) k_trinv_diag(const float* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri) {
+    __shared__ float Rs[kTB][kTB + 1];   // Rs[i][l] = R(i0 + i, i0 + l); then Rs[c][i] = W(i, c)
+    const int i0 = blockIdx.x * kTB, lane = threadIdx.x, nb = min(kTB, q - i0);
+    for (int l = 0; l < kTB; ++l)
+        Rs[lane][l] = (lane < nb && l < nb) ? (lane <= l ? R[int64_t(i0 + l) * ldr + i0 + lane] : 0.f)
+                                            : (lane == l ? 1.f : 0.f);
+    __syncwarp();
+    const float rinv_own = 1.f / Rs[lane][lane];
+    float w[kTB];
+#pragma unroll
+    for (int i = kTB - 1; i >= 0; --i) {
+        float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+        for (int l = i + 1; l < kTB; ++l) s -= Rs[i][l] * w[l];
+        const float ri = __shfl_sync(0xffffffffu, rinv_own, i);
+        w[i] = (i <= lane) ? s * ri : 0.f;
     }
     __syncwarp();
-    if (j < q)
-        for (int i = lane; i < q; i += 32) Ri[int64_t(j) * ldr + i] = i <= j ? b[i] : 0.f;
+#pragma unroll
+    for (int i = 0; i < kTB; ++i) Rs[lane][i] = w[i];   // Rs[c][i] = W(i, c)
+    __syncwarp();
+    for (int c = 0; c < nb; ++c)
+        if (lane < nb) Ri[int64_t(i0 + c) * ldr + i0 + lane] = Rs[c][lane];
+}
+
+// CTA J: block column J of Ri outside its diagonal block.  256 threads; thread t computes rows
+// 4 (t % 8) .. + 3 of column t / 8 of a 32 x 32 block.  X blocks live in shared memory (column pitch
+// 33), the R blocks and W_II are staged transposed (At[m][r] = A(r, m)), double-buffered, the next one
+// loaded while the current one is used.
+__global__ void __launch_bounds__(256) k_trinv_blk(const float* __restrict__ R, int q, int64_t ldr, float* __restrict__ Ri) {
+    extern __shared__ __align__(16) float xs[];               // (J + 1) blocks: xs[K kXS + c 33 + m] = X_KJ(m, c)
+    __shared__ __align__(16) float At[2][kTB * kTB];
+    __shared__ float Ss[kXS];                                  // Ss[c 33 + m] = S(m, c)
+    const int J = blockIdx.x, tid = threadIdx.x, c = tid >> 3, r0 = (tid & 7) * 4;
+    const int j0 = J * kTB;
+    // stage element e = tid + 256 k (k < 4) of a block: row r = e & 31 of A, column m = e >> 5
+    auto load_r = [&](int I, int K, float (&v)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + 256 * k, r = e & 31, m = e >> 5;
+            const int row = I * kTB + r, col = K * kTB + m;
+            v[k] = (row < q && col < q && row <= col) ? R[int64_t(col) * ldr + row] : 0.f;
+        }
+    };
+    auto load_w = [&](int I, float (&v)[4]) {   // W_II from Ri's diagonal block, identity padding
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + 256 * k, r = e & 31, m = e >> 5;
+            const int row = I * kTB + r, col = I * kTB + m;
+            v[k] = (row < q && col < q) ? (r <= m ? Ri[int64_t(col) * ldr + row] : 0.f) : (r == m ? 1.f : 0.f);
+        }
+    };
+    auto store_a = [&](int b, const float (&v)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + 256 * k;
+            At[b][(e >> 5) * kTB + (e & 31)] = v[k];
+        }
+    };
+    // X_JJ = W_JJ
+    {
+        float v[4];
+        load_w(J, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + 256 * k, r = e & 31, m = e >> 5;
+            xs[J * kXS + m * (kTB + 1) + r] = v[k];   // X(r, m): column m, row r
+        }
+    }
+    float nxt[4];
+    int buf = 0;
+    if (J > 0) load_r(J - 1, J, nxt);
+    __syncthreads();
+    for (int I = J - 1; I >= 0; --I) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int K = I + 1; K <= J + 1; ++K) {
+            // K <= J: the product R_IK X_KJ; K = J + 1: W_II, applied to S below
+            store_a(buf, nxt);
+            __syncthreads();
+            if (K < J) load_r(I, K + 1, nxt);
+            else if (K == J) load_w(I, nxt);
+            else if (I > 0) load_r(I - 1, I, nxt);
+            if (K <= J) {
+                const float* X = xs + K * kXS + c * (kTB + 1);
+#pragma unroll 8
+                for (int m = 0; m < kTB; ++m) {
+                    const float4 a = *reinterpret_cast<const float4*>(&At[buf][m * kTB + r0]);
+                    const float x = X[m];
+                    acc[0] = fmaf(a.x, x, acc[0]);
+                    acc[1] = fmaf(a.y, x, acc[1]);
+                    acc[2] = fmaf(a.z, x, acc[2]);
+                    acc[3] = fmaf(a.w, x, acc[3]);
+                }
+                if (K == J) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) Ss[c * (kTB + 1) + r0 + k] = acc[k];
+                }
+            } else {
+                // At[buf] = W_II (transposed); S complete in Ss (written before this iteration's barrier)
+                float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+                for (int m = 0; m < kTB; ++m) {
+                    const float4 a = *reinterpret_cast<const float4*>(&At[buf][m * kTB + r0]);
+                    const float s = Ss[c * (kTB + 1) + m];
+                    o[0] = fmaf(a.x, s, o[0]);
+                    o[1] = fmaf(a.y, s, o[1]);
+                    o[2] = fmaf(a.z, s, o[2]);
+                    o[3] = fmaf(a.w, s, o[3]);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xs[I * kXS + c * (kTB + 1) + r0 + k] = -o[k];
+            }
+            buf ^= 1;
+        }
+    }
+    __syncthreads();
+    // block column J: rows above the diagonal block from X, rows below it zero
+    for (int cc = tid >> 5; cc < kTB; cc += 8) {
+        const int col = j0 + cc;
+        if (col >= q) break;
+        for (int row = tid & 31; row < q; row += 32) {
+            if (row < j0) Ri[int64_t(col) * ldr + row] = xs[(row >> 5) * kXS + cc * (kTB + 1) + (row & 31)];
+            else if (row >= j0 + kTB) Ri[int64_t(col) * ldr + row] = 0.f;
+        }
+    }
 }
 
 // FP64 variant for the accurate orthonormalisation: R (q x q column-major, ldr) holds G on entry
@@ -793,9 +916,12 @@ rsk_status cholesky(rsk_handle* h, const float* G, int q, int64_t ldg, float shi
 
 rsk_status trinv(rsk_handle* h, const float* R, int q, int64_t ldr, float* Ri, cudaStream_t stream) {
     if (q < 1 || q > kTrinvMax) return fail(h, RSK_ERR_UNSUPPORTED, "trinv supports 1 <= q <= %d (got %d)", kTrinvMax, q);
-    const int smem = (kTrinvCols + 32) * q * 4;
-    RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_trinv<<<unsigned((q + kTrinvCols - 1) / kTrinvCols), 1024, smem, stream>>>(R, q, ldr, Ri);
+    const int nblk = (q + kTB - 1) / kTB;
+    const int smem = nblk * kXS * 4;
+    k_trinv_diag<<<unsigned(nblk), kTB, 0, stream>>>(R, q, ldr, Ri);
+    RSK_LAUNCH_CHECK(h);
+    RSK_CUDA_TRY(h, cudaFuncSetAttribute(k_trinv_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_trinv_blk<<<unsigned(nblk), 256, smem, stream>>>(R, q, ldr, Ri);
     RSK_LAUNCH_CHECK(h);
     return RSK_OK;
 }
