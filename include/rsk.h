@@ -430,7 +430,9 @@ rsk_status rsk_qr_econ(rsk_handle* h, const float* X, int64_t m, int64_t q, int6
 rsk_status rsk_cholesky(rsk_handle* h, const float* G, int64_t q, int64_t ldg, float shift_coeff, float* R,
                         int64_t ldr, cudaStream_t stream);
 /* Ri = R^{-1} for an upper triangular R (q x q, ldr; Ri has leading dimension ldr, zeros below the
- * diagonal): back substitution, one warp per column.  q <= 880 (RSK_ERR_UNSUPPORTED beyond). */
+ * diagonal; Ri must not overlap R): blocked over 32 x 32 blocks, the diagonal blocks inverted by back
+ * substitution, then each block column by block back substitution.  q <= 880 (RSK_ERR_UNSUPPORTED
+ * beyond). */
 rsk_status rsk_trinv(rsk_handle* h, const float* R, int64_t q, int64_t ldr, float* Ri, cudaStream_t stream);
 
 /* ---------------------------------------------------------------------------------------------
