@@ -518,7 +518,8 @@ def rsk_autotune_sketch(kernel, dtype, n, k, d, zeta=8, device=None, stream=None
 
 def rsk_gemm_bf16(A, B, nsplit=1, stream=None):
     """D = A @ B.T on the tensor cores: A (M x K) and B (N x K) row-major CUDA BF16; D FP32 (M x N)
-    returned column-major."""
+    returned column-major.  nsplit > 1 splits K that many ways; 0 lets the library choose (splits
+    that fill the SMs, and a short last round of row tiles split over K)."""
     _matrix(A, "A")
     _matrix(B, "B")
     if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or A.shape[1] != B.shape[1]:
@@ -551,7 +552,8 @@ def _gemm_out(M, N, row_major_out, device):
 def rsk_gemm_bf16_ex(A, B, a_mn=False, row_major_out=False, nsplit=1, cluster=0, stream=None):
     """D = op(A) @ B.T on the tensor cores, BF16 operands, FP32 D (M x N).  op(A) = A.T when a_mn (A is
     K x M row-major, read in place as an MN-major operand), else A (M x K).  D row-major when
-    row_major_out, else a column-major view.  cluster: row tiles sharing the B tile (0 automatic)."""
+    row_major_out, else a column-major view.  cluster: row tiles sharing the B tile (0 automatic);
+    nsplit as rsk_gemm_bf16."""
     M, K, N = _gemm_operands(A, B, a_mn, torch.bfloat16)
     D = _gemm_out(M, N, row_major_out, A.device)
     h = handle(A.device)
