@@ -187,9 +187,11 @@ __device__ __forceinline__ int pk(int i, int j, int q) { return i * q - (i * (i 
 //   B  one thread per trailing column t >= c1 forms R(c0:c1, t) = W^T U(c0:c1, t), into the panel
 //      buffer P and the triangle (a product: no dependent chain);
 //   C  the trailing upper triangle takes the rank-kCP update U(a, b) -= sum_k P(k, a) P(k, b), in
-//      4 x 4 register tiles (two 16-byte loads per k), warp w taking tile rows w, w + 16, ... and its
-//      lanes the tiles right of the diagonal.
-// Three barriers per panel; R is written from the packed factor at the end.  A pivot that is not
+//      4 x 4 register tiles (two 16-byte loads per k).  Look-ahead: warp 0 updates only the next
+//      panel's diagonal block and then runs A for it, while the other warps update the rest (tile
+//      rows dealt round-robin, lanes across a row), so the next panel's serial factorisation overlaps
+//      this panel's update.
+// Two barriers per panel; R is written from the packed factor at the end.  A pivot that is not
 // positive (or not finite) stops the factorisation and sets RSK_DEV_BOUNDS.
 constexpr int kCholThreads = 512;  // 128 registers a thread: the 4 x 4 tiles and the solve stay in registers
 template <int kCP>
@@ -219,65 +221,92 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
         for (int i = lane; i <= j; i += 32) U[pk(i, j, q)] = G[int64_t(j) * ldg + i] + (i == j ? shift : 0.f);
     for (int e = tid; e < kCP * (qp - q); e += blockDim.x) P[(e / (qp - q)) * qp + q + e % (qp - q)] = 0.f;
     __syncthreads();
-    for (int c0 = 0; c0 < q; c0 += kCP) {
-        const int c1 = min(q, c0 + kCP), nb = c1 - c0;
-        // A: the diagonal block, in registers: lane j < nb holds column j (a[i] = U(c0+i, c0+j), i <= j);
-        // at step k lane k's diagonal d is broadcast, row k is scaled by d^{-1/2} (lane k keeps d^{1/2}
-        // and d^{-1/2}), and lane j >= i takes a[i] -= R(k, i) R(k, j) with R(k, i) broadcast from lane i.
-        if (warp == 0) {
-            float a[kCP];
+    // A for the panel at c0 (warp 0): the diagonal block, in registers: lane j < nb holds column j
+    // (a[i] = U(c0+i, c0+j), i <= j); at step k lane k's diagonal d is broadcast, row k is scaled by
+    // d^{-1/2} (lane k keeps d^{1/2} and d^{-1/2}), and lane j >= i takes a[i] -= R(k, i) R(k, j) with
+    // R(k, i) broadcast from lane i.  Then W = R_pp^{-1}, lane c taking column c.
+    auto factor_diag = [&](int c0) {
+        const int nb = min(kCP, q - c0);
+        float a[kCP];
 #pragma unroll
-            for (int i = 0; i < kCP; ++i) a[i] = (lane < nb && i <= lane) ? U[pk(c0 + i, c0 + lane, q)] : 0.f;
-            bool bad = false;
-            float inv_own = 1.f;
+        for (int i = 0; i < kCP; ++i) a[i] = (lane < nb && i <= lane) ? U[pk(c0 + i, c0 + lane, q)] : 0.f;
+        bool bad = false;
+        float inv_own = 1.f;
 #pragma unroll
-            for (int k = 0; k < kCP; ++k) {
-                if (k < nb) {
-                    const float dk = __shfl_sync(0xffffffffu, a[k], k);
-                    const bool ok = dk > 0.f && isfinite(dk);
-                    bad = bad || !ok;
-                    const float inv = ok ? rsqrtf(dk) : 1.f;
-                    if (lane == k) {
-                        a[k] = dk * inv;
-                        inv_own = inv;
-                    } else if (lane > k) {
-                        a[k] *= inv;
-                    }
+        for (int k = 0; k < kCP; ++k) {
+            if (k < nb) {
+                const float dk = __shfl_sync(0xffffffffu, a[k], k);
+                const bool ok = dk > 0.f && isfinite(dk);
+                bad = bad || !ok;
+                const float inv = ok ? rsqrtf(dk) : 1.f;
+                if (lane == k) {
+                    a[k] = dk * inv;
+                    inv_own = inv;
+                } else if (lane > k) {
+                    a[k] *= inv;
+                }
 #pragma unroll
-                    for (int i = k + 1; i < kCP; ++i) {
-                        const float rki = __shfl_sync(0xffffffffu, a[k], i);
-                        if (lane >= i) a[i] -= rki * a[k];
-                    }
+                for (int i = k + 1; i < kCP; ++i) {
+                    const float rki = __shfl_sync(0xffffffffu, a[k], i);
+                    if (lane >= i) a[i] -= rki * a[k];
                 }
             }
-            if (lane < nb) {
-#pragma unroll
-                for (int i = 0; i < kCP; ++i)
-                    if (i <= lane) {
-                        U[pk(c0 + i, c0 + lane, q)] = a[i];
-                        Rpp[i * kCP + lane] = a[i];
-                    }
-            }
-            __syncwarp();
-            // W = R_pp^{-1}: lane c, column c, rows i = kCP-1 .. 0:
-            //   W(i, c) = (delta_ic - sum_{l > i} R(i, l) W(l, c)) / R(i, i),  W(l, c) = 0 for l > c
-            float w[kCP];
-#pragma unroll
-            for (int i = kCP - 1; i >= 0; --i) {
-                float s = (i == lane) ? 1.f : 0.f;
-#pragma unroll
-                for (int l = i + 1; l < kCP; ++l)
-                    if (l < nb) s -= Rpp[i * kCP + l] * w[l];
-                const float ri = __shfl_sync(0xffffffffu, inv_own, i);
-                w[i] = (i <= lane && lane < nb) ? s * ri : 0.f;
-            }
-            if (lane < nb) {
-#pragma unroll
-                for (int i = 0; i < kCP; ++i) Wpp[i * kCP + lane] = w[i];
-            }
-            if (lane == 0 && bad) fail_s = 1;
         }
-        __syncthreads();
+        if (lane < nb) {
+#pragma unroll
+            for (int i = 0; i < kCP; ++i)
+                if (i <= lane) {
+                    U[pk(c0 + i, c0 + lane, q)] = a[i];
+                    Rpp[i * kCP + lane] = a[i];
+                }
+        }
+        __syncwarp();
+        // W(i, c) = (delta_ic - sum_{l > i} R(i, l) W(l, c)) / R(i, i), W(l, c) = 0 for l > c
+        float w[kCP];
+#pragma unroll
+        for (int i = kCP - 1; i >= 0; --i) {
+            float s = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+            for (int l = i + 1; l < kCP; ++l)
+                if (l < nb) s -= Rpp[i * kCP + l] * w[l];
+            const float ri = __shfl_sync(0xffffffffu, inv_own, i);
+            w[i] = (i <= lane && lane < nb) ? s * ri : 0.f;
+        }
+        if (lane < nb) {
+#pragma unroll
+            for (int i = 0; i < kCP; ++i) Wpp[i * kCP + lane] = w[i];
+        }
+        if (lane == 0 && bad) fail_s = 1;
+    };
+    // one 4 x 4 tile (a0 <= b0) of the rank-kCP trailing update from the panel buffer
+    auto update_tile = [&](int a0, int b0) {
+        float acc[4][4] = {};
+#pragma unroll
+        for (int k = 0; k < kCP; ++k) {
+            const float4 pa = *reinterpret_cast<const float4*>(P + k * qp + a0);
+            const float4 pb = *reinterpret_cast<const float4*>(P + k * qp + b0);
+            const float va[4] = {pa.x, pa.y, pa.z, pa.w}, vb[4] = {pb.x, pb.y, pb.z, pb.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] = fmaf(va[i], vb[j2], acc[i][j2]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int a = a0 + i;
+            if (a >= q) break;
+            const int base = pk(a, a, q) - a;
+#pragma unroll
+            for (int j2 = 0; j2 < 4; ++j2) {
+                const int b = b0 + j2;
+                if (b >= a && b < q) U[base + b] -= acc[i][j2];
+            }
+        }
+    };
+    if (warp == 0) factor_diag(0);
+    __syncthreads();
+    for (int c0 = 0; c0 < q; c0 += kCP) {
+        const int c1 = min(q, c0 + kCP), nb = c1 - c0;
         if (fail_s) break;
         // B: the panel's rows right of the block, one thread per column: x = W^T U(c0:c1, t)
         for (int tt = c1 + tid; tt < q; tt += blockDim.x) {
@@ -298,34 +327,25 @@ __global__ void __launch_bounds__(kCholThreads) k_cholesky(const float* __restri
         for (int k = nb + warp; k < kCP; k += nw)   // rows of a short last panel: zero
             for (int tt = lane; tt < qp; tt += 32) P[k * qp + tt] = 0.f;
         __syncthreads();
-        // C: trailing update in 4 x 4 tiles (a0 <= b0, both multiples of 4 from c1)
+        // C: trailing update in 4 x 4 tiles (a0 <= b0, both multiples of 4 from c1), tile indices
+        // below nt.  Look-ahead: warp 0 updates the next panel's diagonal block (tile indices below
+        // kb4) and factors it while warps 1 .. nw-1 update every other tile, rows ia = warp - 1,
+        // warp - 1 + (nw - 1), ..., lanes across the row's tiles.
         const int nt = (q - c1 + 3) / 4;
-        for (int ia = warp; ia < nt; ia += nw) {
-            const int a0 = c1 + 4 * ia;
-            for (int ib = ia + lane; ib < nt; ib += 32) {
-                const int b0 = c1 + 4 * ib;
-                float acc[4][4] = {};
-#pragma unroll
-                for (int k = 0; k < kCP; ++k) {
-                    const float4 pa = *reinterpret_cast<const float4*>(P + k * qp + a0);
-                    const float4 pb = *reinterpret_cast<const float4*>(P + k * qp + b0);
-                    const float va[4] = {pa.x, pa.y, pa.z, pa.w}, vb[4] = {pb.x, pb.y, pb.z, pb.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] = fmaf(va[i], vb[j2], acc[i][j2]);
+        const int kb4 = min(kCP / 4, nt);
+        if (warp == 0) {
+            if (nt > 0) {
+                if (lane < kb4 * kb4) {
+                    const int ia = lane / kb4, ib = lane - ia * kb4;
+                    if (ib >= ia) update_tile(c1 + 4 * ia, c1 + 4 * ib);
                 }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int a = a0 + i;
-                    if (a >= q) break;
-                    const int base = pk(a, a, q) - a;
-#pragma unroll
-                    for (int j2 = 0; j2 < 4; ++j2) {
-                        const int b = b0 + j2;
-                        if (b >= a && b < q) U[base + b] -= acc[i][j2];
-                    }
-                }
+                __syncwarp();
+                factor_diag(c1);
+            }
+        } else {
+            for (int ia = warp - 1; ia < nt; ia += nw - 1) {
+                const int ib0 = ia < kb4 ? kb4 : ia;
+                for (int ib = ib0 + lane; ib < nt; ib += 32) update_tile(c1 + 4 * ia, c1 + 4 * ib);
             }
         }
         __syncthreads();
